@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the low-rank stabilizer-decomposition hot path on GB300.
+
+One step = one pass of the whole path over one batch of the n=40 workload
+(2000 random Cliffords + 24 T gates, sparsified to chi = 2^16 terms):
+  init_terms -> apply_clifford -> amplitude (B = 4096 x) -> norm_estimate
+  (L = 256) -> sample chain starts -> chains_init (C = 256) -> Metropolis
+  (T = 16 steps).
+Units per step: chi-term amplitude evaluations = chi * (B + C * (T + 1)).
+`value` is device-resident throughput (inputs already in HBM); `e2e` runs the
+same step through the public API with host buffers and the host<->device
+copies inside the timed region.  L2 is flushed (256 MB write) before every
+timed step.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "χ-term amplitude evals/s"
+UNIT = "term-amplitude evals/s"
+B_X, L_A, C_CH, T_MC = 4096, 256, 256, 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lrstab", choices=["lrstab", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------
+# algorithmic work per unit (integer 32-bit op equivalents; 64-bit word op = 2)
+# ---------------------------------------------------------------------------------
+GATE_OPS = {"S": 4, "SDG": 4, "Z": 2, "CZ": 4, "CX": 12}
+
+
+def clifford_ops_per_term(n, low):
+    """Expected integer ops per term of the lowered circuit."""
+    import numpy as np
+    from paper_1808_00128_gb300 import lrstab
+    inv = {v: k for k, v in lrstab.OP.items()}
+    h_ops = 30 * n + 40
+
+    def gate_cost(g):
+        name = inv[int(g["op"])]
+        if name in ("H", "P0", "P1"):
+            return h_ops
+        return GATE_OPS.get(name, 0)
+
+    total = 0.0
+    for g in low.gates:
+        if inv[int(g["op"])] == "SLOT":
+            s = low.slots[int(g["r"])]
+            nc = int(s["n_choices"])
+            w = np.hypot(s["c_re"][:nc], s["c_im"][:nc])
+            w = w / w.sum()
+            for j in range(nc):
+                sub = low.kgates[s["k_off"][j]: s["k_off"][j] + s["k_len"][j]]
+                total += w[j] * sum(gate_cost(k) for k in sub)
+        else:
+            total += gate_cost(g)
+    return total
+
+
+# ---------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ---------------------------------------------------------------------------------
+def oracle_sample_rates(cfg, n_terms=2, n_x=256, n_a=4, seed_alpha=0):
+    """Per-unit oracle times on a bounded sample of the workload."""
+    from oracle import decomp
+    from oracle import estimators as E
+    from paper_1808_00128_gb300 import workloads
+    n, ops = cfg["n"], cfg["ops"]
+    xs = [int(x) for x in workloads.random_bitstrings(n, n_x, seed=workloads.SEED_BASE + 50)]
+    t0 = time.perf_counter()
+    terms, coefs, _ = decomp.build_decomposition(n, ops, chi=cfg["chi"], mode=cfg["mode"],
+                                                 seed=cfg["seed"],
+                                                 alphas=range(seed_alpha, seed_alpha + n_terms))
+    t_build = (time.perf_counter() - t0) / n_terms
+    t0 = time.perf_counter()
+    for t, b in zip(terms, coefs):
+        for x in xs:
+            b * t.amplitude(x)
+    t_amp = (time.perf_counter() - t0) / (n_terms * n_x)
+    t0 = time.perf_counter()
+    for l in range(n_a):
+        A = E.draw_A(n, 7, l)
+        for t in terms:
+            E.inner_equatorial(t, A)
+    t_inner = (time.perf_counter() - t0) / (n_terms * n_a)
+    return t_build, t_amp, t_inner
+
+
+def oracle_step_time(cfg, rates):
+    t_build, t_amp, t_inner = rates
+    chi = cfg["chi"]
+    return chi * (t_build + (B_X + C_CH * (T_MC + 1)) * t_amp + L_A * t_inner)
+
+
+def units_per_step(chi):
+    return chi * (B_X + C_CH * (T_MC + 1))
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores (bounded sample per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1808_00128_gb300 import workloads
+    cfg = workloads.config_mid()
+    for w in range(args.warmup):
+        oracle_sample_rates(cfg, n_terms=1, n_x=128, n_a=2, seed_alpha=w)
+    times, vals = [], []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle_sample_rates(cfg, n_terms=1, n_x=128, n_a=2, seed_alpha=100 + k)
+        times.append(time.perf_counter() - t0)
+        vals.append(units_per_step(cfg["chi"]) / oracle_step_time(cfg, r))
+    value = statistics.median(vals)
+    sample = ("per step: 1 term of the 2^16-term n=40 decomposition built by the oracle, "
+              "128 amplitude evaluations and 2 equatorial inner products; per-unit times "
+              "scaled to one full step (chi*(B + C*(T+1)) amplitude evals, chi*L inner products)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg["name"], "n": cfg["n"], "chi": cfg["chi"], "batch": B_X,
+                      "L": L_A, "chains": C_CH, "metropolis_steps": T_MC},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lrstab.lib()
+
+    cfg = workloads.config_mid()
+    n, chi, seed = cfg["n"], cfg["chi"], cfg["seed"]
+    low = lrstab.lower_circuit(n, cfg["ops"])
+    x_host = torch.from_numpy(workloads.random_bitstrings(n, B_X, seed=workloads.SEED_BASE + 40)
+                              .view(np.int64)).pin_memory()
+    x_dev = x_host.to(dev)
+    amp = torch.empty((B_X, 2), dtype=torch.float64, device=dev)
+    eta = torch.empty(L_A, dtype=torch.float64, device=dev)
+    x0 = torch.empty(C_CH, dtype=torch.int64, device=dev)
+    xo = torch.empty(C_CH, dtype=torch.int64, device=dev)
+    po = torch.empty(C_CH, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sim = lrstab.Simulator(n, local)
+    stream = torch.cuda.current_stream()
+    phases = ["init_terms", "apply_clifford", "amplitude", "norm_estimate", "chains_init",
+              "metropolis"]
+
+    def step(ev=None, step_idx=0):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        sim.init_terms(low, chi, mode="sparsify", seed=seed)
+        mark(1)
+        sim.apply_clifford(low.gates)
+        mark(2)
+        sim.amplitude(x_dev, out=amp)
+        mark(3)
+        sim.norm_estimate(L_A, seed=1000 + step_idx, eta=eta)
+        mark(4)
+        sim.sample_terms(C_CH, seed=2000 + step_idx, x=x0)
+        sim.chains_init(x0)
+        mark(5)
+        sim.metropolis(T_MC, seed=3000 + step_idx, x_out=xo, p_out=po)
+        mark(6)
+
+    launches_per_step = 1 + 1 + 2 + 2 + 1 + 2 + (1 + 2 * T_MC + 1)
+
+    for w in range(args.warmup):
+        step(step_idx=w)
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            step(evs[k], step_idx=args.warmup + k)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    per_phase = {p: [] for p in phases}
+    step_ms = []
+    for k in range(args.steps):
+        e = evs[k]
+        for i, p in enumerate(phases):
+            per_phase[p].append(e[i].elapsed_time(e[i + 1]))
+        step_ms.append(e[0].elapsed_time(e[6]))
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    units = units_per_step(chi)
+    value = world * units / (ms * 1e-3)
+
+    # ---- roofline of the dominant phase
+    import math
+    ex = sim.export_terms(0, min(chi, 4096))
+    vw = np.array([bin(int(v)).count("1") for v in ex["v"]])
+    xs_np = x_host.numpy().view(np.uint64)
+    xpop = float(np.mean([bin(int(x)).count("1") for x in xs_np]))
+    phase_ms = {p: statistics.mean(v) for p, v in per_phase.items()}
+    ops = {
+        "apply_clifford": chi * clifford_ops_per_term(n, low),
+        "amplitude": chi * B_X * (10 * xpop + 30),
+        "norm_estimate": chi * L_A * float(np.mean(8 * n * n + 4 * vw ** 2)),
+    }
+    mc_bytes = T_MC * (chi * C_CH * (16 + 16 * 0.5) + chi * 16 * n)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    alu_measured = lrstab.alu_probe(local, 4000)
+    rows = {}
+    for p in ("apply_clifford", "amplitude", "norm_estimate"):
+        ach = ops[p] / (phase_ms[p] * 1e-3)
+        rows[p] = {"bound": "alu", "achieved": ach / 1e12, "peak": alu_measured / 1e12,
+                   "unit": "Tops/s", "frac": ach / alu_measured, "ms": phase_ms[p]}
+    ach = mc_bytes / (phase_ms["metropolis"] * 1e-3) / 1e9
+    rows["metropolis"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                          "frac": ach / hbm, "ms": phase_ms["metropolis"]}
+    dom = max(("apply_clifford", "amplitude", "norm_estimate", "metropolis"), key=lambda p: phase_ms[p])
+    roof = dict(rows[dom])
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    roof.pop("ms", None)
+    roof["peak_source"] = ("measured LOP3 probe on this GPU" if roof["bound"] == "alu"
+                           else "MEASURED_PEAKS.json hbm_gbs")
+
+    # ---- e2e: host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        amp_h = torch.empty((B_X, 2), dtype=torch.float64).pin_memory()
+        eta_h = torch.empty(L_A, dtype=torch.float64).pin_memory()
+        xo_h = torch.empty(C_CH, dtype=torch.int64).pin_memory()
+        po_h = torch.empty(C_CH, dtype=torch.float64).pin_memory()
+        e2e_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x_dev.copy_(x_host, non_blocking=True)
+            step(step_idx=100 + k)
+            amp_h.copy_(amp, non_blocking=True)
+            eta_h.copy_(eta, non_blocking=True)
+            xo_h.copy_(xo, non_blocking=True)
+            po_h.copy_(po, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        gate_bytes = len(low.gates) * 4
+        h2d = x_host.numel() * 8 + gate_bytes
+        d2h = amp_h.numel() * 8 + eta_h.numel() * 8 + xo_h.numel() * 8 + po_h.numel() * 8
+        e2e = {"value": world * units / (statistics.mean(e2e_ms) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        rates = oracle_sample_rates(cfg)
+        cpu = {"value": units / oracle_step_time(cfg, rates), "unit": UNIT, "cores": 1,
+               "kind": "oracle",
+               "sample": "2 terms of the n=40 chi=2^16 decomposition built by the oracle, 256 "
+                         "amplitude evals and 4 equatorial inner products per term; per-unit "
+                         "times scaled to one full step",
+               "seconds": round(time.perf_counter() - t0, 1)}
+    sim.close()
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64+f32", "data": "synthetic",
+           "config": {"workload": cfg["name"], "n": n, "chi": chi, "batch": B_X, "L": L_A,
+                      "chains": C_CH, "metropolis_steps": T_MC, "l2": "flushed (256 MB write) "
+                      "before every timed step", "parallelism": f"replicas x{world}"},
+           "roofline": roof, "phases": rows, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

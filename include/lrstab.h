@@ -1,0 +1,255 @@
+/*
+ * lrstab.h -- C ABI of the GB300 low-rank stabilizer-decomposition simulator.
+ *
+ * The library holds chi CH-form stabilizer states (F, G, M, gamma, v, s,
+ * omega) of one n-qubit circuit, n <= 64 (Sec. 4.1, Eqs. (phi), (tableaux),
+ * (Htype) of Bravyi et al., arXiv:1808.00128), together with their
+ * coefficients b_alpha, so that psi = sum_alpha b_alpha phi_alpha
+ * (Eq. (approxU1)).  Its calls follow the paper's problem statement
+ * (Sec. 2.3: a circuit U = D_m V_m ... V_1 D_0 on |0^n>, tasks (a) sampling
+ * and (b) norm estimation):
+ *
+ *   lrs_lower_circuit   split a circuit into Clifford gates and
+ *                       sum-over-Cliffords slots (Sec. 2.3.2, Eq. (Rtheta),
+ *                       Eq. (CCZ_decomposition)); host only
+ *   lrs_init_terms      choose every term's slot choices (exact enumeration
+ *                       or Lemma (Sparsification), Sec. 5.2), set b_alpha and
+ *                       reset every CH-form to |0^n>
+ *   lrs_apply_clifford  push every term through a gate list (Sec. 4.1 update
+ *                       rules, Eqs. (H1)-(H7), Prop. (prop:H), projectors)
+ *   lrs_amplitude       <x|psi> for a batch of x (Eqs. (amplitude),
+ *                       (amplitude1))
+ *   lrs_norm_estimate   eta_l = 2^n |<phi_{A_l}|psi>|^2 for L random
+ *                       equatorial states (Sec. 4.3, Lemmas (Norm
+ *                       Estimation), (Inner Product), (Exponential Sum))
+ *   lrs_chains_init / lrs_metropolis_step
+ *                       single-flip Metropolis chains with the incremental
+ *                       Pauli update Q_y = (U_C^-1 X_j U_C) Q_x (Sec. 4.2)
+ *
+ * Conventions
+ *   - Every function returns lrs_status; nothing throws across the ABI.  On
+ *     error lrs_last_error() returns a message (thread-local, valid until the
+ *     next call on the same thread).
+ *   - A basis string x is a uint64 with bit j holding qubit j; bits >= n must
+ *     be zero.
+ *   - Pointers named *_dev are device pointers (cudaMalloc'ed or from a
+ *     framework allocator) owned by the caller; *_host are host pointers owned
+ *     by the caller.  The library owns the term storage inside lrs_ctx.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device-side
+ *     calls are stream-ordered and asynchronous; they return after enqueuing
+ *     unless stated otherwise.  A context must not be used from two host
+ *     threads at once.
+ *   - Random numbers are drawn on the device from SplitMix64 in counter mode
+ *     (Steele, Lea and Flood 2014):
+ *        mix(z) = z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27;
+ *                 z *= 0x94D049BB133111EB; z ^= z>>31
+ *        rand64(seed, stream, i) = mix(mix(seed ^ mix(stream + G)) + (i+1) G),
+ *        G = 0x9E3779B97F4A7C15; uniform double = (rand64 >> 11) * 2^-53.
+ */
+#ifndef LRSTAB_H
+#define LRSTAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrs_ctx lrs_ctx;
+
+typedef enum {
+    LRS_OK = 0,
+    LRS_ERR_ARG = -1,         /* invalid argument (message says which)          */
+    LRS_ERR_OOM = -2,         /* device allocation failed                       */
+    LRS_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed           */
+    LRS_ERR_TIMEOUT = -4,     /* a device-side wait gave up                     */
+    LRS_ERR_STATE = -5,       /* call out of order (e.g. no terms initialised)  */
+    LRS_ERR_UNSUPPORTED = -6  /* valid request outside what this build supports */
+} lrs_status;
+
+/* ---- lowered gates (what the device executes) ------------------------------- */
+enum {
+    LRS_OP_H = 0,    /* Hadamard on q                                          */
+    LRS_OP_S = 1,    /* S = diag(1, i) on q                                    */
+    LRS_OP_SDG = 2,  /* S^dagger on q                                          */
+    LRS_OP_Z = 3,    /* Z on q                                                 */
+    LRS_OP_CX = 4,   /* CX, control q, target r                                */
+    LRS_OP_CZ = 5,   /* CZ on q, r                                             */
+    LRS_OP_P0 = 6,   /* projector (I + Z_q)/2                                  */
+    LRS_OP_P1 = 7,   /* projector (I - Z_q)/2                                  */
+    LRS_OP_SLOT = 8  /* non-Clifford slot number r: each term applies its K_j  */
+};
+
+typedef struct {
+    uint8_t op;   /* LRS_OP_*                                   */
+    uint8_t q;    /* first qubit                                */
+    uint16_t r;   /* second qubit (CX, CZ) or slot index (SLOT) */
+} lrs_gate;
+
+#define LRS_MAX_CHOICES 8
+
+/* V = sum_j c_j K_j for one non-Clifford gate; K_j is the gate sub-list
+ * k_gates[k_off[j] .. k_off[j] + k_len[j]) (Clifford or projector gates only). */
+typedef struct {
+    int32_t n_choices;                 /* 1..LRS_MAX_CHOICES */
+    int32_t k_off[LRS_MAX_CHOICES];
+    int32_t k_len[LRS_MAX_CHOICES];
+    double c_re[LRS_MAX_CHOICES];
+    double c_im[LRS_MAX_CHOICES];
+} lrs_slot;
+
+/* ---- circuit description (host) --------------------------------------------- */
+enum {
+    LRS_C_H = 0, LRS_C_S = 1, LRS_C_SDG = 2, LRS_C_Z = 3, LRS_C_CX = 4, LRS_C_CZ = 5,
+    LRS_C_T = 6,    /* diag(1, e^{i pi/4})                       */
+    LRS_C_RZ = 7,   /* exp(-i theta Z / 2)                       */
+    LRS_C_CCZ = 8   /* doubly controlled Z on q[0], q[1], q[2]   */
+};
+
+/* How a CCZ is decomposed (Sec. 2.3.2). */
+enum {
+    LRS_CCZ_PROJECTOR = 0,  /* exact 2-term form CCZ = I - 2 P1 P1 P1           */
+    LRS_CCZ_SUM8 = 1        /* 8-term Clifford form with xi = 16/9 (Eq.
+                               (CCZ_decomposition), prefactor 1/6)            */
+};
+
+typedef struct {
+    int32_t kind;      /* LRS_C_*                    */
+    int32_t q[3];      /* qubits (unused ones ignored) */
+    double theta;      /* LRS_C_RZ angle             */
+} lrs_circuit_op;
+
+/* Lower a circuit to Clifford gates plus LRS_OP_SLOT entries and slot tables
+ * (Sec. 2.3.2).  T and RZ(theta) use the optimal 2-term form of Eq. (Rtheta)
+ * ((cos - sin) I + sqrt2 e^{-i pi/4} sin S for theta >= 0, its conjugate on
+ * (I, S^dagger) for theta < 0; T carries its global phase e^{i pi/8}).
+ * Host only, no GPU needed.  Output arrays are caller-owned with the given
+ * capacities; the used counts are written to *n_gates, *n_slots, *n_k_gates.
+ * Errors: LRS_ERR_ARG for a bad op, qubit >= n_qubits, or a capacity too small
+ * (the counts then hold the sizes needed).                                    */
+lrs_status lrs_lower_circuit(int32_t n_qubits, const lrs_circuit_op* ops_host, int64_t n_ops,
+                             int32_t ccz_mode,
+                             lrs_gate* gates_host, int64_t gates_cap, int64_t* n_gates,
+                             lrs_slot* slots_host, int64_t slots_cap, int64_t* n_slots,
+                             lrs_gate* k_gates_host, int64_t k_cap, int64_t* n_k_gates);
+
+/* ---- context ------------------------------------------------------------------ */
+/* Create a context for n_qubits (1..64) on CUDA device `device`.
+ * Errors: LRS_ERR_ARG (n out of range), LRS_ERR_CUDA (bad device).           */
+lrs_status lrs_create(int32_t device, int32_t n_qubits, lrs_ctx** out);
+
+/* Free all device storage of the context.  Synchronises the device.  NULL ok. */
+lrs_status lrs_destroy(lrs_ctx* ctx);
+
+const char* lrs_last_error(void);
+
+/* ---- terms ------------------------------------------------------------------- */
+enum { LRS_MODE_EXACT = 0, LRS_MODE_SPARSIFY = 1 };
+
+/* Allocate (or reuse) storage for the chi terms with global indices
+ * alpha = alpha0 .. alpha0 + chi - 1 of a decomposition with chi_total terms,
+ * and initialise them (a context may hold a contiguous shard of the terms).
+ * EXACT: chi_total must equal prod_p (number of nonzero c_j of slot p); term
+ *   alpha takes the mixed-radix digits of alpha over each slot's nonzero
+ *   choices (slot 0 least significant) and b_alpha = prod_p c_{j_p}.
+ * SPARSIFY (Lemma (Sparsification)): slot p of term alpha takes the first j
+ *   with u < sum_{i<=j} |c_i| / ||c^(p)||_1, u = uniform(seed, alpha, p);
+ *   b_alpha = (||c||_1 / chi_total) prod_p c_{j_p} / |c_{j_p}|,
+ *   ||c||_1 = prod_p ||c^(p)||_1.
+ * Every CH-form is reset to |0^n> (G = F = I, M = 0, gamma = v = s = 0,
+ * omega = 1).  b_alpha is stored as FP32 complex.  Slots and k_gates are
+ * copied; host arrays may be freed on return.  Blocks until the tables are
+ * uploaded, then runs asynchronously on `stream`.
+ * Errors: LRS_ERR_ARG (chi < 1, alpha0 < 0, alpha0 + chi > chi_total, bad
+ * slot tables, qubit >= n, EXACT chi_total mismatch), LRS_ERR_OOM.           */
+lrs_status lrs_init_terms(lrs_ctx* ctx, const lrs_slot* slots_host, int64_t n_slots,
+                          const lrs_gate* k_gates_host, int64_t n_k_gates,
+                          int64_t chi_total, int64_t alpha0, int64_t chi, int32_t mode,
+                          uint64_t seed, void* stream);
+
+/* Apply the lowered gate list to every term (left multiplications for
+ * S, S^dagger, Z, CX, CZ; Eqs. (H1)-(H7) with Prop. (prop:H) for H; the
+ * projective-gate rule of Sec. 4.1 for P0/P1; each term's own K_j for
+ * LRS_OP_SLOT).  The gate list is copied to the device before return.
+ * Readings: rules of one gate are simultaneous; "the first qubit" of V_b is
+ * the lowest index; the single-qubit rewrite takes a = 0 when b = 0.
+ * Errors: LRS_ERR_ARG (qubit >= n, q == r, unknown op, slot index out of
+ * range), LRS_ERR_STATE (no terms).                                          */
+lrs_status lrs_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates,
+                              void* stream);
+
+/* out_dev[2i], out_dev[2i+1] = Re, Im of <x_i|psi> = sum_alpha b_alpha
+ * <x_i|phi_alpha> for i < batch (Eq. (amplitude1) per term).  Per-term values
+ * are exact Z8 phases times powers of sqrt2 times b_alpha; the chi-sum is
+ * accumulated in FP32 (pairwise within a block), then in FP64 across blocks.
+ * x_dev: batch uint64 basis strings.  batch = 0 is a no-op.
+ * Errors: LRS_ERR_ARG (batch < 0, NULL pointers), LRS_ERR_STATE.            */
+lrs_status lrs_amplitude(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch, double* out_dev,
+                         void* stream);
+
+/* eta_dev[l] = 2^n |<phi_{A_l}|psi>|^2 for l < L (Lemma (Norm Estimation)),
+ * A_l in M_n drawn from rand64(seed, l, i): word 0 = low bits of diag(A),
+ * word 1 = high bits, words 2.. = strict upper triangle in row-major order.
+ * Each <phi_{A_l}|phi_alpha> is exact (Lemma (Inner Product) with the exact
+ * exponential sum of Lemma (Exponential Sum)); the chi-sum is FP32 then FP64;
+ * eta is FP64.  If mean_host is not NULL the call synchronises `stream` and
+ * writes the mean of the L values.
+ * Errors: LRS_ERR_ARG (L < 1), LRS_ERR_STATE.                                */
+lrs_status lrs_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta_dev,
+                             double* mean_host, void* stream);
+
+/* Draw count basis strings from the terms (Sec. 4.1, "Simulating
+ * measurements"): term alpha = floor(rand64(seed, i, 0) * chi / 2^64)
+ * (uniform), w = s ^ (rand64(seed, i, 1) & v), x = w G^T.  Writes x_dev[i]
+ * and, if alpha_dev is not NULL, alpha_dev[i].                               */
+lrs_status lrs_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint64_t* x_dev,
+                            int64_t* alpha_dev, void* stream);
+
+/* ---- Metropolis (Sec. 4.2) ------------------------------------------------------ */
+/* Start n_chains chains at x_dev[c]: computes Q_x for every (chain, term) and
+ * P(x) = |<x|psi>|^2.  Needs n <= 62 (Q is packed in 16 bytes).  Storage is
+ * n_chains * chi * 16 bytes, owned by the context.
+ * Errors: LRS_ERR_ARG, LRS_ERR_STATE, LRS_ERR_UNSUPPORTED (n > 62), LRS_ERR_OOM. */
+lrs_status lrs_chains_init(lrs_ctx* ctx, int64_t n_chains, const uint64_t* x_dev, void* stream);
+
+/* Run `steps` Metropolis steps on every chain.  Step t (global index
+ * step0 + t) of chain c proposes y = x ^ e_j with j = (hi32(rand64(seed, c,
+ * 2t)) * n) >> 32 and accepts if P(y) >= P(x), else iff
+ * uniform(seed, c, 2t+1) < P(y)/P(x) (FP64).  Optional outputs (device, may
+ * be NULL): x_out_dev[c] and p_out_dev[c] after the last step, trace_dev
+ * [t * n_chains + c] = x after step t.
+ * Errors: LRS_ERR_ARG (steps < 0), LRS_ERR_STATE (chains not initialised).  */
+lrs_status lrs_metropolis_step(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t step0,
+                               uint64_t* x_out_dev, double* p_out_dev, uint64_t* trace_dev,
+                               void* stream);
+
+/* ---- export (checkpoint / bit-exact parity) ----------------------------------- */
+/* Copy local terms [first, first + count) (global index alpha0 + first ..) to host arrays (each may be NULL):
+ *   F, G, M: count * n uint64, term-major (row p of term i at [i*n + p]);
+ *   gamma: count * n bytes (0..3); v, s: count uint64;
+ *   omega: count int32 = k | zero << 3 | h << 8 (omega = 0 if zero else
+ *          e^{i pi k/4} 2^{-h/2});
+ *   coef: count * 2 float (Re, Im of b_alpha);
+ *   choice: count * n_slots bytes (choice j_p of slot p at [i*n_slots + p]).
+ * Synchronises the device.                                                   */
+lrs_status lrs_export_terms(lrs_ctx* ctx, int64_t first, int64_t count, uint64_t* F_host,
+                            uint64_t* G_host, uint64_t* M_host, uint8_t* gamma_host,
+                            uint64_t* v_host, uint64_t* s_host, int32_t* omega_host,
+                            float* coef_host, uint8_t* choice_host);
+
+/* ---- measurement support ----------------------------------------------------- */
+/* Integer-pipe probe (no counterpart in the paper): runs a kernel of
+ * independent 32-bit LOP3 dependency chains on every SM of `device` for
+ * `iters` iterations per thread and writes the sustained rate in 32-bit
+ * logic operations per second to *ops_per_s (host).  Synchronises the device.
+ * Used as the ALU roofline denominator next to the unit-count derivation.   */
+lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
+
+/* Number of terms, qubits and slots of the context (any pointer may be NULL). */
+lrs_status lrs_info(const lrs_ctx* ctx, int64_t* chi, int32_t* n_qubits, int64_t* n_slots);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRSTAB_H */

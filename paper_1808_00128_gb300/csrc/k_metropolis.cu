@@ -1,0 +1,272 @@
+// Metropolis chains with the incremental Pauli update of Sec. 4.2.
+//
+// State per (chain c, term alpha): Q = i^mu X(u) Z(w) = U_C^{-1} X(x_c) U_C,
+// packed in 16 bytes as (u | mu << 62, w) (needs n <= 62), layout [chain][term].
+// A step proposes y = x ^ e_j; every term updates Q_y = Q_x P_j with
+// P_j = U_C^{-1} X_j U_C = i^{gamma_j} X(F_j) Z(M_j):
+//     mu += gamma_j + 2 parity(w & F_j);  u ^= F_j;  w ^= M_j
+// and contributes b <0|Q_y U_H|s> (Eq. (amplitude1)).  Q is written back only
+// for accepted moves, lazily, at the start of the next step.  The accept test
+// is done in FP64 per chain by a separate small kernel.
+#include "lrs_device.cuh"
+
+namespace {
+
+constexpr int MC_TPB = 128;   // terms per block
+constexpr int MC_CG = 64;     // chains per block (grid.y groups)
+
+__device__ __forceinline__ float2 term_value(uint64_t u, uint64_t w, uint32_t mu, uint64_t s,
+                                             uint64_t nv, uint64_t sv, bool live, int k0, int e0,
+                                             float2 b) {
+    if (!live || ((u ^ s) & nv) != 0) return make_float2(0.f, 0.f);
+    const int sign = (int)(par64(u & w) ^ par64(u & sv));
+    return z8_scale(b, 2 * (int)mu + 4 * sign + k0, e0);
+}
+
+__device__ __forceinline__ float2 block_sum(float2 v, float2 (*red)[MC_TPB / 32], int slot) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+    }
+    if ((threadIdx.x & 31) == 0) red[slot][threadIdx.x >> 5] = v;
+    return v;
+}
+
+// Q from scratch for x_c, and the block partial of <x_c|psi>.
+__global__ void __launch_bounds__(MC_TPB) k_chains_init(TermsView T, const uint64_t* __restrict__ xs,
+                                                        int64_t C, ulonglong2* __restrict__ Q,
+                                                        float2* __restrict__ partial, int64_t n_tiles) {
+    extern __shared__ uint64_t smem[];
+    __shared__ float2 red[MC_CG][MC_TPB / 32];
+    const int n = T.n;
+    const int tid = threadIdx.x;
+    const int64_t tile = blockIdx.x;
+    const int64_t a = tile * MC_TPB + tid;
+    uint64_t* sF = smem + tid;
+    uint64_t* sM = smem + (int64_t)n * MC_TPB + tid;
+    for (int p = 0; p < n; ++p) {
+        sF[p * MC_TPB] = T.F[(int64_t)p * T.cap + a];
+        sM[p * MC_TPB] = T.M[(int64_t)p * T.cap + a];
+    }
+    const uint64_t glo = T.glo[a], ghi = T.ghi[a], v = T.v[a], s = T.s[a];
+    const uint32_t om = T.omega[a];
+    const uint64_t nv = ~v & T.nmask, sv = s & v;
+    const bool live = ((om >> 3) & 1u) == 0u;
+    const int k0 = (int)(om & 7u), e0 = __popcll(v) + (int)(om >> 8);
+    const float2 b = T.coef[a];
+    const int64_t c0 = (int64_t)blockIdx.y * MC_CG;
+    const int nc = (int)(C - c0 < MC_CG ? C - c0 : MC_CG);
+    for (int ci = 0; ci < nc; ++ci) {
+        const int64_t c = c0 + ci;
+        const uint64_t x = xs[c] & T.nmask;   // bits >= n are ignored
+        uint64_t u = 0, w = 0, z = 0;
+        for (uint64_t xr = x; xr; xr &= xr - 1) {
+            const int p = ffs64(xr);
+            const uint64_t Fp = sF[p * MC_TPB];
+            z ^= w & Fp;
+            u ^= Fp;
+            w ^= sM[p * MC_TPB];
+        }
+        const uint32_t mu = ((uint32_t)__popcll(x & glo) + 2u * (uint32_t)__popcll(x & ghi) +
+                             2u * par64(z)) & 3u;
+        Q[c * T.cap + a] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
+        block_sum(term_value(u, w, mu, s, nv, sv, live, k0, e0, b), red, ci);
+    }
+    __syncthreads();
+    if (tid < nc) {
+        float2 acc = red[tid][0];
+        for (int w2 = 1; w2 < MC_TPB / 32; ++w2) { acc.x += red[tid][w2].x; acc.y += red[tid][w2].y; }
+        partial[(c0 + tid) * n_tiles + tile] = acc;
+    }
+}
+
+// One proposal: apply the pending accepted flip, then form the amplitude of y.
+__global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C, ulonglong2* __restrict__ Q,
+                                                          const int32_t* __restrict__ pend,
+                                                          const int32_t* __restrict__ jprop,
+                                                          float2* __restrict__ partial, int64_t n_tiles) {
+    extern __shared__ uint64_t smem[];
+    __shared__ float2 red[MC_CG][MC_TPB / 32];
+    const int n = T.n;
+    const int tid = threadIdx.x;
+    const int64_t tile = blockIdx.x;
+    const int64_t a = tile * MC_TPB + tid;
+    uint64_t* sF = smem + tid;
+    uint64_t* sM = smem + (int64_t)n * MC_TPB + tid;
+    for (int p = 0; p < n; ++p) {
+        sF[p * MC_TPB] = T.F[(int64_t)p * T.cap + a];
+        sM[p * MC_TPB] = T.M[(int64_t)p * T.cap + a];
+    }
+    const uint64_t glo = T.glo[a], ghi = T.ghi[a], v = T.v[a], s = T.s[a];
+    const uint32_t om = T.omega[a];
+    const uint64_t nv = ~v & T.nmask, sv = s & v;
+    const bool live = ((om >> 3) & 1u) == 0u;
+    const int k0 = (int)(om & 7u), e0 = __popcll(v) + (int)(om >> 8);
+    const float2 b = T.coef[a];
+    const uint64_t umask = (1ull << 62) - 1;
+    const int64_t c0 = (int64_t)blockIdx.y * MC_CG;
+    const int nc = (int)(C - c0 < MC_CG ? C - c0 : MC_CG);
+    for (int ci = 0; ci < nc; ++ci) {
+        const int64_t c = c0 + ci;
+        const ulonglong2 q = Q[c * T.cap + a];
+        uint64_t u = q.x & umask, w = q.y;
+        uint32_t mu = (uint32_t)(q.x >> 62);
+        const int pj = pend[c];
+        if (pj >= 0) {   // commit the flip accepted at the previous step
+            const uint64_t Fp = sF[pj * MC_TPB];
+            mu = (mu + (uint32_t)(getb(glo, pj) | (getb(ghi, pj) << 1)) + 2u * par64(w & Fp)) & 3u;
+            u ^= Fp;
+            w ^= sM[pj * MC_TPB];
+            Q[c * T.cap + a] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
+        }
+        const int j = jprop[c];
+        const uint64_t Fj = sF[j * MC_TPB];
+        const uint32_t muy = (mu + (uint32_t)(getb(glo, j) | (getb(ghi, j) << 1)) + 2u * par64(w & Fj)) & 3u;
+        const uint64_t uy = u ^ Fj, wy = w ^ sM[j * MC_TPB];
+        block_sum(term_value(uy, wy, muy, s, nv, sv, live, k0, e0, b), red, ci);
+    }
+    __syncthreads();
+    if (tid < nc) {
+        float2 acc = red[tid][0];
+        for (int w2 = 1; w2 < MC_TPB / 32; ++w2) { acc.x += red[tid][w2].x; acc.y += red[tid][w2].y; }
+        partial[(c0 + tid) * n_tiles + tile] = acc;
+    }
+}
+
+__device__ __forceinline__ double chain_reduce(const float2* __restrict__ partial, int64_t c,
+                                               int64_t n_tiles) {
+    double re = 0.0, im = 0.0;
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const float2 p = partial[c * n_tiles + t];
+        re += (double)p.x;
+        im += (double)p.y;
+    }
+    __shared__ double sre[256], sim[256];
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            sre[threadIdx.x] += sre[threadIdx.x + off];
+            sim[threadIdx.x] += sim[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    return sre[0] * sre[0] + sim[0] * sim[0];
+}
+
+__device__ __forceinline__ int draw_j(uint64_t seed, int64_t c, int64_t step, int n) {
+    const uint64_t r = sm64_at(sm64_key(seed, (uint64_t)c), (uint64_t)(2 * step));
+    return (int)(((r >> 32) * (uint64_t)n) >> 32);
+}
+
+__global__ void k_chains_set(const float2* __restrict__ partial, int64_t n_tiles, const uint64_t* xs,
+                             uint64_t nmask, uint64_t* cx, double* cp, int32_t* pend) {
+    const int64_t c = blockIdx.x;
+    const double p = chain_reduce(partial, c, n_tiles);
+    if (threadIdx.x == 0) {
+        cx[c] = xs[c] & nmask;
+        cp[c] = p;
+        pend[c] = -1;
+    }
+}
+
+__global__ void k_metro_first(int64_t C, uint64_t seed, int64_t step, int n, int32_t* jprop) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C) jprop[c] = draw_j(seed, c, step, n);
+}
+
+// FP64 accept test (Sec. 4.2) and the proposal index of the next step.
+__global__ void k_metro_accept(const float2* __restrict__ partial, int64_t n_tiles, uint64_t seed,
+                               int64_t step, int n, uint64_t* cx, double* cp, int32_t* pend,
+                               int32_t* jprop, uint64_t* trace, int64_t C) {
+    const int64_t c = blockIdx.x;
+    const double py = chain_reduce(partial, c, n_tiles);
+    if (threadIdx.x == 0) {
+        const double px = cp[c];
+        const int j = jprop[c];
+        bool acc;
+        if (py >= px) {
+            acc = true;
+        } else {
+            const double r = sm64_unit(sm64_at(sm64_key(seed, (uint64_t)c), (uint64_t)(2 * step + 1)));
+            acc = r < py / px;
+        }
+        if (acc) {
+            cx[c] ^= 1ull << j;
+            cp[c] = py;
+            pend[c] = j;
+        } else {
+            pend[c] = -1;
+        }
+        if (trace) trace[c] = cx[c];
+        jprop[c] = draw_j(seed, c, step + 1, n);
+    }
+}
+
+__global__ void k_metro_out(int64_t C, const uint64_t* cx, const double* cp, uint64_t* x_out,
+                            double* p_out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    if (x_out) x_out[c] = cx[c];
+    if (p_out) p_out[c] = cp[c];
+}
+
+}  // namespace
+
+static size_t mc_smem(const lrs_ctx* ctx) { return (size_t)2 * ctx->n * MC_TPB * sizeof(uint64_t); }
+
+static lrs_status mc_attrs() {
+    const int mx = 2 * 64 * MC_TPB * (int)sizeof(uint64_t);
+    LRS_CUDA(cudaFuncSetAttribute(k_chains_init, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    return LRS_OK;
+}
+
+lrs_status launch_chains_init(lrs_ctx* ctx, const uint64_t* x, cudaStream_t st) {
+    const int64_t C = ctx->n_chains;
+    const int64_t n_tiles = ctx->cap / MC_TPB;
+    void* scr = nullptr;
+    lrs_status rc = lrs_scratch(ctx, (size_t)C * n_tiles * sizeof(float2), &scr);
+    if (rc != LRS_OK) return rc;
+    rc = mc_attrs();
+    if (rc != LRS_OK) return rc;
+    float2* partial = (float2*)scr;
+    dim3 grid((unsigned)n_tiles, (unsigned)((C + MC_CG - 1) / MC_CG));
+    k_chains_init<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), x, C, ctx->Q, partial, n_tiles);
+    LRS_LAUNCH_CHECK("chains_init kernel");
+    k_chains_set<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, x, ctx->nmask, ctx->cx, ctx->cp,
+                                              ctx->pend);
+    LRS_LAUNCH_CHECK("chains_set kernel");
+    return LRS_OK;
+}
+
+lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t step0,
+                             uint64_t* x_out, double* p_out, uint64_t* trace, cudaStream_t st) {
+    const int64_t C = ctx->n_chains;
+    const int64_t n_tiles = ctx->cap / MC_TPB;
+    void* scr = nullptr;
+    const size_t part_bytes = (size_t)C * n_tiles * sizeof(float2);
+    lrs_status rc = lrs_scratch(ctx, part_bytes + (size_t)C * sizeof(int32_t) + 256, &scr);
+    if (rc != LRS_OK) return rc;
+    rc = mc_attrs();
+    if (rc != LRS_OK) return rc;
+    float2* partial = (float2*)scr;
+    int32_t* jprop = (int32_t*)((char*)scr + ((part_bytes + 255) & ~(size_t)255));
+    k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, seed, step0, ctx->n, jprop);
+    LRS_LAUNCH_CHECK("metropolis first kernel");
+    dim3 grid((unsigned)n_tiles, (unsigned)((C + MC_CG - 1) / MC_CG));
+    for (int64_t t = 0; t < steps; ++t) {
+        k_metro_propose<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop,
+                                                            partial, n_tiles);
+        LRS_LAUNCH_CHECK("metropolis propose kernel");
+        k_metro_accept<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, seed, step0 + t, ctx->n, ctx->cx,
+                                                     ctx->cp, ctx->pend, jprop,
+                                                     trace ? trace + t * C : nullptr, C);
+        LRS_LAUNCH_CHECK("metropolis accept kernel");
+    }
+    k_metro_out<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->cx, ctx->cp, x_out, p_out);
+    LRS_LAUNCH_CHECK("metropolis out kernel");
+    return LRS_OK;
+}

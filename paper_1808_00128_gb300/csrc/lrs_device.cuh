@@ -1,0 +1,258 @@
+// Device helpers: counter RNG, bit utilities, Z8 phases, CH-form gate rules.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lrs_internal.h"
+
+// ---- SplitMix64 in counter mode (Steele, Lea, Flood 2014) ------------------------
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+__host__ __device__ __forceinline__ uint64_t sm64_key(uint64_t seed, uint64_t stream) {
+    return sm64_mix(seed ^ sm64_mix(stream + 0x9E3779B97F4A7C15ull));
+}
+__host__ __device__ __forceinline__ uint64_t sm64_at(uint64_t key, uint64_t i) {
+    return sm64_mix(key + (i + 1) * 0x9E3779B97F4A7C15ull);
+}
+__host__ __device__ __forceinline__ double sm64_unit(uint64_t r) {
+    return (double)(r >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// ---- bits ----------------------------------------------------------------------
+__device__ __forceinline__ uint32_t par64(uint64_t x) {
+    return __popc((uint32_t)x ^ (uint32_t)(x >> 32)) & 1u;
+}
+__device__ __forceinline__ int ffs64(uint64_t x) {  // index of lowest set bit, x != 0
+    return __ffsll((long long)x) - 1;
+}
+__device__ __forceinline__ uint64_t bit64(int j) { return 1ull << j; }
+__device__ __forceinline__ uint64_t getb(uint64_t x, int j) { return (x >> j) & 1ull; }
+
+// ---- exact Z8 phase times power of sqrt2, rounded once to FP32 -------------------
+// returns b * exp(i pi ph / 4) * 2^(-e/2)  (ph any int, e any int)
+__device__ __forceinline__ float2 z8_scale(float2 b, int ph, int e) {
+    ph &= 7;
+    // odd e: 2^(-1/2) factor; odd ph: (1+i)/sqrt2 factor.  Both odd: (1+i)/2 exact.
+    const float r2 = 0.70710678118654752440f;
+    float2 z = b;
+    int halfe;
+    if (e >= 0) halfe = e >> 1; else halfe = -((-e + 1) >> 1);   // floor(e/2)
+    bool oddE = (e - 2 * halfe) != 0;                             // e = 2 halfe + oddE
+    if (ph & 1) {
+        // multiply by (1+i): (x - y) + i (x + y)
+        float2 t = make_float2(z.x - z.y, z.x + z.y);
+        if (oddE) {
+            z = make_float2(t.x * 0.5f, t.y * 0.5f);       // (1+i)/2 = e^{i pi/4} / sqrt2
+        } else {
+            z = make_float2(t.x * r2, t.y * r2);           // (1+i)/sqrt2
+        }
+    } else if (oddE) {
+        z = make_float2(z.x * r2, z.y * r2);
+    }
+    // remaining i^(ph >> 1)
+    switch ((ph >> 1) & 3) {
+        case 1: z = make_float2(-z.y, z.x); break;
+        case 2: z = make_float2(-z.x, -z.y); break;
+        case 3: z = make_float2(z.y, -z.x); break;
+        default: break;
+    }
+    return make_float2(ldexpf(z.x, -halfe), ldexpf(z.y, -halfe));
+}
+
+// ---- compensated FP32 complex accumulation (Kahan) ------------------------------
+struct KahanC {
+    float2 s, c;
+    __device__ __forceinline__ void init() { s = make_float2(0.f, 0.f); c = s; }
+    __device__ __forceinline__ void add(float2 x) {
+        float yx = x.x - c.x, yy = x.y - c.y;
+        float tx = s.x + yx, ty = s.y + yy;
+        c.x = (tx - s.x) - yx;
+        c.y = (ty - s.y) - yy;
+        s.x = tx; s.y = ty;
+    }
+    __device__ __forceinline__ float2 value() const { return make_float2(s.x - c.x, s.y - c.y); }
+};
+
+// ---- CH-form state in registers, rows behind an accessor ------------------------
+struct TermRegs {
+    uint64_t glo, ghi, v, s;
+    uint32_t k;     // omega phase (mod 8 in use)
+    uint32_t h;     // omega = 2^(-h/2) ...
+    uint32_t zero;  // omega = 0
+};
+
+__device__ __forceinline__ uint32_t gamma_get(const TermRegs& t, int p) {
+    return (uint32_t)(getb(t.glo, p) | (getb(t.ghi, p) << 1));
+}
+__device__ __forceinline__ void gamma_set(TermRegs& t, int p, uint32_t g) {
+    uint64_t m = bit64(p);
+    t.glo = (t.glo & ~m) | ((uint64_t)(g & 1u) << p);
+    t.ghi = (t.ghi & ~m) | ((uint64_t)((g >> 1) & 1u) << p);
+}
+
+// Single-qubit rewrite H^{vq}(|yq> + i^d |1-yq>) = sqrt2 e^{i pi dk/4} S^a H^b |c>,
+// after mapping yq = 1 to yq = 0 (k += 2d, d -> -d).  Entry = a | b<<1 | c<<2 | dk<<3,
+// indexed [vq*4 + d].  For b = 0 the entry takes a = 0.
+__device__ __forceinline__ uint32_t sq_entry(int vq, int d) {
+    // vq=0: d0 (0,1,0,0) d1 (1,1,0,0) d2 (0,1,1,0) d3 (1,1,1,0)
+    // vq=1: d0 (0,0,0,0) d1 (1,1,1,1) d2 (0,0,1,0) d3 (1,1,0,7)
+    const uint32_t tab[8] = {0x2u, 0x3u, 0x6u, 0x7u, 0x0u, 0x7u | (1u << 3), 0x4u, 0x3u | (7u << 3)};
+    return tab[vq * 4 + d];
+}
+
+// Prop. (prop:H): U_H(|t> + i^delta |u>) = sqrt2 e^{i pi k1/4} W_C W_H |s'> for t != u.
+// Applies U_C <- U_C W_C to every row (fused fan-out of right multiplications,
+// then R[S_q] when a = 1), updates v, s and adds k1 to the phase.
+template <class Rows>
+__device__ __forceinline__ void prop_h(Rows& R, TermRegs& T, int n, uint64_t t, uint64_t u,
+                                       uint32_t delta) {
+    const uint64_t d = t ^ u;
+    const uint64_t V0 = d & ~T.v;
+    const uint64_t V1 = d & T.v;
+    int q;
+    uint64_t mA, m1, mB;
+    if (V0) {  // V_C = prod_{i in V0\q} CX_{q,i} prod_{i in V1} CZ_{q,i}
+        q = ffs64(V0);
+        mA = V0 & ~bit64(q);
+        m1 = V1;
+        mB = 0;
+    } else {   // V_C = prod_{i in V1\q} CX_{i,q}
+        q = ffs64(V1);
+        mA = 0;
+        m1 = 0;
+        mB = V1 & ~bit64(q);
+    }
+    uint64_t y;
+    if (getb(t, q)) y = u ^ bit64(q); else y = t;
+    const int yq = (int)getb(y, q);
+    const int vq = (int)getb(T.v, q);
+    uint32_t dd = delta & 3u;
+    if (yq) {
+        T.k += 2u * dd;
+        dd = (4u - dd) & 3u;
+    }
+    const uint32_t e = sq_entry(vq, (int)dd);
+    const uint64_t a = e & 1u, b = (e >> 1) & 1u, c = (e >> 2) & 1u;
+    T.k += e >> 3;
+
+    uint64_t add2 = 0, sub1 = 0;
+    for (int p = 0; p < n; ++p) {
+        uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
+        const uint64_t gq = getb(Gp, q), fq = getb(Fp, q), mq = getb(Mp, q);
+        const uint64_t f1 = par64(Fp & m1);
+        // R[CX_{q,i}], i in mA:  G[p,q] ^= G[p,i]; F[p,i] ^= F[p,q]; M[p,q] ^= M[p,i]
+        // R[CZ_{q,i}], i in m1:  M[p,q] ^= F[p,i]; M[p,i] ^= F[p,q]; gamma_p += 2 F[p,q] F[p,i]
+        // R[CX_{i,q}], i in mB:  G[p,i] ^= G[p,q]; F[p,q] ^= F[p,i]; M[p,i] ^= M[p,q]
+        const uint64_t Gn = Gp ^ ((uint64_t)par64(Gp & mA) << q) ^ (mB & (0ull - gq));
+        const uint64_t Fn = Fp ^ (mA & (0ull - fq)) ^ ((uint64_t)par64(Fp & mB) << q);
+        uint64_t Mn = Mp ^ ((uint64_t)par64((Mp & mA) ^ (Fp & m1)) << q) ^ (m1 & (0ull - fq)) ^
+                      (mB & (0ull - mq));
+        add2 |= (fq & f1) << p;
+        // R[S_q] when a = 1: M[p,q] ^= F[p,q]; gamma_p -= F[p,q]
+        const uint64_t fs = a & getb(Fn, q);
+        Mn ^= fs << q;
+        sub1 |= fs << p;
+        R.G(p) = Gn;
+        R.F(p) = Fn;
+        R.M(p) = Mn;
+    }
+    // gamma += 2 add2, then gamma -= sub1 (bit-plane Z4 arithmetic)
+    T.ghi ^= add2;
+    T.ghi ^= sub1 & ~T.glo;
+    T.glo ^= sub1;
+    T.v = (T.v & ~bit64(q)) | (b << q);
+    T.s = (y & ~bit64(q)) | (c << q);
+}
+
+// Hadamard on qubit p (Eqs. (H1)-(H7)).
+template <class Rows>
+__device__ __forceinline__ void gate_h(Rows& R, TermRegs& T, int n, uint64_t nmask, int p) {
+    if (T.zero) return;
+    const uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
+    const uint64_t nv = ~T.v & nmask;
+    const uint64_t t = T.s ^ (Gp & T.v);
+    const uint64_t u = T.s ^ (Fp & nv) ^ (Mp & T.v);
+    const uint32_t alpha = par64(Gp & nv & T.s);
+    const uint32_t beta = par64((Mp & nv & T.s) ^ (Fp & T.v & (Mp ^ T.s)));
+    const uint32_t delta = (gamma_get(T, p) + 2u * (alpha + beta)) & 3u;
+    T.k += 4u * alpha;
+    if (t == u) {
+        // 2^{-1/2}(1 + i^delta), delta odd: e^{+-i pi/4}
+        T.k += (delta == 1u) ? 1u : 7u;
+        T.s = t;
+        return;
+    }
+    prop_h(R, T, n, t, u, delta);
+}
+
+// Projector (I + (-1)^sigma Z_j)/2 (Sec. 4.1, projective gates).
+template <class Rows>
+__device__ __forceinline__ void gate_proj(Rows& R, TermRegs& T, int n, uint64_t nmask, int j,
+                                          uint32_t sigma) {
+    if (T.zero) return;
+    const uint64_t Gj = R.G(j);
+    const uint64_t nv = ~T.v & nmask;
+    const uint64_t t = T.s ^ (Gj & T.v);
+    const uint32_t sg = (sigma + par64(Gj & nv & T.s)) & 1u;
+    if (t == T.s) {
+        if (sg) T.zero = 1u;
+        return;
+    }
+    prop_h(R, T, n, T.s, t, 2u * sg);
+    T.h += 1u;
+}
+
+// Left multiplications (Sec. 4.1 update rules).
+template <class Rows>
+__device__ __forceinline__ void gate_s(Rows& R, TermRegs& T, int q, uint32_t dg) {
+    // S: dg = 3 (gamma_q -= 1); S^dagger: dg = 1; both M_q ^= G_q.
+    R.M(q) ^= R.G(q);
+    gamma_set(T, q, (gamma_get(T, q) + dg) & 3u);
+}
+template <class Rows>
+__device__ __forceinline__ void gate_z(Rows& R, TermRegs& T, int q) {
+    (void)R;
+    T.ghi ^= bit64(q);
+}
+template <class Rows>
+__device__ __forceinline__ void gate_cz(Rows& R, TermRegs& T, int q, int r) {
+    (void)T;
+    const uint64_t Gq = R.G(q), Gr = R.G(r);
+    R.M(q) ^= Gr;
+    R.M(r) ^= Gq;
+}
+template <class Rows>
+__device__ __forceinline__ void gate_cx(Rows& R, TermRegs& T, int q, int r) {
+    const uint64_t Mq = R.M(q), Fr = R.F(r);
+    const uint32_t g = (gamma_get(T, q) + gamma_get(T, r) + 2u * par64(Mq & Fr)) & 3u;
+    gamma_set(T, q, g);
+    R.G(r) ^= R.G(q);
+    R.F(q) ^= Fr;
+    R.M(q) = Mq ^ R.M(r);
+}
+
+template <class Rows>
+__device__ __forceinline__ void apply_gate(Rows& R, TermRegs& T, int n, uint64_t nmask, lrs_gate g) {
+    switch (g.op) {
+        case LRS_OP_H: gate_h(R, T, n, nmask, g.q); break;
+        case LRS_OP_S: gate_s(R, T, g.q, 3u); break;
+        case LRS_OP_SDG: gate_s(R, T, g.q, 1u); break;
+        case LRS_OP_Z: gate_z(R, T, g.q); break;
+        case LRS_OP_CX: gate_cx(R, T, g.q, g.r); break;
+        case LRS_OP_CZ: gate_cz(R, T, g.q, g.r); break;
+        case LRS_OP_P0: gate_proj(R, T, n, nmask, g.q, 0u); break;
+        case LRS_OP_P1: gate_proj(R, T, n, nmask, g.q, 1u); break;
+        default: break;
+    }
+}
+
+__host__ __device__ __forceinline__ uint32_t omega_pack(uint32_t k, uint32_t zero, uint32_t h) {
+    return (k & 7u) | ((zero & 1u) << 3) | (h << 8);
+}

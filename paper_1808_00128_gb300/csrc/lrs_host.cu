@@ -1,0 +1,502 @@
+// Host side of the C ABI: argument checks, storage, slot tables, lowering.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lrs_device.cuh"
+#include "lrs_internal.h"
+
+static thread_local char g_err[512] = "";
+
+lrs_status lrs_fail(lrs_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+lrs_status lrs_cuda_check(cudaError_t e, const char* what) {
+    return lrs_fail(e == cudaErrorMemoryAllocation ? LRS_ERR_OOM : LRS_ERR_CUDA, "%s: %s", what,
+                    cudaGetErrorString(e));
+}
+
+extern "C" const char* lrs_last_error(void) { return g_err; }
+
+lrs_status lrs_ensure(void** ptr, size_t* have, size_t bytes) {
+    if (*have >= bytes && *ptr) return LRS_OK;
+    if (*ptr) {
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        *have = 0;
+    }
+    if (bytes == 0) return LRS_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return lrs_cuda_check(e, "cudaMalloc");
+    }
+    *have = bytes;
+    return LRS_OK;
+}
+
+lrs_status lrs_scratch(lrs_ctx* ctx, size_t bytes, void** out) {
+    lrs_status rc = lrs_ensure(&ctx->scratch, &ctx->scratch_bytes, bytes);
+    *out = ctx->scratch;
+    return rc;
+}
+
+static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+// ---------------------------------------------------------------------------------
+// Lowering (Sec. 2.3.2): T and RZ(theta) -> 2-term slot (Eq. (Rtheta)); CCZ ->
+// projector form I - 2 P1 P1 P1, or the 8-term form of Eq. (CCZ_decomposition)
+// with prefactor 1/6.
+// ---------------------------------------------------------------------------------
+namespace {
+struct Lowering {
+    std::vector<lrs_gate> gates;
+    std::vector<lrs_slot> slots;
+    std::vector<lrs_gate> kg;
+    void add_choice(lrs_slot& s, double re, double im, std::initializer_list<lrs_gate> k) {
+        const int j = s.n_choices++;
+        s.c_re[j] = re;
+        s.c_im[j] = im;
+        s.k_off[j] = (int32_t)kg.size();
+        s.k_len[j] = (int32_t)k.size();
+        for (const lrs_gate& g : k) kg.push_back(g);
+    }
+};
+lrs_gate mk(int op, int q, int r = 0) {
+    lrs_gate g;
+    g.op = (uint8_t)op;
+    g.q = (uint8_t)q;
+    g.r = (uint16_t)r;
+    return g;
+}
+}  // namespace
+
+extern "C" lrs_status lrs_lower_circuit(int32_t n, const lrs_circuit_op* ops, int64_t n_ops,
+                                        int32_t ccz_mode, lrs_gate* gates, int64_t gates_cap,
+                                        int64_t* n_gates, lrs_slot* slots, int64_t slots_cap,
+                                        int64_t* n_slots, lrs_gate* k_gates, int64_t k_cap,
+                                        int64_t* n_k_gates) {
+    if (n < 1 || n > 64) return lrs_fail(LRS_ERR_ARG, "n_qubits must be in 1..64 (got %d)", n);
+    if (n_ops < 0 || (n_ops > 0 && !ops)) return lrs_fail(LRS_ERR_ARG, "bad ops array");
+    if (ccz_mode != LRS_CCZ_PROJECTOR && ccz_mode != LRS_CCZ_SUM8)
+        return lrs_fail(LRS_ERR_ARG, "unknown ccz_mode %d", ccz_mode);
+    Lowering L;
+    const double r2 = sqrt(2.0);
+    for (int64_t i = 0; i < n_ops; ++i) {
+        const lrs_circuit_op& o = ops[i];
+        int nq = 1;
+        if (o.kind == LRS_C_CX || o.kind == LRS_C_CZ) nq = 2;
+        if (o.kind == LRS_C_CCZ) nq = 3;
+        if (o.kind < LRS_C_H || o.kind > LRS_C_CCZ)
+            return lrs_fail(LRS_ERR_ARG, "op %lld: unknown kind %d", (long long)i, o.kind);
+        for (int t = 0; t < nq; ++t) {
+            if (o.q[t] < 0 || o.q[t] >= n)
+                return lrs_fail(LRS_ERR_ARG, "op %lld: qubit %d out of range", (long long)i, o.q[t]);
+            for (int t2 = 0; t2 < t; ++t2)
+                if (o.q[t] == o.q[t2])
+                    return lrs_fail(LRS_ERR_ARG, "op %lld: repeated qubit %d", (long long)i, o.q[t]);
+        }
+        switch (o.kind) {
+            case LRS_C_H: L.gates.push_back(mk(LRS_OP_H, o.q[0])); break;
+            case LRS_C_S: L.gates.push_back(mk(LRS_OP_S, o.q[0])); break;
+            case LRS_C_SDG: L.gates.push_back(mk(LRS_OP_SDG, o.q[0])); break;
+            case LRS_C_Z: L.gates.push_back(mk(LRS_OP_Z, o.q[0])); break;
+            case LRS_C_CX: L.gates.push_back(mk(LRS_OP_CX, o.q[0], o.q[1])); break;
+            case LRS_C_CZ: L.gates.push_back(mk(LRS_OP_CZ, o.q[0], o.q[1])); break;
+            case LRS_C_T:
+            case LRS_C_RZ: {
+                // R(theta) = (cos(th/2) - sin(th/2)) I + sqrt2 e^{-i pi/4} sin(th/2) S, th >= 0;
+                // conjugate on (I, S^dagger) for theta < 0.  T = e^{i pi/8} R(pi/4).
+                const double theta = (o.kind == LRS_C_T) ? M_PI / 4 : o.theta;
+                const double th = fabs(theta);
+                const double c0 = cos(th / 2) - sin(th / 2);
+                const double sn = sin(th / 2);
+                // sqrt2 e^{-i pi/4} = 1 - i
+                double c1re = sn, c1im = (theta >= 0) ? -sn : sn;
+                double g_re = 1.0, g_im = 0.0;
+                if (o.kind == LRS_C_T) { g_re = cos(M_PI / 8); g_im = sin(M_PI / 8); }
+                lrs_slot s;
+                memset(&s, 0, sizeof(s));
+                L.add_choice(s, g_re * c0, g_im * c0, {});
+                L.add_choice(s, g_re * c1re - g_im * c1im, g_re * c1im + g_im * c1re,
+                             {mk(theta >= 0 ? LRS_OP_S : LRS_OP_SDG, o.q[0])});
+                (void)r2;
+                L.gates.push_back(mk(LRS_OP_SLOT, 0, (int)L.slots.size()));
+                L.slots.push_back(s);
+                break;
+            }
+            case LRS_C_CCZ: {
+                const int a = o.q[0], b = o.q[1], c = o.q[2];
+                lrs_slot s;
+                memset(&s, 0, sizeof(s));
+                if (ccz_mode == LRS_CCZ_PROJECTOR) {
+                    L.add_choice(s, 1.0, 0.0, {});
+                    L.add_choice(s, -2.0, 0.0, {mk(LRS_OP_P1, a), mk(LRS_OP_P1, b), mk(LRS_OP_P1, c)});
+                } else {
+                    const double w = 1.0 / 6.0;
+                    L.add_choice(s, w, 0, {});
+                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b)});
+                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, c)});
+                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, b, c)});
+                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, a, c), mk(LRS_OP_Z, a)});
+                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, b, c), mk(LRS_OP_Z, b)});
+                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, c), mk(LRS_OP_CZ, b, c), mk(LRS_OP_Z, c)});
+                    L.add_choice(s, -w, 0,
+                                 {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, a, c), mk(LRS_OP_CZ, b, c),
+                                  mk(LRS_OP_Z, a), mk(LRS_OP_Z, b), mk(LRS_OP_Z, c)});
+                }
+                L.gates.push_back(mk(LRS_OP_SLOT, 0, (int)L.slots.size()));
+                L.slots.push_back(s);
+                break;
+            }
+        }
+        if (L.slots.size() > 65535) return lrs_fail(LRS_ERR_ARG, "more than 65535 slots");
+    }
+    if (n_gates) *n_gates = (int64_t)L.gates.size();
+    if (n_slots) *n_slots = (int64_t)L.slots.size();
+    if (n_k_gates) *n_k_gates = (int64_t)L.kg.size();
+    if ((int64_t)L.gates.size() > gates_cap || (int64_t)L.slots.size() > slots_cap ||
+        (int64_t)L.kg.size() > k_cap)
+        return lrs_fail(LRS_ERR_ARG, "output capacity too small (need %zu gates, %zu slots, %zu k_gates)",
+                        L.gates.size(), L.slots.size(), L.kg.size());
+    if (!L.gates.empty()) memcpy(gates, L.gates.data(), L.gates.size() * sizeof(lrs_gate));
+    if (!L.slots.empty()) memcpy(slots, L.slots.data(), L.slots.size() * sizeof(lrs_slot));
+    if (!L.kg.empty()) memcpy(k_gates, L.kg.data(), L.kg.size() * sizeof(lrs_gate));
+    return LRS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------------
+static void free_terms(lrs_ctx* c) {
+    cudaFree(c->F); cudaFree(c->G); cudaFree(c->M);
+    cudaFree(c->glo); cudaFree(c->ghi); cudaFree(c->v); cudaFree(c->s);
+    cudaFree(c->omega); cudaFree(c->coef); cudaFree(c->choice);
+    c->F = c->G = c->M = c->glo = c->ghi = c->v = c->s = nullptr;
+    c->omega = nullptr; c->coef = nullptr; c->choice = nullptr;
+    c->cap = 0; c->chi = 0; c->choice_slots_cap = 0; c->have_terms = false;
+}
+
+static void free_chains(lrs_ctx* c) {
+    cudaFree(c->Q); cudaFree(c->cx); cudaFree(c->cp); cudaFree(c->pend);
+    c->Q = nullptr; c->cx = nullptr; c->cp = nullptr; c->pend = nullptr;
+    c->Q_bytes = 0; c->chains_cap = 0; c->n_chains = 0;
+}
+
+extern "C" lrs_status lrs_create(int32_t device, int32_t n_qubits, lrs_ctx** out) {
+    if (!out) return lrs_fail(LRS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 64)
+        return lrs_fail(LRS_ERR_ARG, "n_qubits must be in 1..64 (got %d)", n_qubits);
+    int count = 0;
+    LRS_CUDA(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return lrs_fail(LRS_ERR_ARG, "bad device %d", device);
+    LRS_CUDA(cudaSetDevice(device));
+    lrs_ctx* c = new lrs_ctx();
+    c->device = device;
+    c->n = n_qubits;
+    c->nmask = n_qubits == 64 ? ~0ull : ((1ull << n_qubits) - 1);
+    *out = c;
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_destroy(lrs_ctx* c) {
+    if (!c) return LRS_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_terms(c);
+    free_chains(c);
+    cudaFree(c->slots_dev); cudaFree(c->kgates_dev); cudaFree(c->gates_dev); cudaFree(c->scratch);
+    delete c;
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_info(const lrs_ctx* c, int64_t* chi, int32_t* n, int64_t* n_slots) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (chi) *chi = c->chi;
+    if (n) *n = c->n;
+    if (n_slots) *n_slots = c->n_slots;
+    return LRS_OK;
+}
+
+static lrs_status check_gate(const lrs_ctx* c, const lrs_gate& g, int64_t n_slots, bool allow_slot,
+                             int64_t idx, const char* what) {
+    if (g.op > LRS_OP_SLOT) return lrs_fail(LRS_ERR_ARG, "%s %lld: unknown op %d", what, (long long)idx, g.op);
+    if (g.op == LRS_OP_SLOT) {
+        if (!allow_slot) return lrs_fail(LRS_ERR_ARG, "%s %lld: nested slot", what, (long long)idx);
+        if ((int64_t)g.r >= n_slots)
+            return lrs_fail(LRS_ERR_ARG, "%s %lld: slot %d out of range (%lld slots)", what, (long long)idx,
+                            g.r, (long long)n_slots);
+        return LRS_OK;
+    }
+    if (g.q >= c->n) return lrs_fail(LRS_ERR_ARG, "%s %lld: qubit %d >= n", what, (long long)idx, g.q);
+    if (g.op == LRS_OP_CX || g.op == LRS_OP_CZ) {
+        if (g.r >= c->n) return lrs_fail(LRS_ERR_ARG, "%s %lld: qubit %d >= n", what, (long long)idx, g.r);
+        if (g.r == g.q) return lrs_fail(LRS_ERR_ARG, "%s %lld: q == r", what, (long long)idx);
+    }
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_init_terms(lrs_ctx* c, const lrs_slot* slots, int64_t n_slots,
+                                     const lrs_gate* k_gates, int64_t n_k_gates, int64_t chi_total,
+                                     int64_t alpha0, int64_t chi, int32_t mode, uint64_t seed,
+                                     void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (chi < 1) return lrs_fail(LRS_ERR_ARG, "chi must be >= 1 (got %lld)", (long long)chi);
+    if (alpha0 < 0 || chi_total < 1 || alpha0 + chi > chi_total)
+        return lrs_fail(LRS_ERR_ARG, "term range [%lld, %lld) outside chi_total = %lld", (long long)alpha0,
+                        (long long)(alpha0 + chi), (long long)chi_total);
+    if (chi > (1ll << 34)) return lrs_fail(LRS_ERR_ARG, "chi too large");
+    if (mode != LRS_MODE_EXACT && mode != LRS_MODE_SPARSIFY)
+        return lrs_fail(LRS_ERR_ARG, "unknown mode %d", mode);
+    if (n_slots < 0 || (n_slots > 0 && !slots) || n_k_gates < 0 || (n_k_gates > 0 && !k_gates))
+        return lrs_fail(LRS_ERR_ARG, "bad slot tables");
+    if (n_slots > 65535) return lrs_fail(LRS_ERR_ARG, "too many slots");
+    LRS_CUDA(cudaSetDevice(c->device));
+    // validate tables and build the device copies
+    std::vector<DevSlot> ds((size_t)n_slots);
+    double l1 = 1.0;
+    long double exact_chi = 1.0L;
+    for (int64_t p = 0; p < n_slots; ++p) {
+        const lrs_slot& s = slots[p];
+        if (s.n_choices < 1 || s.n_choices > LRS_MAX_CHOICES)
+            return lrs_fail(LRS_ERR_ARG, "slot %lld: n_choices %d", (long long)p, s.n_choices);
+        DevSlot& d = ds[(size_t)p];
+        memset(&d, 0, sizeof(d));
+        d.n_choices = s.n_choices;
+        double norm = 0.0;
+        for (int j = 0; j < s.n_choices; ++j) {
+            if (s.k_len[j] < 0 || s.k_off[j] < 0 || (int64_t)s.k_off[j] + s.k_len[j] > n_k_gates)
+                return lrs_fail(LRS_ERR_ARG, "slot %lld choice %d: bad gate range", (long long)p, j);
+            for (int e = 0; e < s.k_len[j]; ++e) {
+                lrs_status rc = check_gate(c, k_gates[s.k_off[j] + e], 0, false, s.k_off[j] + e, "k_gate");
+                if (rc != LRS_OK) return rc;
+            }
+            d.k_off[j] = s.k_off[j];
+            d.k_len[j] = s.k_len[j];
+            d.c_re[j] = s.c_re[j];
+            d.c_im[j] = s.c_im[j];
+            norm += hypot(s.c_re[j], s.c_im[j]);
+            if (s.c_re[j] != 0.0 || s.c_im[j] != 0.0) d.nz_idx[d.n_nonzero++] = j;
+        }
+        if (d.n_nonzero == 0) return lrs_fail(LRS_ERR_ARG, "slot %lld: all coefficients zero", (long long)p);
+        double acc = 0.0;
+        for (int j = 0; j < s.n_choices; ++j) {
+            const double a = hypot(s.c_re[j], s.c_im[j]);
+            acc += a / norm;
+            d.cdf[j] = acc;
+            d.ph_re[j] = a > 0 ? s.c_re[j] / a : 0.0;
+            d.ph_im[j] = a > 0 ? s.c_im[j] / a : 0.0;
+        }
+        l1 *= norm;
+        exact_chi *= d.n_nonzero;
+    }
+    if (mode == LRS_MODE_EXACT && (exact_chi > 1e18L || (int64_t)exact_chi != chi_total))
+        return lrs_fail(LRS_ERR_ARG, "EXACT mode needs chi_total = %.0Lf (got %lld)", exact_chi,
+                        (long long)chi_total);
+
+    // (re)allocate term storage
+    const int64_t cap = (chi + LRS_TERM_ALIGN - 1) / LRS_TERM_ALIGN * LRS_TERM_ALIGN;
+    if (cap != c->cap || n_slots > c->choice_slots_cap) {
+        free_terms(c);
+        free_chains(c);
+        const size_t rows = (size_t)c->n * cap * sizeof(uint64_t);
+        const size_t vec = (size_t)cap * sizeof(uint64_t);
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = cudaMalloc(&c->F, rows);
+        if (e == cudaSuccess) e = cudaMalloc(&c->G, rows);
+        if (e == cudaSuccess) e = cudaMalloc(&c->M, rows);
+        if (e == cudaSuccess) e = cudaMalloc(&c->glo, vec);
+        if (e == cudaSuccess) e = cudaMalloc(&c->ghi, vec);
+        if (e == cudaSuccess) e = cudaMalloc(&c->v, vec);
+        if (e == cudaSuccess) e = cudaMalloc(&c->s, vec);
+        if (e == cudaSuccess) e = cudaMalloc(&c->omega, (size_t)cap * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&c->coef, (size_t)cap * sizeof(float2));
+        const int64_t cs = std::max<int64_t>(n_slots, 1);
+        if (e == cudaSuccess) e = cudaMalloc(&c->choice, (size_t)cs * cap);
+        if (e != cudaSuccess) {
+            free_terms(c);
+            return lrs_cuda_check(e, "term storage");
+        }
+        c->cap = cap;
+        c->choice_slots_cap = cs;
+    }
+    c->chi = chi;
+    c->alpha0 = alpha0;
+    c->chi_total = chi_total;
+    c->n_chains = 0;
+    // slot tables
+    size_t have = (size_t)c->slots_cap * sizeof(DevSlot);
+    lrs_status rc = lrs_ensure((void**)&c->slots_dev, &have, std::max<size_t>(1, ds.size()) * sizeof(DevSlot));
+    if (rc != LRS_OK) return rc;
+    c->slots_cap = (int64_t)(have / sizeof(DevSlot));
+    have = (size_t)c->kgates_cap * sizeof(lrs_gate);
+    rc = lrs_ensure((void**)&c->kgates_dev, &have, std::max<int64_t>(1, n_k_gates) * sizeof(lrs_gate));
+    if (rc != LRS_OK) return rc;
+    c->kgates_cap = (int64_t)(have / sizeof(lrs_gate));
+    cudaStream_t st = as_stream(stream);
+    if (n_slots > 0)
+        LRS_CUDA(cudaMemcpyAsync(c->slots_dev, ds.data(), ds.size() * sizeof(DevSlot),
+                                 cudaMemcpyHostToDevice, st));
+    if (n_k_gates > 0)
+        LRS_CUDA(cudaMemcpyAsync(c->kgates_dev, k_gates, (size_t)n_k_gates * sizeof(lrs_gate),
+                                 cudaMemcpyHostToDevice, st));
+    LRS_CUDA(cudaStreamSynchronize(st));   // host tables may be freed on return
+    c->n_slots = n_slots;
+    c->slots_host.assign(slots, slots + n_slots);
+    c->kgates_host.assign(k_gates, k_gates + n_k_gates);
+    rc = launch_init_terms(c, mode, seed, l1 / (double)chi_total, st);
+    if (rc != LRS_OK) return rc;
+    c->have_terms = true;
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_apply_clifford(lrs_ctx* c, const lrs_gate* gates, int64_t n_gates,
+                                         void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "lrs_init_terms has not been called");
+    if (n_gates < 0 || (n_gates > 0 && !gates)) return lrs_fail(LRS_ERR_ARG, "bad gate array");
+    if (n_gates == 0) return LRS_OK;
+    for (int64_t i = 0; i < n_gates; ++i) {
+        lrs_status rc = check_gate(c, gates[i], c->n_slots, true, i, "gate");
+        if (rc != LRS_OK) return rc;
+    }
+    LRS_CUDA(cudaSetDevice(c->device));
+    size_t have = (size_t)c->gates_cap * sizeof(lrs_gate);
+    lrs_status rc = lrs_ensure((void**)&c->gates_dev, &have, (size_t)n_gates * sizeof(lrs_gate));
+    if (rc != LRS_OK) return rc;
+    c->gates_cap = (int64_t)(have / sizeof(lrs_gate));
+    cudaStream_t st = as_stream(stream);
+    LRS_CUDA(cudaMemcpyAsync(c->gates_dev, gates, (size_t)n_gates * sizeof(lrs_gate),
+                             cudaMemcpyHostToDevice, st));
+    LRS_CUDA(cudaStreamSynchronize(st));   // pageable source: keep the copy complete on return
+    c->n_chains = 0;                        // chain states refer to the old terms
+    return launch_apply_clifford(c, c->gates_dev, n_gates, st);
+}
+
+extern "C" lrs_status lrs_amplitude(lrs_ctx* c, const uint64_t* x, int64_t batch, double* out,
+                                    void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (batch < 0) return lrs_fail(LRS_ERR_ARG, "batch < 0");
+    if (batch > 0 && (!x || !out)) return lrs_fail(LRS_ERR_ARG, "NULL buffer");
+    LRS_CUDA(cudaSetDevice(c->device));
+    return launch_amplitude(c, x, batch, out, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_norm_estimate(lrs_ctx* c, int64_t L, uint64_t seed, double* eta,
+                                        double* mean_host, void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (L < 1) return lrs_fail(LRS_ERR_ARG, "L must be >= 1");
+    if (!eta) return lrs_fail(LRS_ERR_ARG, "eta is NULL");
+    LRS_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    lrs_status rc = launch_norm_estimate(c, L, seed, eta, st);
+    if (rc != LRS_OK) return rc;
+    if (mean_host) {
+        std::vector<double> h((size_t)L);
+        LRS_CUDA(cudaMemcpyAsync(h.data(), eta, (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LRS_CUDA(cudaStreamSynchronize(st));
+        double m = 0.0;
+        for (double x : h) m += x;
+        *mean_host = m / (double)L;
+    }
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_sample_terms(lrs_ctx* c, int64_t count, uint64_t seed, uint64_t* x,
+                                       int64_t* alpha, void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (count < 0 || (count > 0 && !x)) return lrs_fail(LRS_ERR_ARG, "bad output");
+    LRS_CUDA(cudaSetDevice(c->device));
+    return launch_sample_terms(c, count, seed, x, alpha, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_chains_init(lrs_ctx* c, int64_t n_chains, const uint64_t* x, void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (c->n > 62) return lrs_fail(LRS_ERR_UNSUPPORTED, "Metropolis needs n <= 62");
+    if (n_chains < 1 || !x) return lrs_fail(LRS_ERR_ARG, "bad chains");
+    if (n_chains > 65535) return lrs_fail(LRS_ERR_ARG, "at most 65535 chains");
+    LRS_CUDA(cudaSetDevice(c->device));
+    const size_t qb = (size_t)n_chains * c->cap * sizeof(ulonglong2);
+    lrs_status rc = lrs_ensure((void**)&c->Q, &c->Q_bytes, qb);
+    if (rc != LRS_OK) return rc;
+    if (n_chains > c->chains_cap) {
+        cudaFree(c->cx); cudaFree(c->cp); cudaFree(c->pend);
+        c->cx = nullptr; c->cp = nullptr; c->pend = nullptr;
+        c->chains_cap = 0;
+        LRS_CUDA(cudaMalloc(&c->cx, (size_t)n_chains * sizeof(uint64_t)));
+        LRS_CUDA(cudaMalloc(&c->cp, (size_t)n_chains * sizeof(double)));
+        LRS_CUDA(cudaMalloc(&c->pend, (size_t)n_chains * sizeof(int32_t)));
+        c->chains_cap = n_chains;
+    }
+    c->n_chains = n_chains;
+    return launch_chains_init(c, x, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_metropolis_step(lrs_ctx* c, int64_t steps, uint64_t seed, int64_t step0,
+                                          uint64_t* x_out, double* p_out, uint64_t* trace, void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (c->n_chains < 1) return lrs_fail(LRS_ERR_STATE, "chains not initialised");
+    if (steps < 0 || step0 < 0) return lrs_fail(LRS_ERR_ARG, "steps < 0");
+    LRS_CUDA(cudaSetDevice(c->device));
+    return launch_metropolis(c, steps, seed, step0, x_out, p_out, trace, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_export_terms(lrs_ctx* c, int64_t first, int64_t count, uint64_t* F,
+                                       uint64_t* G, uint64_t* M, uint8_t* gamma, uint64_t* v,
+                                       uint64_t* s, int32_t* omega, float* coef, uint8_t* choice) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (first < 0 || count < 0 || first + count > c->chi) return lrs_fail(LRS_ERR_ARG, "bad range");
+    if (count == 0) return LRS_OK;
+    LRS_CUDA(cudaSetDevice(c->device));
+    LRS_CUDA(cudaDeviceSynchronize());
+    const int n = c->n;
+    std::vector<uint64_t> buf((size_t)count);
+    auto rows = [&](const uint64_t* src, uint64_t* dst) -> lrs_status {
+        for (int p = 0; p < n; ++p) {
+            LRS_CUDA(cudaMemcpy(buf.data(), src + (int64_t)p * c->cap + first, (size_t)count * 8,
+                                cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < count; ++i) dst[i * n + p] = buf[(size_t)i];
+        }
+        return LRS_OK;
+    };
+    lrs_status rc;
+    if (F && (rc = rows(c->F, F)) != LRS_OK) return rc;
+    if (G && (rc = rows(c->G, G)) != LRS_OK) return rc;
+    if (M && (rc = rows(c->M, M)) != LRS_OK) return rc;
+    if (gamma) {
+        std::vector<uint64_t> lo((size_t)count), hi((size_t)count);
+        LRS_CUDA(cudaMemcpy(lo.data(), c->glo + first, (size_t)count * 8, cudaMemcpyDeviceToHost));
+        LRS_CUDA(cudaMemcpy(hi.data(), c->ghi + first, (size_t)count * 8, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < count; ++i)
+            for (int p = 0; p < n; ++p)
+                gamma[i * n + p] = (uint8_t)(((lo[(size_t)i] >> p) & 1) | (((hi[(size_t)i] >> p) & 1) << 1));
+    }
+    if (v) LRS_CUDA(cudaMemcpy(v, c->v + first, (size_t)count * 8, cudaMemcpyDeviceToHost));
+    if (s) LRS_CUDA(cudaMemcpy(s, c->s + first, (size_t)count * 8, cudaMemcpyDeviceToHost));
+    if (omega) LRS_CUDA(cudaMemcpy(omega, c->omega + first, (size_t)count * 4, cudaMemcpyDeviceToHost));
+    if (coef) LRS_CUDA(cudaMemcpy(coef, c->coef + first, (size_t)count * 8, cudaMemcpyDeviceToHost));
+    if (choice && c->n_slots > 0) {
+        std::vector<uint8_t> cb((size_t)count);
+        for (int64_t p = 0; p < c->n_slots; ++p) {
+            LRS_CUDA(cudaMemcpy(cb.data(), c->choice + p * c->cap + first, (size_t)count,
+                                cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < count; ++i) choice[i * c->n_slots + p] = cb[(size_t)i];
+        }
+    }
+    return LRS_OK;
+}

@@ -1,0 +1,133 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (see include/lrstab.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lrstab.h"
+
+// Term storage is padded to a multiple of this many terms; padding terms are
+// valid |0^n> CH-forms with b = 0, so kernels need no tail checks.
+#define LRS_TERM_ALIGN 256
+
+// Device copy of one slot table.
+struct DevSlot {
+    int32_t n_choices;
+    int32_t n_nonzero;                 // radix in exact mode
+    int32_t nz_idx[LRS_MAX_CHOICES];   // nonzero choices in index order
+    int32_t k_off[LRS_MAX_CHOICES];
+    int32_t k_len[LRS_MAX_CHOICES];
+    double cdf[LRS_MAX_CHOICES];       // cumulative |c_j| / ||c||_1 (sparsify)
+    double c_re[LRS_MAX_CHOICES], c_im[LRS_MAX_CHOICES];     // c_j (exact)
+    double ph_re[LRS_MAX_CHOICES], ph_im[LRS_MAX_CHOICES];   // c_j / |c_j| (sparsify)
+};
+
+// Plain view of the term arrays passed to kernels by value.
+struct TermsView {
+    int32_t n;          // qubits
+    uint64_t nmask;     // low n bits set
+    int64_t chi;        // number of real terms held
+    int64_t alpha0;     // global index of local term 0
+    int64_t cap;        // allocated (multiple of LRS_TERM_ALIGN), row stride
+    uint64_t* F;        // [n][cap]
+    uint64_t* G;        // [n][cap]
+    uint64_t* M;        // [n][cap]
+    uint64_t* glo;      // [cap] gamma bit-plane 0 (bit p = bit 0 of gamma_p)
+    uint64_t* ghi;      // [cap] gamma bit-plane 1
+    uint64_t* v;        // [cap]
+    uint64_t* s;        // [cap]
+    uint32_t* omega;    // [cap] k | zero << 3 | h << 8
+    float2* coef;       // [cap] b_alpha
+    uint8_t* choice;    // [n_slots][cap]
+    int64_t n_slots;
+    const DevSlot* slots;
+    const lrs_gate* kgates;
+};
+
+struct lrs_ctx {
+    int device = 0;
+    int n = 0;
+    uint64_t nmask = 0;
+    int64_t chi = 0;
+    int64_t alpha0 = 0;
+    int64_t chi_total = 0;
+    int64_t cap = 0;
+    bool have_terms = false;
+
+    uint64_t *F = nullptr, *G = nullptr, *M = nullptr;
+    uint64_t *glo = nullptr, *ghi = nullptr, *v = nullptr, *s = nullptr;
+    uint32_t* omega = nullptr;
+    float2* coef = nullptr;
+    uint8_t* choice = nullptr;
+    int64_t choice_slots_cap = 0;
+
+    int64_t n_slots = 0;
+    DevSlot* slots_dev = nullptr;
+    int64_t slots_cap = 0;
+    lrs_gate* kgates_dev = nullptr;
+    int64_t kgates_cap = 0;
+    std::vector<lrs_slot> slots_host;
+    std::vector<lrs_gate> kgates_host;
+
+    lrs_gate* gates_dev = nullptr;
+    int64_t gates_cap = 0;
+
+    // scratch for partial sums
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+
+    // Metropolis chains
+    int64_t n_chains = 0;
+    ulonglong2* Q = nullptr;        // [chain][cap]: (u | mu << 62, w)
+    size_t Q_bytes = 0;
+    uint64_t* cx = nullptr;         // [chain] current x
+    double* cp = nullptr;           // [chain] P(x) (unnormalised)
+    int32_t* pend = nullptr;        // [chain] pending accepted flip (-1 none)
+    int64_t chains_cap = 0;
+
+    TermsView view() const {
+        TermsView t;
+        t.n = n; t.nmask = nmask; t.chi = chi; t.alpha0 = alpha0; t.cap = cap;
+        t.F = F; t.G = G; t.M = M; t.glo = glo; t.ghi = ghi; t.v = v; t.s = s;
+        t.omega = omega; t.coef = coef; t.choice = choice; t.n_slots = n_slots;
+        t.slots = slots_dev; t.kgates = kgates_dev;
+        return t;
+    }
+};
+
+// ---- error reporting -----------------------------------------------------------
+lrs_status lrs_fail(lrs_status st, const char* fmt, ...);
+lrs_status lrs_cuda_check(cudaError_t e, const char* what);
+#define LRS_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return lrs_cuda_check(e_, #call);    \
+    } while (0)
+#define LRS_LAUNCH_CHECK(what)                                      \
+    do {                                                            \
+        cudaError_t e_ = cudaGetLastError();                        \
+        if (e_ != cudaSuccess) return lrs_cuda_check(e_, what);     \
+    } while (0)
+
+// Grow a device buffer to at least `bytes` (contents not kept).
+lrs_status lrs_ensure(void** ptr, size_t* have, size_t bytes);
+lrs_status lrs_scratch(lrs_ctx* ctx, size_t bytes, void** out);
+
+// ---- launchers implemented in the kernel translation units --------------------
+lrs_status launch_init_terms(lrs_ctx* ctx, int32_t mode, uint64_t seed, double scale,
+                             cudaStream_t st);
+lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates,
+                                 cudaStream_t st);
+lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
+                            cudaStream_t st);
+lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta,
+                                cudaStream_t st);
+lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint64_t* x,
+                               int64_t* alpha, cudaStream_t st);
+lrs_status launch_chains_init(lrs_ctx* ctx, const uint64_t* x, cudaStream_t st);
+lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t step0,
+                             uint64_t* x_out, double* p_out, uint64_t* trace, cudaStream_t st);

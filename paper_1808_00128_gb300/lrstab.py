@@ -1,0 +1,261 @@
+"""ctypes binding of liblrstab.so (argument marshalling only).
+
+Every computation happens in the CUDA library; this module converts Python
+circuits and torch tensors into the C ABI's plain pointers and sizes.  There
+is no CPU fallback: if the library is missing or a call fails, it raises.
+
+Device buffers are torch tensors on the context's device (PyTorch serves as
+the device allocator and stream provider).  Basis strings are 64-bit words
+(torch.int64 or torch.uint64 tensors) holding qubit j in bit j.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrstab.so")
+
+# ---- C enums (include/lrstab.h) ----------------------------------------------------
+OP = dict(H=0, S=1, SDG=2, Z=3, CX=4, CZ=5, P0=6, P1=7, SLOT=8)
+CKIND = dict(H=0, S=1, SDG=2, Z=3, CX=4, CZ=5, T=6, RZ=7, CCZ=8)
+CCZ_MODE = dict(proj=0, sum8=1)
+MODE = dict(exact=0, sparsify=1)
+STATUS = {0: "LRS_OK", -1: "LRS_ERR_ARG", -2: "LRS_ERR_OOM", -3: "LRS_ERR_CUDA",
+          -4: "LRS_ERR_TIMEOUT", -5: "LRS_ERR_STATE", -6: "LRS_ERR_UNSUPPORTED"}
+
+GATE_DT = np.dtype([("op", "u1"), ("q", "u1"), ("r", "<u2")])
+SLOT_DT = np.dtype([("n_choices", "<i4"), ("k_off", "<i4", (8,)), ("k_len", "<i4", (8,)),
+                    ("c_re", "<f8", (8,)), ("c_im", "<f8", (8,))], align=True)
+COP_DT = np.dtype([("kind", "<i4"), ("q", "<i4", (3,)), ("theta", "<f8")], align=True)
+
+EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", "lrs_init_terms",
+            "lrs_apply_clifford", "lrs_amplitude", "lrs_norm_estimate", "lrs_sample_terms",
+            "lrs_chains_init", "lrs_metropolis_step", "lrs_export_terms", "lrs_info",
+            "lrs_alu_probe"]
+
+
+class LrsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load liblrstab.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, u64 = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64
+    L.lrs_last_error.restype = C.c_char_p
+    sigs = {
+        "lrs_lower_circuit": [i32, vp, i64, i32, vp, i64, vp, vp, i64, vp, vp, i64, vp],
+        "lrs_create": [i32, i32, vp],
+        "lrs_destroy": [vp],
+        "lrs_init_terms": [vp, vp, i64, vp, i64, i64, i64, i64, i32, u64, vp],
+        "lrs_apply_clifford": [vp, vp, i64, vp],
+        "lrs_amplitude": [vp, vp, i64, vp, vp],
+        "lrs_norm_estimate": [vp, i64, u64, vp, vp, vp],
+        "lrs_sample_terms": [vp, i64, u64, vp, vp, vp],
+        "lrs_chains_init": [vp, i64, vp, vp],
+        "lrs_metropolis_step": [vp, i64, u64, i64, vp, vp, vp, vp],
+        "lrs_export_terms": [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+        "lrs_info": [vp, vp, vp, vp],
+        "lrs_alu_probe": [i32, i64, vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise LrsError(rc, lib().lrs_last_error().decode())
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- circuits ------------------------------------------------------------------------
+def circuit_ops(ops) -> np.ndarray:
+    """Workload tuples ('H', q), ('CX', c, t), ('RZ', q, theta), ... -> lrs_circuit_op[]."""
+    arr = np.zeros(len(ops), dtype=COP_DT)
+    for i, op in enumerate(ops):
+        name = op[0]
+        arr[i]["kind"] = CKIND[name]
+        if name == "RZ":
+            arr[i]["q"][0] = op[1]
+            arr[i]["theta"] = op[2]
+        else:
+            for t, q in enumerate(op[1:]):
+                arr[i]["q"][t] = q
+    return arr
+
+
+class Lowered:
+    """Lowered circuit: gates (with SLOT entries), slot tables and K_j gate lists."""
+
+    def __init__(self, gates, slots, kgates):
+        self.gates, self.slots, self.kgates = gates, slots, kgates
+
+    @property
+    def exact_chi(self) -> int:
+        out = 1
+        for s in self.slots:
+            nz = int(np.count_nonzero((s["c_re"][: s["n_choices"]] != 0) |
+                                      (s["c_im"][: s["n_choices"]] != 0)))
+            out *= nz
+        return out
+
+
+def lower_circuit(n: int, ops, ccz_mode: str = "proj") -> Lowered:
+    cops = circuit_ops(ops)
+    ng, ns, nk = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    # first call sizes the outputs
+    gates = np.zeros(max(1, 2 * len(ops)), GATE_DT)
+    slots = np.zeros(max(1, len(ops)), SLOT_DT)
+    kg = np.zeros(max(1, 8 * len(ops)), GATE_DT)
+    rc = lib().lrs_lower_circuit(n, _ptr(cops), len(ops), CCZ_MODE[ccz_mode], _ptr(gates), len(gates),
+                                 C.byref(ng), _ptr(slots), len(slots), C.byref(ns), _ptr(kg), len(kg),
+                                 C.byref(nk))
+    _check(rc)
+    return Lowered(gates[: ng.value].copy(), slots[: ns.value].copy(), kg[: nk.value].copy())
+
+
+def gates_array(gates) -> np.ndarray:
+    """('H', q) / ('CX', q, r) / ('P1', q) / ('SLOT', p) tuples -> lrs_gate[]."""
+    arr = np.zeros(len(gates), GATE_DT)
+    for i, g in enumerate(gates):
+        arr[i]["op"] = OP[g[0]]
+        if g[0] == "SLOT":
+            arr[i]["r"] = g[1]
+        else:
+            arr[i]["q"] = g[1]
+            if len(g) > 2:
+                arr[i]["r"] = g[2]
+    return arr
+
+
+def alu_probe(device: int = 0, iters: int = 20000) -> float:
+    """Sustained 32-bit LOP3 rate of the device (ops/s)."""
+    out = C.c_double(0.0)
+    _check(lib().lrs_alu_probe(device, iters, C.byref(out)))
+    return out.value
+
+
+# ---- simulator context ------------------------------------------------------------------
+class Simulator:
+    """One lrs_ctx: chi CH-form terms of an n-qubit circuit on one GPU."""
+
+    def __init__(self, n: int, device: int = 0):
+        self.n = n
+        self.device = device
+        h = C.c_void_p()
+        _check(lib().lrs_create(device, n, C.byref(h)))
+        self._h = h
+        self.chi = 0
+        self.n_slots = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lrs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls
+    def init_terms(self, lowered: Lowered, chi: int, mode: str = "sparsify", seed: int = 0,
+                   alpha0: int = 0, chi_total: int | None = None, stream=None):
+        """Terms alpha0 .. alpha0+chi-1 of a chi_total-term decomposition (default: all)."""
+        chi_total = chi if chi_total is None else chi_total
+        _check(lib().lrs_init_terms(self._h, _ptr(lowered.slots), len(lowered.slots),
+                                    _ptr(lowered.kgates), len(lowered.kgates), chi_total, alpha0, chi,
+                                    MODE[mode], seed & (2 ** 64 - 1), _stream(stream)))
+        self.chi = chi
+        self.alpha0 = alpha0
+        self.chi_total = chi_total
+        self.n_slots = len(lowered.slots)
+
+    def apply_clifford(self, gates: np.ndarray, stream=None):
+        _check(lib().lrs_apply_clifford(self._h, _ptr(gates), len(gates), _stream(stream)))
+
+    def amplitude(self, x, out=None, stream=None):
+        """x: int64/uint64 CUDA tensor [B] -> float64 CUDA tensor [B, 2] (Re, Im)."""
+        import torch
+        if out is None:
+            out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
+        _check(lib().lrs_amplitude(self._h, _ptr(x), x.numel(), _ptr(out), _stream(stream)))
+        return out
+
+    def norm_estimate(self, L: int, seed: int, eta=None, want_mean: bool = False, stream=None):
+        import torch
+        if eta is None:
+            eta = torch.empty(L, dtype=torch.float64, device=f"cuda:{self.device}")
+        mean = C.c_double(0.0)
+        _check(lib().lrs_norm_estimate(self._h, L, seed & (2 ** 64 - 1), _ptr(eta),
+                                       C.byref(mean) if want_mean else None, _stream(stream)))
+        return (eta, mean.value) if want_mean else eta
+
+    def sample_terms(self, count: int, seed: int, x=None, alpha=None, stream=None):
+        import torch
+        if x is None:
+            x = torch.empty(count, dtype=torch.int64, device=f"cuda:{self.device}")
+        _check(lib().lrs_sample_terms(self._h, count, seed & (2 ** 64 - 1), _ptr(x), _ptr(alpha),
+                                      _stream(stream)))
+        return x
+
+    def chains_init(self, x, stream=None):
+        _check(lib().lrs_chains_init(self._h, x.numel(), _ptr(x), _stream(stream)))
+
+    def metropolis(self, steps: int, seed: int, step0: int = 0, x_out=None, p_out=None, trace=None,
+                   stream=None):
+        _check(lib().lrs_metropolis_step(self._h, steps, seed & (2 ** 64 - 1), step0, _ptr(x_out),
+                                         _ptr(p_out), _ptr(trace), _stream(stream)))
+
+    def export_terms(self, first: int = 0, count: int | None = None) -> dict:
+        count = self.chi - first if count is None else count
+        n, ns = self.n, self.n_slots
+        out = dict(F=np.zeros((count, n), np.uint64), G=np.zeros((count, n), np.uint64),
+                   M=np.zeros((count, n), np.uint64), gamma=np.zeros((count, n), np.uint8),
+                   v=np.zeros(count, np.uint64), s=np.zeros(count, np.uint64),
+                   omega=np.zeros(count, np.int32), coef=np.zeros((count, 2), np.float32),
+                   choice=np.zeros((count, max(ns, 1)), np.uint8))
+        _check(lib().lrs_export_terms(self._h, first, count, *[_ptr(out[k]) for k in
+                                      ("F", "G", "M", "gamma", "v", "s", "omega", "coef", "choice")]))
+        return out

@@ -15,9 +15,9 @@ A circuit is a list of plain tuples acting on qubits 0..n-1:
 Basis strings are n-bit integers with bit j holding qubit j.
 
 The workload shapes follow the paper's experiments: random Clifford+T
-circuits (Sec. 3.2 / Table 1 scale), QAOA on Max-E3LIN2 (Sec. 3.4.1) and the
-hidden-shift circuits (Sec. 3.4.2), whose exact instances are not published in
-the paper; these generators are seeded stand-ins with the same structure.
+circuits, QAOA on Max-E3LIN2 (Sec. 2.4.1) and the hidden-shift circuits
+(Sec. 2.4.2), whose exact instances are not published in the paper; these
+generators are seeded stand-ins with the same structure.
 """
 from __future__ import annotations
 
@@ -157,7 +157,7 @@ SEED_BASE = 180800128
 def config_tiny():
     """n=10, 200 random Cliffords + 6 T; exact 2-term T -> chi = 64."""
     ops = random_clifford_t(10, 200, 6, SEED_BASE + 1)
-    return dict(name="clifford_t_n10_t6_exact", n=10, ops=ops, chi=64, mode="exact",
+    return dict(name="clifford_t_n10_t6_exact", n=10, ops=ops, chi=64, mode="exact", seed=0,
                 batch=1024, L=64)
 
 
@@ -165,13 +165,13 @@ def config_mid():
     """n=40, 2000 random Cliffords + 24 T; sparsified to chi = 2^16."""
     ops = random_clifford_t(40, 2000, 24, SEED_BASE + 2)
     return dict(name="clifford_t_n40_t24_chi65536", n=40, ops=ops, chi=1 << 16,
-                mode="sparsify", batch=4096, L=256)
+                mode="sparsify", seed=SEED_BASE + 12, batch=4096, L=256, chains=256)
 
 
 def config_hidden_shift():
     """n=40 hidden shift with 16 CCZ; exact projector form of CCZ -> chi = 2^16."""
     ops, s = hidden_shift_circuit(40, 16, SEED_BASE + 3)
-    return dict(name="hidden_shift_n40_ccz16", n=40, ops=ops, chi=1 << 16, mode="exact",
+    return dict(name="hidden_shift_n40_ccz16", n=40, ops=ops, chi=1 << 16, mode="exact", seed=0,
                 shift=s, chains=1024, batch=4096, L=256)
 
 
@@ -179,4 +179,4 @@ def config_qaoa(beta: float = 0.2, chi: int = 1 << 20):
     """n=50 QAOA p=1 on Max-E3LIN2 (degree 4), gamma=0.3."""
     ops, inst = qaoa_e3lin2_circuit(50, 4, 0.3, beta, SEED_BASE + 4)
     return dict(name="qaoa_e3lin2_n50", n=50, ops=ops, chi=chi, mode="sparsify",
-                instance=inst, chains=256, steps=10000, L=512)
+                seed=SEED_BASE + 14, instance=inst, chains=256, steps=10000, L=512)
