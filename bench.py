@@ -136,7 +136,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------------
-def oracle_sample_rates(cfg, n_terms=2, n_x=256, n_a=4, seed_alpha=0):
+def oracle_sample_rates(cfg, n_terms=24, n_x=256, n_a=8, seed_alpha=0):
     """Per-unit oracle times on a bounded sample of the workload."""
     from oracle import decomp
     from oracle import estimators as E
@@ -359,8 +359,8 @@ def main():
         rates = oracle_sample_rates(cfg)
         cpu = {"value": units / oracle_step_time(cfg, rates), "unit": UNIT, "cores": 1,
                "kind": "oracle",
-               "sample": "2 terms of the n=40 chi=2^16 decomposition built by the oracle, 256 "
-                         "amplitude evals and 4 equatorial inner products per term; per-unit "
+               "sample": "24 terms of the n=40 chi=2^16 decomposition built by the oracle, 256 "
+                         "amplitude evals and 8 equatorial inner products per term; per-unit "
                          "times scaled to one full step",
                "seconds": round(time.perf_counter() - t0, 1)}
     sim.close()

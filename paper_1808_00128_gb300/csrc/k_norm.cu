@@ -253,6 +253,8 @@ lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* 
     if (rc != LRS_OK) return rc;
     float2* partial = (float2*)scr;
     const size_t smem = (size_t)2 * ctx->n * NRM_TPB * sizeof(uint64_t);
+    LRS_CUDA(cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  2 * 64 * NRM_TPB * (int)sizeof(uint64_t)));
     const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
     if (lblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "L too large");
     dim3 grid((unsigned)n_tiles, (unsigned)lblocks);
