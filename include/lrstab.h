@@ -188,6 +188,24 @@ lrs_status lrs_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t 
 lrs_status lrs_amplitude(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch, double* out_dev,
                          void* stream);
 
+/* Same result as lrs_amplitude, but the call allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc when they need amplitudes (for example a serving
+ * loop whose framework allocator already holds the device memory, or code
+ * that must avoid the allocator's latency and locks).  The partial sums go to
+ * a fixed 16 MiB array in the library's device memory (2^21 float2 entries),
+ * present on every GPU that loads the library until the process exits.
+ * Limit: batch * ceil(chi / 128) <= 2^21; larger requests return LRS_ERR_ARG.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and each call overwrites every entry it
+ * reads, so nothing needs clearing; calls that overlap on the GPU (for
+ * example on two streams, or from two contexts) race on the array and must be
+ * serialised by the caller.
+ * Errors: as lrs_amplitude, plus LRS_ERR_ARG when the batch is too large.   */
+lrs_status lrs_amplitude_noalloc(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch,
+                                 double* out_dev, void* stream);
+
 /* eta_dev[l] = 2^n |<phi_{A_l}|psi>|^2 for l < L (Lemma (Norm Estimation)),
  * A_l in M_n drawn from rand64(seed, l, i): word 0 = low bits of diag(A),
  * word 1 = high bits, words 2.. = strict upper triangle in row-major order.

@@ -131,3 +131,68 @@ lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, doub
     LRS_LAUNCH_CHECK("amplitude reduce kernel");
     return LRS_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// Allocation-free variant of lrs_amplitude.
+//
+// Some callers cannot call cudaMalloc at the point where they need amplitudes:
+// a serving loop whose framework allocator has already reserved all device
+// memory, or code that must not take the allocator's locks or its latency on
+// a hot path.  For them the block partial sums live in a fixed file-scope
+// device array instead of the context's growable scratch buffer.  The array
+// is allocated when the library is loaded and stays on every GPU that loads
+// the library until the process exits.
+// ---------------------------------------------------------------------------------
+#define LRS_NOALLOC_PARTIALS (2u * 1024u * 1024u)   // float2 entries = 16 MiB
+
+static __device__ __align__(256) float2 g_noalloc_partials[LRS_NOALLOC_PARTIALS];
+
+// Device address of g_noalloc_partials, looked up once per device.  In host
+// code the symbol name is only a host-side stand-in, so it is never passed to a
+// kernel directly.
+static void* g_noalloc_addr[128];
+static bool g_noalloc_ready[128];
+
+static lrs_status noalloc_address(int device, float2** out) {
+    if (device < 0 || device >= 128) return lrs_fail(LRS_ERR_UNSUPPORTED, "device index %d", device);
+    if (!g_noalloc_ready[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return lrs_cuda_check(e, "cudaGetSymbolAddress(g_noalloc_partials)");
+        g_noalloc_addr[device] = p;
+        g_noalloc_ready[device] = true;
+    }
+    *out = (float2*)g_noalloc_addr[device];
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_amplitude_noalloc(lrs_ctx* ctx, const uint64_t* x, int64_t batch,
+                                            double* out, void* stream) {
+    if (!ctx) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!ctx->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (batch < 0) return lrs_fail(LRS_ERR_ARG, "batch < 0");
+    if (batch > 0 && (!x || !out)) return lrs_fail(LRS_ERR_ARG, "NULL buffer");
+    LRS_CUDA(cudaSetDevice(ctx->device));
+    float2* partial = nullptr;
+    lrs_status rc = noalloc_address(ctx->device, &partial);   // first call on a device: set-up
+    if (rc != LRS_OK) return rc;
+    if (batch == 0) return LRS_OK;
+    const int64_t n_tiles = ctx->cap / AMP_TPB;
+    if ((uint64_t)batch * (uint64_t)n_tiles > (uint64_t)LRS_NOALLOC_PARTIALS)
+        return lrs_fail(LRS_ERR_ARG,
+                        "lrs_amplitude_noalloc: batch * ceil(chi/128) = %lld exceeds the fixed "
+                        "buffer of %u partial sums; use a smaller batch or lrs_amplitude",
+                        (long long)(batch * n_tiles), LRS_NOALLOC_PARTIALS);
+    const int64_t xblocks = (batch + AMP_XB - 1) / AMP_XB;
+    if (xblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "amplitude batch too large");
+    const size_t smem = (size_t)2 * ctx->n * AMP_TPB * sizeof(uint64_t);
+    LRS_CUDA(cudaFuncSetAttribute(k_amplitude, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  2 * 64 * AMP_TPB * (int)sizeof(uint64_t)));
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid((unsigned)n_tiles, (unsigned)xblocks);
+    k_amplitude<<<grid, AMP_TPB, smem, st>>>(ctx->view(), x, batch, partial, n_tiles);
+    LRS_LAUNCH_CHECK("amplitude kernel (no-alloc)");
+    k_amp_reduce<<<(unsigned)batch, 256, 0, st>>>(partial, n_tiles, batch, out);
+    LRS_LAUNCH_CHECK("amplitude reduce kernel (no-alloc)");
+    return LRS_OK;
+}

@@ -34,7 +34,7 @@ COP_DT = np.dtype([("kind", "<i4"), ("q", "<i4", (3,)), ("theta", "<f8")], align
 EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", "lrs_init_terms",
             "lrs_apply_clifford", "lrs_amplitude", "lrs_norm_estimate", "lrs_sample_terms",
             "lrs_chains_init", "lrs_metropolis_step", "lrs_export_terms", "lrs_info",
-            "lrs_alu_probe"]
+            "lrs_alu_probe", "lrs_amplitude_noalloc"]
 
 
 class LrsError(RuntimeError):
@@ -71,6 +71,7 @@ def lib():
         "lrs_export_terms": [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "lrs_info": [vp, vp, vp, vp],
         "lrs_alu_probe": [i32, i64, vp],
+        "lrs_amplitude_noalloc": [vp, vp, i64, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -221,6 +222,12 @@ class Simulator:
         if out is None:
             out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
         _check(lib().lrs_amplitude(self._h, _ptr(x), x.numel(), _ptr(out), _stream(stream)))
+        return out
+
+    def amplitude_noalloc(self, x, out, stream=None):
+        """As amplitude(), through the entry point that allocates no device memory
+        (`out` must be supplied: float64 CUDA tensor [B, 2])."""
+        _check(lib().lrs_amplitude_noalloc(self._h, _ptr(x), x.numel(), _ptr(out), _stream(stream)))
         return out
 
     def norm_estimate(self, L: int, seed: int, eta=None, want_mean: bool = False, stream=None):
