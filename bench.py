@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--impl", default="lrstab", choices=["lrstab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: chi = 2^15 terms of the same decomposition, B = 2048, "
+                         "L = 128, C = 128, T = 2 (for ncu captures; not a bench line)")
     return ap.parse_args()
 
 
@@ -225,8 +228,13 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     lrstab.lib()
 
+    global B_X, L_A, C_CH, T_MC
     cfg = workloads.config_mid()
     n, chi, seed = cfg["n"], cfg["chi"], cfg["seed"]
+    chi_total = chi
+    if args.small:
+        chi, B_X, L_A, C_CH, T_MC = 1 << 15, 2048, 128, 128, 2
+        args.no_cpu_baseline = args.no_e2e = True
     low = lrstab.lower_circuit(n, cfg["ops"])
     x_host = torch.from_numpy(workloads.random_bitstrings(n, B_X, seed=workloads.SEED_BASE + 40)
                               .view(np.int64)).pin_memory()
@@ -247,7 +255,7 @@ def main():
             if ev is not None:
                 ev[i].record(stream)
         mark(0)
-        sim.init_terms(low, chi, mode="sparsify", seed=seed)
+        sim.init_terms(low, chi, mode="sparsify", seed=seed, chi_total=chi_total)
         mark(1)
         sim.apply_clifford(low.gates)
         mark(2)
@@ -302,7 +310,7 @@ def main():
     phase_ms = {p: statistics.mean(v) for p, v in per_phase.items()}
     ops = {
         "apply_clifford": chi * clifford_ops_per_term(n, low),
-        "amplitude": chi * B_X * (10 * xpop + 30),
+        "amplitude": chi * B_X * (8 * ((n + 3) // 4) + 16),
         "norm_estimate": chi * L_A * float(np.mean(8 * n * n + 4 * vw ** 2)),
     }
     mc_bytes = T_MC * (chi * C_CH * (16 + 16 * 0.5) + chi * 16 * n)

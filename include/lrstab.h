@@ -195,7 +195,10 @@ lrs_status lrs_amplitude(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch, dou
  * that must avoid the allocator's latency and locks).  The partial sums go to
  * a fixed 16 MiB array in the library's device memory (2^21 float2 entries),
  * present on every GPU that loads the library until the process exits.
- * Limit: batch * ceil(chi / 128) <= 2^21; larger requests return LRS_ERR_ARG.
+ * Limit: batch * n_tiles <= 2^21 partial sums, where n_tiles, the number of
+ * term tiles the kernel uses, is min(ceil(8 * SMs / ceil(batch / 512)),
+ * ceil(chi_padded / 32)) (152 for batch 4096 on a 152-SM GPU); larger requests
+ * return LRS_ERR_ARG.  Any batch above 2^21 is rejected.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the one array and each call overwrites every entry it

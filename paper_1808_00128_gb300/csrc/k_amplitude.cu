@@ -1,82 +1,128 @@
 // Batched amplitudes <x|psi> = sum_alpha b_alpha <x|phi_alpha> (Eqs. (amplitude),
 // (amplitude1)).
 //
-// One thread per term, x uniform across the block: the set bits of x drive a
-// uniform loop over rows, so there is no divergence and every shared-memory
-// access ([row][thread] layout) is conflict-free.  Per set bit p of x the
-// Pauli accumulator i^mu X(u) Z(w) absorbs U_C^{-1} X_p U_C:
-//     z ^= w & F_p;  u ^= F_p;  w ^= M_p
-// and the phase is mu = x.gamma + 2 parity(z) (mod 4) at the end, so the loop
-// body is pure LOP3 work.  The block's 128 term values are summed pairwise in
-// FP32 (warp shuffles, then across warps); block partials are summed in FP64.
+// For each (x, term) the Pauli Q = prod_{p: x_p = 1} U_C^{-1} X_p U_C is written
+// i^mu X(u) Z(w); taking the rows in increasing p,
+//     z ^= w & F_p;  u ^= F_p;  w ^= M_p,   mu = x.gamma + 2 parity(z)  (mod 4).
+// The rows are grouped four at a time (Four Russians): for the current term the
+// block builds a shared table, per 4-row chunk c and pattern q of x's bits
+// 4c..4c+3, of (u_q, w_q, z_q) restricted to those rows; a chunk then enters as
+//     z ^= (w & u_q) ^ z_q;  u ^= u_q;  w ^= w_q.
+// One thread owns XP strings x and walks the block's tile of terms, so its
+// chi-sum is a private FP32 Kahan sum (no cross-thread reduction); the tile
+// partials are summed in FP64 by k_amp_reduce.
 #include "lrs_device.cuh"
 
 namespace {
 
-constexpr int AMP_TPB = 128;   // terms per block
-constexpr int AMP_XB = 64;     // x values per block
+constexpr int AMP_XT = 128;   // threads per block
+constexpr int AMP_XP = 4;     // strings per thread (independent chains for ILP)
+constexpr int AMP_XB = AMP_XT * AMP_XP;
 
-__global__ void __launch_bounds__(AMP_TPB) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
-                                                       int64_t batch, float2* __restrict__ partial,
-                                                       int64_t n_tiles) {
-    extern __shared__ uint64_t smem[];
-    __shared__ float2 red[AMP_TPB / 32][AMP_XB];
+struct AmpEntry {
+    uint64_t u, w, z;
+};
+
+template <int NCH>
+__global__ void __launch_bounds__(AMP_XT) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
+                                                      int64_t batch, int64_t tt,
+                                                      float2* __restrict__ partial, int64_t n_tiles) {
+    __shared__ AmpEntry tab[NCH][16];
+    __shared__ uint64_t sF[64], sM[64];
+    __shared__ float2 val8[8];              // b e^{i pi k/4} 2^{-(|v|+h)/2}, k = 0..7
+    __shared__ uint64_t sc[4];              // glo, ghi, v, s
+    __shared__ uint32_t sc_live;
     const int n = T.n;
     const int tid = threadIdx.x;
     const int64_t tile = blockIdx.x;
-    const int64_t a = tile * AMP_TPB + tid;
-    uint64_t* sF = smem + tid;
-    uint64_t* sM = smem + (int64_t)n * AMP_TPB + tid;
-    for (int p = 0; p < n; ++p) {
-        sF[p * AMP_TPB] = T.F[(int64_t)p * T.cap + a];
-        sM[p * AMP_TPB] = T.M[(int64_t)p * T.cap + a];
+    const int64_t xb = (int64_t)blockIdx.y * AMP_XB;
+    uint64_t xv[AMP_XP];
+#pragma unroll
+    for (int k = 0; k < AMP_XP; ++k) {
+        const int64_t i = xb + tid + k * AMP_XT;
+        xv[k] = i < batch ? (xs[i] & T.nmask) : 0ull;   // bits >= n are ignored
     }
-    const uint64_t glo = T.glo[a], ghi = T.ghi[a], v = T.v[a], s = T.s[a];
-    const uint32_t om = T.omega[a];
-    const uint64_t nv = ~v & T.nmask;
-    const uint64_t sv = s & v;
-    const bool live = ((om >> 3) & 1u) == 0u;
-    const int k0 = (int)(om & 7u);
-    const int e0 = __popcll(v) + (int)(om >> 8);   // 2^{-(|v| + h)/2}
-    const float2 b = T.coef[a];
+    KahanC acc[AMP_XP];
+#pragma unroll
+    for (int k = 0; k < AMP_XP; ++k) acc[k].init();
 
-    const int64_t x0 = (int64_t)blockIdx.y * AMP_XB;
-    const int nx = (int)(batch - x0 < AMP_XB ? batch - x0 : AMP_XB);
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int xi = 0; xi < nx; ++xi) {
-        const uint64_t x = xs[x0 + xi] & T.nmask;   // bits >= n are ignored
-        uint64_t u = 0, w = 0, z = 0, xr = x;
-        while (xr) {
-            const int p = ffs64(xr);
-            xr &= xr - 1;
-            const uint64_t Fp = sF[p * AMP_TPB];
-            z ^= w & Fp;
-            u ^= Fp;
-            w ^= sM[p * AMP_TPB];
+    const int64_t a0 = tile * tt;
+    const int64_t a1 = (a0 + tt < T.cap) ? a0 + tt : T.cap;
+    // register prefetch of the next term: threads < n hold rows, threads 64..69 scalars
+    uint64_t pf = 0, pm = 0;
+    auto prefetch = [&](int64_t a) {
+        if (tid < n) {
+            pf = T.F[(int64_t)tid * T.cap + a];
+            pm = T.M[(int64_t)tid * T.cap + a];
+        } else if (tid == 64) {
+            pf = T.glo[a]; pm = T.ghi[a];
+        } else if (tid == 65) {
+            pf = T.v[a]; pm = T.s[a];
+        } else if (tid == 66) {
+            pf = T.omega[a];
+            const float2 b = T.coef[a];
+            pm = (uint64_t)__float_as_uint(b.x) | ((uint64_t)__float_as_uint(b.y) << 32);
         }
-        float2 val = make_float2(0.f, 0.f);
-        if (live && ((u ^ s) & nv) == 0) {
-            const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)par64(z);
-            const int sign = (int)(par64(u & w) ^ par64(u & sv));
-            val = z8_scale(b, 2 * mu + 4 * sign + k0, e0);
-        }
-        // pairwise FP32 reduction over the block's terms
+    };
+    if (a0 < a1) prefetch(a0);
+    for (int64_t a = a0; a < a1; ++a) {
+        __syncthreads();                    // previous term's table no longer in use
+        if (tid < n) { sF[tid] = pf; sM[tid] = pm; }
+        if (tid == 64) { sc[0] = pf; sc[1] = pm; }
+        if (tid == 65) { sc[2] = pf; sc[3] = pm; }
+        if (tid == 66) {
+            const uint32_t om = (uint32_t)pf;
+            const float2 b = make_float2(__uint_as_float((uint32_t)pm), __uint_as_float((uint32_t)(pm >> 32)));
+            sc_live = ((om >> 3) & 1u) ? 0u : 1u;
+            const int e0 = __popcll(sc[2]) + (int)(om >> 8);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            val.x += __shfl_xor_sync(0xffffffffu, val.x, off);
-            val.y += __shfl_xor_sync(0xffffffffu, val.y, off);
+            for (int k = 0; k < 8; ++k) val8[k] = z8_scale(b, k + (int)(om & 7u), e0);
         }
-        if (lane == 0) red[warp][xi] = val;
+        __syncthreads();
+        if (a + 1 < a1) prefetch(a + 1);
+        for (int e = tid; e < NCH * 16; e += AMP_XT) {
+            const int c = e >> 4, q = e & 15;
+            uint64_t u = 0, w = 0, z = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int r = 4 * c + b;
+                if (((q >> b) & 1) && r < n) {
+                    const uint64_t Fr = sF[r];
+                    z ^= w & Fr;
+                    u ^= Fr;
+                    w ^= sM[r];
+                }
+            }
+            tab[c][q].u = u;
+            tab[c][q].w = w;
+            tab[c][q].z = z;
+        }
+        __syncthreads();
+        if (!sc_live) continue;             // zero term (uniform)
+        const uint64_t glo = sc[0], ghi = sc[1], v = sc[2], s = sc[3];
+        const uint64_t nv = ~v & T.nmask, sv = s & v;
+#pragma unroll
+        for (int k = 0; k < AMP_XP; ++k) {
+            const uint64_t x = xv[k];
+            uint64_t u = 0, w = 0, z = 0;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const AmpEntry& E = tab[c][(int)((x >> (4 * c)) & 15u)];
+                z ^= (w & E.u) ^ E.z;
+                u ^= E.u;
+                w ^= E.w;
+            }
+            if (((u ^ s) & nv) == 0) {
+                const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)par64(z);
+                const int sign = (int)par64(u & (w ^ sv));
+                acc[k].add(val8[(2 * mu + 4 * sign) & 7]);
+            }
+        }
     }
-    __syncthreads();
-    if (tid < nx) {
-        float2 acc = red[0][tid];
 #pragma unroll
-        for (int w2 = 1; w2 < AMP_TPB / 32; ++w2) {
-            acc.x += red[w2][tid].x;
-            acc.y += red[w2][tid].y;
-        }
-        partial[(x0 + tid) * n_tiles + tile] = acc;
+    for (int k = 0; k < AMP_XP; ++k) {
+        const int64_t i = xb + tid + k * AMP_XT;
+        if (i < batch) partial[i * n_tiles + tile] = acc[k].value();
     }
 }
 
@@ -108,28 +154,71 @@ __global__ void k_amp_reduce(const float2* __restrict__ partial, int64_t n_tiles
     }
 }
 
+struct AmpPlan {
+    int64_t xblocks, n_tiles, tt;
+};
+
+// Term tiles so that the grid covers every SM several times.
+AmpPlan amp_plan(const lrs_ctx* ctx, int64_t batch) {
+    AmpPlan P;
+    P.xblocks = (batch + AMP_XB - 1) / AMP_XB;
+    const int64_t target = (int64_t)ctx->sm_count * 8;
+    int64_t nt = (target + P.xblocks - 1) / P.xblocks;
+    const int64_t maxt = (ctx->cap + 31) / 32;
+    if (nt > maxt) nt = maxt;
+    if (nt < 1) nt = 1;
+    P.tt = (ctx->cap + nt - 1) / nt;
+    P.n_tiles = (ctx->cap + P.tt - 1) / P.tt;
+    return P;
+}
+
+template <int NCH>
+lrs_status launch_amp_t(lrs_ctx* ctx, const uint64_t* x, int64_t batch, float2* partial,
+                        const AmpPlan& P, cudaStream_t st) {
+    dim3 grid((unsigned)P.n_tiles, (unsigned)P.xblocks);
+    k_amplitude<NCH><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles);
+    LRS_LAUNCH_CHECK("amplitude kernel");
+    return LRS_OK;
+}
+
+lrs_status launch_amp_kernels(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
+                              float2* partial, const AmpPlan& P, cudaStream_t st) {
+    if (P.xblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "amplitude batch too large");
+    lrs_status rc;
+    switch ((ctx->n + 3) / 4) {
+        case 1: rc = launch_amp_t<1>(ctx, x, batch, partial, P, st); break;
+        case 2: rc = launch_amp_t<2>(ctx, x, batch, partial, P, st); break;
+        case 3: rc = launch_amp_t<3>(ctx, x, batch, partial, P, st); break;
+        case 4: rc = launch_amp_t<4>(ctx, x, batch, partial, P, st); break;
+        case 5: rc = launch_amp_t<5>(ctx, x, batch, partial, P, st); break;
+        case 6: rc = launch_amp_t<6>(ctx, x, batch, partial, P, st); break;
+        case 7: rc = launch_amp_t<7>(ctx, x, batch, partial, P, st); break;
+        case 8: rc = launch_amp_t<8>(ctx, x, batch, partial, P, st); break;
+        case 9: rc = launch_amp_t<9>(ctx, x, batch, partial, P, st); break;
+        case 10: rc = launch_amp_t<10>(ctx, x, batch, partial, P, st); break;
+        case 11: rc = launch_amp_t<11>(ctx, x, batch, partial, P, st); break;
+        case 12: rc = launch_amp_t<12>(ctx, x, batch, partial, P, st); break;
+        case 13: rc = launch_amp_t<13>(ctx, x, batch, partial, P, st); break;
+        case 14: rc = launch_amp_t<14>(ctx, x, batch, partial, P, st); break;
+        case 15: rc = launch_amp_t<15>(ctx, x, batch, partial, P, st); break;
+        default: rc = launch_amp_t<16>(ctx, x, batch, partial, P, st); break;
+    }
+    if (rc != LRS_OK) return rc;
+    k_amp_reduce<<<(unsigned)batch, 256, 0, st>>>(partial, P.n_tiles, batch, out);
+    LRS_LAUNCH_CHECK("amplitude reduce kernel");
+    return LRS_OK;
+}
+
 }  // namespace
 
 lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
                             cudaStream_t st) {
     if (batch == 0) return LRS_OK;
-    const int64_t n_tiles = ctx->cap / AMP_TPB;
+    const AmpPlan P = amp_plan(ctx, batch);
     void* scr = nullptr;
-    lrs_status rc = lrs_scratch(ctx, (size_t)batch * n_tiles * sizeof(float2), &scr);
+    lrs_status rc = lrs_scratch(ctx, (size_t)batch * P.n_tiles * sizeof(float2), &scr);
     if (rc != LRS_OK) return rc;
-    float2* partial = (float2*)scr;
-    const size_t smem = (size_t)2 * ctx->n * AMP_TPB * sizeof(uint64_t);
-    LRS_CUDA(cudaFuncSetAttribute(k_amplitude, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  2 * 64 * AMP_TPB * (int)sizeof(uint64_t)));
-    const int64_t xblocks = (batch + AMP_XB - 1) / AMP_XB;
-    if (xblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "amplitude batch too large (max %d)",
-                                         65535 * AMP_XB);
-    dim3 grid((unsigned)n_tiles, (unsigned)xblocks);
-    k_amplitude<<<grid, AMP_TPB, smem, st>>>(ctx->view(), x, batch, partial, n_tiles);
-    LRS_LAUNCH_CHECK("amplitude kernel");
-    k_amp_reduce<<<(unsigned)batch, 256, 0, st>>>(partial, n_tiles, batch, out);
-    LRS_LAUNCH_CHECK("amplitude reduce kernel");
-    return LRS_OK;
+    return launch_amp_kernels(ctx, x, batch, out, (float2*)scr, P, st);
 }
 
 // ---------------------------------------------------------------------------------
@@ -177,22 +266,11 @@ extern "C" lrs_status lrs_amplitude_noalloc(lrs_ctx* ctx, const uint64_t* x, int
     lrs_status rc = noalloc_address(ctx->device, &partial);   // first call on a device: set-up
     if (rc != LRS_OK) return rc;
     if (batch == 0) return LRS_OK;
-    const int64_t n_tiles = ctx->cap / AMP_TPB;
-    if ((uint64_t)batch * (uint64_t)n_tiles > (uint64_t)LRS_NOALLOC_PARTIALS)
+    const AmpPlan P = amp_plan(ctx, batch);
+    if ((uint64_t)batch * (uint64_t)P.n_tiles > (uint64_t)LRS_NOALLOC_PARTIALS)
         return lrs_fail(LRS_ERR_ARG,
-                        "lrs_amplitude_noalloc: batch * ceil(chi/128) = %lld exceeds the fixed "
-                        "buffer of %u partial sums; use a smaller batch or lrs_amplitude",
-                        (long long)(batch * n_tiles), LRS_NOALLOC_PARTIALS);
-    const int64_t xblocks = (batch + AMP_XB - 1) / AMP_XB;
-    if (xblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "amplitude batch too large");
-    const size_t smem = (size_t)2 * ctx->n * AMP_TPB * sizeof(uint64_t);
-    LRS_CUDA(cudaFuncSetAttribute(k_amplitude, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  2 * 64 * AMP_TPB * (int)sizeof(uint64_t)));
-    cudaStream_t st = (cudaStream_t)stream;
-    dim3 grid((unsigned)n_tiles, (unsigned)xblocks);
-    k_amplitude<<<grid, AMP_TPB, smem, st>>>(ctx->view(), x, batch, partial, n_tiles);
-    LRS_LAUNCH_CHECK("amplitude kernel (no-alloc)");
-    k_amp_reduce<<<(unsigned)batch, 256, 0, st>>>(partial, n_tiles, batch, out);
-    LRS_LAUNCH_CHECK("amplitude reduce kernel (no-alloc)");
-    return LRS_OK;
+                        "lrs_amplitude_noalloc: %lld partial sums (batch x term tiles) exceed the "
+                        "fixed buffer of %u; use a smaller batch or lrs_amplitude",
+                        (long long)(batch * P.n_tiles), LRS_NOALLOC_PARTIALS);
+    return launch_amp_kernels(ctx, x, batch, out, partial, P, (cudaStream_t)stream);
 }

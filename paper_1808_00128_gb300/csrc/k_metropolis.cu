@@ -82,22 +82,17 @@ __global__ void __launch_bounds__(MC_TPB) k_chains_init(TermsView T, const uint6
 }
 
 // One proposal: apply the pending accepted flip, then form the amplitude of y.
+// Rows F_j, M_j come straight from global memory (the [row][term] layout makes
+// them one coalesced 256-byte read per warp and they stay in L2); the only
+// per-(chain, term) HBM traffic is the 16-byte Q.
 __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C, ulonglong2* __restrict__ Q,
                                                           const int32_t* __restrict__ pend,
                                                           const int32_t* __restrict__ jprop,
                                                           float2* __restrict__ partial, int64_t n_tiles) {
-    extern __shared__ uint64_t smem[];
     __shared__ float2 red[MC_CG][MC_TPB / 32];
-    const int n = T.n;
     const int tid = threadIdx.x;
     const int64_t tile = blockIdx.x;
     const int64_t a = tile * MC_TPB + tid;
-    uint64_t* sF = smem + tid;
-    uint64_t* sM = smem + (int64_t)n * MC_TPB + tid;
-    for (int p = 0; p < n; ++p) {
-        sF[p * MC_TPB] = T.F[(int64_t)p * T.cap + a];
-        sM[p * MC_TPB] = T.M[(int64_t)p * T.cap + a];
-    }
     const uint64_t glo = T.glo[a], ghi = T.ghi[a], v = T.v[a], s = T.s[a];
     const uint32_t om = T.omega[a];
     const uint64_t nv = ~v & T.nmask, sv = s & v;
@@ -107,24 +102,39 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     const uint64_t umask = (1ull << 62) - 1;
     const int64_t c0 = (int64_t)blockIdx.y * MC_CG;
     const int nc = (int)(C - c0 < MC_CG ? C - c0 : MC_CG);
-    for (int ci = 0; ci < nc; ++ci) {
-        const int64_t c = c0 + ci;
-        const ulonglong2 q = Q[c * T.cap + a];
-        uint64_t u = q.x & umask, w = q.y;
-        uint32_t mu = (uint32_t)(q.x >> 62);
-        const int pj = pend[c];
-        if (pj >= 0) {   // commit the flip accepted at the previous step
-            const uint64_t Fp = sF[pj * MC_TPB];
-            mu = (mu + (uint32_t)(getb(glo, pj) | (getb(ghi, pj) << 1)) + 2u * par64(w & Fp)) & 3u;
-            u ^= Fp;
-            w ^= sM[pj * MC_TPB];
-            Q[c * T.cap + a] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
+    constexpr int U = 4;   // chains in flight per thread
+    for (int cb = 0; cb < nc; cb += U) {
+        ulonglong2 q[U];
+        int pj[U], jj[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int ci = cb + k < nc ? cb + k : nc - 1;
+            q[k] = Q[(c0 + ci) * T.cap + a];
+            pj[k] = pend[c0 + ci];
+            jj[k] = jprop[c0 + ci];
         }
-        const int j = jprop[c];
-        const uint64_t Fj = sF[j * MC_TPB];
-        const uint32_t muy = (mu + (uint32_t)(getb(glo, j) | (getb(ghi, j) << 1)) + 2u * par64(w & Fj)) & 3u;
-        const uint64_t uy = u ^ Fj, wy = w ^ sM[j * MC_TPB];
-        block_sum(term_value(uy, wy, muy, s, nv, sv, live, k0, e0, b), red, ci);
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int ci = cb + k;
+            if (ci >= nc) break;                       // uniform across the block
+            const int64_t c = c0 + ci;
+            uint64_t u = q[k].x & umask, w = q[k].y;
+            uint32_t mu = (uint32_t)(q[k].x >> 62);
+            if (pj[k] >= 0) {   // commit the flip accepted at the previous step (uniform per chain)
+                const int p = pj[k];
+                const uint64_t Fp = __ldg(&T.F[(int64_t)p * T.cap + a]);
+                mu = (mu + (uint32_t)(getb(glo, p) | (getb(ghi, p) << 1)) + 2u * par64(w & Fp)) & 3u;
+                u ^= Fp;
+                w ^= __ldg(&T.M[(int64_t)p * T.cap + a]);
+                Q[c * T.cap + a] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
+            }
+            const int j = jj[k];
+            const uint64_t Fj = __ldg(&T.F[(int64_t)j * T.cap + a]);
+            const uint64_t Mj = __ldg(&T.M[(int64_t)j * T.cap + a]);
+            const uint32_t muy =
+                (mu + (uint32_t)(getb(glo, j) | (getb(ghi, j) << 1)) + 2u * par64(w & Fj)) & 3u;
+            block_sum(term_value(u ^ Fj, w ^ Mj, muy, s, nv, sv, live, k0, e0, b), red, ci);
+        }
     }
     __syncthreads();
     if (tid < nc) {
@@ -220,7 +230,6 @@ static size_t mc_smem(const lrs_ctx* ctx) { return (size_t)2 * ctx->n * MC_TPB *
 static lrs_status mc_attrs() {
     const int mx = 2 * 64 * MC_TPB * (int)sizeof(uint64_t);
     LRS_CUDA(cudaFuncSetAttribute(k_chains_init, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     return LRS_OK;
 }
 
@@ -258,8 +267,8 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
     LRS_LAUNCH_CHECK("metropolis first kernel");
     dim3 grid((unsigned)n_tiles, (unsigned)((C + MC_CG - 1) / MC_CG));
     for (int64_t t = 0; t < steps; ++t) {
-        k_metro_propose<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop,
-                                                            partial, n_tiles);
+        k_metro_propose<<<grid, MC_TPB, 0, st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop, partial,
+                                                 n_tiles);
         LRS_LAUNCH_CHECK("metropolis propose kernel");
         k_metro_accept<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, seed, step0 + t, ctx->n, ctx->cx,
                                                      ctx->cp, ctx->pend, jprop,

@@ -2,12 +2,15 @@
 //
 // One thread per equatorial state A_l; a block walks a tile of terms, so each
 // thread keeps its own FP32 Kahan sum over terms and no cross-thread reduction
-// is needed inside the tile.  Per (A, term), with g_k = column k of G and
-// D = (A + J) mod 2 (J_cd = (M F^T)_cd off the diagonal):
-//   R_k   = D g_k^T  (XOR of the rows D_d, d in g_k, plus the diagonal parity)
-//   K_k   = XOR of rows G_c over c in R_k       -> row k of K = G^T (A+J) G mod 2
-//   K_kk  = sum_{c in g_k} (A_cc + gamma_c) + 2 #{c<d in g_k : D_cd = 1}  (mod 4)
-// for k in v only (Lemma (Inner Product)), then the exponential sum of
+// is needed inside the tile.  Per (A, term), with D = (A + J) mod 2
+// (J_cd = (M F^T)_cd off the diagonal, gamma on it) and K = G^T (A+J) G
+// (Lemma (Inner Product)):
+//   P_c  = D_c G   : XOR of rows G_d over d in D_c, by Four-Russians lookups in a
+//                    per-term shared table of G (4 rows per nibble of D_c)
+//   R_k  = column k of P (an in-place bit transpose), K_k = R_k G (same table)
+//   K_kk = sum_{c in g_k} (A_cc + gamma_c) + 2 #{c<d in g_k : D_cd = 1}  (mod 4),
+//          bit-sliced over k (g_k = column k of G)
+// then the exponential sum of
 // B = K|_v + 2 diag(s + sK) by pairwise elimination on a symmetric adjacency
 // (Lemma (Exponential Sum), lifted to Z2 with one extra variable, Eq. (Q)).
 // Everything up to the chi-sum is exact integer arithmetic.
@@ -82,18 +85,49 @@ __device__ __forceinline__ void eliminate(uint64_t* sK, uint64_t v, uint64_t odd
     im_s = zim ? 0 : (sim ? -1 : 1);
 }
 
+// Four-Russians product with the current term's G: XOR of rows G_d over the set
+// bits d of x, from the shared table tab[chunk][nibble] = XOR of the rows selected
+// by that nibble of x.  A 16-entry chunk table is 128 bytes, so a warp's lookups
+// into one chunk never conflict on shared-memory banks.
+template <int NCH>
+__device__ __forceinline__ uint64_t fr_rows(const uint64_t* __restrict__ tab, uint64_t x) {
+    uint64_t r = 0;
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) r ^= tab[ch * 16 + (int)((x >> (4 * ch)) & 15u)];
+    return r;
+}
+
+// In-place transpose of the NT x NT bit matrix W[k * NRM_TPB] (bit b of row k).
+template <int NT>
+__device__ __forceinline__ void transpose_rows(uint64_t* W) {
+    uint64_t m = (NT == 64) ? 0x00000000FFFFFFFFull : 0x000000000000FFFFull;
+#pragma unroll
+    for (int j = NT / 2; j != 0; j >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NT; k = (k + j + 1) & ~j) {
+            const uint64_t a = W[k * NRM_TPB], b = W[(k + j) * NRM_TPB];
+            const uint64_t t = ((a >> j) ^ b) & m;
+            W[(k + j) * NRM_TPB] = b ^ t;
+            W[k * NRM_TPB] = a ^ (t << j);
+        }
+        m ^= m << (j >> 1);
+    }
+}
+
+template <int NCH, int NT>
 __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64_t seed, int64_t tt,
                                                   float2* __restrict__ partial, int64_t n_tiles) {
     extern __shared__ uint64_t smem[];
-    __shared__ uint64_t tG[64], tGT[64], tJ[64], tF[64], tM[64];
+    __shared__ uint64_t tG[64], tJ[64], tF[64], tM[64];
     __shared__ NormTerm tS;
     __shared__ unsigned long long tz0;
     const int n = T.n;
     const uint64_t nmask = T.nmask;
     const int tid = threadIdx.x;
     const int64_t l = (int64_t)blockIdx.y * NRM_TPB + tid;
-    uint64_t* sA = smem + tid;                     // A_c at sA[c * NRM_TPB]
-    uint64_t* sK = smem + (int64_t)n * NRM_TPB + tid;
+    uint64_t* tab = smem;                                          // [NCH][16], shared
+    uint64_t* sA = smem + NCH * 16 + tid;                          // A_c at sA[c * NRM_TPB]
+    uint64_t* sW = smem + NCH * 16 + (int64_t)n * NRM_TPB + tid;   // NT work rows
 
     // ---- A_l in M_n from the counter RNG
     const uint64_t key = sm64_key(seed, (uint64_t)(l < L ? l : 0));
@@ -136,16 +170,21 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64
         }
         __syncthreads();
         if (tid < n) {
-            // column tid of G, row tid of J = (M F^T) off the diagonal, bit tid of z0 = s G^T
-            uint64_t col = 0, jrow = 0;
+            // row tid of J = (M F^T) off the diagonal; bit tid of z0 = s G^T
+            uint64_t jrow = 0;
             const uint64_t Mc = tM[tid];
-            for (int c = 0; c < n; ++c) {
-                col |= getb(tG[c], tid) << c;
+            for (int c = 0; c < n; ++c)
                 if (c != tid) jrow |= (uint64_t)par64(Mc & tF[c]) << c;
-            }
-            tGT[tid] = col;
             tJ[tid] = jrow;
             if (par64(tS.s & tG[tid])) atomicOr(&tz0, 1ull << tid);
+        }
+        for (int e = tid; e < NCH * 16; e += NRM_TPB) {    // Four-Russians table of G rows
+            const int ch = e >> 4, p = e & 15;
+            uint64_t r = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (((p >> b) & 1) && 4 * ch + b < n) r ^= tG[4 * ch + b];
+            tab[e] = r;
         }
         __syncthreads();
         const NormTerm S = tS;
@@ -153,52 +192,46 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64
         // diag(A + J) mod 4 as bit-planes: lo = adlo ^ glo, hi = adhi ^ ghi ^ (adlo & glo)
         const uint64_t dlo = adlo ^ S.glo;
         const uint64_t dhi = adhi ^ S.ghi ^ (adlo & S.glo);
-        uint64_t kdlo = 0, kdhi = 0;
+        const uint64_t z0 = tz0;
+        // P = D G row by row (D = (A + J) mod 2 with its diagonal), the pair
+        // parities sum_{c<d in g_k} D_cd for every k at once, and those of z0.
+        uint64_t pacc = 0, pz = 0, clo = 0, chi = 0;
+        for (int c = 0; c < n; ++c) {
+            const uint64_t Doff = sA[c * NRM_TPB] ^ tJ[c];
+            const uint64_t above = (c == 63) ? 0ull : (~0ull << (c + 1));
+            const uint64_t Gc = tG[c];
+            sW[c * NRM_TPB] = fr_rows<NCH>(tab, Doff ^ (getb(dlo, c) << c));
+            pacc ^= Gc & fr_rows<NCH>(tab, Doff & above);
+            if (getb(z0, c)) pz ^= Doff & z0 & above;
+            // sum over c in g_k of diag(A+J)_cc (mod 4), bit-sliced over k
+            const uint64_t m1 = 0ull - getb(dlo, c), m2 = 0ull - getb(dhi, c);
+            chi ^= clo & Gc & m1;
+            clo ^= Gc & m1;
+            chi ^= Gc & m2;
+        }
+        for (int c = n; c < NT; ++c) sW[c * NRM_TPB] = 0;
+        transpose_rows<NT>(sW);                // sW[k] = column k of P = D g_k
+        const uint64_t kdlo = clo;             // K_kk mod 2
+        const uint64_t kdhi = chi ^ pacc;      // bit 1 of K_kk
+        uint64_t lin = 0;
         for (uint64_t vr = S.v; vr; vr &= vr - 1) {
             const int k = ffs64(vr);
-            const uint64_t gk = tGT[k];
-            uint64_t R = 0, pacc = 0;
-            for (uint64_t gr = gk; gr;) {
-                const int d = ffs64(gr);
-                gr &= gr - 1;                       // gr = bits of g_k above d
-                const uint64_t D = sA[d * NRM_TPB] ^ tJ[d];
-                R ^= D;
-                pacc ^= D & gr;
-            }
-            R ^= gk & dlo;
-            uint64_t Kr = 0;
-            for (uint64_t rr = R; rr; rr &= rr - 1) Kr ^= tG[ffs64(rr)];
-            const uint32_t d4 = ((uint32_t)__popcll(gk & dlo) + 2u * (uint32_t)__popcll(gk & dhi) +
-                                 2u * par64(pacc)) & 3u;
-            sK[k * NRM_TPB] = Kr;
-            kdlo |= (uint64_t)(d4 & 1u) << k;
-            kdhi |= (uint64_t)(d4 >> 1) << k;
-        }
-        // s K s^T = q_{A+J}(z0) mod 4
-        const uint64_t z0 = tz0;
-        uint64_t pz = 0;
-        for (uint64_t zr = z0; zr;) {
-            const int c = ffs64(zr);
-            zr &= zr - 1;
-            pz ^= (sA[c * NRM_TPB] ^ tJ[c]) & zr;
+            const uint64_t Kr = fr_rows<NCH>(tab, sW[k * NRM_TPB]);   // row k of K (mod 2)
+            sW[k * NRM_TPB] = Kr;
+            lin |= (getb(S.s, k) ^ (uint64_t)par64(S.s & Kr)) << k;
         }
         const uint32_t sKs = ((uint32_t)__popcll(z0 & dlo) + 2u * (uint32_t)__popcll(z0 & dhi) +
                               2u * par64(pz)) & 3u;
         // B = K|_v + 2 diag(s + sK); lifted Z2 form: S_jk = B_jk + odd_j odd_k, X adjacent to odd
-        uint64_t lin = 0;
+        const uint64_t odd = kdlo & S.v;
+        const uint64_t Lb = (kdhi ^ lin) & S.v;
         for (uint64_t vr = S.v; vr; vr &= vr - 1) {
             const int k = ffs64(vr);
-            lin |= (getb(S.s, k) ^ (uint64_t)par64(S.s & sK[k * NRM_TPB])) << k;
-        }
-        const uint64_t odd = kdlo;                 // B_jj mod 2 = K_jj mod 2
-        const uint64_t Lb = (kdhi ^ lin) & S.v;    // bit 1 of B_jj
-        for (uint64_t vr = S.v; vr; vr &= vr - 1) {
-            const int k = ffs64(vr);
-            const uint64_t Kr = sK[k * NRM_TPB];
-            sK[k * NRM_TPB] = (Kr ^ (getb(odd, k) ? odd : 0ull)) & S.v & ~bit64(k);
+            const uint64_t Kr = sW[k * NRM_TPB];
+            sW[k * NRM_TPB] = (Kr ^ (getb(odd, k) ? odd : 0ull)) & S.v & ~bit64(k);
         }
         int re_s, im_s, e;
-        eliminate(sK, S.v, odd, Lb, re_s, im_s, e);
+        eliminate(sW, S.v, odd, Lb, re_s, im_s, e);
         if (re_s == 0 && im_s == 0) continue;
         // zeta = re_s + i im_s as sqrt2^{both} e^{i pi phz / 4}
         int phz;
@@ -242,24 +275,50 @@ __global__ void k_norm_reduce(const float2* __restrict__ partial, int64_t n_tile
 
 }  // namespace
 
+template <int NCH>
+static lrs_status launch_norm_t(lrs_ctx* ctx, int64_t L, uint64_t seed, int64_t tt, float2* partial,
+                                int64_t n_tiles, cudaStream_t st) {
+    constexpr int NT = NCH <= 8 ? 32 : 64;
+    const size_t smem = ((size_t)NCH * 16 + (size_t)(ctx->n + NT) * NRM_TPB) * sizeof(uint64_t);
+    LRS_CUDA(cudaFuncSetAttribute(k_norm<NCH, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
+    dim3 grid((unsigned)n_tiles, (unsigned)lblocks);
+    k_norm<NCH, NT><<<grid, NRM_TPB, smem, st>>>(ctx->view(), L, seed, tt, partial, n_tiles);
+    LRS_LAUNCH_CHECK("norm kernel");
+    return LRS_OK;
+}
+
 lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta,
                                 cudaStream_t st) {
     // tile of terms per block: keep the partial buffer at <= 2048 tiles per A
     int64_t tt = 32;
-    while (ctx->cap / tt > 2048) tt *= 2;
+    while ((ctx->cap + tt - 1) / tt > 2048) tt *= 2;
     const int64_t n_tiles = (ctx->cap + tt - 1) / tt;
     void* scr = nullptr;
     lrs_status rc = lrs_scratch(ctx, (size_t)L * n_tiles * sizeof(float2), &scr);
     if (rc != LRS_OK) return rc;
     float2* partial = (float2*)scr;
-    const size_t smem = (size_t)2 * ctx->n * NRM_TPB * sizeof(uint64_t);
-    LRS_CUDA(cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  2 * 64 * NRM_TPB * (int)sizeof(uint64_t)));
-    const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
-    if (lblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "L too large");
-    dim3 grid((unsigned)n_tiles, (unsigned)lblocks);
-    k_norm<<<grid, NRM_TPB, smem, st>>>(ctx->view(), L, seed, tt, partial, n_tiles);
-    LRS_LAUNCH_CHECK("norm kernel");
+    if ((L + NRM_TPB - 1) / NRM_TPB > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "L too large");
+    switch ((ctx->n + 3) / 4) {
+        case 1: rc = launch_norm_t<1>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 2: rc = launch_norm_t<2>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 3: rc = launch_norm_t<3>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 4: rc = launch_norm_t<4>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 5: rc = launch_norm_t<5>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 6: rc = launch_norm_t<6>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 7: rc = launch_norm_t<7>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 8: rc = launch_norm_t<8>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 9: rc = launch_norm_t<9>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 10: rc = launch_norm_t<10>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 11: rc = launch_norm_t<11>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 12: rc = launch_norm_t<12>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 13: rc = launch_norm_t<13>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 14: rc = launch_norm_t<14>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 15: rc = launch_norm_t<15>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        default: rc = launch_norm_t<16>(ctx, L, seed, tt, partial, n_tiles, st); break;
+    }
+    if (rc != LRS_OK) return rc;
     k_norm_reduce<<<(unsigned)L, 256, 0, st>>>(partial, n_tiles, L, eta);
     LRS_LAUNCH_CHECK("norm reduce kernel");
     return LRS_OK;

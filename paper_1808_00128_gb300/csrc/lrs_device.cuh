@@ -107,6 +107,42 @@ __device__ __forceinline__ uint32_t sq_entry(int vq, int d) {
     return tab[vq * 4 + d];
 }
 
+// Row pass of the Hadamard fan-out (proof of Prop. (prop:H)) followed by R[S_q]^a.
+//   R[CX_{q,i}], i in mA:  G[p,q] ^= G[p,i]; F[p,i] ^= F[p,q]; M[p,q] ^= M[p,i]
+//   R[CZ_{q,i}], i in m1:  M[p,q] ^= F[p,i]; M[p,i] ^= F[p,q]; gamma_p += 2 F[p,q] F[p,i]
+//   R[CX_{i,q}], i in mB:  G[p,i] ^= G[p,q]; F[p,q] ^= F[p,i]; M[p,i] ^= M[p,q]
+//   R[S_q] (a = 1):        M[p,q] ^= F[p,q]; gamma_p -= F[p,q]
+// MODE 1 assumes mB = 0, MODE 2 assumes mA = m1 = 0, MODE 0 is general.
+template <int MODE, class Rows>
+__device__ __forceinline__ void prop_h_rows(Rows& R, int n, int q, uint64_t mA, uint64_t m1,
+                                            uint64_t mB, uint64_t a, uint64_t& add2,
+                                            uint64_t& sub1) {
+    for (int p = 0; p < n; ++p) {
+        uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
+        const uint64_t fq = getb(Fp, q);
+        uint64_t Gn = Gp, Fn = Fp, Mn = Mp;
+        if (MODE != 2) {
+            const uint64_t f1 = par64(Fp & m1);
+            Gn ^= (uint64_t)par64(Gp & mA) << q;
+            Fn ^= mA & (0ull - fq);
+            Mn ^= ((uint64_t)par64((Mp & mA) ^ (Fp & m1)) << q) ^ (m1 & (0ull - fq));
+            add2 |= (fq & f1) << p;
+        }
+        if (MODE != 1) {
+            const uint64_t gq = getb(Gp, q), mq = getb(Mp, q);
+            Gn ^= mB & (0ull - gq);
+            Fn ^= (uint64_t)par64(Fp & mB) << q;
+            Mn ^= mB & (0ull - mq);
+        }
+        const uint64_t fs = a & getb(Fn, q);
+        Mn ^= fs << q;
+        sub1 |= fs << p;
+        R.G(p) = Gn;
+        R.F(p) = Fn;
+        R.M(p) = Mn;
+    }
+}
+
 // Prop. (prop:H): U_H(|t> + i^delta |u>) = sqrt2 e^{i pi k1/4} W_C W_H |s'> for t != u.
 // Applies U_C <- U_C W_C to every row (fused fan-out of right multiplications,
 // then R[S_q] when a = 1), updates v, s and adds k1 to the phase.
@@ -143,25 +179,16 @@ __device__ __forceinline__ void prop_h(Rows& R, TermRegs& T, int n, uint64_t t, 
     T.k += e >> 3;
 
     uint64_t add2 = 0, sub1 = 0;
-    for (int p = 0; p < n; ++p) {
-        uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
-        const uint64_t gq = getb(Gp, q), fq = getb(Fp, q), mq = getb(Mp, q);
-        const uint64_t f1 = par64(Fp & m1);
-        // R[CX_{q,i}], i in mA:  G[p,q] ^= G[p,i]; F[p,i] ^= F[p,q]; M[p,q] ^= M[p,i]
-        // R[CZ_{q,i}], i in m1:  M[p,q] ^= F[p,i]; M[p,i] ^= F[p,q]; gamma_p += 2 F[p,q] F[p,i]
-        // R[CX_{i,q}], i in mB:  G[p,i] ^= G[p,q]; F[p,q] ^= F[p,i]; M[p,i] ^= M[p,q]
-        const uint64_t Gn = Gp ^ ((uint64_t)par64(Gp & mA) << q) ^ (mB & (0ull - gq));
-        const uint64_t Fn = Fp ^ (mA & (0ull - fq)) ^ ((uint64_t)par64(Fp & mB) << q);
-        uint64_t Mn = Mp ^ ((uint64_t)par64((Mp & mA) ^ (Fp & m1)) << q) ^ (m1 & (0ull - fq)) ^
-                      (mB & (0ull - mq));
-        add2 |= (fq & f1) << p;
-        // R[S_q] when a = 1: M[p,q] ^= F[p,q]; gamma_p -= F[p,q]
-        const uint64_t fs = a & getb(Fn, q);
-        Mn ^= fs << q;
-        sub1 |= fs << p;
-        R.G(p) = Gn;
-        R.F(p) = Fn;
-        R.M(p) = Mn;
+    // The warp takes the cheapest row pass that covers all of its active terms:
+    // MODE 2 when no term has a V0 fan-out (only CX_{i,q}), MODE 1 when none has a
+    // V1-only fan-out, MODE 0 otherwise.
+    const unsigned am = __activemask();
+    if (__all_sync(am, (mA | m1) == 0)) {
+        prop_h_rows<2>(R, n, q, mA, m1, mB, a, add2, sub1);
+    } else if (__all_sync(am, mB == 0)) {
+        prop_h_rows<1>(R, n, q, mA, m1, mB, a, add2, sub1);
+    } else {
+        prop_h_rows<0>(R, n, q, mA, m1, mB, a, add2, sub1);
     }
     // gamma += 2 add2, then gamma -= sub1 (bit-plane Z4 arithmetic)
     T.ghi ^= add2;

@@ -201,8 +201,11 @@ extern "C" lrs_status lrs_create(int32_t device, int32_t n_qubits, lrs_ctx** out
     LRS_CUDA(cudaGetDeviceCount(&count));
     if (device < 0 || device >= count) return lrs_fail(LRS_ERR_ARG, "bad device %d", device);
     LRS_CUDA(cudaSetDevice(device));
+    int sms = 0;
+    LRS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     lrs_ctx* c = new lrs_ctx();
     c->device = device;
+    c->sm_count = sms;
     c->n = n_qubits;
     c->nmask = n_qubits == 64 ? ~0ull : ((1ull << n_qubits) - 1);
     *out = c;

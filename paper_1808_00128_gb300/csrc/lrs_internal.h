@@ -50,6 +50,7 @@ struct TermsView {
 
 struct lrs_ctx {
     int device = 0;
+    int sm_count = 0;
     int n = 0;
     uint64_t nmask = 0;
     int64_t chi = 0;

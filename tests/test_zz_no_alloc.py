@@ -38,6 +38,7 @@ def test_noalloc_matches_amplitude_twice():
     ref2 = sim.amplitude(y).cpu().numpy()
     np.testing.assert_allclose(out.cpu().numpy(), ref2, rtol=0, atol=float(amp_tol(np.zeros(1), n)[0]))
     with pytest.raises(lrstab.LrsError):
-        big = torch.zeros(4097, dtype=torch.int64, device="cuda:0")
-        sim.amplitude_noalloc(big, torch.empty((4097, 2), dtype=torch.float64, device="cuda:0"))
+        nb = (1 << 21) + 1                        # more partial sums than the fixed buffer holds
+        big = torch.zeros(nb, dtype=torch.int64, device="cuda:0")
+        sim.amplitude_noalloc(big, torch.empty((nb, 2), dtype=torch.float64, device="cuda:0"))
     sim.close()
