@@ -245,6 +245,59 @@ lrs_status lrs_metropolis_step(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64
                                uint64_t* x_out_dev, double* p_out_dev, uint64_t* trace_dev,
                                void* stream);
 
+/* ---- learned proposal (MADE network; the paper proposes single flips only) ----- */
+/* The paper's Metropolis chain (Sec. 4.2) uses single bit flips and notes that
+ * its mixing time is generally unknown.  These calls add an independent
+ * proposal y ~ q learned from chain samples: q(x) = prod_i q(x_i | x_<i), a
+ * masked autoencoder (MADE) n -> H -> H -> n with ReLU hidden layers and
+ * Bernoulli outputs; input degree i+1, hidden degree m(k) = (k mod (n-1)) + 1,
+ * masks W1[k,i]: m(k) >= i+1, W2[k2,k1]: m(k2) >= m(k1), W3[i,k]: i+1 > m(k).
+ * Products run on the tensor cores with BF16 operands (round-to-nearest-even
+ * copies of FP32 master weights, BF16 activations and backward signals) and
+ * FP32 accumulation; biases, logits, gradients and AdamW state are FP32.
+ * Parameters are packed as W1 [H][n], b1 [H], W2 [H][H], b2 [H], W3 [n][H],
+ * b3 [n] (row-major, FP32).                                                    */
+typedef struct lrs_mlp lrs_mlp;
+
+/* 2 <= n <= 64, hidden a multiple of 64 in 64..4096.  Parameters start at 0. */
+lrs_status lrs_mlp_create(int32_t device, int32_t n, int32_t hidden, lrs_mlp** out);
+lrs_status lrs_mlp_destroy(lrs_mlp* mlp);
+lrs_status lrs_mlp_info(const lrs_mlp* mlp, int32_t* n, int32_t* hidden, int64_t* n_params);
+/* Upload packed FP32 parameters (host, n_params floats); resets AdamW state. */
+lrs_status lrs_mlp_set_params(lrs_mlp* mlp, const float* params_host);
+/* Download packed parameters and/or the last gradients (host, may be NULL).
+ * Synchronises the device.                                                     */
+lrs_status lrs_mlp_get_params(lrs_mlp* mlp, float* params_host, float* grads_host);
+/* logits_dev [batch][n] (may be NULL) and log q(x) per row (may be NULL) for
+ * basis strings x_dev[batch].                                                  */
+lrs_status lrs_mlp_forward(lrs_mlp* mlp, const uint64_t* x_dev, int64_t batch, float* logits_dev,
+                           float* logq_dev, void* stream);
+/* Gradients of the mean negative log-likelihood over x_dev[batch] (kept in the
+ * network; read with lrs_mlp_get_params); *loss_dev = mean NLL (may be NULL). */
+lrs_status lrs_mlp_backward(lrs_mlp* mlp, const uint64_t* x_dev, int64_t batch, float* loss_dev,
+                            void* stream);
+/* lrs_mlp_backward followed by one AdamW step (decoupled weight decay wd,
+ * bias-corrected moments) on the masked gradients.                            */
+lrs_status lrs_mlp_train_step(lrs_mlp* mlp, const uint64_t* x_dev, int64_t batch, float lr,
+                              float beta1, float beta2, float eps, float wd, float* loss_dev,
+                              void* stream);
+/* count samples y ~ q, bit by bit in qubit order: bit i of sample k is
+ * [u < sigmoid(logit_i)] with u = uniform(seed, 2^40 + sample0 + k, i)
+ * (FP32 compare); logq_dev[k] = log q(y_k).                                   */
+lrs_status lrs_mlp_sample(lrs_mlp* mlp, int64_t count, uint64_t seed, int64_t sample0,
+                          uint64_t* y_dev, float* logq_dev, void* stream);
+
+/* Metropolis-Hastings with the learned independent proposal on the chains of
+ * lrs_chains_init: step t (global step0 + t) draws y_c ~ q (sample index
+ * t * n_chains + c), evaluates P(y) = |<y|psi>|^2 exactly by lrs_amplitude's
+ * kernels, and accepts with probability min(1, P(y) q(x) / (P(x) q(y))) (FP64;
+ * uniform(seed, c, t)); a chain at P(x) = 0 always accepts.  Outputs as
+ * lrs_metropolis_step; accepts_dev[c] (may be NULL) is incremented per accepted
+ * move.  A later lrs_metropolis_step first rebuilds the single-flip state.     */
+lrs_status lrs_metropolis_learned(lrs_ctx* ctx, lrs_mlp* mlp, int64_t steps, uint64_t seed,
+                                  int64_t step0, uint64_t* x_out_dev, double* p_out_dev,
+                                  uint64_t* trace_dev, int64_t* accepts_dev, void* stream);
+
 /* ---- export (checkpoint / bit-exact parity) ----------------------------------- */
 /* Copy local terms [first, first + count) (global index alpha0 + first ..) to host arrays (each may be NULL):
  *   F, G, M: count * n uint64, term-major (row p of term i at [i*n + p]);

@@ -215,6 +215,33 @@ __global__ void k_metro_accept(const float2* __restrict__ partial, int64_t n_til
     }
 }
 
+// Metropolis-Hastings with an independent learned proposal q: accept y with
+// probability min(1, P(y) q(x) / (P(x) q(y))), FP64; the uniform of step t of
+// chain c is uniform(seed, c, t).
+__global__ void k_mh_accept(const double* __restrict__ ampy, const uint64_t* __restrict__ y,
+                            const float* __restrict__ lqy, uint64_t seed, int64_t step, int64_t C,
+                            uint64_t* cx, double* cp, float* lqx, uint64_t* trace, int64_t* accepts) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const double py = ampy[2 * c] * ampy[2 * c] + ampy[2 * c + 1] * ampy[2 * c + 1];
+    const double px = cp[c];
+    bool acc;
+    if (px <= 0.0) {
+        acc = true;
+    } else {
+        const double ratio = (py / px) * exp((double)lqx[c] - (double)lqy[c]);
+        const double r = sm64_unit(sm64_at(sm64_key(seed, (uint64_t)c), (uint64_t)step));
+        acc = ratio >= 1.0 || r < ratio;
+    }
+    if (acc) {
+        cx[c] = y[c];
+        cp[c] = py;
+        lqx[c] = lqy[c];
+        if (accepts) accepts[c] += 1;
+    }
+    if (trace) trace[c] = cx[c];
+}
+
 __global__ void k_metro_out(int64_t C, const uint64_t* cx, const double* cp, uint64_t* x_out,
                             double* p_out) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,5 +304,61 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
     }
     k_metro_out<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->cx, ctx->cp, x_out, p_out);
     LRS_LAUNCH_CHECK("metropolis out kernel");
+    return LRS_OK;
+}
+
+lrs_status launch_metropolis_learned(lrs_ctx* ctx, lrs_mlp* mlp, int64_t steps, uint64_t seed, int64_t step0,
+                                     uint64_t* x_out, double* p_out, uint64_t* trace, int64_t* accepts,
+                                     cudaStream_t st) {
+    const int64_t C = ctx->n_chains;
+    if (C > ctx->mh_cap) {
+        cudaFree(ctx->ybuf); cudaFree(ctx->lqy); cudaFree(ctx->lqx); cudaFree(ctx->ampy);
+        ctx->ybuf = nullptr; ctx->lqy = nullptr; ctx->lqx = nullptr; ctx->ampy = nullptr;
+        ctx->mh_cap = 0;
+        LRS_CUDA(cudaMalloc(&ctx->ybuf, (size_t)C * sizeof(uint64_t)));
+        LRS_CUDA(cudaMalloc(&ctx->lqy, (size_t)C * sizeof(float)));
+        LRS_CUDA(cudaMalloc(&ctx->lqx, (size_t)C * sizeof(float)));
+        LRS_CUDA(cudaMalloc(&ctx->ampy, (size_t)C * 2 * sizeof(double)));
+        ctx->mh_cap = C;
+    }
+    // log q of the current states under the current network
+    lrs_status rc = lrs_mlp_forward(mlp, ctx->cx, C, nullptr, ctx->lqx, st);
+    if (rc != LRS_OK) return rc;
+    for (int64_t t = 0; t < steps; ++t) {
+        const int64_t step = step0 + t;
+        rc = lrs_mlp_sample(mlp, C, seed, step * C, ctx->ybuf, ctx->lqy, st);
+        if (rc != LRS_OK) return rc;
+        rc = launch_amplitude(ctx, ctx->ybuf, C, ctx->ampy, st);
+        if (rc != LRS_OK) return rc;
+        k_mh_accept<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(ctx->ampy, ctx->ybuf, ctx->lqy, seed, step, C,
+                                                                  ctx->cx, ctx->cp, ctx->lqx,
+                                                                  trace ? trace + t * C : nullptr, accepts);
+        LRS_LAUNCH_CHECK("learned MH accept kernel");
+    }
+    ctx->q_stale = true;
+    k_metro_out<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->cx, ctx->cp, x_out, p_out);
+    LRS_LAUNCH_CHECK("metropolis out kernel");
+    return LRS_OK;
+}
+
+// Rebuild Q for the chains' current strings (after learned moves).
+lrs_status launch_chains_refresh(lrs_ctx* ctx, cudaStream_t st) {
+    void* scr = nullptr;
+    const int64_t C = ctx->n_chains;
+    // copy cx aside: chains_init reads x and writes cx
+    lrs_status rc = lrs_scratch(ctx, (size_t)C * (ctx->cap / MC_TPB) * sizeof(float2) + (size_t)C * 8 + 512, &scr);
+    if (rc != LRS_OK) return rc;
+    uint64_t* xcopy = (uint64_t*)((char*)scr + (((size_t)C * (ctx->cap / MC_TPB) * sizeof(float2) + 255) & ~(size_t)255));
+    LRS_CUDA(cudaMemcpyAsync(xcopy, ctx->cx, (size_t)C * 8, cudaMemcpyDeviceToDevice, st));
+    const int64_t n_tiles = ctx->cap / MC_TPB;
+    rc = mc_attrs();
+    if (rc != LRS_OK) return rc;
+    float2* partial = (float2*)scr;
+    dim3 grid((unsigned)n_tiles, (unsigned)((C + MC_CG - 1) / MC_CG));
+    k_chains_init<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), xcopy, C, ctx->Q, partial, n_tiles);
+    LRS_LAUNCH_CHECK("chains refresh kernel");
+    k_chains_set<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, xcopy, ctx->nmask, ctx->cx, ctx->cp, ctx->pend);
+    LRS_LAUNCH_CHECK("chains refresh set kernel");
+    ctx->q_stale = false;
     return LRS_OK;
 }

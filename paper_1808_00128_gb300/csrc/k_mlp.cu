@@ -1,0 +1,661 @@
+// Learned Metropolis-Hastings proposal: a MADE autoregressive Bernoulli network
+// n -> H -> H -> n (ReLU), BF16 operands with FP32 accumulation on the tensor
+// cores, trained by AdamW on chain samples, sampled bit by bit.
+//
+// Precision: FP32 master weights; the GEMMs read BF16 (round-to-nearest-even)
+// copies of the masked weights and BF16 activations H1, H2 and backward signals
+// dZ3, dZ2, dZ1; accumulation, biases, logits and gradients are FP32.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "lrs_device.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+struct lrs_mlp {
+    int device = 0;
+    int n = 0, NP = 64, H = 0;
+    // FP32 master parameters and AdamW moments (device)
+    float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *W3 = nullptr, *b3 = nullptr;
+    float *mW = nullptr, *vW = nullptr;   // moments for all parameters, packed
+    float *grad = nullptr;                // gradients, packed like the parameters
+    float *mask = nullptr;                // MADE masks, packed like the weights (1 for biases)
+    int64_t n_params = 0;
+    int64_t off[6] = {0};                 // offsets of W1 b1 W2 b2 W3 b3 in the packed arrays
+    int64_t step = 0;
+    // BF16 masked copies used by the GEMMs
+    bf16 *W1b = nullptr;   // [H][NP]
+    bf16 *W2b = nullptr;   // [H][H]
+    bf16 *W3b = nullptr;   // [NP][H]   (rows >= n are zero)
+    bf16 *W2t = nullptr;   // [H][H]    W2b transposed
+    bf16 *W3t = nullptr;   // [H][NP]   W3b transposed
+    // activations / workspace (grown on demand)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// mma.sync BF16 GEMM: C[M x N] = A[M x K] . B[N x K]^T, both operands K-contiguous,
+// K a multiple of 32, FP32 accumulation, fused epilogue.
+// ------------------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* smem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(s));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t b0,
+                                         const uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(128) k_gemm_tn(const bf16* __restrict__ A, int lda,
+                                                 const bf16* __restrict__ B, int ldb, int M, int N,
+                                                 int K, Epi epi) {
+    __shared__ __align__(16) bf16 sA[2][GBM][GBK + GPAD];
+    __shared__ __align__(16) bf16 sB[2][GBN][GBK + GPAD];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+    auto load = [&](int stage, int k0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int chunk = tid + i * 128;
+            const int r = chunk >> 2, c = (chunk & 3) * 8;
+            const int gm = m0 + r, gn = n0 + r;
+            cp_async16(&sA[stage][r][c], A + (size_t)(gm < M ? gm : M - 1) * lda + k0 + c, gm < M ? 16 : 0);
+            cp_async16(&sB[stage][r][c], B + (size_t)(gn < N ? gn : N - 1) * ldb + k0 + c, gn < N ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+    const int nk = K / GBK;
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        if (kt + 1 < nk) {
+            load((kt + 1) & 1, (kt + 1) * GBK);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int st = kt & 1;
+#pragma unroll
+        for (int kk = 0; kk < GBK; kk += 16) {
+            uint32_t af[2][4], bq[2][4];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int r = wm * 32 + mi * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+                const int c = kk + (lane >> 4) * 8;
+                ldmatrix_x4(af[mi], &sA[st][r][c]);
+            }
+#pragma unroll
+            for (int nj = 0; nj < 2; ++nj) {
+                const int r = wn * 32 + nj * 16 + (lane & 7) + (lane >> 4) * 8;
+                const int c = kk + ((lane >> 3) & 1) * 8;
+                ldmatrix_x4(bq[nj], &sB[st][r][c]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni)
+                    mma_bf16(acc[mi][ni], af[mi], bq[ni >> 1][(ni & 1) * 2], bq[ni >> 1][(ni & 1) * 2 + 1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int row = m0 + wm * 32 + mi * 16 + (lane >> 2) + 8 * (e >> 1);
+                const int col = n0 + wn * 32 + ni * 8 + (lane & 3) * 2 + (e & 1);
+                if (row < M && col < N) epi(row, col, acc[mi][ni][e]);
+            }
+}
+
+// ---- epilogues ------------------------------------------------------------------------
+struct EpiBiasReluBf16 {     // out = bf16(relu(acc + bias))
+    const float* bias;
+    bf16* out;
+    int ldo;
+    __device__ __forceinline__ void operator()(int r, int c, float v) const {
+        out[(size_t)r * ldo + c] = __float2bfloat16_rn(fmaxf(v + bias[c], 0.f));
+    }
+};
+struct EpiBiasF32 {          // out = acc + bias (columns >= nvalid get 0)
+    const float* bias;
+    float* out;
+    int ldo, nvalid;
+    __device__ __forceinline__ void operator()(int r, int c, float v) const {
+        out[(size_t)r * ldo + c] = c < nvalid ? v + bias[c] : 0.f;
+    }
+};
+struct EpiReluGrad {         // dZ = acc * [H > 0]; FP32 and BF16 copies
+    const bf16* act;
+    int lda;
+    float* out32;
+    bf16* out16;
+    int ldo;
+    __device__ __forceinline__ void operator()(int r, int c, float v) const {
+        const float d = __bfloat162float(act[(size_t)r * lda + c]) > 0.f ? v : 0.f;
+        out32[(size_t)r * ldo + c] = d;
+        out16[(size_t)r * ldo + c] = __float2bfloat16_rn(d);
+    }
+};
+struct EpiStoreF32 {
+    float* out;
+    int ldo;
+    __device__ __forceinline__ void operator()(int r, int c, float v) const { out[(size_t)r * ldo + c] = v; }
+};
+
+template <class Epi>
+lrs_status gemm_tn(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, Epi epi,
+                   cudaStream_t st) {
+    if (K % GBK != 0) return lrs_fail(LRS_ERR_ARG, "gemm: K=%d not a multiple of %d", K, GBK);
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+    k_gemm_tn<Epi><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, epi);
+    LRS_LAUNCH_CHECK("mma gemm");
+    return LRS_OK;
+}
+
+// ---- elementwise kernels ----------------------------------------------------------------
+// bitstrings -> X [Mp][NP] bf16 (rows >= M zero)
+__global__ void k_expand_bits(const uint64_t* __restrict__ xs, int M, int Mp, int n, int NP, bf16* X) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)Mp * NP) return;
+    const int r = (int)(i / NP), c = (int)(i % NP);
+    const float v = (r < M && c < n) ? (float)((xs[r] >> c) & 1ull) : 0.f;
+    X[i] = __float2bfloat16_rn(v);
+}
+
+// out[c][r] = in[r][c] for an R x C bf16 matrix
+__global__ void k_transpose_bf16(const bf16* __restrict__ in, int R, int C, bf16* __restrict__ out) {
+    __shared__ bf16 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        tile[j][threadIdx.x] = (r < R && c < C) ? in[(size_t)r * C + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int c = c0 + j, r = r0 + threadIdx.x;
+        if (c < C && r < R) out[(size_t)c * R + r] = tile[threadIdx.x][j];
+    }
+}
+
+// dZ3 = (sigmoid(z) - x) / M for valid rows / columns; per-row NLL
+__global__ void k_logit_grad(const float* __restrict__ logits, const uint64_t* __restrict__ xs, int M,
+                             int Mp, int n, int NP, float* d32, bf16* d16, float* nll_rows) {
+    const int r = blockIdx.x;
+    const int c = threadIdx.x;   // NP threads
+    float d = 0.f, l = 0.f;
+    if (r < M && c < n) {
+        const float z = logits[(size_t)r * NP + c];
+        const float x = (float)((xs[r] >> c) & 1ull);
+        const float s = 1.f / (1.f + expf(-z));
+        d = (s - x) / (float)M;
+        l = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))) - x * z;   // softplus(z) - x z
+    }
+    d32[(size_t)r * NP + c] = d;
+    d16[(size_t)r * NP + c] = __float2bfloat16_rn(d);
+    // row NLL
+    __shared__ float red[64];
+    red[c] = l;
+    __syncthreads();
+    for (int off = 32; off > 0; off >>= 1) {
+        if (c < off) red[c] += red[c + off];
+        __syncthreads();
+    }
+    if (c == 0 && nll_rows && r < M) nll_rows[r] = red[0];
+}
+
+// column sums of an FP32 [rows][ld] matrix -> out[c] (first `cols` columns)
+__global__ void k_colsum(const float* __restrict__ a, int rows, int ld, int cols, float* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += a[(size_t)r * ld + c];
+    out[c] = s;
+}
+
+__global__ void k_mean(const float* __restrict__ v, int m, float* out) {
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < m; i += 256) s += v[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0] / (float)m;
+}
+
+// copy a padded FP32 gradient block into the packed gradient array
+__global__ void k_copy_grad(const float* __restrict__ src, int rows, int cols, int lds, float* dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    dst[i] = src[(size_t)(i / cols) * lds + (i % cols)];
+}
+
+__global__ void k_apply_mask(float* __restrict__ g, const float* __restrict__ mask, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) g[i] *= mask[i];
+}
+
+// AdamW on the packed parameters (masked gradients)
+__global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, const float* __restrict__ mask,
+                        float* __restrict__ m, float* __restrict__ v, int64_t count, float lr, float b1,
+                        float b2, float eps, float wd, float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i] * mask[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    p[i] = p[i] - lr * (mh / (sqrtf(vh) + eps) + wd * p[i]);
+}
+
+// BF16 masked copies (and transposes) of the weights
+__global__ void k_refresh_bf16(const float* __restrict__ W1, const float* __restrict__ W2,
+                               const float* __restrict__ W3, const float* __restrict__ mask, int64_t o1,
+                               int64_t o2, int64_t o3, int n, int NP, int H, bf16* W1b, bf16* W2b,
+                               bf16* W3b, bf16* W2t, bf16* W3t) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n1 = (int64_t)H * NP, n2 = (int64_t)H * H, n3 = (int64_t)NP * H;
+    if (i < n1) {
+        const int k = (int)(i / NP), c = (int)(i % NP);
+        const float w = c < n ? W1[(int64_t)k * n + c] * mask[o1 + (int64_t)k * n + c] : 0.f;
+        W1b[i] = __float2bfloat16_rn(w);
+    } else if (i < n1 + n2) {
+        const int64_t j = i - n1;
+        const int k2 = (int)(j / H), k1 = (int)(j % H);
+        const bf16 w = __float2bfloat16_rn(W2[j] * mask[o2 + j]);
+        W2b[j] = w;
+        W2t[(int64_t)k1 * H + k2] = w;
+    } else if (i < n1 + n2 + n3) {
+        const int64_t j = i - n1 - n2;
+        const int r = (int)(j / H), k = (int)(j % H);
+        const float wv = r < n ? W3[(int64_t)r * H + k] * mask[o3 + (int64_t)r * H + k] : 0.f;
+        const bf16 w = __float2bfloat16_rn(wv);
+        W3b[j] = w;
+        W3t[(int64_t)k * NP + r] = w;
+    }
+}
+
+// log q(x) per row from logits: -sum_i softplus(z_i) - x_i z_i
+__global__ void k_logq(const float* __restrict__ logits, const uint64_t* __restrict__ xs, int M, int n,
+                       int NP, float* out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    float s = 0.f;
+    for (int c = 0; c < n; ++c) {
+        const float z = logits[(size_t)r * NP + c];
+        const float x = (float)((xs[r] >> c) & 1ull);
+        s += fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))) - x * z;
+    }
+    out[r] = -s;
+}
+
+// ---- autoregressive sampling ---------------------------------------------------------------
+// Z1 [M][H] fp32 starts at b1; H1 = bf16(relu(Z1)); y = 0, logq = 0.
+__global__ void k_sample_init(const float* __restrict__ b1, int Mp, int H, int count, float* Z1, bf16* H1,
+                              uint64_t* y, float* logq) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (int64_t)Mp * H) {
+        const float z = b1[i % H];
+        Z1[i] = z;
+        H1[i] = __float2bfloat16_rn(fmaxf(z, 0.f));
+    }
+    if (i < count) {
+        y[i] = 0ull;
+        logq[i] = 0.f;
+    }
+}
+
+// bit i of every sample: logit_i = H2[r] . W3b[i] + b3[i]; y_i = [u < sigmoid];
+// then Z1 += y_i W1b[:, i] and H1 = bf16(relu(Z1)).  One warp per row.
+__global__ void k_sample_bit(const bf16* __restrict__ H2, const bf16* __restrict__ W3b,
+                             const float* __restrict__ b3, const bf16* __restrict__ W1b, int M, int H,
+                             int NP, int i, uint64_t seed, int64_t sid0, float* Z1, bf16* H1, uint64_t* y,
+                             float* logq) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= M) return;
+    const int r = warp;
+    float s = 0.f;
+    for (int k = lane; k < H; k += 32)
+        s += __bfloat162float(H2[(size_t)r * H + k]) * __bfloat162float(W3b[(size_t)i * H + k]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const float z = s + b3[i];
+    const float p = 1.f / (1.f + expf(-z));
+    // uniform draw: rand64(seed, 2^40 + sample id, bit i)
+    const double u = sm64_unit(sm64_at(sm64_key(seed, (1ull << 40) + (uint64_t)(sid0 + r)), (uint64_t)i));
+    const int bit = (float)u < p ? 1 : 0;
+    if (lane == 0) {
+        if (bit) y[r] |= 1ull << i;
+        logq[r] += -(fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))) - (float)bit * z);
+    }
+    if (bit) {
+        for (int k = lane; k < H; k += 32) {
+            const float zz = Z1[(size_t)r * H + k] + __bfloat162float(W1b[(size_t)k * NP + i]);
+            Z1[(size_t)r * H + k] = zz;
+            H1[(size_t)r * H + k] = __float2bfloat16_rn(fmaxf(zz, 0.f));
+        }
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct MlpWS {   // workspace views for a batch of Mp rows
+    bf16 *X, *H1, *H2, *D3, *D2, *D1, *T1, *T2;
+    float *logits, *d3f, *d2f, *d1f, *gW, *nll, *Z1;
+    uint64_t* ybuf;
+    float* lqbuf;
+};
+
+lrs_status mlp_ws(lrs_mlp* m, int Mp, MlpWS& w) {
+    const size_t NP = m->NP, H = m->H;
+    size_t sz[] = {Mp * NP * 2, Mp * H * 2, Mp * H * 2, Mp * NP * 2, Mp * H * 2, Mp * H * 2,
+                   H * (size_t)Mp * 2, H * (size_t)Mp * 2, Mp * NP * 4, Mp * NP * 4, Mp * H * 4,
+                   Mp * H * 4, H * H * 4, (size_t)Mp * 4, Mp * H * 4, (size_t)Mp * 8, (size_t)Mp * 4};
+    size_t total = 0;
+    for (size_t s : sz) total += align256(s);
+    lrs_status rc = lrs_ensure(&m->ws, &m->ws_bytes, total);
+    if (rc != LRS_OK) return rc;
+    char* p = (char*)m->ws;
+    void* ptrs[17];
+    for (int i = 0; i < 17; ++i) {
+        ptrs[i] = p;
+        p += align256(sz[i]);
+    }
+    w.X = (bf16*)ptrs[0]; w.H1 = (bf16*)ptrs[1]; w.H2 = (bf16*)ptrs[2]; w.D3 = (bf16*)ptrs[3];
+    w.D2 = (bf16*)ptrs[4]; w.D1 = (bf16*)ptrs[5]; w.T1 = (bf16*)ptrs[6]; w.T2 = (bf16*)ptrs[7];
+    w.logits = (float*)ptrs[8]; w.d3f = (float*)ptrs[9]; w.d2f = (float*)ptrs[10]; w.d1f = (float*)ptrs[11];
+    w.gW = (float*)ptrs[12]; w.nll = (float*)ptrs[13]; w.Z1 = (float*)ptrs[14];
+    w.ybuf = (uint64_t*)ptrs[15]; w.lqbuf = (float*)ptrs[16];
+    return LRS_OK;
+}
+
+int pad64(int64_t M) { return (int)((M + 63) / 64 * 64); }
+
+lrs_status mlp_forward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, cudaStream_t st) {
+    const int Mp = pad64(M), NP = m->NP, H = m->H;
+    const int64_t tot = (int64_t)Mp * NP;
+    k_expand_bits<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(xs, M, Mp, m->n, NP, w.X);
+    LRS_LAUNCH_CHECK("expand bits");
+    lrs_status rc;
+    if ((rc = gemm_tn(w.X, NP, m->W1b, NP, Mp, H, NP, EpiBiasReluBf16{m->b1, w.H1, H}, st)) != LRS_OK) return rc;
+    if ((rc = gemm_tn(w.H1, H, m->W2b, H, Mp, H, H, EpiBiasReluBf16{m->b2, w.H2, H}, st)) != LRS_OK) return rc;
+    return gemm_tn(w.H2, H, m->W3b, H, Mp, NP, H, EpiBiasF32{m->b3, w.logits, NP, m->n}, st);
+}
+
+void transpose(const bf16* in, int R, int C, bf16* out, cudaStream_t st) {
+    dim3 grid((C + 31) / 32, (R + 31) / 32), blk(32, 8);
+    k_transpose_bf16<<<grid, blk, 0, st>>>(in, R, C, out);
+}
+
+// forward + backward into m->grad; loss (mean NLL) to loss_dev
+lrs_status mlp_backward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, float* loss_dev,
+                        cudaStream_t st) {
+    const int Mp = pad64(M), NP = m->NP, H = m->H, n = m->n;
+    lrs_status rc = mlp_forward(m, xs, M, w, st);
+    if (rc != LRS_OK) return rc;
+    k_logit_grad<<<Mp, NP, 0, st>>>(w.logits, xs, M, Mp, n, NP, w.d3f, w.D3, w.nll);
+    LRS_LAUNCH_CHECK("logit grad");
+    if (loss_dev) {
+        k_mean<<<1, 256, 0, st>>>(w.nll, M, loss_dev);
+        LRS_LAUNCH_CHECK("mean");
+    }
+    float* g = m->grad;
+    // dW3 = dZ3^T H2   [NP x H]
+    transpose(w.D3, Mp, NP, w.T1, st);
+    transpose(w.H2, Mp, H, w.T2, st);
+    if ((rc = gemm_tn(w.T1, Mp, w.T2, Mp, NP, H, Mp, EpiStoreF32{w.gW, H}, st)) != LRS_OK) return rc;
+    k_copy_grad<<<(n * H + 255) / 256, 256, 0, st>>>(w.gW, n, H, H, g + m->off[4]);
+    k_colsum<<<1, 64, 0, st>>>(w.d3f, Mp, NP, n, g + m->off[5]);
+    // dZ2 = (dZ3 W3) * [H2 > 0]
+    if ((rc = gemm_tn(w.D3, NP, m->W3t, NP, Mp, H, NP, EpiReluGrad{w.H2, H, w.d2f, w.D2, H}, st)) != LRS_OK)
+        return rc;
+    // dW2 = dZ2^T H1   [H x H]
+    transpose(w.D2, Mp, H, w.T1, st);
+    transpose(w.H1, Mp, H, w.T2, st);
+    if ((rc = gemm_tn(w.T1, Mp, w.T2, Mp, H, H, Mp, EpiStoreF32{g + m->off[2], H}, st)) != LRS_OK) return rc;
+    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(w.d2f, Mp, H, H, g + m->off[3]);
+    // dZ1 = (dZ2 W2) * [H1 > 0]
+    if ((rc = gemm_tn(w.D2, H, m->W2t, H, Mp, H, H, EpiReluGrad{w.H1, H, w.d1f, w.D1, H}, st)) != LRS_OK)
+        return rc;
+    // dW1 = dZ1^T X   [H x NP] -> packed [H x n]
+    transpose(w.D1, Mp, H, w.T1, st);
+    transpose(w.X, Mp, NP, w.T2, st);
+    if ((rc = gemm_tn(w.T1, Mp, w.T2, Mp, H, NP, Mp, EpiStoreF32{w.gW, NP}, st)) != LRS_OK) return rc;
+    k_copy_grad<<<(H * n + 255) / 256, 256, 0, st>>>(w.gW, H, n, NP, g + m->off[0]);
+    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(w.d1f, Mp, H, H, g + m->off[1]);
+    k_apply_mask<<<(unsigned)((m->n_params + 255) / 256), 256, 0, st>>>(g, m->mask, m->n_params);
+    LRS_LAUNCH_CHECK("backward");
+    return LRS_OK;
+}
+
+lrs_status refresh_bf16(lrs_mlp* m, cudaStream_t st) {
+    const int64_t tot = (int64_t)m->H * m->NP * 2 + (int64_t)m->H * m->H;
+    k_refresh_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+        m->W1, m->W2, m->W3, m->mask, m->off[0], m->off[2], m->off[4], m->n, m->NP, m->H, m->W1b, m->W2b,
+        m->W3b, m->W2t, m->W3t);
+    LRS_LAUNCH_CHECK("refresh bf16 weights");
+    return LRS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" lrs_status lrs_mlp_create(int32_t device, int32_t n, int32_t hidden, lrs_mlp** out) {
+    if (!out) return lrs_fail(LRS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 2 || n > 64) return lrs_fail(LRS_ERR_ARG, "MADE needs 2 <= n <= 64 (got %d)", n);
+    if (hidden < 64 || hidden > 4096 || hidden % 64) return lrs_fail(LRS_ERR_ARG, "hidden must be a multiple of 64 in 64..4096");
+    LRS_CUDA(cudaSetDevice(device));
+    lrs_mlp* m = new lrs_mlp();
+    m->device = device;
+    m->n = n;
+    m->H = hidden;
+    const int64_t H = hidden;
+    const int64_t sizes[6] = {H * n, H, H * H, H, (int64_t)n * H, n};
+    int64_t o = 0;
+    for (int i = 0; i < 6; ++i) {
+        m->off[i] = o;
+        o += sizes[i];
+    }
+    m->n_params = o;
+    const size_t pb = (size_t)o * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    float* params = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&params, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->mW, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->vW, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->grad, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->mask, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->W1b, (size_t)H * 64 * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&m->W2b, (size_t)H * H * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&m->W3b, (size_t)64 * H * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&m->W2t, (size_t)H * H * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&m->W3t, (size_t)H * 64 * 2);
+    if (e != cudaSuccess) {
+        delete m;
+        return lrs_cuda_check(e, "mlp storage");
+    }
+    m->W1 = params + m->off[0]; m->b1 = params + m->off[1]; m->W2 = params + m->off[2];
+    m->b2 = params + m->off[3]; m->W3 = params + m->off[4]; m->b3 = params + m->off[5];
+    // MADE masks: input degree i+1, hidden m(k) = (k mod (n-1)) + 1
+    std::vector<float> mk((size_t)o, 1.f);
+    for (int64_t k = 0; k < H; ++k) {
+        const int mk1 = (int)(k % (n - 1)) + 1;
+        for (int i = 0; i < n; ++i) mk[(size_t)(m->off[0] + k * n + i)] = mk1 >= i + 1 ? 1.f : 0.f;
+        for (int64_t k1 = 0; k1 < H; ++k1) {
+            const int m1 = (int)(k1 % (n - 1)) + 1;
+            mk[(size_t)(m->off[2] + k * H + k1)] = mk1 >= m1 ? 1.f : 0.f;
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int64_t k = 0; k < H; ++k) {
+            const int m2 = (int)(k % (n - 1)) + 1;
+            mk[(size_t)(m->off[4] + i * H + k)] = (i + 1) > m2 ? 1.f : 0.f;
+        }
+    LRS_CUDA(cudaMemcpy(m->mask, mk.data(), pb, cudaMemcpyHostToDevice));
+    LRS_CUDA(cudaMemset(params, 0, pb));
+    LRS_CUDA(cudaMemset(m->mW, 0, pb));
+    LRS_CUDA(cudaMemset(m->vW, 0, pb));
+    LRS_CUDA(cudaMemset(m->grad, 0, pb));
+    *out = m;
+    lrs_status rc = refresh_bf16(m, 0);
+    if (rc != LRS_OK) return rc;
+    LRS_CUDA(cudaDeviceSynchronize());
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_mlp_destroy(lrs_mlp* m) {
+    if (!m) return LRS_OK;
+    cudaSetDevice(m->device);
+    cudaDeviceSynchronize();
+    cudaFree(m->W1);   // start of the packed parameters
+    cudaFree(m->mW); cudaFree(m->vW); cudaFree(m->grad); cudaFree(m->mask);
+    cudaFree(m->W1b); cudaFree(m->W2b); cudaFree(m->W3b); cudaFree(m->W2t); cudaFree(m->W3t);
+    cudaFree(m->ws);
+    delete m;
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_mlp_set_params(lrs_mlp* m, const float* params_host) {
+    if (!m || !params_host) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    LRS_CUDA(cudaSetDevice(m->device));
+    const size_t pb = (size_t)m->n_params * sizeof(float);
+    LRS_CUDA(cudaMemcpy(m->W1, params_host, pb, cudaMemcpyHostToDevice));
+    LRS_CUDA(cudaMemset(m->mW, 0, pb));
+    LRS_CUDA(cudaMemset(m->vW, 0, pb));
+    m->step = 0;
+    lrs_status rc = refresh_bf16(m, 0);
+    if (rc != LRS_OK) return rc;
+    LRS_CUDA(cudaDeviceSynchronize());
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_mlp_get_params(lrs_mlp* m, float* params_host, float* grads_host) {
+    if (!m) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    LRS_CUDA(cudaSetDevice(m->device));
+    LRS_CUDA(cudaDeviceSynchronize());
+    const size_t pb = (size_t)m->n_params * sizeof(float);
+    if (params_host) LRS_CUDA(cudaMemcpy(params_host, m->W1, pb, cudaMemcpyDeviceToHost));
+    if (grads_host) LRS_CUDA(cudaMemcpy(grads_host, m->grad, pb, cudaMemcpyDeviceToHost));
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_mlp_info(const lrs_mlp* m, int32_t* n, int32_t* hidden, int64_t* n_params) {
+    if (!m) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (n) *n = m->n;
+    if (hidden) *hidden = m->H;
+    if (n_params) *n_params = m->n_params;
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_mlp_forward(lrs_mlp* m, const uint64_t* x, int64_t batch, float* logits,
+                                      float* logq, void* stream) {
+    if (!m || batch < 0 || (batch > 0 && !x)) return lrs_fail(LRS_ERR_ARG, "bad arguments");
+    if (batch == 0) return LRS_OK;
+    if (batch > (1 << 24)) return lrs_fail(LRS_ERR_ARG, "batch too large");
+    LRS_CUDA(cudaSetDevice(m->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    MlpWS w;
+    lrs_status rc = mlp_ws(m, pad64(batch), w);
+    if (rc != LRS_OK) return rc;
+    if ((rc = mlp_forward(m, x, (int)batch, w, st)) != LRS_OK) return rc;
+    if (logits)
+        LRS_CUDA(cudaMemcpy2DAsync(logits, (size_t)m->n * 4, w.logits, (size_t)m->NP * 4, (size_t)m->n * 4,
+                                   (size_t)batch, cudaMemcpyDeviceToDevice, st));
+    if (logq) {
+        k_logq<<<(unsigned)((batch + 127) / 128), 128, 0, st>>>(w.logits, x, (int)batch, m->n, m->NP, logq);
+        LRS_LAUNCH_CHECK("logq");
+    }
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_mlp_backward(lrs_mlp* m, const uint64_t* x, int64_t batch, float* loss,
+                                       void* stream) {
+    if (!m || batch < 1 || !x) return lrs_fail(LRS_ERR_ARG, "bad arguments");
+    if (batch > (1 << 24)) return lrs_fail(LRS_ERR_ARG, "batch too large");
+    LRS_CUDA(cudaSetDevice(m->device));
+    MlpWS w;
+    lrs_status rc = mlp_ws(m, pad64(batch), w);
+    if (rc != LRS_OK) return rc;
+    return mlp_backward(m, x, (int)batch, w, loss, (cudaStream_t)stream);
+}
+
+extern "C" lrs_status lrs_mlp_train_step(lrs_mlp* m, const uint64_t* x, int64_t batch, float lr,
+                                         float beta1, float beta2, float eps, float wd, float* loss,
+                                         void* stream) {
+    lrs_status rc = lrs_mlp_backward(m, x, batch, loss, stream);
+    if (rc != LRS_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    m->step += 1;
+    const float c1 = 1.f - powf(beta1, (float)m->step), c2 = 1.f - powf(beta2, (float)m->step);
+    k_adamw<<<(unsigned)((m->n_params + 255) / 256), 256, 0, st>>>(m->W1, m->grad, m->mask, m->mW, m->vW,
+                                                                    m->n_params, lr, beta1, beta2, eps, wd,
+                                                                    c1, c2);
+    LRS_LAUNCH_CHECK("adamw");
+    return refresh_bf16(m, st);
+}
+
+extern "C" lrs_status lrs_mlp_sample(lrs_mlp* m, int64_t count, uint64_t seed, int64_t sample0,
+                                     uint64_t* y, float* logq, void* stream) {
+    if (!m || count < 0 || (count > 0 && (!y || !logq))) return lrs_fail(LRS_ERR_ARG, "bad arguments");
+    if (count == 0) return LRS_OK;
+    if (count > (1 << 24)) return lrs_fail(LRS_ERR_ARG, "count too large");
+    LRS_CUDA(cudaSetDevice(m->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int M = (int)count, Mp = pad64(count), H = m->H;
+    MlpWS w;
+    lrs_status rc = mlp_ws(m, Mp, w);
+    if (rc != LRS_OK) return rc;
+    const int64_t tot = (int64_t)Mp * H;
+    k_sample_init<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m->b1, Mp, H, M, w.Z1, w.H1, y, logq);
+    LRS_LAUNCH_CHECK("sample init");
+    for (int i = 0; i < m->n; ++i) {
+        if ((rc = gemm_tn(w.H1, H, m->W2b, H, Mp, H, H, EpiBiasReluBf16{m->b2, w.H2, H}, st)) != LRS_OK) return rc;
+        k_sample_bit<<<(unsigned)((M * 32 + 127) / 128), 128, 0, st>>>(w.H2, m->W3b, m->b3, m->W1b, M, H, m->NP,
+                                                                     i, seed, sample0, w.Z1, w.H1, y, logq);
+        LRS_LAUNCH_CHECK("sample bit");
+    }
+    return LRS_OK;
+}

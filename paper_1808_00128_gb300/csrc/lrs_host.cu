@@ -190,6 +190,8 @@ static void free_chains(lrs_ctx* c) {
     cudaFree(c->Q); cudaFree(c->cx); cudaFree(c->cp); cudaFree(c->pend);
     c->Q = nullptr; c->cx = nullptr; c->cp = nullptr; c->pend = nullptr;
     c->Q_bytes = 0; c->chains_cap = 0; c->n_chains = 0;
+    cudaFree(c->ybuf); cudaFree(c->lqy); cudaFree(c->lqx); cudaFree(c->ampy);
+    c->ybuf = nullptr; c->lqy = nullptr; c->lqx = nullptr; c->ampy = nullptr; c->mh_cap = 0;
 }
 
 extern "C" lrs_status lrs_create(int32_t device, int32_t n_qubits, lrs_ctx** out) {
@@ -446,6 +448,7 @@ extern "C" lrs_status lrs_chains_init(lrs_ctx* c, int64_t n_chains, const uint64
         c->chains_cap = n_chains;
     }
     c->n_chains = n_chains;
+    c->q_stale = false;
     return launch_chains_init(c, x, as_stream(stream));
 }
 
@@ -455,7 +458,25 @@ extern "C" lrs_status lrs_metropolis_step(lrs_ctx* c, int64_t steps, uint64_t se
     if (c->n_chains < 1) return lrs_fail(LRS_ERR_STATE, "chains not initialised");
     if (steps < 0 || step0 < 0) return lrs_fail(LRS_ERR_ARG, "steps < 0");
     LRS_CUDA(cudaSetDevice(c->device));
+    if (c->q_stale) {
+        lrs_status rc = launch_chains_refresh(c, as_stream(stream));
+        if (rc != LRS_OK) return rc;
+    }
     return launch_metropolis(c, steps, seed, step0, x_out, p_out, trace, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_metropolis_learned(lrs_ctx* c, lrs_mlp* mlp, int64_t steps, uint64_t seed,
+                                             int64_t step0, uint64_t* x_out, double* p_out,
+                                             uint64_t* trace, int64_t* accepts, void* stream) {
+    if (!c || !mlp) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (c->n_chains < 1) return lrs_fail(LRS_ERR_STATE, "chains not initialised");
+    if (steps < 0 || step0 < 0) return lrs_fail(LRS_ERR_ARG, "steps < 0");
+    int32_t mn = 0;
+    lrs_mlp_info(mlp, &mn, nullptr, nullptr);
+    if (mn != c->n) return lrs_fail(LRS_ERR_ARG, "network width %d != n = %d", mn, c->n);
+    LRS_CUDA(cudaSetDevice(c->device));
+    return launch_metropolis_learned(c, mlp, steps, seed, step0, x_out, p_out, trace, accepts,
+                                     as_stream(stream));
 }
 
 extern "C" lrs_status lrs_export_terms(lrs_ctx* c, int64_t first, int64_t count, uint64_t* F,

@@ -89,6 +89,13 @@ struct lrs_ctx {
     double* cp = nullptr;           // [chain] P(x) (unnormalised)
     int32_t* pend = nullptr;        // [chain] pending accepted flip (-1 none)
     int64_t chains_cap = 0;
+    bool q_stale = false;           // x moved by learned proposals: Q must be rebuilt
+    // learned-proposal Metropolis-Hastings buffers
+    uint64_t* ybuf = nullptr;       // [chain] proposals
+    float* lqy = nullptr;           // [chain] log q(y)
+    float* lqx = nullptr;           // [chain] log q(x)
+    double* ampy = nullptr;         // [chain][2] <y|psi>
+    int64_t mh_cap = 0;
 
     TermsView view() const {
         TermsView t;
@@ -132,3 +139,7 @@ lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint6
 lrs_status launch_chains_init(lrs_ctx* ctx, const uint64_t* x, cudaStream_t st);
 lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t step0,
                              uint64_t* x_out, double* p_out, uint64_t* trace, cudaStream_t st);
+lrs_status launch_metropolis_learned(lrs_ctx* ctx, lrs_mlp* mlp, int64_t steps, uint64_t seed,
+                                     int64_t step0, uint64_t* x_out, double* p_out, uint64_t* trace,
+                                     int64_t* accepts, cudaStream_t st);
+lrs_status launch_chains_refresh(lrs_ctx* ctx, cudaStream_t st);

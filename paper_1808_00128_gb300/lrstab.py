@@ -34,7 +34,9 @@ COP_DT = np.dtype([("kind", "<i4"), ("q", "<i4", (3,)), ("theta", "<f8")], align
 EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", "lrs_init_terms",
             "lrs_apply_clifford", "lrs_amplitude", "lrs_norm_estimate", "lrs_sample_terms",
             "lrs_chains_init", "lrs_metropolis_step", "lrs_export_terms", "lrs_info",
-            "lrs_alu_probe", "lrs_amplitude_noalloc"]
+            "lrs_alu_probe", "lrs_amplitude_noalloc", "lrs_mlp_create", "lrs_mlp_destroy",
+            "lrs_mlp_info", "lrs_mlp_set_params", "lrs_mlp_get_params", "lrs_mlp_forward",
+            "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned"]
 
 
 class LrsError(RuntimeError):
@@ -72,6 +74,16 @@ def lib():
         "lrs_info": [vp, vp, vp, vp],
         "lrs_alu_probe": [i32, i64, vp],
         "lrs_amplitude_noalloc": [vp, vp, i64, vp, vp],
+        "lrs_mlp_create": [i32, i32, i32, vp],
+        "lrs_mlp_destroy": [vp],
+        "lrs_mlp_info": [vp, vp, vp, vp],
+        "lrs_mlp_set_params": [vp, vp],
+        "lrs_mlp_get_params": [vp, vp, vp],
+        "lrs_mlp_forward": [vp, vp, i64, vp, vp, vp],
+        "lrs_mlp_backward": [vp, vp, i64, vp, vp],
+        "lrs_mlp_train_step": [vp, vp, i64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, vp, vp],
+        "lrs_mlp_sample": [vp, i64, u64, i64, vp, vp, vp],
+        "lrs_metropolis_learned": [vp, vp, i64, u64, i64, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -266,3 +278,86 @@ class Simulator:
         _check(lib().lrs_export_terms(self._h, first, count, *[_ptr(out[k]) for k in
                                       ("F", "G", "M", "gamma", "v", "s", "omega", "coef", "choice")]))
         return out
+
+
+# ---- learned proposal ---------------------------------------------------------------------
+class MLP:
+    """MADE proposal network (lrs_mlp) on one GPU."""
+
+    def __init__(self, n: int, hidden: int = 512, device: int = 0):
+        self.n, self.hidden, self.device = n, hidden, device
+        h = C.c_void_p()
+        _check(lib().lrs_mlp_create(device, n, hidden, C.byref(h)))
+        self._h = h
+        npar = C.c_int64(0)
+        _check(lib().lrs_mlp_info(h, None, None, C.byref(npar)))
+        self.n_params = npar.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lrs_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, params: dict) -> np.ndarray:
+        return np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
+                               for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+    def unpack(self, flat: np.ndarray) -> dict:
+        n, H = self.n, self.hidden
+        shapes = dict(W1=(H, n), b1=(H,), W2=(H, H), b2=(H,), W3=(n, H), b3=(n,))
+        out, o = {}, 0
+        for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+            sz = int(np.prod(shapes[k]))
+            out[k] = flat[o:o + sz].reshape(shapes[k])
+            o += sz
+        return out
+
+    def set_params(self, params: dict):
+        flat = np.ascontiguousarray(self.pack(params))
+        _check(lib().lrs_mlp_set_params(self._h, _ptr(flat)))
+
+    def get_params(self):
+        p = np.zeros(self.n_params, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        _check(lib().lrs_mlp_get_params(self._h, _ptr(p), _ptr(g)))
+        return self.unpack(p), self.unpack(g)
+
+    def forward(self, x, stream=None):
+        import torch
+        logits = torch.empty((x.numel(), self.n), dtype=torch.float32, device=x.device)
+        logq = torch.empty(x.numel(), dtype=torch.float32, device=x.device)
+        _check(lib().lrs_mlp_forward(self._h, _ptr(x), x.numel(), _ptr(logits), _ptr(logq),
+                                     _stream(stream)))
+        return logits, logq
+
+    def backward(self, x, stream=None):
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(lib().lrs_mlp_backward(self._h, _ptr(x), x.numel(), _ptr(loss), _stream(stream)))
+        return loss
+
+    def train_step(self, x, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0, loss=None,
+                   stream=None):
+        _check(lib().lrs_mlp_train_step(self._h, _ptr(x), x.numel(), lr, beta1, beta2, eps, wd,
+                                        _ptr(loss), _stream(stream)))
+
+    def sample(self, count: int, seed: int, sample0: int = 0, stream=None):
+        import torch
+        y = torch.empty(count, dtype=torch.int64, device=f"cuda:{self.device}")
+        lq = torch.empty(count, dtype=torch.float32, device=f"cuda:{self.device}")
+        _check(lib().lrs_mlp_sample(self._h, count, seed & (2 ** 64 - 1), sample0, _ptr(y), _ptr(lq),
+                                    _stream(stream)))
+        return y, lq
+
+
+def metropolis_learned(sim: "Simulator", mlp: MLP, steps: int, seed: int, step0: int = 0,
+                       x_out=None, p_out=None, trace=None, accepts=None, stream=None):
+    _check(lib().lrs_metropolis_learned(sim._h, mlp._h, steps, seed & (2 ** 64 - 1), step0,
+                                        _ptr(x_out), _ptr(p_out), _ptr(trace), _ptr(accepts),
+                                        _stream(stream)))

@@ -1,0 +1,155 @@
+"""Parity of the learned proposal (MADE network on BF16 tensor cores) with the
+FP64 oracle that emulates the same BF16 rounding points, and of the learned
+Metropolis-Hastings chain with an oracle replay.  Gradient tolerance: relative
+Frobenius error <= 2e-3 per tensor."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import estimators as E
+from oracle import mlp as omlp
+from oracle import rng as orng
+from paper_1808_00128_gb300 import lrstab, workloads
+from tests._gpu import oracle_terms, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _x(n, count, seed):
+    return torch.from_numpy(workloads.random_bitstrings(n, count, seed).view(np.int64)).cuda()
+
+
+def _relfro(a, b):
+    return np.linalg.norm(np.asarray(a, float) - np.asarray(b, float)) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.parametrize("n,H,batch", [(10, 64, 100), (50, 512, 300), (64, 128, 64)])
+def test_forward_and_gradients(n, H, batch):
+    require_cuda()
+    params = omlp.init_params(n, H, seed=n + H)
+    net = lrstab.MLP(n, H)
+    net.set_params(params)
+    x = _x(n, batch, 5)
+    logits, logq = net.forward(x)
+    X = omlp.bits_matrix(x.cpu().numpy().view(np.uint64), n)
+    want, _ = omlp.forward(params, X)
+    assert _relfro(logits.cpu().numpy(), want) <= 2e-3
+    np.testing.assert_allclose(logq.cpu().numpy(), -omlp.nll(want, X), rtol=2e-3, atol=2e-3)
+    loss = net.backward(x).cpu().numpy()[0]
+    wl, wg = omlp.loss_and_grads(params, X)
+    assert loss == pytest.approx(wl, rel=1e-4)
+    _, grads = net.get_params()
+    for k in wg:
+        assert _relfro(grads[k], wg[k]) <= 2e-3, k
+        if k.startswith("W"):
+            M = dict(zip(("W1", "W2", "W3"), omlp.masks(n, H)))[k]
+            assert np.all(grads[k][M == 0] == 0)
+
+
+def test_adamw_training_tracks_oracle():
+    require_cuda()
+    n, H = 12, 64
+    params = omlp.init_params(n, H, seed=3)
+    net = lrstab.MLP(n, H)
+    net.set_params(params)
+    x = _x(n, 256, 9)
+    X = omlp.bits_matrix(x.cpu().numpy().view(np.uint64), n)
+    st = {}
+    p_or = params
+    for _ in range(5):
+        net.train_step(x, lr=1e-3)
+        _, g = omlp.loss_and_grads(p_or, X)
+        p_or = omlp.adamw(p_or, g, st, lr=1e-3)
+    got, _ = net.get_params()
+    for k in p_or:
+        assert _relfro(got[k], p_or[k]) <= 1e-2, k
+    lg = net.backward(x).cpu().numpy()[0]
+    lo, _ = omlp.loss_and_grads(p_or, X)
+    assert lg == pytest.approx(lo, rel=2e-3)
+
+
+@pytest.mark.parametrize("n,H", [(8, 64), (40, 256)])
+def test_sampling_matches_oracle(n, H):
+    require_cuda()
+    params = omlp.init_params(n, H, seed=11)
+    net = lrstab.MLP(n, H)
+    net.set_params(params)
+    count, seed, s0 = 200, 77, 1000
+    y, lq = net.sample(count, seed, s0)
+    y = y.cpu().numpy().view(np.uint64)
+    lq = lq.cpu().numpy()
+    U = np.array([[orng.uniform(seed, (1 << 40) + s0 + k, i) for i in range(n)] for k in range(count)])
+    Xo, lqo = omlp.sample(params, U)
+    Y = omlp.bits_matrix(y, n)
+    ties = 0
+    for k in range(count):
+        if not np.array_equal(Y[k], Xo[k]):
+            # the first differing bit must be a near tie between u and q(bit = 1 | prefix)
+            i = int(np.argmax(Y[k] != Xo[k]))
+            logits, _ = omlp.forward(params, Xo[k:k + 1])
+            p = 1 / (1 + np.exp(-logits[0, i]))
+            assert abs(U[k, i] - p) < 1e-3, (k, i, U[k, i], p)
+            ties += 1
+            continue
+        assert lq[k] == pytest.approx(lqo[k], abs=5e-3)
+    assert ties <= 3
+
+
+def test_learned_metropolis_replay():
+    """MH with the learned independent proposal, replayed by the oracle: same
+    proposals (up to sampler near-ties) and the same accept decisions."""
+    require_cuda()
+    cfg = workloads.config_tiny()
+    n, ops, chi = cfg["n"], cfg["ops"], cfg["chi"]
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, 0)
+    sim.init_terms(low, chi, mode="exact")
+    sim.apply_clifford(low.gates)
+    H = 64
+    params = omlp.init_params(n, H, seed=21)
+    net = lrstab.MLP(n, H)
+    net.set_params(params)
+    C, T, seed = 48, 12, 555
+    x0 = sim.sample_terms(C, seed=4)
+    sim.chains_init(x0)
+    trace = torch.empty((T, C), dtype=torch.int64, device="cuda:0")
+    acc = torch.zeros(C, dtype=torch.int64, device="cuda:0")
+    lrstab.metropolis_learned(sim, net, T, seed, trace=trace, accepts=acc)
+    trace = trace.cpu().numpy().view(np.uint64)
+    x0 = x0.cpu().numpy().view(np.uint64)
+    terms, coefs, _ = oracle_terms(n, ops, chi, "exact")
+    skipped = 0
+    for c in range(C):
+        x = int(x0[c])
+        px = E.probability(terms, coefs, x)
+        lqx = omlp.log_prob(params, omlp.bits_matrix([x], n))[0]
+        for t in range(T):
+            sid = t * C + c
+            U = np.array([[orng.uniform(seed, (1 << 40) + sid, i) for i in range(n)]])
+            Y, lqy = omlp.sample(params, U)
+            y = int(sum(int(b) << i for i, b in enumerate(Y[0])))
+            g = int(trace[t, c])
+            if g not in (x, y):
+                skipped += 1        # a sampler near tie changed the proposal: stop replaying
+                break
+            py = E.probability(terms, coefs, y)
+            if px <= 0:
+                want = True
+            else:
+                ratio = (py / px) * np.exp(lqx - lqy[0])
+                r = orng.uniform(seed, c, t)
+                want = ratio >= 1 or r < ratio
+                if abs(ratio - r) <= 1e-3 * max(ratio, 1e-300):
+                    want = (g == y)
+            if y == x:
+                want_state = x
+            else:
+                want_state = y if want else x
+            assert g == want_state, (c, t)
+            if g == y and y != x:
+                x, px, lqx = y, py, lqy[0]
+            elif y == x:
+                pass
+    assert skipped <= 3
+    assert int(acc.sum()) > 0
+    sim.close()
