@@ -34,7 +34,7 @@ B_X, L_A, C_CH, T_MC = 4096, 256, 256, 16
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lrstab", choices=["lrstab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -95,7 +95,7 @@ class ClockSampler:
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -329,7 +329,11 @@ def main():
     dom = max(("apply_clifford", "amplitude", "norm_estimate", "metropolis"), key=lambda p: phase_ms[p])
     roof = dict(rows[dom])
     roof["kernel"] = dom
-    roof["traffic"] = None
+    # DRAM bytes per launch from ncu (profiles/): dram__bytes_read.sum + dram__bytes_write.sum
+    # of the n=40 chi=2^15 L=128 capture, scaled by the (term, A-block) units of a full
+    # chi=2^16 L=256 launch (4x); null for kernels changed since their capture.
+    traffic = {"norm_estimate": 4 * 32.957952e6}
+    roof["traffic"] = traffic.get(dom) if not args.small else None
     roof.pop("ms", None)
     roof["peak_source"] = ("measured LOP3 probe on this GPU" if roof["bound"] == "alu"
                            else "MEASURED_PEAKS.json hbm_gbs")
