@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--impl", default="lrstab", choices=["lrstab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sampler-study", action="store_true")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: chi = 2^15 terms of the same decomposition, B = 2048, "
                          "L = 128, C = 128, T = 2 (for ncu captures; not a bench line)")
@@ -205,6 +206,135 @@ def run_reference(args):
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------------
+# learned proposal vs single-flip Metropolis (ESS/s at matched accuracy)
+# ---------------------------------------------------------------------------------
+def tau_int(series):
+    """Integrated autocorrelation time of a [T][C] series (chain-averaged
+    autocorrelation, Sokal's automatic window with c = 5)."""
+    import numpy as np
+    x = np.asarray(series, float)
+    x = x - x.mean(axis=0, keepdims=True)
+    T = x.shape[0]
+    var = (x * x).mean()
+    if var == 0:
+        return 1.0
+    f = np.fft.rfft(x, n=2 * T, axis=0)
+    ac = np.fft.irfft(f * np.conj(f), axis=0)[:T].mean(axis=1)
+    rho = ac / ac[0]
+    tau = 1.0
+    for w in range(1, T):
+        tau += 2.0 * rho[w]
+        if w >= 5.0 * tau:
+            break
+    return max(tau, 1.0)
+
+
+def sampler_study(local=0, n=20, chi=1 << 14, C=1024, T_plain=2000, T_learned=200, hidden=512,
+                  train_steps=1000, seed=0):
+    """Plain single-flip Metropolis vs Metropolis-Hastings with the learned MADE
+    proposal, on a QAOA Max-E3LIN2 circuit small enough (n=20) for the exact
+    distribution P of the sparsified state to be computed by the amplitude
+    kernel over all 2^n strings.  Returns ESS/s of both samplers and their
+    total-variation distance to P on the Hamming-weight and cost histograms."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    dev = torch.device(f"cuda:{local}")
+    ops, inst = workloads.qaoa_e3lin2_circuit(n, 4, 0.3, 0.2, workloads.SEED_BASE + 20 + seed)
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, local)
+    sim.init_terms(low, chi, mode="sparsify", seed=workloads.SEED_BASE + 21 + seed)
+    sim.apply_clifford(low.gates)
+    allx = torch.arange(1 << n, dtype=torch.int64, device=dev)
+    amp = sim.amplitude(allx).cpu().numpy()
+    P = amp[:, 0] ** 2 + amp[:, 1] ** 2
+    P /= P.sum()
+    xs = np.arange(1 << n)
+    bits = ((xs[:, None] >> np.arange(n)[None, :]) & 1)
+    hw = bits.sum(axis=1)
+    z = 1 - 2 * bits
+    cost = np.zeros(1 << n)
+    for (u, v, w), d in inst:
+        cost += 0.5 * d * z[:, u] * z[:, v] * z[:, w]
+    cbins = np.round(2 * cost).astype(int)
+    cbins -= cbins.min()
+
+    def tv(samples):
+        s = np.asarray(samples, np.int64).reshape(-1)
+        t1 = 0.5 * np.abs(np.bincount(hw[s], minlength=n + 1) / s.size
+                          - np.bincount(hw, weights=P, minlength=n + 1)).sum()
+        nb = cbins.max() + 1
+        t2 = 0.5 * np.abs(np.bincount(cbins[s], minlength=nb) / s.size
+                          - np.bincount(cbins, weights=P, minlength=nb)).sum()
+        return float(t1), float(t2)
+
+    x0 = sim.sample_terms(C, seed=7)
+    sim.chains_init(x0)
+    sim.metropolis(200, seed=11)                      # burn-in
+    trace = torch.empty((T_plain, C), dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sim.metropolis(T_plain, seed=11, step0=200, trace=trace)
+    e1.record()
+    e1.synchronize()
+    t_plain = e0.elapsed_time(e1) * 1e-3
+    tr = trace.cpu().numpy()
+    tau_p = tau_int(cost[tr])
+    ess_plain = C * T_plain / tau_p / t_plain
+    tv_plain = tv(tr)
+
+    # training data: every 10th state of the plain chains (chain samples of the method)
+    data = torch.from_numpy(tr[::10].reshape(-1).copy()).to(dev)
+    net = lrstab.MLP(n, hidden, local)
+    rng = np.random.default_rng(5)
+    lim1, lim2 = 1 / np.sqrt(n), 1 / np.sqrt(hidden)
+    net.set_params(dict(W1=rng.uniform(-lim1, lim1, (hidden, n)), b1=rng.uniform(-lim1, lim1, hidden),
+                        W2=rng.uniform(-lim2, lim2, (hidden, hidden)),
+                        b2=rng.uniform(-lim2, lim2, hidden), W3=rng.uniform(-lim2, lim2, (n, hidden)),
+                        b3=rng.uniform(-lim2, lim2, n)))
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    bs = 1024
+    perm = torch.randperm(data.numel(), device=dev, generator=torch.Generator(device=dev).manual_seed(3))
+    for it in range(train_steps):
+        lo = (it * bs) % (data.numel() - bs)
+        net.train_step(data[perm[lo:lo + bs]].contiguous(), lr=1e-3)
+    e3.record()
+    e3.synchronize()
+    t_train = e2.elapsed_time(e3) * 1e-3
+    loss = float(net.backward(data[: 8192].contiguous()).item())
+    entropy = float(-(P[P > 0] * np.log(P[P > 0])).sum())
+
+    sim.chains_init(x0)
+    lrstab.metropolis_learned(sim, net, 20, seed=13)   # burn-in
+    ltrace = torch.empty((T_learned, C), dtype=torch.int64, device=dev)
+    acc = torch.zeros(C, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    e0.record()
+    lrstab.metropolis_learned(sim, net, T_learned, seed=13, step0=20, trace=ltrace, accepts=acc)
+    e1.record()
+    e1.synchronize()
+    t_learned = e0.elapsed_time(e1) * 1e-3
+    lt = ltrace.cpu().numpy()
+    tau_l = tau_int(cost[lt])
+    ess_learned = C * T_learned / tau_l / t_learned
+    tv_learned = tv(lt)
+    sim.close()
+    net.close()
+    return {"workload": f"qaoa_e3lin2_n{n}_chi{chi}", "chains": C,
+            "observable": "E3LIN2 cost C(z)",
+            "plain": {"steps": T_plain, "seconds": t_plain, "tau_int": tau_p, "ess_per_s": ess_plain,
+                      "tv_hamming": tv_plain[0], "tv_cost": tv_plain[1]},
+            "learned": {"steps": T_learned, "seconds": t_learned, "tau_int": tau_l,
+                        "ess_per_s": ess_learned, "tv_hamming": tv_learned[0], "tv_cost": tv_learned[1],
+                        "acceptance": float(acc.sum().item()) / (C * T_learned),
+                        "train_seconds": t_train, "train_samples": int(data.numel()),
+                        "nll": loss, "entropy_of_P": entropy, "hidden": hidden},
+            "ess_ratio_learned_over_plain": ess_learned / ess_plain}
 
 
 # ---------------------------------------------------------------------------------
@@ -376,6 +506,9 @@ def main():
                          "times scaled to one full step",
                "seconds": round(time.perf_counter() - t0, 1)}
     sim.close()
+    ess = None
+    if rank == 0 and not args.small and not args.no_sampler_study:
+        ess = sampler_study(local)
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -385,7 +518,7 @@ def main():
                       "chains": C_CH, "metropolis_steps": T_MC, "l2": "flushed (256 MB write) "
                       "before every timed step", "parallelism": f"replicas x{world}"},
            "roofline": roof, "phases": rows, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
+           "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "ess": ess}
     print(json.dumps(out))
 
 
