@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sampler-study", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the QAOA n=50 and batching studies")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: chi = 2^15 terms of the same decomposition, B = 2048, "
                          "L = 128, C = 128, T = 2 (for ncu captures; not a bench line)")
@@ -338,6 +340,123 @@ def sampler_study(local=0, n=20, chi=1 << 14, C=1024, T_plain=2000, T_learned=20
 
 
 # ---------------------------------------------------------------------------------
+# QAOA n=50 at chi = 2^20 (gate updates, amplitudes, Metropolis) and batching of
+# 8 circuits of uneven chi in one persistent launch
+# ---------------------------------------------------------------------------------
+def _ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def qaoa_study(local=0, chi=1 << 20, B=4096, C=256, T=64, alu_peak=None, hbm_peak=6695.2):
+    """Config-4 shapes: n=50 Max-E3LIN2 QAOA (gamma 0.3, beta 0.2), chi = 2^20."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    cfg = workloads.config_qaoa(chi=chi)
+    n = cfg["n"]
+    low = lrstab.lower_circuit(n, cfg["ops"])
+    sim = lrstab.Simulator(n, local)
+    sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"])
+    ops_term = clifford_ops_per_term(n, low)
+    dev = torch.device(f"cuda:{local}")
+    x = torch.from_numpy(workloads.random_bitstrings(n, B, workloads.SEED_BASE + 41).view(np.int64)).to(dev)
+    out = torch.empty((B, 2), dtype=torch.float64, device=dev)
+    res = {"workload": f"qaoa_e3lin2_n50_chi{chi}", "n": n, "chi": chi, "gates": len(low.gates),
+           "slots": len(low.slots)}
+    # apply_clifford (re-init each rep; timed alone)
+    ts = []
+    for rep in range(3):
+        sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"])
+        a, b = _ev()
+        a.record()
+        sim.apply_clifford(low.gates)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    t_apply = min(ts) * 1e-3
+    ach = chi * ops_term / t_apply
+    res["apply_clifford"] = {"ms": t_apply * 1e3, "term_gates_per_s": chi * len(low.gates) / t_apply,
+                             "achieved_Tops": ach / 1e12, "frac": ach / alu_peak if alu_peak else None}
+    # amplitude
+    sim.amplitude(x, out=out)
+    ts = []
+    for rep in range(3):
+        a, b = _ev()
+        a.record()
+        sim.amplitude(x, out=out)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    t_amp = min(ts) * 1e-3
+    ach = chi * B * (8 * ((n + 3) // 4) + 16) / t_amp
+    res["amplitude"] = {"ms": t_amp * 1e3, "x_term_per_s": chi * B / t_amp, "achieved_Tops": ach / 1e12,
+                        "frac": ach / alu_peak if alu_peak else None, "batch": B}
+    # Metropolis (flip chains), graph-replayed steps
+    x0 = sim.sample_terms(C, seed=5)
+    sim.chains_init(x0)
+    sim.metropolis(T, seed=6)
+    torch.cuda.synchronize()
+    a, b = _ev()
+    a.record()
+    sim.metropolis(T, seed=6, step0=T)
+    b.record()
+    b.synchronize()
+    t_mc = a.elapsed_time(b) * 1e-3
+    byts = T * (chi * C * (16 + 16 * 0.5) + chi * 16 * n)
+    res["metropolis"] = {"ms_per_step": t_mc * 1e3 / T, "chain_term_steps_per_s": chi * C * T / t_mc,
+                         "achieved_GBs": byts / t_mc / 1e9, "frac": byts / t_mc / 1e9 / hbm_peak,
+                         "chains": C}
+    sim.close()
+    return res
+
+
+def batch_study(local=0, k=8, seed=0):
+    """8 QAOA n=50 circuits (seeds +i) with chi_i = 2^e_i, e_i uniform in 14..20:
+    term-gate throughput of one batched persistent launch vs one launch per circuit."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    rng = np.random.default_rng(workloads.SEED_BASE + 5 + seed)
+    exps = [int(e) for e in rng.integers(14, 21, size=k)]
+    sims, lows, work = [], [], 0
+    for i, e in enumerate(exps):
+        ops, _ = workloads.qaoa_e3lin2_circuit(50, 4, 0.3, 0.2, workloads.SEED_BASE + 4 + i)
+        low = lrstab.lower_circuit(50, ops)
+        s = lrstab.Simulator(50, local)
+        s.init_terms(low, 1 << e, mode="sparsify", seed=workloads.SEED_BASE + 14 + i)
+        sims.append(s)
+        lows.append(low)
+        work += (1 << e) * len(low.gates)
+
+    def reinit():
+        for i, (s, low) in enumerate(zip(sims, lows)):
+            s.init_terms(low, 1 << exps[i], mode="sparsify", seed=workloads.SEED_BASE + 14 + i)
+
+    res = {"chi": [1 << e for e in exps]}
+    for mode in ("per_circuit", "batched"):
+        ts = []
+        for rep in range(2):
+            reinit()
+            torch.cuda.synchronize()
+            a, b = _ev()
+            a.record()
+            if mode == "batched":
+                lrstab.apply_clifford_batch(sims, [l.gates for l in lows])
+            else:
+                for s, low in zip(sims, lows):
+                    s.apply_clifford(low.gates)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        res[mode] = {"ms": min(ts), "term_gates_per_s": work / (min(ts) * 1e-3)}
+    res["speedup"] = res["per_circuit"]["ms"] / res["batched"]["ms"]
+    for s in sims:
+        s.close()
+    return res
+
+
+# ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
 def main():
@@ -403,6 +522,11 @@ def main():
 
     for w in range(args.warmup):
         step(step_idx=w)
+    torch.cuda.synchronize()
+    from paper_1808_00128_gb300 import autotune
+    tuned = {k: v for k, (v, ms) in autotune.tune(sim, x=x_dev, L=L_A, chains=C_CH,
+                                                   cache_path=os.environ.get("LRS_TUNE_CACHE")).items()}
+    step(step_idx=args.warmup)
     torch.cuda.synchronize()
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
@@ -506,9 +630,12 @@ def main():
                          "times scaled to one full step",
                "seconds": round(time.perf_counter() - t0, 1)}
     sim.close()
-    ess = None
+    ess = qaoa = batch = None
     if rank == 0 and not args.small and not args.no_sampler_study:
         ess = sampler_study(local)
+    if rank == 0 and not args.small and not args.no_extra:
+        qaoa = qaoa_study(local, alu_peak=alu_measured, hbm_peak=hbm)
+        batch = batch_study(local)
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -516,9 +643,10 @@ def main():
            "vs_baseline": None, "dtype": "u64+f32", "data": "synthetic",
            "config": {"workload": cfg["name"], "n": n, "chi": chi, "batch": B_X, "L": L_A,
                       "chains": C_CH, "metropolis_steps": T_MC, "l2": "flushed (256 MB write) "
-                      "before every timed step", "parallelism": f"replicas x{world}"},
+                      "before every timed step", "parallelism": f"replicas x{world}", "tuned": tuned},
            "roofline": roof, "phases": rows, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "ess": ess}
+           "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "ess": ess,
+           "qaoa_n50": qaoa, "batch8": batch}
     print(json.dumps(out))
 
 

@@ -179,6 +179,15 @@ lrs_status lrs_init_terms(lrs_ctx* ctx, const lrs_slot* slots_host, int64_t n_sl
 lrs_status lrs_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates,
                               void* stream);
 
+/* Batched form of lrs_apply_clifford for several circuits (contexts on one
+ * device, e.g. decompositions of uneven chi): context i receives gate list i
+ * (copied before return).  All tiles of all circuits run in one persistent
+ * launch whose blocks take work from a shared counter.  Same rules and errors
+ * as lrs_apply_clifford, plus LRS_ERR_ARG for repeated contexts or contexts
+ * on different devices.                                                      */
+lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_gate* const* gates_host,
+                                    const int64_t* n_gates, int32_t count, void* stream);
+
 /* out_dev[2i], out_dev[2i+1] = Re, Im of <x_i|psi> = sum_alpha b_alpha
  * <x_i|phi_alpha> for i < batch (Eq. (amplitude1) per term).  Per-term values
  * are exact Z8 phases times powers of sqrt2 times b_alpha; the chi-sum is
@@ -196,9 +205,10 @@ lrs_status lrs_amplitude(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch, dou
  * a fixed 16 MiB array in the library's device memory (2^21 float2 entries),
  * present on every GPU that loads the library until the process exits.
  * Limit: batch * n_tiles <= 2^21 partial sums, where n_tiles, the number of
- * term tiles the kernel uses, is min(ceil(8 * SMs / ceil(batch / 512)),
- * ceil(chi_padded / 32)) (152 for batch 4096 on a 152-SM GPU); larger requests
- * return LRS_ERR_ARG.  Any batch above 2^21 is rejected.
+ * term tiles the kernel uses, is min(ceil(b * SMs / ceil(batch / 512)),
+ * ceil(chi_padded / 32)) with b = LRS_TUNE_AMP_BLOCKS_PER_SM (default 8: 152
+ * tiles for batch 4096 on a 152-SM GPU); larger requests return LRS_ERR_ARG.
+ * Any batch above 2^21 is rejected.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the one array and each call overwrites every entry it
@@ -319,6 +329,20 @@ lrs_status lrs_export_terms(lrs_ctx* ctx, int64_t first, int64_t count, uint64_t
  * logic operations per second to *ops_per_s (host).  Synchronises the device.
  * Used as the ALU roofline denominator next to the unit-count derivation.   */
 lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
+
+/* Launch-shape knobs of a context, chosen by timing (the package's autotuner);
+ * they change speed and the grouping of the FP32 partial sums, not the
+ * per-term exact values.  The paper has no counterpart.
+ *   LRS_TUNE_AMP_BLOCKS_PER_SM    amplitude grid target, blocks per SM (1..64, 8)
+ *   LRS_TUNE_NORM_MAX_TILES       norm estimate, maximum term tiles (1..2^20, 2048)
+ *   LRS_TUNE_MC_CHAINS_PER_BLOCK  Metropolis chains per block (1..64, 64)       */
+enum {
+    LRS_TUNE_AMP_BLOCKS_PER_SM = 0,
+    LRS_TUNE_NORM_MAX_TILES = 1,
+    LRS_TUNE_MC_CHAINS_PER_BLOCK = 2
+};
+lrs_status lrs_set_tuning(lrs_ctx* ctx, int32_t param, int64_t value);
+lrs_status lrs_get_tuning(const lrs_ctx* ctx, int32_t param, int64_t* value);
 
 /* Number of terms, qubits and slots of the context (any pointer may be NULL). */
 lrs_status lrs_info(const lrs_ctx* ctx, int64_t* chi, int32_t* n_qubits, int64_t* n_slots);

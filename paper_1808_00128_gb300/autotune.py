@@ -1,0 +1,84 @@
+"""Launch-shape autotuner for the C library.
+
+Times each candidate value of a context's launch knobs (lrs_set_tuning) on the
+caller's actual workload with CUDA events and keeps the fastest.  Choices are
+cached in a JSON file keyed by knob, register width n, padded term count and
+batch size, so a later run with the same shapes reuses them without timing.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+CANDIDATES = {
+    "amp_blocks_per_sm": [2, 4, 8, 16, 32],
+    "norm_max_tiles": [256, 512, 1024, 2048, 4096],
+    "mc_chains_per_block": [16, 32, 64],
+}
+
+
+def _time_ms(fn, reps: int = 3) -> float:
+    import torch
+    fn()                                   # warm-up (and any lazy set-up)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _load(path):
+    if path and os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def _save(path, cache):
+    if path:
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_path: str | None = None,
+         reps: int = 3) -> dict:
+    """Pick the fastest knob values for the given workload and set them on `sim`.
+
+    x: amplitude batch (CUDA int64 tensor); L: number of equatorial states for
+    norm estimation; chains: the chain count (chains must already be
+    initialised on `sim`).  Returns {knob: (value, ms)}.
+    """
+    import torch
+    cache = _load(cache_path)
+    chosen = {}
+    jobs = []
+    if x is not None:
+        out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
+        jobs.append(("amp_blocks_per_sm", x.numel(), lambda: sim.amplitude(x, out=out)))
+    if L:
+        eta = torch.empty(L, dtype=torch.float64, device=f"cuda:{sim.device}")
+        jobs.append(("norm_max_tiles", L, lambda: sim.norm_estimate(L, seed=1, eta=eta)))
+    if chains:
+        jobs.append(("mc_chains_per_block", chains, lambda: sim.metropolis(8, seed=1)))
+    for knob, batch, fn in jobs:
+        key = f"{knob}|n={sim.n}|chi={sim.chi}|batch={batch}"
+        if key in cache:
+            sim.set_tuning(knob, cache[key]["value"])
+            chosen[knob] = (cache[key]["value"], cache[key]["ms"])
+            continue
+        best = None
+        for v in CANDIDATES[knob]:
+            sim.set_tuning(knob, v)
+            ms = _time_ms(fn, reps)
+            if best is None or ms < best[1]:
+                best = (v, ms)
+        sim.set_tuning(knob, best[0])
+        cache[key] = {"value": best[0], "ms": best[1]}
+        chosen[knob] = best
+    _save(cache_path, cache)
+    return chosen

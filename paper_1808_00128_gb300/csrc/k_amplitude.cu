@@ -162,7 +162,7 @@ struct AmpPlan {
 AmpPlan amp_plan(const lrs_ctx* ctx, int64_t batch) {
     AmpPlan P;
     P.xblocks = (batch + AMP_XB - 1) / AMP_XB;
-    const int64_t target = (int64_t)ctx->sm_count * 8;
+    const int64_t target = (int64_t)ctx->sm_count * ctx->tune_amp_bps;
     int64_t nt = (target + P.xblocks - 1) / P.xblocks;
     const int64_t maxt = (ctx->cap + 31) / 32;
     if (nt > maxt) nt = maxt;

@@ -8,6 +8,8 @@
 // and contributes b <0|Q_y U_H|s> (Eq. (amplitude1)).  Q is written back only
 // for accepted moves, lazily, at the start of the next step.  The accept test
 // is done in FP64 per chain by a separate small kernel.
+#include <string.h>
+
 #include "lrs_device.cuh"
 
 namespace {
@@ -36,7 +38,8 @@ __device__ __forceinline__ float2 block_sum(float2 v, float2 (*red)[MC_TPB / 32]
 // Q from scratch for x_c, and the block partial of <x_c|psi>.
 __global__ void __launch_bounds__(MC_TPB) k_chains_init(TermsView T, const uint64_t* __restrict__ xs,
                                                         int64_t C, ulonglong2* __restrict__ Q,
-                                                        float2* __restrict__ partial, int64_t n_tiles) {
+                                                        float2* __restrict__ partial, int64_t n_tiles,
+                                                        int cg) {
     extern __shared__ uint64_t smem[];
     __shared__ float2 red[MC_CG][MC_TPB / 32];
     const int n = T.n;
@@ -55,8 +58,8 @@ __global__ void __launch_bounds__(MC_TPB) k_chains_init(TermsView T, const uint6
     const bool live = ((om >> 3) & 1u) == 0u;
     const int k0 = (int)(om & 7u), e0 = __popcll(v) + (int)(om >> 8);
     const float2 b = T.coef[a];
-    const int64_t c0 = (int64_t)blockIdx.y * MC_CG;
-    const int nc = (int)(C - c0 < MC_CG ? C - c0 : MC_CG);
+    const int64_t c0 = (int64_t)blockIdx.y * cg;
+    const int nc = (int)(C - c0 < cg ? C - c0 : cg);
     for (int ci = 0; ci < nc; ++ci) {
         const int64_t c = c0 + ci;
         const uint64_t x = xs[c] & T.nmask;   // bits >= n are ignored
@@ -88,7 +91,8 @@ __global__ void __launch_bounds__(MC_TPB) k_chains_init(TermsView T, const uint6
 __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C, ulonglong2* __restrict__ Q,
                                                           const int32_t* __restrict__ pend,
                                                           const int32_t* __restrict__ jprop,
-                                                          float2* __restrict__ partial, int64_t n_tiles) {
+                                                          float2* __restrict__ partial, int64_t n_tiles,
+                                                          int cg) {
     __shared__ float2 red[MC_CG][MC_TPB / 32];
     const int tid = threadIdx.x;
     const int64_t tile = blockIdx.x;
@@ -100,8 +104,8 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     const int k0 = (int)(om & 7u), e0 = __popcll(v) + (int)(om >> 8);
     const float2 b = T.coef[a];
     const uint64_t umask = (1ull << 62) - 1;
-    const int64_t c0 = (int64_t)blockIdx.y * MC_CG;
-    const int nc = (int)(C - c0 < MC_CG ? C - c0 : MC_CG);
+    const int64_t c0 = (int64_t)blockIdx.y * cg;
+    const int nc = (int)(C - c0 < cg ? C - c0 : cg);
     constexpr int U = 4;   // chains in flight per thread
     for (int cb = 0; cb < nc; cb += U) {
         ulonglong2 q[U];
@@ -182,17 +186,27 @@ __global__ void k_chains_set(const float2* __restrict__ partial, int64_t n_tiles
     }
 }
 
-__global__ void k_metro_first(int64_t C, uint64_t seed, int64_t step, int n, int32_t* jprop) {
+// Per-call parameters live in device memory so that a captured graph of steps
+// can be replayed: step t of a launch uses global step P->step0 + t.
+__global__ void k_mc_set(McParams* P, uint64_t seed, int64_t step0) {
+    P->seed = seed;
+    P->step0 = step0;
+}
+__global__ void k_mc_advance(McParams* P, int64_t by) { P->step0 += by; }
+
+__global__ void k_metro_first(int64_t C, const McParams* __restrict__ P, int n, int32_t* jprop) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < C) jprop[c] = draw_j(seed, c, step, n);
+    if (c < C) jprop[c] = draw_j(P->seed, c, P->step0, n);
 }
 
 // FP64 accept test (Sec. 4.2) and the proposal index of the next step.
-__global__ void k_metro_accept(const float2* __restrict__ partial, int64_t n_tiles, uint64_t seed,
-                               int64_t step, int n, uint64_t* cx, double* cp, int32_t* pend,
-                               int32_t* jprop, uint64_t* trace, int64_t C) {
+__global__ void k_metro_accept(const float2* __restrict__ partial, int64_t n_tiles,
+                               const McParams* __restrict__ P, int64_t t, int n, uint64_t* cx, double* cp,
+                               int32_t* pend, int32_t* jprop, uint64_t* trace, int64_t C) {
     const int64_t c = blockIdx.x;
     const double py = chain_reduce(partial, c, n_tiles);
+    const uint64_t seed = P->seed;
+    const int64_t step = P->step0 + t;
     if (threadIdx.x == 0) {
         const double px = cp[c];
         const int j = jprop[c];
@@ -269,12 +283,69 @@ lrs_status launch_chains_init(lrs_ctx* ctx, const uint64_t* x, cudaStream_t st) 
     rc = mc_attrs();
     if (rc != LRS_OK) return rc;
     float2* partial = (float2*)scr;
-    dim3 grid((unsigned)n_tiles, (unsigned)((C + MC_CG - 1) / MC_CG));
-    k_chains_init<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), x, C, ctx->Q, partial, n_tiles);
+    dim3 grid((unsigned)n_tiles, (unsigned)((C + ctx->tune_mc_cg - 1) / ctx->tune_mc_cg));
+    k_chains_init<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), x, C, ctx->Q, partial, n_tiles,
+                                                      (int)ctx->tune_mc_cg);
     LRS_LAUNCH_CHECK("chains_init kernel");
     k_chains_set<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, x, ctx->nmask, ctx->cx, ctx->cp,
                                               ctx->pend);
     LRS_LAUNCH_CHECK("chains_set kernel");
+    return LRS_OK;
+}
+
+// Enqueue steps t0 .. t0 + count - 1 (relative to P->step0) of the flip chains.
+static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2* partial, int32_t* jprop,
+                                uint64_t* trace, cudaStream_t st) {
+    const int64_t C = ctx->n_chains;
+    const int64_t n_tiles = ctx->cap / MC_TPB;
+    const int cg = (int)ctx->tune_mc_cg;
+    dim3 grid((unsigned)n_tiles, (unsigned)((C + cg - 1) / cg));
+    for (int64_t t = t0; t < t0 + count; ++t) {
+        k_metro_propose<<<grid, MC_TPB, 0, st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop, partial,
+                                                 n_tiles, cg);
+        LRS_LAUNCH_CHECK("metropolis propose kernel");
+        k_metro_accept<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, ctx->mc_par, t, ctx->n, ctx->cx,
+                                                     ctx->cp, ctx->pend, jprop,
+                                                     trace ? trace + t * C : nullptr, C);
+        LRS_LAUNCH_CHECK("metropolis accept kernel");
+    }
+    return LRS_OK;
+}
+
+// One CUDA graph holding LRS_MC_GRAPH_STEPS steps followed by step0 += steps;
+// rebuilt whenever the buffers it was captured with change.
+static lrs_status mc_graph(lrs_ctx* ctx, float2* partial, int32_t* jprop, cudaGraphExec_t* out) {
+    const void* key[6] = {partial, jprop, ctx->Q, ctx->F,
+                          (void*)(intptr_t)(ctx->n_chains * 128 + ctx->tune_mc_cg),
+                          (void*)(intptr_t)ctx->cap};
+    if (ctx->mc_exec && memcmp(key, ctx->mc_key, sizeof(key)) == 0) {
+        *out = (cudaGraphExec_t)ctx->mc_exec;
+        return LRS_OK;
+    }
+    if (ctx->mc_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->mc_exec);
+    ctx->mc_exec = nullptr;
+    if (!ctx->cap_stream) LRS_CUDA(cudaStreamCreateWithFlags((cudaStream_t*)&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = (cudaStream_t)ctx->cap_stream;
+    LRS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    lrs_status rc = enqueue_steps(ctx, 0, LRS_MC_GRAPH_STEPS, partial, jprop, nullptr, cs);
+    if (rc == LRS_OK) {
+        k_mc_advance<<<1, 1, 0, cs>>>(ctx->mc_par, LRS_MC_GRAPH_STEPS);
+        if (cudaGetLastError() != cudaSuccess) rc = lrs_fail(LRS_ERR_CUDA, "graph advance kernel");
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (rc != LRS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return lrs_cuda_check(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return lrs_cuda_check(e, "cudaGraphInstantiate");
+    ctx->mc_exec = ex;
+    memcpy(ctx->mc_key, key, sizeof(key));
+    *out = ex;
     return LRS_OK;
 }
 
@@ -288,20 +359,23 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
     if (rc != LRS_OK) return rc;
     rc = mc_attrs();
     if (rc != LRS_OK) return rc;
+    if (!ctx->mc_par) LRS_CUDA(cudaMalloc(&ctx->mc_par, sizeof(McParams)));
     float2* partial = (float2*)scr;
     int32_t* jprop = (int32_t*)((char*)scr + ((part_bytes + 255) & ~(size_t)255));
-    k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, seed, step0, ctx->n, jprop);
+    k_mc_set<<<1, 1, 0, st>>>(ctx->mc_par, seed, step0);
+    k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->mc_par, ctx->n, jprop);
     LRS_LAUNCH_CHECK("metropolis first kernel");
-    dim3 grid((unsigned)n_tiles, (unsigned)((C + MC_CG - 1) / MC_CG));
-    for (int64_t t = 0; t < steps; ++t) {
-        k_metro_propose<<<grid, MC_TPB, 0, st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop, partial,
-                                                 n_tiles);
-        LRS_LAUNCH_CHECK("metropolis propose kernel");
-        k_metro_accept<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, seed, step0 + t, ctx->n, ctx->cx,
-                                                     ctx->cp, ctx->pend, jprop,
-                                                     trace ? trace + t * C : nullptr, C);
-        LRS_LAUNCH_CHECK("metropolis accept kernel");
+    int64_t done = 0;
+    if (!trace && steps >= LRS_MC_GRAPH_STEPS) {
+        // replay a captured graph of LRS_MC_GRAPH_STEPS steps (one launch instead of 2 per step)
+        cudaGraphExec_t ex = nullptr;
+        rc = mc_graph(ctx, partial, jprop, &ex);
+        if (rc != LRS_OK) return rc;
+        for (; done + LRS_MC_GRAPH_STEPS <= steps; done += LRS_MC_GRAPH_STEPS)
+            LRS_CUDA(cudaGraphLaunch(ex, st));
     }
+    rc = enqueue_steps(ctx, trace ? 0 : 0, steps - done, partial, jprop, trace, st);
+    if (rc != LRS_OK) return rc;
     k_metro_out<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->cx, ctx->cp, x_out, p_out);
     LRS_LAUNCH_CHECK("metropolis out kernel");
     return LRS_OK;
@@ -354,8 +428,9 @@ lrs_status launch_chains_refresh(lrs_ctx* ctx, cudaStream_t st) {
     rc = mc_attrs();
     if (rc != LRS_OK) return rc;
     float2* partial = (float2*)scr;
-    dim3 grid((unsigned)n_tiles, (unsigned)((C + MC_CG - 1) / MC_CG));
-    k_chains_init<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), xcopy, C, ctx->Q, partial, n_tiles);
+    dim3 grid((unsigned)n_tiles, (unsigned)((C + ctx->tune_mc_cg - 1) / ctx->tune_mc_cg));
+    k_chains_init<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), xcopy, C, ctx->Q, partial, n_tiles,
+                                                      (int)ctx->tune_mc_cg);
     LRS_LAUNCH_CHECK("chains refresh kernel");
     k_chains_set<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, xcopy, ctx->nmask, ctx->cx, ctx->cp, ctx->pend);
     LRS_LAUNCH_CHECK("chains refresh set kernel");

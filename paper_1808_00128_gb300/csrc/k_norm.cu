@@ -293,7 +293,7 @@ lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* 
                                 cudaStream_t st) {
     // tile of terms per block: keep the partial buffer at <= 2048 tiles per A
     int64_t tt = 32;
-    while ((ctx->cap + tt - 1) / tt > 2048) tt *= 2;
+    while ((ctx->cap + tt - 1) / tt > ctx->tune_norm_tiles) tt *= 2;
     const int64_t n_tiles = (ctx->cap + tt - 1) / tt;
     void* scr = nullptr;
     lrs_status rc = lrs_scratch(ctx, (size_t)L * n_tiles * sizeof(float2), &scr);

@@ -1,5 +1,7 @@
 // Term initialisation (exact enumeration / sparsification) and the fused
 // Clifford-circuit kernel.
+#include <vector>
+
 #include "lrs_device.cuh"
 
 namespace {
@@ -71,11 +73,11 @@ struct SmemRows {
 };
 constexpr int APPLY_TPB = SmemRows::APPLY_TPB_STRIDE;
 
-__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford(TermsView T, const lrs_gate* __restrict__ gates,
-                                                              int64_t n_gates) {
-    extern __shared__ uint64_t smem[];
+// One tile of APPLY_TPB terms through the whole gate list.
+__device__ __forceinline__ void apply_tile(const TermsView& T, const lrs_gate* __restrict__ gates,
+                                           int64_t n_gates, int64_t tile, uint64_t* smem) {
     const int n = T.n;
-    const int64_t a = (int64_t)blockIdx.x * APPLY_TPB + threadIdx.x;  // cap % APPLY_TPB == 0
+    const int64_t a = tile * APPLY_TPB + threadIdx.x;   // cap % APPLY_TPB == 0
     SmemRows R{smem + threadIdx.x, n};
     for (int p = 0; p < n; ++p) {
         R.F(p) = T.F[(int64_t)p * T.cap + a];
@@ -105,6 +107,42 @@ __global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford(TermsView T, const
     }
     T.glo[a] = S.glo; T.ghi[a] = S.ghi; T.v[a] = S.v; T.s[a] = S.s;
     T.omega[a] = omega_pack(S.k, S.zero, S.h);
+}
+
+__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford(TermsView T, const lrs_gate* __restrict__ gates,
+                                                              int64_t n_gates) {
+    extern __shared__ uint64_t smem[];
+    apply_tile(T, gates, n_gates, blockIdx.x, smem);
+}
+
+// Several circuits of uneven chi in one persistent launch: blocks pull global
+// tile indices from an atomic counter; circuit c owns tiles [first[c], first[c+1]).
+struct ApplyItem {
+    TermsView T;
+    const lrs_gate* gates;
+    int64_t n_gates;
+    int64_t first_tile;
+};
+
+__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford_batch(const ApplyItem* __restrict__ items,
+                                                                    int count, int64_t total_tiles,
+                                                                    unsigned long long* counter) {
+    extern __shared__ uint64_t smem[];
+    __shared__ long long s_idx;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_idx = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t idx = s_idx;
+        if (idx >= total_tiles) break;
+        int lo = 0, hi = count - 1;          // last item with first_tile <= idx
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].first_tile <= idx) lo = mid; else hi = mid - 1;
+        }
+        const ApplyItem& it = items[lo];
+        apply_tile(it.T, it.gates, it.n_gates, idx - it.first_tile, smem);
+    }
 }
 
 // ---- sample x from single terms (Sec. 4.1, "Simulating measurements") --------------
@@ -155,5 +193,39 @@ lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint6
     k_sample_terms<<<(unsigned)((count + tpb - 1) / tpb), tpb, 0, st>>>(ctx->view(), count, seed, x,
                                                                         alpha);
     LRS_LAUNCH_CHECK("sample_terms kernel");
+    return LRS_OK;
+}
+
+lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cudaStream_t st,
+                                       void** dev_buf, size_t* dev_buf_bytes) {
+    std::vector<ApplyItem> items((size_t)count);
+    int64_t tiles = 0;
+    int nmax = 1;
+    for (int32_t i = 0; i < count; ++i) {
+        items[(size_t)i].T = ctxs[i]->view();
+        items[(size_t)i].gates = ctxs[i]->gates_dev;
+        items[(size_t)i].n_gates = ctxs[i]->batch_n_gates;
+        items[(size_t)i].first_tile = tiles;
+        tiles += ctxs[i]->cap / APPLY_TPB;
+        if (ctxs[i]->n > nmax) nmax = ctxs[i]->n;
+    }
+    const size_t bytes = 256 + items.size() * sizeof(ApplyItem);
+    lrs_status rc = lrs_ensure(dev_buf, dev_buf_bytes, bytes);
+    if (rc != LRS_OK) return rc;
+    unsigned long long* counter = (unsigned long long*)*dev_buf;
+    ApplyItem* ditems = (ApplyItem*)((char*)*dev_buf + 256);
+    LRS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    LRS_CUDA(cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(ApplyItem), cudaMemcpyHostToDevice, st));
+    LRS_CUDA(cudaStreamSynchronize(st));   // host item table may go out of scope
+    const size_t smem = (size_t)3 * nmax * APPLY_TPB * sizeof(uint64_t);
+    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  3 * 64 * APPLY_TPB * (int)sizeof(uint64_t)));
+    int per_sm = 0;
+    LRS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_clifford_batch, APPLY_TPB, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)ctxs[0]->sm_count * per_sm;
+    if (grid > tiles) grid = tiles;
+    k_apply_clifford_batch<<<(unsigned)grid, APPLY_TPB, smem, st>>>(ditems, count, tiles, counter);
+    LRS_LAUNCH_CHECK("batched apply_clifford kernel");
     return LRS_OK;
 }

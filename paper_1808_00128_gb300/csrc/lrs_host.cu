@@ -221,6 +221,10 @@ extern "C" lrs_status lrs_destroy(lrs_ctx* c) {
     free_terms(c);
     free_chains(c);
     cudaFree(c->slots_dev); cudaFree(c->kgates_dev); cudaFree(c->gates_dev); cudaFree(c->scratch);
+    cudaFree(c->mc_par);
+    cudaFree(c->batch_buf);
+    if (c->mc_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->mc_exec);
+    if (c->cap_stream) cudaStreamDestroy((cudaStream_t)c->cap_stream);
     delete c;
     return LRS_OK;
 }
@@ -388,6 +392,40 @@ extern "C" lrs_status lrs_apply_clifford(lrs_ctx* c, const lrs_gate* gates, int6
     return launch_apply_clifford(c, c->gates_dev, n_gates, st);
 }
 
+extern "C" lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_gate* const* gates,
+                                               const int64_t* n_gates, int32_t count, void* stream) {
+    if (!ctxs || !gates || !n_gates || count < 1) return lrs_fail(LRS_ERR_ARG, "bad batch arguments");
+    const int dev = ctxs[0] ? ctxs[0]->device : -1;
+    for (int32_t i = 0; i < count; ++i) {
+        lrs_ctx* c = ctxs[i];
+        if (!c) return lrs_fail(LRS_ERR_ARG, "ctx %d is NULL", i);
+        if (c->device != dev) return lrs_fail(LRS_ERR_ARG, "contexts on different devices");
+        if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "ctx %d has no terms", i);
+        for (int32_t j = 0; j < i; ++j)
+            if (ctxs[j] == c) return lrs_fail(LRS_ERR_ARG, "ctx %d repeated", i);
+        if (n_gates[i] < 0 || (n_gates[i] > 0 && !gates[i])) return lrs_fail(LRS_ERR_ARG, "bad gate array %d", i);
+        for (int64_t g = 0; g < n_gates[i]; ++g) {
+            lrs_status rc = check_gate(c, gates[i][g], c->n_slots, true, g, "gate");
+            if (rc != LRS_OK) return rc;
+        }
+    }
+    LRS_CUDA(cudaSetDevice(dev));
+    cudaStream_t st = as_stream(stream);
+    for (int32_t i = 0; i < count; ++i) {
+        lrs_ctx* c = ctxs[i];
+        size_t have = (size_t)c->gates_cap * sizeof(lrs_gate);
+        lrs_status rc = lrs_ensure((void**)&c->gates_dev, &have, (size_t)std::max<int64_t>(1, n_gates[i]) * sizeof(lrs_gate));
+        if (rc != LRS_OK) return rc;
+        c->gates_cap = (int64_t)(have / sizeof(lrs_gate));
+        if (n_gates[i] > 0)
+            LRS_CUDA(cudaMemcpyAsync(c->gates_dev, gates[i], (size_t)n_gates[i] * sizeof(lrs_gate),
+                                     cudaMemcpyHostToDevice, st));
+        c->batch_n_gates = n_gates[i];
+        c->n_chains = 0;
+    }
+    return launch_apply_clifford_batch(ctxs, count, st, &ctxs[0]->batch_buf, &ctxs[0]->batch_buf_bytes);
+}
+
 extern "C" lrs_status lrs_amplitude(lrs_ctx* c, const uint64_t* x, int64_t batch, double* out,
                                     void* stream) {
     if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
@@ -523,4 +561,34 @@ extern "C" lrs_status lrs_export_terms(lrs_ctx* c, int64_t first, int64_t count,
         }
     }
     return LRS_OK;
+}
+
+extern "C" lrs_status lrs_set_tuning(lrs_ctx* c, int32_t param, int64_t value) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    switch (param) {
+        case LRS_TUNE_AMP_BLOCKS_PER_SM:
+            if (value < 1 || value > 64) return lrs_fail(LRS_ERR_ARG, "amp blocks per SM in 1..64");
+            c->tune_amp_bps = value;
+            return LRS_OK;
+        case LRS_TUNE_NORM_MAX_TILES:
+            if (value < 1 || value > (1 << 20)) return lrs_fail(LRS_ERR_ARG, "norm tiles in 1..2^20");
+            c->tune_norm_tiles = value;
+            return LRS_OK;
+        case LRS_TUNE_MC_CHAINS_PER_BLOCK:
+            if (value < 1 || value > 64) return lrs_fail(LRS_ERR_ARG, "chains per block in 1..64");
+            c->tune_mc_cg = value;
+            return LRS_OK;
+        default:
+            return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
+    }
+}
+
+extern "C" lrs_status lrs_get_tuning(const lrs_ctx* c, int32_t param, int64_t* value) {
+    if (!c || !value) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    switch (param) {
+        case LRS_TUNE_AMP_BLOCKS_PER_SM: *value = c->tune_amp_bps; return LRS_OK;
+        case LRS_TUNE_NORM_MAX_TILES: *value = c->tune_norm_tiles; return LRS_OK;
+        case LRS_TUNE_MC_CHAINS_PER_BLOCK: *value = c->tune_mc_cg; return LRS_OK;
+        default: return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
+    }
 }

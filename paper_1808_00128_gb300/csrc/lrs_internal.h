@@ -14,6 +14,14 @@
 // valid |0^n> CH-forms with b = 0, so kernels need no tail checks.
 #define LRS_TERM_ALIGN 256
 
+// Per-call parameters of the flip-chain kernels (device memory, so a captured
+// graph of steps can be replayed with new values).
+struct McParams {
+    uint64_t seed;
+    int64_t step0;
+};
+#define LRS_MC_GRAPH_STEPS 16
+
 // Device copy of one slot table.
 struct DevSlot {
     int32_t n_choices;
@@ -76,10 +84,18 @@ struct lrs_ctx {
 
     lrs_gate* gates_dev = nullptr;
     int64_t gates_cap = 0;
+    int64_t batch_n_gates = 0;      // gate count uploaded for a batched launch
 
     // scratch for partial sums
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // launch-shape tuning (lrs_set_tuning)
+    int64_t tune_amp_bps = 8;       // amplitude: target blocks per SM
+    int64_t tune_norm_tiles = 2048; // norm: maximum term tiles per A-block column
+    int64_t tune_mc_cg = 64;        // Metropolis: chains per block (1..64)
+    // work table of batched launches led by this context
+    void* batch_buf = nullptr;
+    size_t batch_buf_bytes = 0;
 
     // Metropolis chains
     int64_t n_chains = 0;
@@ -90,6 +106,10 @@ struct lrs_ctx {
     int32_t* pend = nullptr;        // [chain] pending accepted flip (-1 none)
     int64_t chains_cap = 0;
     bool q_stale = false;           // x moved by learned proposals: Q must be rebuilt
+    McParams* mc_par = nullptr;     // device parameters of the flip-chain kernels
+    void* mc_exec = nullptr;        // cudaGraphExec_t of LRS_MC_GRAPH_STEPS steps
+    const void* mc_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* cap_stream = nullptr;     // cudaStream_t used for graph capture
     // learned-proposal Metropolis-Hastings buffers
     uint64_t* ybuf = nullptr;       // [chain] proposals
     float* lqy = nullptr;           // [chain] log q(y)
@@ -143,3 +163,5 @@ lrs_status launch_metropolis_learned(lrs_ctx* ctx, lrs_mlp* mlp, int64_t steps, 
                                      int64_t step0, uint64_t* x_out, double* p_out, uint64_t* trace,
                                      int64_t* accepts, cudaStream_t st);
 lrs_status launch_chains_refresh(lrs_ctx* ctx, cudaStream_t st);
+lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cudaStream_t st,
+                                       void** dev_buf, size_t* dev_buf_bytes);

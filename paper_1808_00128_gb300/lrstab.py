@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "liblrstab.so")
 OP = dict(H=0, S=1, SDG=2, Z=3, CX=4, CZ=5, P0=6, P1=7, SLOT=8)
 CKIND = dict(H=0, S=1, SDG=2, Z=3, CX=4, CZ=5, T=6, RZ=7, CCZ=8)
 CCZ_MODE = dict(proj=0, sum8=1)
+TUNE = dict(amp_blocks_per_sm=0, norm_max_tiles=1, mc_chains_per_block=2)
 MODE = dict(exact=0, sparsify=1)
 STATUS = {0: "LRS_OK", -1: "LRS_ERR_ARG", -2: "LRS_ERR_OOM", -3: "LRS_ERR_CUDA",
           -4: "LRS_ERR_TIMEOUT", -5: "LRS_ERR_STATE", -6: "LRS_ERR_UNSUPPORTED"}
@@ -36,7 +37,8 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_chains_init", "lrs_metropolis_step", "lrs_export_terms", "lrs_info",
             "lrs_alu_probe", "lrs_amplitude_noalloc", "lrs_mlp_create", "lrs_mlp_destroy",
             "lrs_mlp_info", "lrs_mlp_set_params", "lrs_mlp_get_params", "lrs_mlp_forward",
-            "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned"]
+            "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned",
+            "lrs_apply_clifford_batch", "lrs_set_tuning", "lrs_get_tuning"]
 
 
 class LrsError(RuntimeError):
@@ -84,6 +86,9 @@ def lib():
         "lrs_mlp_train_step": [vp, vp, i64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, vp, vp],
         "lrs_mlp_sample": [vp, i64, u64, i64, vp, vp, vp],
         "lrs_metropolis_learned": [vp, vp, i64, u64, i64, vp, vp, vp, vp, vp],
+        "lrs_apply_clifford_batch": [vp, vp, vp, i32, vp],
+        "lrs_set_tuning": [vp, i32, i64],
+        "lrs_get_tuning": [vp, i32, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -267,6 +272,14 @@ class Simulator:
         _check(lib().lrs_metropolis_step(self._h, steps, seed & (2 ** 64 - 1), step0, _ptr(x_out),
                                          _ptr(p_out), _ptr(trace), _stream(stream)))
 
+    def set_tuning(self, name: str, value: int):
+        _check(lib().lrs_set_tuning(self._h, TUNE[name], int(value)))
+
+    def get_tuning(self, name: str) -> int:
+        v = C.c_int64(0)
+        _check(lib().lrs_get_tuning(self._h, TUNE[name], C.byref(v)))
+        return v.value
+
     def export_terms(self, first: int = 0, count: int | None = None) -> dict:
         count = self.chi - first if count is None else count
         n, ns = self.n, self.n_slots
@@ -361,3 +374,13 @@ def metropolis_learned(sim: "Simulator", mlp: MLP, steps: int, seed: int, step0:
     _check(lib().lrs_metropolis_learned(sim._h, mlp._h, steps, seed & (2 ** 64 - 1), step0,
                                         _ptr(x_out), _ptr(p_out), _ptr(trace), _ptr(accepts),
                                         _stream(stream)))
+
+
+def apply_clifford_batch(sims, gate_lists, stream=None):
+    """One persistent launch pushing each Simulator's terms through its gate list."""
+    k = len(sims)
+    handles = (C.c_void_p * k)(*[s._h.value for s in sims])
+    garrs = [np.ascontiguousarray(g) for g in gate_lists]
+    ptrs = (C.c_void_p * k)(*[g.ctypes.data for g in garrs])
+    counts = (C.c_int64 * k)(*[len(g) for g in garrs])
+    _check(lib().lrs_apply_clifford_batch(handles, ptrs, counts, k, _stream(stream)))

@@ -1,0 +1,76 @@
+"""Batched execution of several circuits of uneven chi in one persistent launch,
+Metropolis steps replayed from a captured CUDA graph, and the launch-shape
+autotuner: none of them may change results."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1808_00128_gb300 import autotune, lrstab, workloads
+from tests._gpu import amp_tol, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def test_batched_apply_matches_single_launches():
+    require_cuda()
+    n = 20
+    sims, lows = [], []
+    for i, chi in enumerate([300, 4096, 1000, 256 * 7]):     # uneven, ragged term counts
+        ops, _ = workloads.qaoa_e3lin2_circuit(n, 4, 0.3, 0.2, seed=100 + i)
+        low = lrstab.lower_circuit(n, ops)
+        s = lrstab.Simulator(n, 0)
+        s.init_terms(low, chi, mode="sparsify", seed=7 + i)
+        sims.append(s)
+        lows.append(low)
+    lrstab.apply_clifford_batch(sims, [l.gates for l in lows])
+    for i, (s, low) in enumerate(zip(sims, lows)):
+        ref = lrstab.Simulator(n, 0)
+        ref.init_terms(low, s.chi, mode="sparsify", seed=7 + i)
+        ref.apply_clifford(low.gates)
+        a, b = s.export_terms(), ref.export_terms()
+        for k in ("F", "G", "M", "gamma", "v", "s", "omega", "coef", "choice"):
+            assert np.array_equal(a[k], b[k]), (i, k)
+        ref.close()
+    for s in sims:
+        s.close()
+
+
+def test_tuning_knobs_keep_results():
+    require_cuda()
+    cfg = workloads.config_mid()
+    n, ops = cfg["n"], cfg["ops"]
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, 0)
+    sim.init_terms(low, 1 << 14, mode="sparsify", seed=cfg["seed"], chi_total=1 << 16)
+    sim.apply_clifford(low.gates)
+    x = torch.cat([sim.sample_terms(700, seed=3),
+                   torch.from_numpy(workloads.random_bitstrings(n, 300, 4).view(np.int64)).cuda()])
+    base = sim.amplitude(x).cpu().numpy()
+    eta0 = sim.norm_estimate(96, seed=5).cpu().numpy()
+    want = base[:, 0] + 1j * base[:, 1]
+    for v in (1, 3, 32):
+        sim.set_tuning("amp_blocks_per_sm", v)
+        got = sim.amplitude(x).cpu().numpy()
+        assert np.all(np.abs(got[:, 0] + 1j * got[:, 1] - want) <= amp_tol(want, n, 0.5))
+    for v in (64, 512, 4096):
+        sim.set_tuning("norm_max_tiles", v)
+        eta = sim.norm_estimate(96, seed=5).cpu().numpy()
+        assert np.all(np.abs(eta - eta0) <= 1e-5 * np.maximum(eta0, 0.25))
+    with pytest.raises(lrstab.LrsError):
+        sim.set_tuning("mc_chains_per_block", 65)
+    # chains per block: same trajectory
+    x0 = sim.sample_terms(100, seed=9)
+    outs = []
+    for cg in (64, 7):
+        sim.set_tuning("mc_chains_per_block", cg)
+        sim.chains_init(x0)
+        xo = torch.empty(100, dtype=torch.int64, device="cuda:0")
+        sim.metropolis(40, seed=2, x_out=xo)     # 40 steps: two graph replays + 8 direct steps
+        outs.append(xo.cpu())
+    assert torch.equal(outs[0], outs[1])
+    chosen = autotune.tune(sim, x=x, L=64, chains=100)
+    assert set(chosen) == {"amp_blocks_per_sm", "norm_max_tiles", "mc_chains_per_block"}
+    for k, (v, ms) in chosen.items():
+        assert v in autotune.CANDIDATES[k] and ms > 0
+        assert sim.get_tuning(k) == v
+    sim.close()
