@@ -378,7 +378,10 @@ def qaoa_study(local=0, chi=1 << 20, B=4096, C=256, T=64, alu_peak=None, hbm_pea
     ach = chi * ops_term / t_apply
     res["apply_clifford"] = {"ms": t_apply * 1e3, "term_gates_per_s": chi * len(low.gates) / t_apply,
                              "achieved_Tops": ach / 1e12, "frac": ach / alu_peak if alu_peak else None}
-    # amplitude
+    # amplitude (launch shape autotuned for this batch)
+    from paper_1808_00128_gb300 import autotune
+    tuned = {k: v for k, (v, ms) in autotune.tune(sim, x=x).items()}
+    res["tuned"] = tuned
     sim.amplitude(x, out=out)
     ts = []
     for rep in range(3):

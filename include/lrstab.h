@@ -181,8 +181,9 @@ lrs_status lrs_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t 
 
 /* Batched form of lrs_apply_clifford for several circuits (contexts on one
  * device, e.g. decompositions of uneven chi): context i receives gate list i
- * (copied before return).  All tiles of all circuits run in one persistent
- * launch whose blocks take work from a shared counter.  Same rules and errors
+ * (copied before return).  All tiles of all circuits run in one launch (up to
+ * 12 circuits per launch); each block finds its circuit from its block index.
+ * Same rules and errors
  * as lrs_apply_clifford, plus LRS_ERR_ARG for repeated contexts or contexts
  * on different devices.                                                      */
 lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_gate* const* gates_host,

@@ -1,5 +1,7 @@
 // Term initialisation (exact enumeration / sparsification) and the fused
 // Clifford-circuit kernel.
+#include <string.h>
+
 #include <vector>
 
 #include "lrs_device.cuh"
@@ -74,7 +76,7 @@ struct SmemRows {
 constexpr int APPLY_TPB = SmemRows::APPLY_TPB_STRIDE;
 
 // One tile of APPLY_TPB terms through the whole gate list.
-__device__ __forceinline__ void apply_tile(const TermsView& T, const lrs_gate* __restrict__ gates,
+__device__ __forceinline__ void apply_tile(const TermsView T, const lrs_gate* __restrict__ gates,
                                            int64_t n_gates, int64_t tile, uint64_t* smem) {
     const int n = T.n;
     const int64_t a = tile * APPLY_TPB + threadIdx.x;   // cap % APPLY_TPB == 0
@@ -115,34 +117,27 @@ __global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford(TermsView T, const
     apply_tile(T, gates, n_gates, blockIdx.x, smem);
 }
 
-// Several circuits of uneven chi in one persistent launch: blocks pull global
-// tile indices from an atomic counter; circuit c owns tiles [first[c], first[c+1]).
-struct ApplyItem {
-    TermsView T;
-    const lrs_gate* gates;
-    int64_t n_gates;
-    int64_t first_tile;
+// Several circuits of uneven chi in one launch: block b runs global tile b; the
+// circuit table is a kernel parameter, so the circuit lookup and every value read
+// from it are warp-uniform (as in the single-circuit kernel).  The hardware block
+// scheduler balances the uneven circuits.
+#define LRS_APPLY_BATCH_MAX 12
+struct ApplyBatch {
+    int count;
+    int64_t first_tile[LRS_APPLY_BATCH_MAX + 1];
+    TermsView T[LRS_APPLY_BATCH_MAX];
+    const lrs_gate* gates[LRS_APPLY_BATCH_MAX];
+    int64_t n_gates[LRS_APPLY_BATCH_MAX];
 };
 
-__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford_batch(const ApplyItem* __restrict__ items,
-                                                                    int count, int64_t total_tiles,
-                                                                    unsigned long long* counter) {
+__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford_batch(const __grid_constant__ ApplyBatch B) {
     extern __shared__ uint64_t smem[];
-    __shared__ long long s_idx;
-    while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_idx = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const int64_t idx = s_idx;
-        if (idx >= total_tiles) break;
-        int lo = 0, hi = count - 1;          // last item with first_tile <= idx
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (items[mid].first_tile <= idx) lo = mid; else hi = mid - 1;
-        }
-        const ApplyItem& it = items[lo];
-        apply_tile(it.T, it.gates, it.n_gates, idx - it.first_tile, smem);
-    }
+    const int64_t tile = blockIdx.x;
+    int c = 0;
+#pragma unroll 1
+    for (int i = 1; i < B.count; ++i)
+        if (B.first_tile[i] <= tile) c = i;
+    apply_tile(B.T[c], B.gates[c], B.n_gates[c], tile - B.first_tile[c], smem);
 }
 
 // ---- sample x from single terms (Sec. 4.1, "Simulating measurements") --------------
@@ -198,34 +193,29 @@ lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint6
 
 lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cudaStream_t st,
                                        void** dev_buf, size_t* dev_buf_bytes) {
-    std::vector<ApplyItem> items((size_t)count);
-    int64_t tiles = 0;
-    int nmax = 1;
-    for (int32_t i = 0; i < count; ++i) {
-        items[(size_t)i].T = ctxs[i]->view();
-        items[(size_t)i].gates = ctxs[i]->gates_dev;
-        items[(size_t)i].n_gates = ctxs[i]->batch_n_gates;
-        items[(size_t)i].first_tile = tiles;
-        tiles += ctxs[i]->cap / APPLY_TPB;
-        if (ctxs[i]->n > nmax) nmax = ctxs[i]->n;
-    }
-    const size_t bytes = 256 + items.size() * sizeof(ApplyItem);
-    lrs_status rc = lrs_ensure(dev_buf, dev_buf_bytes, bytes);
-    if (rc != LRS_OK) return rc;
-    unsigned long long* counter = (unsigned long long*)*dev_buf;
-    ApplyItem* ditems = (ApplyItem*)((char*)*dev_buf + 256);
-    LRS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
-    LRS_CUDA(cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(ApplyItem), cudaMemcpyHostToDevice, st));
-    LRS_CUDA(cudaStreamSynchronize(st));   // host item table may go out of scope
-    const size_t smem = (size_t)3 * nmax * APPLY_TPB * sizeof(uint64_t);
+    (void)dev_buf;
+    (void)dev_buf_bytes;
     LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   3 * 64 * APPLY_TPB * (int)sizeof(uint64_t)));
-    int per_sm = 0;
-    LRS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_clifford_batch, APPLY_TPB, smem));
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)ctxs[0]->sm_count * per_sm;
-    if (grid > tiles) grid = tiles;
-    k_apply_clifford_batch<<<(unsigned)grid, APPLY_TPB, smem, st>>>(ditems, count, tiles, counter);
-    LRS_LAUNCH_CHECK("batched apply_clifford kernel");
+    for (int32_t base = 0; base < count; base += LRS_APPLY_BATCH_MAX) {
+        ApplyBatch B;
+        memset(&B, 0, sizeof(B));
+        B.count = (count - base < LRS_APPLY_BATCH_MAX) ? count - base : LRS_APPLY_BATCH_MAX;
+        int64_t tiles = 0;
+        int nmax = 1;
+        for (int i = 0; i < B.count; ++i) {
+            const lrs_ctx* c = ctxs[base + i];
+            B.T[i] = c->view();
+            B.gates[i] = c->gates_dev;
+            B.n_gates[i] = c->batch_n_gates;
+            B.first_tile[i] = tiles;
+            tiles += c->cap / APPLY_TPB;
+            if (c->n > nmax) nmax = c->n;
+        }
+        B.first_tile[B.count] = tiles;
+        const size_t smem = (size_t)3 * nmax * APPLY_TPB * sizeof(uint64_t);
+        k_apply_clifford_batch<<<(unsigned)tiles, APPLY_TPB, smem, st>>>(B);
+        LRS_LAUNCH_CHECK("batched apply_clifford kernel");
+    }
     return LRS_OK;
 }

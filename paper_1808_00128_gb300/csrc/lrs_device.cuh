@@ -117,6 +117,7 @@ template <int MODE, class Rows>
 __device__ __forceinline__ void prop_h_rows(Rows& R, int n, int q, uint64_t mA, uint64_t m1,
                                             uint64_t mB, uint64_t a, uint64_t& add2,
                                             uint64_t& sub1) {
+#pragma unroll 2
     for (int p = 0; p < n; ++p) {
         uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
         const uint64_t fq = getb(Fp, q);
