@@ -55,16 +55,27 @@ GATE_OPS = {"S": 4, "SDG": 4, "Z": 2, "CZ": 4, "CX": 12}
 
 
 def clifford_ops_per_term(n, low):
-    """Expected integer ops per term of the lowered circuit."""
+    """Expected integer ops per term of the lowered circuit.
+
+    An H on a qubit no earlier gate has touched acts on |0> and needs no row pass
+    (no fan-out, a = 0): it is counted at its constant part (40), every other
+    H or projector at 30n + 40."""
     import numpy as np
     from paper_1808_00128_gb300 import lrstab
     inv = {v: k for k, v in lrstab.OP.items()}
     h_ops = 30 * n + 40
+    touched = set()
 
     def gate_cost(g):
         name = inv[int(g["op"])]
+        q = int(g["q"])
         if name in ("H", "P0", "P1"):
-            return h_ops
+            cost = h_ops if (q in touched or name != "H") else 40
+            touched.add(q)
+            return cost
+        touched.add(q)
+        if name in ("CX", "CZ"):
+            touched.add(int(g["r"]))
         return GATE_OPS.get(name, 0)
 
     total = 0.0
@@ -74,9 +85,19 @@ def clifford_ops_per_term(n, low):
             nc = int(s["n_choices"])
             w = np.hypot(s["c_re"][:nc], s["c_im"][:nc])
             w = w / w.sum()
+            snap = set(touched)
+            acc = 0.0
             for j in range(nc):
+                touched.clear()
+                touched.update(snap)
                 sub = low.kgates[s["k_off"][j]: s["k_off"][j] + s["k_len"][j]]
-                total += w[j] * sum(gate_cost(k) for k in sub)
+                acc += w[j] * sum(gate_cost(k) for k in sub)
+            touched.clear()
+            touched.update(snap)
+            for j in range(nc):
+                for k in low.kgates[s["k_off"][j]: s["k_off"][j] + s["k_len"][j]]:
+                    touched.add(int(k["q"]))
+            total += acc
         else:
             total += gate_cost(g)
     return total

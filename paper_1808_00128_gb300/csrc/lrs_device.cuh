@@ -112,7 +112,8 @@ __device__ __forceinline__ uint32_t sq_entry(int vq, int d) {
 //   R[CZ_{q,i}], i in m1:  M[p,q] ^= F[p,i]; M[p,i] ^= F[p,q]; gamma_p += 2 F[p,q] F[p,i]
 //   R[CX_{i,q}], i in mB:  G[p,i] ^= G[p,q]; F[p,q] ^= F[p,i]; M[p,i] ^= M[p,q]
 //   R[S_q] (a = 1):        M[p,q] ^= F[p,q]; gamma_p -= F[p,q]
-// MODE 1 assumes mB = 0, MODE 2 assumes mA = m1 = 0, MODE 0 is general.
+// MODE 1 assumes mB = 0, MODE 2 assumes mA = m1 = 0, MODE 3 assumes no fan-out
+// (mA = m1 = mB = 0: only R[S_q]), MODE 0 is general.
 template <int MODE, class Rows>
 __device__ __forceinline__ void prop_h_rows(Rows& R, int n, int q, uint64_t mA, uint64_t m1,
                                             uint64_t mB, uint64_t a, uint64_t& add2,
@@ -122,14 +123,14 @@ __device__ __forceinline__ void prop_h_rows(Rows& R, int n, int q, uint64_t mA, 
         uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
         const uint64_t fq = getb(Fp, q);
         uint64_t Gn = Gp, Fn = Fp, Mn = Mp;
-        if (MODE != 2) {
+        if (MODE != 2 && MODE != 3) {
             const uint64_t f1 = par64(Fp & m1);
             Gn ^= (uint64_t)par64(Gp & mA) << q;
             Fn ^= mA & (0ull - fq);
             Mn ^= ((uint64_t)par64((Mp & mA) ^ (Fp & m1)) << q) ^ (m1 & (0ull - fq));
             add2 |= (fq & f1) << p;
         }
-        if (MODE != 1) {
+        if (MODE != 1 && MODE != 3) {
             const uint64_t gq = getb(Gp, q), mq = getb(Mp, q);
             Gn ^= mB & (0ull - gq);
             Fn ^= (uint64_t)par64(Fp & mB) << q;
@@ -184,7 +185,10 @@ __device__ __forceinline__ void prop_h(Rows& R, TermRegs& T, int n, uint64_t t, 
     // MODE 2 when no term has a V0 fan-out (only CX_{i,q}), MODE 1 when none has a
     // V1-only fan-out, MODE 0 otherwise.
     const unsigned am = __activemask();
-    if (__all_sync(am, (mA | m1) == 0)) {
+    if (__all_sync(am, (mA | m1 | mB) == 0)) {
+        // no fan-out anywhere in the warp (e.g. H on |0>): only R[S_q], if any term needs it
+        if (__any_sync(am, a != 0)) prop_h_rows<3>(R, n, q, mA, m1, mB, a, add2, sub1);
+    } else if (__all_sync(am, (mA | m1) == 0)) {
         prop_h_rows<2>(R, n, q, mA, m1, mB, a, add2, sub1);
     } else if (__all_sync(am, mB == 0)) {
         prop_h_rows<1>(R, n, q, mA, m1, mB, a, add2, sub1);
