@@ -503,7 +503,7 @@ def main():
 
     global B_X, L_A, C_CH, T_MC
     cfg = workloads.config_mid()
-    n, chi, seed = cfg["n"], cfg["chi"], cfg["seed"]
+    n, chi, seed = cfg["n"], cfg["chi"], cfg["seed"] + 1000 * rank   # rank r: its own instance
     chi_total = chi
     if args.small:
         chi, B_X, L_A, C_CH, T_MC = 1 << 15, 2048, 128, 128, 2
@@ -571,11 +571,8 @@ def main():
         for i, p in enumerate(phases):
             per_phase[p].append(e[i].elapsed_time(e[i + 1]))
         step_ms.append(e[0].elapsed_time(e[6]))
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_1808_00128_gb300 import sharding
+    ms = sharding.max_over_ranks(statistics.mean(step_ms), device=dev)
     units = units_per_step(chi)
     value = world * units / (ms * 1e-3)
 
