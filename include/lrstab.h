@@ -274,6 +274,21 @@ typedef struct lrs_mlp lrs_mlp;
 lrs_status lrs_mlp_create(int32_t device, int32_t n, int32_t hidden, lrs_mlp** out);
 lrs_status lrs_mlp_destroy(lrs_mlp* mlp);
 lrs_status lrs_mlp_info(const lrs_mlp* mlp, int32_t* n, int32_t* hidden, int64_t* n_params);
+/* GEMM kernel used by every product of the network (default TCGEN05):
+ *   LRS_MLP_GEMM_TCGEN05   5th-generation tensor cores: one thread issues
+ *                          tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) on
+ *                          128 x 64 tiles from shared memory, the accumulator
+ *                          lives in tensor memory, completion arrives on an
+ *                          mbarrier whose wait is bounded (a wait that gives
+ *                          up sets a flag that the next synchronising call,
+ *                          lrs_mlp_get_params or lrs_mlp_set_gemm, reports as
+ *                          LRS_ERR_TIMEOUT)
+ *   LRS_MLP_GEMM_MMA_SYNC  warp-level mma.sync m16n8k16 on 64 x 64 tiles
+ * Both accumulate exact BF16 products in FP32; results differ only in the
+ * order of the FP32 additions.  Synchronises the device.                       */
+enum { LRS_MLP_GEMM_TCGEN05 = 0, LRS_MLP_GEMM_MMA_SYNC = 1 };
+lrs_status lrs_mlp_set_gemm(lrs_mlp* mlp, int32_t kind);
+lrs_status lrs_mlp_get_gemm(const lrs_mlp* mlp, int32_t* kind);
 /* Upload packed FP32 parameters (host, n_params floats); resets AdamW state. */
 lrs_status lrs_mlp_set_params(lrs_mlp* mlp, const float* params_host);
 /* Download packed parameters and/or the last gradients (host, may be NULL).

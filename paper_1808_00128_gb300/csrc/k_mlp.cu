@@ -20,6 +20,8 @@ struct lrs_mlp {
     int n = 0, NP = 64, H = 0;
     // FP32 master parameters and AdamW moments (device)
     float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *W3 = nullptr, *b3 = nullptr;
+    int gemm = 0;                         // LRS_MLP_GEMM_TCGEN05 or LRS_MLP_GEMM_MMA_SYNC
+    int* err = nullptr;                   // device flag: a tensor-core completion wait gave up
     float *mW = nullptr, *vW = nullptr;   // moments for all parameters, packed
     float *grad = nullptr;                // gradients, packed like the parameters
     float *mask = nullptr;                // MADE masks, packed like the weights (1 for biases)
@@ -143,6 +145,148 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const bf16* __restrict__ A, int
             }
 }
 
+// ------------------------------------------------------------------------------------
+// tcgen05 (5th-generation tensor core) GEMM: C[M x N] = A[M x K] . B[N x K]^T with BF16
+// K-major operands in shared memory (no swizzle, 8-row x 16-byte core matrices),
+// the FP32 accumulator in tensor memory (128 lanes x TN columns), one thread
+// issuing tcgen05.mma, completion through tcgen05.commit on an mbarrier (bounded
+// wait), and a tcgen05.ld epilogue.  M % 128 == 0, N % TN == 0, K % 64 == 0.
+// ------------------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_BK = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (M/N-direction) byte offsets between core matrices, descriptor version 1,
+// base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t phase) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int TN, class Epi>
+__global__ void __launch_bounds__(128) k_gemm_tc(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
+                                                 int ldb, int M, int N, int K, Epi epi, int* err) {
+    __shared__ __align__(1024) uint8_t sA[TC_M * TC_BK * 2];
+    __shared__ __align__(1024) uint8_t sB[TN * TC_BK * 2];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "n"(TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = tc_idesc(TC_M, TN);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int k0 = 0; k0 < K && ok; k0 += TC_BK) {
+        // core matrix (row group g, k-chunk j) at ((g * 8 + j) * 128) bytes, row r%8 at +16 (r%8)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int chunk = tid + i * 128;
+            const int r = chunk >> 3, j = chunk & 7;
+            const int gm = m0 + r;
+            const uint32_t off = (uint32_t)(((r >> 3) * 8 + j) * 128 + (r & 7) * 16);
+            cp_async16(sA + off, A + (size_t)(gm < M ? gm : M - 1) * lda + k0 + j * 8, gm < M ? 16 : 0);
+        }
+#pragma unroll
+        for (int i = 0; i < TN * 8 / 128; ++i) {
+            const int chunk = tid + i * 128;
+            const int r = chunk >> 3, j = chunk & 7;
+            const int gn = n0 + r;
+            const uint32_t off = (uint32_t)(((r >> 3) * 8 + j) * 128 + (r & 7) * 16);
+            cp_async16(sB + off, B + (size_t)(gn < N ? gn : N - 1) * ldb + k0 + j * 8, gn < N ? 16 : 0);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // copies -> tensor-core reads
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint64_t da = tc_smem_desc(smem_u32(sA) + kk * 256, 128, 1024);
+                const uint64_t db = tc_smem_desc(smem_u32(sB) + kk * 256, 128, 1024);
+                const uint32_t accum = (k0 > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&mbar))
+                         : "memory");
+        }
+        // MMAs done: the shared tiles may be overwritten (the verdict is made block-uniform)
+        ok = __syncthreads_and(mbar_wait(smem_u32(&mbar), phase)) != 0;
+        phase ^= 1u;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < N) epi(row, col, __uint_as_float(r[j]));
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TN) : "memory");
+}
+
 // ---- epilogues ------------------------------------------------------------------------
 struct EpiBiasReluBf16 {     // out = bf16(relu(acc + bias))
     const float* bias;
@@ -178,9 +322,20 @@ struct EpiStoreF32 {
     __device__ __forceinline__ void operator()(int r, int c, float v) const { out[(size_t)r * ldo + c] = v; }
 };
 
+// C = A . B^T with the network's GEMM kernel: tcgen05 (128 x 64 tiles, K in steps of
+// 64) or mma.sync (64 x 64 tiles, K in steps of 32).  Every product of the network
+// has N and K multiples of 64.
 template <class Epi>
-lrs_status gemm_tn(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, Epi epi,
-                   cudaStream_t st) {
+lrs_status gemm_tn(const lrs_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
+                   Epi epi, cudaStream_t st) {
+    if (m->gemm == LRS_MLP_GEMM_TCGEN05) {
+        if (K % TC_BK != 0 || N % 64 != 0)
+            return lrs_fail(LRS_ERR_ARG, "gemm: N=%d, K=%d not multiples of 64", N, K);
+        dim3 grid(N / 64, (M + TC_M - 1) / TC_M);
+        k_gemm_tc<64, Epi><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, epi, m->err);
+        LRS_LAUNCH_CHECK("tcgen05 gemm");
+        return LRS_OK;
+    }
     if (K % GBK != 0) return lrs_fail(LRS_ERR_ARG, "gemm: K=%d not a multiple of %d", K, GBK);
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
     k_gemm_tn<Epi><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, epi);
@@ -417,9 +572,9 @@ lrs_status mlp_forward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, cu
     k_expand_bits<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(xs, M, Mp, m->n, NP, w.X);
     LRS_LAUNCH_CHECK("expand bits");
     lrs_status rc;
-    if ((rc = gemm_tn(w.X, NP, m->W1b, NP, Mp, H, NP, EpiBiasReluBf16{m->b1, w.H1, H}, st)) != LRS_OK) return rc;
-    if ((rc = gemm_tn(w.H1, H, m->W2b, H, Mp, H, H, EpiBiasReluBf16{m->b2, w.H2, H}, st)) != LRS_OK) return rc;
-    return gemm_tn(w.H2, H, m->W3b, H, Mp, NP, H, EpiBiasF32{m->b3, w.logits, NP, m->n}, st);
+    if ((rc = gemm_tn(m, w.X, NP, m->W1b, NP, Mp, H, NP, EpiBiasReluBf16{m->b1, w.H1, H}, st)) != LRS_OK) return rc;
+    if ((rc = gemm_tn(m, w.H1, H, m->W2b, H, Mp, H, H, EpiBiasReluBf16{m->b2, w.H2, H}, st)) != LRS_OK) return rc;
+    return gemm_tn(m, w.H2, H, m->W3b, H, Mp, NP, H, EpiBiasF32{m->b3, w.logits, NP, m->n}, st);
 }
 
 void transpose(const bf16* in, int R, int C, bf16* out, cudaStream_t st) {
@@ -443,24 +598,24 @@ lrs_status mlp_backward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, f
     // dW3 = dZ3^T H2   [NP x H]
     transpose(w.D3, Mp, NP, w.T1, st);
     transpose(w.H2, Mp, H, w.T2, st);
-    if ((rc = gemm_tn(w.T1, Mp, w.T2, Mp, NP, H, Mp, EpiStoreF32{w.gW, H}, st)) != LRS_OK) return rc;
+    if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, NP, H, Mp, EpiStoreF32{w.gW, H}, st)) != LRS_OK) return rc;
     k_copy_grad<<<(n * H + 255) / 256, 256, 0, st>>>(w.gW, n, H, H, g + m->off[4]);
     k_colsum<<<1, 64, 0, st>>>(w.d3f, Mp, NP, n, g + m->off[5]);
     // dZ2 = (dZ3 W3) * [H2 > 0]
-    if ((rc = gemm_tn(w.D3, NP, m->W3t, NP, Mp, H, NP, EpiReluGrad{w.H2, H, w.d2f, w.D2, H}, st)) != LRS_OK)
+    if ((rc = gemm_tn(m, w.D3, NP, m->W3t, NP, Mp, H, NP, EpiReluGrad{w.H2, H, w.d2f, w.D2, H}, st)) != LRS_OK)
         return rc;
     // dW2 = dZ2^T H1   [H x H]
     transpose(w.D2, Mp, H, w.T1, st);
     transpose(w.H1, Mp, H, w.T2, st);
-    if ((rc = gemm_tn(w.T1, Mp, w.T2, Mp, H, H, Mp, EpiStoreF32{g + m->off[2], H}, st)) != LRS_OK) return rc;
+    if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, H, H, Mp, EpiStoreF32{g + m->off[2], H}, st)) != LRS_OK) return rc;
     k_colsum<<<(H + 127) / 128, 128, 0, st>>>(w.d2f, Mp, H, H, g + m->off[3]);
     // dZ1 = (dZ2 W2) * [H1 > 0]
-    if ((rc = gemm_tn(w.D2, H, m->W2t, H, Mp, H, H, EpiReluGrad{w.H1, H, w.d1f, w.D1, H}, st)) != LRS_OK)
+    if ((rc = gemm_tn(m, w.D2, H, m->W2t, H, Mp, H, H, EpiReluGrad{w.H1, H, w.d1f, w.D1, H}, st)) != LRS_OK)
         return rc;
     // dW1 = dZ1^T X   [H x NP] -> packed [H x n]
     transpose(w.D1, Mp, H, w.T1, st);
     transpose(w.X, Mp, NP, w.T2, st);
-    if ((rc = gemm_tn(w.T1, Mp, w.T2, Mp, H, NP, Mp, EpiStoreF32{w.gW, NP}, st)) != LRS_OK) return rc;
+    if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, H, NP, Mp, EpiStoreF32{w.gW, NP}, st)) != LRS_OK) return rc;
     k_copy_grad<<<(H * n + 255) / 256, 256, 0, st>>>(w.gW, H, n, NP, g + m->off[0]);
     k_colsum<<<(H + 127) / 128, 128, 0, st>>>(w.d1f, Mp, H, H, g + m->off[1]);
     k_apply_mask<<<(unsigned)((m->n_params + 255) / 256), 256, 0, st>>>(g, m->mask, m->n_params);
@@ -513,6 +668,8 @@ extern "C" lrs_status lrs_mlp_create(int32_t device, int32_t n, int32_t hidden, 
     if (e == cudaSuccess) e = cudaMalloc(&m->W3b, (size_t)64 * H * 2);
     if (e == cudaSuccess) e = cudaMalloc(&m->W2t, (size_t)H * H * 2);
     if (e == cudaSuccess) e = cudaMalloc(&m->W3t, (size_t)H * 64 * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
     if (e != cudaSuccess) {
         delete m;
         return lrs_cuda_check(e, "mlp storage");
@@ -553,6 +710,7 @@ extern "C" lrs_status lrs_mlp_destroy(lrs_mlp* m) {
     cudaFree(m->W1);   // start of the packed parameters
     cudaFree(m->mW); cudaFree(m->vW); cudaFree(m->grad); cudaFree(m->mask);
     cudaFree(m->W1b); cudaFree(m->W2b); cudaFree(m->W3b); cudaFree(m->W2t); cudaFree(m->W3t);
+    cudaFree(m->err);
     cudaFree(m->ws);
     delete m;
     return LRS_OK;
@@ -572,13 +730,44 @@ extern "C" lrs_status lrs_mlp_set_params(lrs_mlp* m, const float* params_host) {
     return LRS_OK;
 }
 
+// Reads (and clears) the device flag that a tcgen05 GEMM sets when its completion
+// wait gives up; the caller has synchronised the device.
+static lrs_status mlp_check_err(lrs_mlp* m) {
+    int flag = 0;
+    LRS_CUDA(cudaMemcpy(&flag, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        LRS_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+        return lrs_fail(LRS_ERR_TIMEOUT, "a tcgen05 GEMM gave up waiting for its MMAs; results are invalid");
+    }
+    return LRS_OK;
+}
+
 extern "C" lrs_status lrs_mlp_get_params(lrs_mlp* m, float* params_host, float* grads_host) {
     if (!m) return lrs_fail(LRS_ERR_ARG, "NULL argument");
     LRS_CUDA(cudaSetDevice(m->device));
     LRS_CUDA(cudaDeviceSynchronize());
+    lrs_status rc = mlp_check_err(m);
+    if (rc != LRS_OK) return rc;
     const size_t pb = (size_t)m->n_params * sizeof(float);
     if (params_host) LRS_CUDA(cudaMemcpy(params_host, m->W1, pb, cudaMemcpyDeviceToHost));
     if (grads_host) LRS_CUDA(cudaMemcpy(grads_host, m->grad, pb, cudaMemcpyDeviceToHost));
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_mlp_set_gemm(lrs_mlp* m, int32_t kind) {
+    if (!m) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (kind != LRS_MLP_GEMM_TCGEN05 && kind != LRS_MLP_GEMM_MMA_SYNC)
+        return lrs_fail(LRS_ERR_ARG, "unknown GEMM kernel %d", kind);
+    LRS_CUDA(cudaSetDevice(m->device));
+    LRS_CUDA(cudaDeviceSynchronize());
+    lrs_status rc = mlp_check_err(m);
+    m->gemm = kind;
+    return rc;
+}
+
+extern "C" lrs_status lrs_mlp_get_gemm(const lrs_mlp* m, int32_t* kind) {
+    if (!m || !kind) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    *kind = m->gemm;
     return LRS_OK;
 }
 
@@ -652,7 +841,7 @@ extern "C" lrs_status lrs_mlp_sample(lrs_mlp* m, int64_t count, uint64_t seed, i
     k_sample_init<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m->b1, Mp, H, M, w.Z1, w.H1, y, logq);
     LRS_LAUNCH_CHECK("sample init");
     for (int i = 0; i < m->n; ++i) {
-        if ((rc = gemm_tn(w.H1, H, m->W2b, H, Mp, H, H, EpiBiasReluBf16{m->b2, w.H2, H}, st)) != LRS_OK) return rc;
+        if ((rc = gemm_tn(m, w.H1, H, m->W2b, H, Mp, H, H, EpiBiasReluBf16{m->b2, w.H2, H}, st)) != LRS_OK) return rc;
         k_sample_bit<<<(unsigned)((M * 32 + 127) / 128), 128, 0, st>>>(w.H2, m->W3b, m->b3, m->W1b, M, H, m->NP,
                                                                      i, seed, sample0, w.Z1, w.H1, y, logq);
         LRS_LAUNCH_CHECK("sample bit");

@@ -36,7 +36,7 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_apply_clifford", "lrs_amplitude", "lrs_norm_estimate", "lrs_sample_terms",
             "lrs_chains_init", "lrs_metropolis_step", "lrs_export_terms", "lrs_info",
             "lrs_alu_probe", "lrs_amplitude_noalloc", "lrs_mlp_create", "lrs_mlp_destroy",
-            "lrs_mlp_info", "lrs_mlp_set_params", "lrs_mlp_get_params", "lrs_mlp_forward",
+            "lrs_mlp_info", "lrs_mlp_set_gemm", "lrs_mlp_get_gemm", "lrs_mlp_set_params", "lrs_mlp_get_params", "lrs_mlp_forward",
             "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned",
             "lrs_apply_clifford_batch", "lrs_set_tuning", "lrs_get_tuning"]
 
@@ -79,6 +79,8 @@ def lib():
         "lrs_mlp_create": [i32, i32, i32, vp],
         "lrs_mlp_destroy": [vp],
         "lrs_mlp_info": [vp, vp, vp, vp],
+        "lrs_mlp_set_gemm": [vp, i32],
+        "lrs_mlp_get_gemm": [vp, vp],
         "lrs_mlp_set_params": [vp, vp],
         "lrs_mlp_get_params": [vp, vp, vp],
         "lrs_mlp_forward": [vp, vp, i64, vp, vp, vp],
@@ -316,6 +318,18 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+    GEMM_TCGEN05, GEMM_MMA_SYNC = 0, 1
+
+    @property
+    def gemm(self) -> int:
+        k = C.c_int32(0)
+        _check(lib().lrs_mlp_get_gemm(self._h, C.byref(k)))
+        return k.value
+
+    @gemm.setter
+    def gemm(self, kind: int):
+        _check(lib().lrs_mlp_set_gemm(self._h, kind))
 
     def pack(self, params: dict) -> np.ndarray:
         return np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
