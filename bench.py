@@ -480,6 +480,52 @@ def batch_study(local=0, k=8, seed=0):
     return res
 
 
+def mlp_gemm_study(local=0, n=64, H=2048, batch=16384, reps=5, bf16_peak=None):
+    """Tensor-core throughput of the learned proposal's products: forward pass and
+    one AdamW training step of the MADE network (n=64, H=2048, 16384 rows), with the
+    tcgen05 GEMM and with the mma.sync GEMM.  FLOPs count the padded products
+    (input width 64): forward 2 B (64 H + H^2 + 64 H), backward 2 B (2 * 64 H +
+    2 H^2 + 64 H)."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    dev = torch.device(f"cuda:{local}")
+    net = lrstab.MLP(n, H, local)
+    rng = np.random.default_rng(9)
+    lim1, lim2 = 1 / np.sqrt(n), 1 / np.sqrt(H)
+    net.set_params(dict(W1=rng.uniform(-lim1, lim1, (H, n)), b1=rng.uniform(-lim1, lim1, H),
+                        W2=rng.uniform(-lim2, lim2, (H, H)), b2=rng.uniform(-lim2, lim2, H),
+                        W3=rng.uniform(-lim2, lim2, (n, H)), b3=rng.uniform(-lim2, lim2, n)))
+    x = torch.from_numpy(workloads.random_bitstrings(n, batch, workloads.SEED_BASE + 51).view(np.int64)).to(dev)
+    logits = torch.empty((batch, n), dtype=torch.float32, device=dev)
+    f_fwd = 2.0 * batch * (64 * H + H * H + H * 64)
+    f_train = f_fwd + 2.0 * batch * (2 * 64 * H + 2 * H * H + 64 * H)
+    res = {"n": n, "hidden": H, "batch": batch, "gflop_forward": f_fwd / 1e9, "gflop_train_step": f_train / 1e9}
+    for name, kind in (("tcgen05", lrstab.MLP.GEMM_TCGEN05), ("mma_sync", lrstab.MLP.GEMM_MMA_SYNC)):
+        net.gemm = kind
+        row = {}
+        for what, fn, fl in (("forward", lambda: net.forward(x), f_fwd),
+                             ("train_step", lambda: net.train_step(x, lr=0.0), f_train)):
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                a, b = _ev()
+                a.record()
+                fn()
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            t = min(ts) * 1e-3
+            row[what] = {"ms": t * 1e3, "tflops": fl / t / 1e12,
+                         "frac_of_bf16_peak": fl / t / 1e12 / bf16_peak if bf16_peak else None}
+        res[name] = row
+    net.get_params()   # synchronises; reports a tcgen05 completion wait that gave up
+    res["speedup_forward"] = res["mma_sync"]["forward"]["ms"] / res["tcgen05"]["forward"]["ms"]
+    net.close()
+    return res
+
+
 # ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
@@ -651,12 +697,13 @@ def main():
                          "times scaled to one full step",
                "seconds": round(time.perf_counter() - t0, 1)}
     sim.close()
-    ess = qaoa = batch = None
+    ess = qaoa = batch = gemm = None
     if rank == 0 and not args.small and not args.no_sampler_study:
         ess = sampler_study(local)
     if rank == 0 and not args.small and not args.no_extra:
         qaoa = qaoa_study(local, alu_peak=alu_measured, hbm_peak=hbm)
         batch = batch_study(local)
+        gemm = mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops"))
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -667,7 +714,7 @@ def main():
                       "before every timed step", "parallelism": f"replicas x{world}", "tuned": tuned},
            "roofline": roof, "phases": rows, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "ess": ess,
-           "qaoa_n50": qaoa, "batch8": batch}
+           "qaoa_n50": qaoa, "batch8": batch, "mlp_gemm": gemm}
     print(json.dumps(out))
 
 

@@ -5,6 +5,8 @@
 // Precision: FP32 master weights; the GEMMs read BF16 (round-to-nearest-even)
 // copies of the masked weights and BF16 activations H1, H2 and backward signals
 // dZ3, dZ2, dZ1; accumulation, biases, logits and gradients are FP32.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -146,26 +148,58 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const bf16* __restrict__ A, int
 }
 
 // ------------------------------------------------------------------------------------
-// tcgen05 (5th-generation tensor core) GEMM: C[M x N] = A[M x K] . B[N x K]^T with BF16
-// K-major operands in shared memory (no swizzle, 8-row x 16-byte core matrices),
-// the FP32 accumulator in tensor memory (128 lanes x TN columns), one thread
-// issuing tcgen05.mma, completion through tcgen05.commit on an mbarrier (bounded
-// wait), and a tcgen05.ld epilogue.  M % 128 == 0, N % TN == 0, K % 64 == 0.
+// tcgen05 (5th-generation tensor core) GEMM: C[M x N] = A[M x K] . B[N x K]^T, BF16
+// operands, FP32 accumulator in tensor memory.  One CTA computes a 128 x TN tile:
+//   warp 0, lane 0   TMA producer: 128 x 64 and TN x 64 boxes (128-byte swizzle) into
+//                    a ring of ST shared-memory stages, completion counted in bytes on
+//                    full[s]; a stage is refilled after the MMAs that read it arrive on
+//                    empty[s]
+//   warp 1, lane 0   MMA issuer: four tcgen05.mma (K = 16 each) per stage, then
+//                    tcgen05.commit -> empty[s]; after the last stage -> done
+//   all four warps   epilogue: tcgen05.ld of their 32 accumulator lanes (rows),
+//                    fused element-wise output
+// Every wait is bounded in time; a wait that gives up sets *err and the tile is not
+// written.  Rows >= M read as zero (TMA out-of-bounds fill).  N % TN == 0, K % 64 == 0.
 // ------------------------------------------------------------------------------------
 constexpr int TC_M = 128, TC_BK = 64;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase with the given parity to complete; false after TC_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    if (mbar_try(addr, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(addr, parity))
+        if (global_ns() - t0 > TC_WAIT_NS) return false;
+    return true;
+}
 
-// Shared-memory matrix descriptor: start address, leading (K-direction) and
-// stride (M/N-direction) byte offsets between core matrices, descriptor version 1,
-// base offset 0, no swizzle.
-__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor for a K-major operand stored as 128-byte rows with
+// the 128-byte swizzle (the layout a TMA box of 64 BF16 x rows with that swizzle
+// writes): start address, stride between 8-row groups 1024 bytes, descriptor
+// version 1, swizzle mode 2 (128 B).  The leading offset is unused for this layout.
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -174,74 +208,91 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t phase) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(addr), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
+template <int TN, int ST>
+struct TcShape {
+    static constexpr int A_BYTES = TC_M * TC_BK * 2;
+    static constexpr int B_BYTES = TN * TC_BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;        // a multiple of 1024
+    static constexpr int SMEM = ST * STAGE + 1024;          // + alignment slack
+};
 
-template <int TN, class Epi>
-__global__ void __launch_bounds__(128) k_gemm_tc(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
-                                                 int ldb, int M, int N, int K, Epi epi, int* err) {
-    __shared__ __align__(1024) uint8_t sA[TC_M * TC_BK * 2];
-    __shared__ __align__(1024) uint8_t sB[TN * TC_BK * 2];
-    __shared__ __align__(8) uint64_t mbar;
+template <int TN, int ST, class Epi>
+__global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                 const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+                                                 Epi epi, int* err) {
+    using S = TcShape<TN, ST>;
+    extern __shared__ uint8_t tc_dyn[];
+    __shared__ __align__(8) uint64_t full[ST], empty[ST], done;
     __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag, consumed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TN;
+    const int nk = K / TC_BK;
+    const uint32_t sbase = (smem_u32(tc_dyn) + 1023u) & ~1023u;
+
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
                      "n"(TN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)) : "memory");
+    if (tid == 32) {
+        for (int i = 0; i < ST; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[i])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        abort_flag = 0;
+        consumed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = tc_idesc(TC_M, TN);
-    uint32_t phase = 0;
-    bool ok = true;
-    for (int k0 = 0; k0 < K && ok; k0 += TC_BK) {
-        // core matrix (row group g, k-chunk j) at ((g * 8 + j) * 128) bytes, row r%8 at +16 (r%8)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int chunk = tid + i * 128;
-            const int r = chunk >> 3, j = chunk & 7;
-            const int gm = m0 + r;
-            const uint32_t off = (uint32_t)(((r >> 3) * 8 + j) * 128 + (r & 7) * 16);
-            cp_async16(sA + off, A + (size_t)(gm < M ? gm : M - 1) * lda + k0 + j * 8, gm < M ? 16 : 0);
+
+    int issued = 0;
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % ST;
+            if (kt >= ST && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((kt / ST) - 1) & 1u)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (*(volatile int*)&abort_flag) break;
+            const uint32_t fb = smem_u32(&full[s]);
+            const uint32_t sa = sbase + (uint32_t)(s * S::STAGE), sb = sa + (uint32_t)S::A_BYTES;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(S::STAGE)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(sa),
+                "l"((uint64_t)&tmA), "r"(kt * TC_BK), "r"(m0), "r"(fb)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(sb),
+                "l"((uint64_t)&tmB), "r"(kt * TC_BK), "r"(n0), "r"(fb)
+                : "memory");
+            issued = kt + 1;
         }
-#pragma unroll
-        for (int i = 0; i < TN * 8 / 128; ++i) {
-            const int chunk = tid + i * 128;
-            const int r = chunk >> 3, j = chunk & 7;
-            const int gn = n0 + r;
-            const uint32_t off = (uint32_t)(((r >> 3) * 8 + j) * 128 + (r & 7) * 16);
-            cp_async16(sB + off, B + (size_t)(gn < N ? gn : N - 1) * ldb + k0 + j * 8, gn < N ? 16 : 0);
-        }
-        cp_async_commit();
-        cp_async_wait<0>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // copies -> tensor-core reads
-        __syncthreads();
-        if (tid == 0) {
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = tc_idesc(TC_M, TN);
+        int kt = 0;
+        for (; kt < nk; ++kt) {
+            const int s = kt % ST;
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(kt / ST) & 1u)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t sa = sbase + (uint32_t)(s * S::STAGE), sb = sa + (uint32_t)S::A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                const uint64_t da = tc_smem_desc(smem_u32(sA) + kk * 256, 128, 1024);
-                const uint64_t db = tc_smem_desc(smem_u32(sB) + kk * 256, 128, 1024);
-                const uint32_t accum = (k0 > 0 || kk > 0) ? 1u : 0u;
+                const uint64_t da = tc_desc_sw128(sa + kk * 32), db = tc_desc_sw128(sb + kk * 32);
+                const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -249,15 +300,28 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const bf16* __restrict__ A, int
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_u32(&mbar))
+                             smem_u32(&empty[s]))
                          : "memory");
         }
-        // MMAs done: the shared tiles may be overwritten (the verdict is made block-uniform)
-        ok = __syncthreads_and(mbar_wait(smem_u32(&mbar), phase)) != 0;
-        phase ^= 1u;
+        consumed = kt;
+        // arrives once every MMA issued above has completed (also after an abort)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
     }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (ok) {
+    __syncwarp();
+    bool ok = mbar_wait(smem_u32(&done), 0u);
+    ok = __syncthreads_and(ok && !*(volatile int*)&abort_flag) != 0;
+    if (!ok) {
+        if (tid == 32) mbar_wait(smem_u32(&done), 0u);   // the MMAs issued so far have finished
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // let the producer's copies that no MMA waited for land before the CTA exits
+            for (int kt = consumed; kt < issued; ++kt)
+                if (!mbar_wait(smem_u32(&full[kt % ST]), (uint32_t)(kt / ST) & 1u)) break;
+        }
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const int row = m0 + warp * 32 + lane;
 #pragma unroll
         for (int c0 = 0; c0 < TN; c0 += 16) {
@@ -271,15 +335,12 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const bf16* __restrict__ A, int
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             if (row < M) {
+                float v[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col < N) epi(row, col, __uint_as_float(r[j]));
-                }
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+                epi.row16(row, n0 + c0, v);
             }
         }
-    } else if (tid == 0) {
-        atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -287,13 +348,80 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const bf16* __restrict__ A, int
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TN) : "memory");
 }
 
+// Host side: cuTensorMapEncodeTiled through the runtime's driver entry point.
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
+    return fn;
+}
+
+// 2-D map of a row-major BF16 matrix [rows][cols] (row stride ld elements), boxes of
+// 64 columns x box_rows rows, 128-byte swizzle, zero fill outside.
+lrs_status tmap_2d(CUtensorMap* tm, const bf16* ptr, int rows, int cols, int ld, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return lrs_fail(LRS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    if (((uintptr_t)ptr & 15u) || (ld * 2) % 16 || cols % TC_BK)
+        return lrs_fail(LRS_ERR_ARG, "gemm operand not 16-byte aligned (ld=%d, cols=%d)", ld, cols);
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return lrs_fail(LRS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LRS_OK;
+}
+
+template <int TN, int ST, class Epi>
+lrs_status launch_gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, Epi epi, int* err,
+                          cudaStream_t st) {
+    CUtensorMap ta, tb;
+    lrs_status rc;
+    if ((rc = tmap_2d(&ta, A, M, K, lda, TC_M)) != LRS_OK) return rc;
+    if ((rc = tmap_2d(&tb, B, N, K, ldb, TN)) != LRS_OK) return rc;
+    constexpr int smem = TcShape<TN, ST>::SMEM;
+    LRS_CUDA(cudaFuncSetAttribute(k_gemm_tc<TN, ST, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid(N / TN, (M + TC_M - 1) / TC_M);
+    k_gemm_tc<TN, ST, Epi><<<grid, 128, smem, st>>>(ta, tb, M, N, K, epi, err);
+    LRS_LAUNCH_CHECK("tcgen05 gemm");
+    return LRS_OK;
+}
+
 // ---- epilogues ------------------------------------------------------------------------
+// operator() takes one element (mma.sync kernel); row16 takes 16 consecutive columns
+// c0..c0+15 of one row (tcgen05 kernel: one accumulator lane, c0 % 16 == 0, row
+// strides multiples of 64 elements, so every access below is a 16-byte vector).
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
 struct EpiBiasReluBf16 {     // out = bf16(relu(acc + bias))
     const float* bias;
     bf16* out;
     int ldo;
     __device__ __forceinline__ void operator()(int r, int c, float v) const {
         out[(size_t)r * ldo + c] = __float2bfloat16_rn(fmaxf(v + bias[c], 0.f));
+    }
+    __device__ __forceinline__ void row16(int r, int c0, const float (&v)[16]) const {
+        uint32_t p[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 b = __ldg(reinterpret_cast<const float4*>(bias + c0) + q);
+            p[2 * q] = pack_bf16x2(fmaxf(v[4 * q] + b.x, 0.f), fmaxf(v[4 * q + 1] + b.y, 0.f));
+            p[2 * q + 1] = pack_bf16x2(fmaxf(v[4 * q + 2] + b.z, 0.f), fmaxf(v[4 * q + 3] + b.w, 0.f));
+        }
+        uint4* o = reinterpret_cast<uint4*>(out + (size_t)r * ldo + c0);
+        o[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        o[1] = make_uint4(p[4], p[5], p[6], p[7]);
     }
 };
 struct EpiBiasF32 {          // out = acc + bias (columns >= nvalid get 0)
@@ -302,6 +430,19 @@ struct EpiBiasF32 {          // out = acc + bias (columns >= nvalid get 0)
     int ldo, nvalid;
     __device__ __forceinline__ void operator()(int r, int c, float v) const {
         out[(size_t)r * ldo + c] = c < nvalid ? v + bias[c] : 0.f;
+    }
+    __device__ __forceinline__ void row16(int r, int c0, const float (&v)[16]) const {
+        float4* o = reinterpret_cast<float4*>(out + (size_t)r * ldo + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float t[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = c0 + 4 * q + e;
+                t[e] = c < nvalid ? v[4 * q + e] + __ldg(bias + c) : 0.f;   // bias has nvalid entries
+            }
+            o[q] = make_float4(t[0], t[1], t[2], t[3]);
+        }
     }
 };
 struct EpiReluGrad {         // dZ = acc * [H > 0]; FP32 and BF16 copies
@@ -315,15 +456,37 @@ struct EpiReluGrad {         // dZ = acc * [H > 0]; FP32 and BF16 copies
         out32[(size_t)r * ldo + c] = d;
         out16[(size_t)r * ldo + c] = __float2bfloat16_rn(d);
     }
+    __device__ __forceinline__ void row16(int r, int c0, const float (&v)[16]) const {
+        const uint4* a4 = reinterpret_cast<const uint4*>(act + (size_t)r * lda + c0);
+        uint4 ar[2] = {a4[0], a4[1]};
+        const bf16* a = reinterpret_cast<const bf16*>(ar);
+        float d[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) d[j] = __bfloat162float(a[j]) > 0.f ? v[j] : 0.f;
+        float4* o32 = reinterpret_cast<float4*>(out32 + (size_t)r * ldo + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o32[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+        uint32_t p[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[q] = pack_bf16x2(d[2 * q], d[2 * q + 1]);
+        uint4* o16 = reinterpret_cast<uint4*>(out16 + (size_t)r * ldo + c0);
+        o16[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        o16[1] = make_uint4(p[4], p[5], p[6], p[7]);
+    }
 };
 struct EpiStoreF32 {
     float* out;
     int ldo;
     __device__ __forceinline__ void operator()(int r, int c, float v) const { out[(size_t)r * ldo + c] = v; }
+    __device__ __forceinline__ void row16(int r, int c0, const float (&v)[16]) const {
+        float4* o = reinterpret_cast<float4*>(out + (size_t)r * ldo + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
 };
 
-// C = A . B^T with the network's GEMM kernel: tcgen05 (128 x 64 tiles, K in steps of
-// 64) or mma.sync (64 x 64 tiles, K in steps of 32).  Every product of the network
+// C = A . B^T with the network's GEMM kernel: tcgen05 (128 x 128 or 128 x 64 tiles, K
+// in steps of 64) or mma.sync (64 x 64 tiles, K in steps of 32).  Every product of the network
 // has N and K multiples of 64.
 template <class Epi>
 lrs_status gemm_tn(const lrs_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
@@ -331,10 +494,11 @@ lrs_status gemm_tn(const lrs_mlp* m, const bf16* A, int lda, const bf16* B, int 
     if (m->gemm == LRS_MLP_GEMM_TCGEN05) {
         if (K % TC_BK != 0 || N % 64 != 0)
             return lrs_fail(LRS_ERR_ARG, "gemm: N=%d, K=%d not multiples of 64", N, K);
-        dim3 grid(N / 64, (M + TC_M - 1) / TC_M);
-        k_gemm_tc<64, Epi><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, epi, m->err);
-        LRS_LAUNCH_CHECK("tcgen05 gemm");
-        return LRS_OK;
+        // 128-column tiles when they still give every SM a tile, else 64
+        const int64_t tiles128 = (int64_t)((M + TC_M - 1) / TC_M) * (N / 128);
+        if (N % 128 == 0 && tiles128 >= 148)
+            return launch_gemm_tc<128, 3>(A, lda, B, ldb, M, N, K, epi, m->err, st);
+        return launch_gemm_tc<64, 4>(A, lda, B, ldb, M, N, K, epi, m->err, st);
     }
     if (K % GBK != 0) return lrs_fail(LRS_ERR_ARG, "gemm: K=%d not a multiple of %d", K, GBK);
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
@@ -394,12 +558,32 @@ __global__ void k_logit_grad(const float* __restrict__ logits, const uint64_t* _
     if (c == 0 && nll_rows && r < M) nll_rows[r] = red[0];
 }
 
-// column sums of an FP32 [rows][ld] matrix -> out[c] (first `cols` columns)
-__global__ void k_colsum(const float* __restrict__ a, int rows, int ld, int cols, float* out) {
+// column sums of an FP32 [rows][ld] matrix -> out[c] (first `cols` columns), in two
+// deterministic passes: block (x, y) sums rows y*chunk .. (y+1)*chunk - 1 of 64
+// columns into part[y][c] (4 row lanes, then a fixed-order combine); then each
+// column adds its COLSUM_CHUNKS partials in order.
+constexpr int COLSUM_CHUNKS = 128;
+
+__global__ void __launch_bounds__(256) k_colsum_part(const float* __restrict__ a, int rows, int ld, int cols,
+                                                     float* __restrict__ part) {
+    __shared__ float red[4][64];
+    const int cx = threadIdx.x & 63, ry = threadIdx.x >> 6;
+    const int c = blockIdx.x * 64 + cx;
+    const int chunk = (rows + COLSUM_CHUNKS - 1) / COLSUM_CHUNKS;
+    const int r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
+    float s = 0.f;
+    if (c < cols)
+        for (int r = r0 + ry; r < r1; r += 4) s += a[(size_t)r * ld + c];
+    red[ry][cx] = s;
+    __syncthreads();
+    if (ry == 0 && c < cols) part[(size_t)blockIdx.y * cols + c] = (red[0][cx] + red[1][cx]) + (red[2][cx] + red[3][cx]);
+}
+
+__global__ void k_colsum_fin(const float* __restrict__ part, int cols, float* __restrict__ out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cols) return;
     float s = 0.f;
-    for (int r = 0; r < rows; ++r) s += a[(size_t)r * ld + c];
+    for (int y = 0; y < COLSUM_CHUNKS; ++y) s += part[(size_t)y * cols + c];
     out[c] = s;
 }
 
@@ -539,20 +723,22 @@ struct MlpWS {   // workspace views for a batch of Mp rows
     float *logits, *d3f, *d2f, *d1f, *gW, *nll, *Z1;
     uint64_t* ybuf;
     float* lqbuf;
+    float* colp;   // [COLSUM_CHUNKS][H] column-sum partials
 };
 
 lrs_status mlp_ws(lrs_mlp* m, int Mp, MlpWS& w) {
     const size_t NP = m->NP, H = m->H;
     size_t sz[] = {Mp * NP * 2, Mp * H * 2, Mp * H * 2, Mp * NP * 2, Mp * H * 2, Mp * H * 2,
                    H * (size_t)Mp * 2, H * (size_t)Mp * 2, Mp * NP * 4, Mp * NP * 4, Mp * H * 4,
-                   Mp * H * 4, H * H * 4, (size_t)Mp * 4, Mp * H * 4, (size_t)Mp * 8, (size_t)Mp * 4};
+                   Mp * H * 4, H * H * 4, (size_t)Mp * 4, Mp * H * 4, (size_t)Mp * 8, (size_t)Mp * 4,
+                   (size_t)COLSUM_CHUNKS * H * 4};
     size_t total = 0;
     for (size_t s : sz) total += align256(s);
     lrs_status rc = lrs_ensure(&m->ws, &m->ws_bytes, total);
     if (rc != LRS_OK) return rc;
     char* p = (char*)m->ws;
-    void* ptrs[17];
-    for (int i = 0; i < 17; ++i) {
+    void* ptrs[18];
+    for (int i = 0; i < 18; ++i) {
         ptrs[i] = p;
         p += align256(sz[i]);
     }
@@ -560,7 +746,7 @@ lrs_status mlp_ws(lrs_mlp* m, int Mp, MlpWS& w) {
     w.D2 = (bf16*)ptrs[4]; w.D1 = (bf16*)ptrs[5]; w.T1 = (bf16*)ptrs[6]; w.T2 = (bf16*)ptrs[7];
     w.logits = (float*)ptrs[8]; w.d3f = (float*)ptrs[9]; w.d2f = (float*)ptrs[10]; w.d1f = (float*)ptrs[11];
     w.gW = (float*)ptrs[12]; w.nll = (float*)ptrs[13]; w.Z1 = (float*)ptrs[14];
-    w.ybuf = (uint64_t*)ptrs[15]; w.lqbuf = (float*)ptrs[16];
+    w.ybuf = (uint64_t*)ptrs[15]; w.lqbuf = (float*)ptrs[16]; w.colp = (float*)ptrs[17];
     return LRS_OK;
 }
 
@@ -575,6 +761,11 @@ lrs_status mlp_forward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, cu
     if ((rc = gemm_tn(m, w.X, NP, m->W1b, NP, Mp, H, NP, EpiBiasReluBf16{m->b1, w.H1, H}, st)) != LRS_OK) return rc;
     if ((rc = gemm_tn(m, w.H1, H, m->W2b, H, Mp, H, H, EpiBiasReluBf16{m->b2, w.H2, H}, st)) != LRS_OK) return rc;
     return gemm_tn(m, w.H2, H, m->W3b, H, Mp, NP, H, EpiBiasF32{m->b3, w.logits, NP, m->n}, st);
+}
+
+void colsum(const float* a, int rows, int ld, int cols, float* part, float* out, cudaStream_t st) {
+    k_colsum_part<<<dim3((cols + 63) / 64, COLSUM_CHUNKS), 256, 0, st>>>(a, rows, ld, cols, part);
+    k_colsum_fin<<<(cols + 127) / 128, 128, 0, st>>>(part, cols, out);
 }
 
 void transpose(const bf16* in, int R, int C, bf16* out, cudaStream_t st) {
@@ -600,7 +791,7 @@ lrs_status mlp_backward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, f
     transpose(w.H2, Mp, H, w.T2, st);
     if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, NP, H, Mp, EpiStoreF32{w.gW, H}, st)) != LRS_OK) return rc;
     k_copy_grad<<<(n * H + 255) / 256, 256, 0, st>>>(w.gW, n, H, H, g + m->off[4]);
-    k_colsum<<<1, 64, 0, st>>>(w.d3f, Mp, NP, n, g + m->off[5]);
+    colsum(w.d3f, Mp, NP, n, w.colp, g + m->off[5], st);
     // dZ2 = (dZ3 W3) * [H2 > 0]
     if ((rc = gemm_tn(m, w.D3, NP, m->W3t, NP, Mp, H, NP, EpiReluGrad{w.H2, H, w.d2f, w.D2, H}, st)) != LRS_OK)
         return rc;
@@ -608,7 +799,7 @@ lrs_status mlp_backward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, f
     transpose(w.D2, Mp, H, w.T1, st);
     transpose(w.H1, Mp, H, w.T2, st);
     if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, H, H, Mp, EpiStoreF32{g + m->off[2], H}, st)) != LRS_OK) return rc;
-    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(w.d2f, Mp, H, H, g + m->off[3]);
+    colsum(w.d2f, Mp, H, H, w.colp, g + m->off[3], st);
     // dZ1 = (dZ2 W2) * [H1 > 0]
     if ((rc = gemm_tn(m, w.D2, H, m->W2t, H, Mp, H, H, EpiReluGrad{w.H1, H, w.d1f, w.D1, H}, st)) != LRS_OK)
         return rc;
@@ -617,7 +808,7 @@ lrs_status mlp_backward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, f
     transpose(w.X, Mp, NP, w.T2, st);
     if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, H, NP, Mp, EpiStoreF32{w.gW, NP}, st)) != LRS_OK) return rc;
     k_copy_grad<<<(H * n + 255) / 256, 256, 0, st>>>(w.gW, H, n, NP, g + m->off[0]);
-    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(w.d1f, Mp, H, H, g + m->off[1]);
+    colsum(w.d1f, Mp, H, H, w.colp, g + m->off[1], st);
     k_apply_mask<<<(unsigned)((m->n_params + 255) / 256), 256, 0, st>>>(g, m->mask, m->n_params);
     LRS_LAUNCH_CHECK("backward");
     return LRS_OK;
