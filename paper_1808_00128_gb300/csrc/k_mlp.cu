@@ -203,9 +203,31 @@ __device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N >> 3, M >> 4.
-__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Descriptor for an MN-major operand: the stage holds 64 x 64 boxes (64 consecutive
+// M (or N) values = one 128-byte swizzled row per K index); 8-row K groups 1024
+// bytes apart, 64-wide MN blocks 8192 bytes apart.
+__device__ __forceinline__ uint64_t tc_desc_mn_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(8192 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, N >> 3, M >> 4; both
+// operands K-major, or (mn) both MN-major.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N, bool mn = false) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (mn ? (1u << 15) | (1u << 16) : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 
 template <int TN, int ST>
@@ -216,7 +238,7 @@ struct TcShape {
     static constexpr int SMEM = ST * STAGE + 1024;          // + alignment slack
 };
 
-template <int TN, int ST, class Epi>
+template <int TN, int ST, bool MN, class Epi>
 __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                  const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
                                                  Epi epi, int* err) {
@@ -265,21 +287,20 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
             const uint32_t sa = sbase + (uint32_t)(s * S::STAGE), sb = sa + (uint32_t)S::A_BYTES;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(S::STAGE)
                          : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];\n" ::"r"(sa),
-                "l"((uint64_t)&tmA), "r"(kt * TC_BK), "r"(m0), "r"(fb)
-                : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];\n" ::"r"(sb),
-                "l"((uint64_t)&tmB), "r"(kt * TC_BK), "r"(n0), "r"(fb)
-                : "memory");
+            if constexpr (!MN) {
+                tma_load_2d(sa, &tmA, kt * TC_BK, m0, fb);
+                tma_load_2d(sb, &tmB, kt * TC_BK, n0, fb);
+            } else {
+#pragma unroll
+                for (int h = 0; h < TC_M / 64; ++h) tma_load_2d(sa + h * 8192, &tmA, m0 + 64 * h, kt * TC_BK, fb);
+#pragma unroll
+                for (int j = 0; j < TN / 64; ++j) tma_load_2d(sb + j * 8192, &tmB, n0 + 64 * j, kt * TC_BK, fb);
+            }
             issued = kt + 1;
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        constexpr uint32_t idesc = tc_idesc(TC_M, TN);
+        constexpr uint32_t idesc = tc_idesc(TC_M, TN, MN);
         int kt = 0;
         for (; kt < nk; ++kt) {
             const int s = kt % ST;
@@ -291,7 +312,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
             const uint32_t sa = sbase + (uint32_t)(s * S::STAGE), sb = sa + (uint32_t)S::A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                const uint64_t da = tc_desc_sw128(sa + kk * 32), db = tc_desc_sw128(sb + kk * 32);
+                const uint64_t da = MN ? tc_desc_mn_sw128(sa + kk * 2048) : tc_desc_sw128(sa + kk * 32);
+                const uint64_t db = MN ? tc_desc_mn_sw128(sb + kk * 2048) : tc_desc_sw128(sb + kk * 32);
                 const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -380,19 +402,40 @@ lrs_status tmap_2d(CUtensorMap* tm, const bf16* ptr, int rows, int cols, int ld,
     return LRS_OK;
 }
 
-template <int TN, int ST, class Epi>
+// MN = false: A [M][lda], B [N][ldb] (K contiguous).  MN = true: A [K][lda] holds
+// A^T and B [K][ldb] holds B^T (M and N contiguous), so C = A . B^T needs no
+// transposed copies.
+template <int TN, int ST, bool MN, class Epi>
 lrs_status launch_gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, Epi epi, int* err,
                           cudaStream_t st) {
     CUtensorMap ta, tb;
     lrs_status rc;
-    if ((rc = tmap_2d(&ta, A, M, K, lda, TC_M)) != LRS_OK) return rc;
-    if ((rc = tmap_2d(&tb, B, N, K, ldb, TN)) != LRS_OK) return rc;
+    if (!MN) {
+        if ((rc = tmap_2d(&ta, A, M, K, lda, TC_M)) != LRS_OK) return rc;
+        if ((rc = tmap_2d(&tb, B, N, K, ldb, TN)) != LRS_OK) return rc;
+    } else {
+        if ((rc = tmap_2d(&ta, A, K, M, lda, 64)) != LRS_OK) return rc;
+        if ((rc = tmap_2d(&tb, B, K, N, ldb, 64)) != LRS_OK) return rc;
+    }
     constexpr int smem = TcShape<TN, ST>::SMEM;
-    LRS_CUDA(cudaFuncSetAttribute(k_gemm_tc<TN, ST, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    LRS_CUDA(cudaFuncSetAttribute(k_gemm_tc<TN, ST, MN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     dim3 grid(N / TN, (M + TC_M - 1) / TC_M);
-    k_gemm_tc<TN, ST, Epi><<<grid, 128, smem, st>>>(ta, tb, M, N, K, epi, err);
+    k_gemm_tc<TN, ST, MN, Epi><<<grid, 128, smem, st>>>(ta, tb, M, N, K, epi, err);
     LRS_LAUNCH_CHECK("tcgen05 gemm");
     return LRS_OK;
+}
+
+// Tile width for an M x N output: the widest of 256, 128, 64 that divides N and still
+// gives every SM a tile.
+template <bool MN, class Epi>
+lrs_status gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, Epi epi, int* err,
+                   cudaStream_t st) {
+    if (K % TC_BK != 0 || N % 64 != 0 || (MN && M % 64 != 0))
+        return lrs_fail(LRS_ERR_ARG, "gemm: M=%d, N=%d, K=%d not multiples of 64", M, N, K);
+    const int64_t mt = (M + TC_M - 1) / TC_M;
+    if (N % 256 == 0 && mt * (N / 256) >= 148) return launch_gemm_tc<256, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
+    if (N % 128 == 0 && mt * (N / 128) >= 148) return launch_gemm_tc<128, 3, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
+    return launch_gemm_tc<64, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
 }
 
 // ---- epilogues ------------------------------------------------------------------------
@@ -485,20 +528,14 @@ struct EpiStoreF32 {
     }
 };
 
-// C = A . B^T with the network's GEMM kernel: tcgen05 (128 x 128 or 128 x 64 tiles, K
-// in steps of 64) or mma.sync (64 x 64 tiles, K in steps of 32).  Every product of the network
+// C = A . B^T with the network's GEMM kernel: tcgen05 (128 x 256, 128 x 128 or 128 x 64
+// tiles, K in steps of 64) or mma.sync (64 x 64 tiles, K in steps of 32).  Every product of the network
 // has N and K multiples of 64.
 template <class Epi>
 lrs_status gemm_tn(const lrs_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
                    Epi epi, cudaStream_t st) {
     if (m->gemm == LRS_MLP_GEMM_TCGEN05) {
-        if (K % TC_BK != 0 || N % 64 != 0)
-            return lrs_fail(LRS_ERR_ARG, "gemm: N=%d, K=%d not multiples of 64", N, K);
-        // 128-column tiles when they still give every SM a tile, else 64
-        const int64_t tiles128 = (int64_t)((M + TC_M - 1) / TC_M) * (N / 128);
-        if (N % 128 == 0 && tiles128 >= 148)
-            return launch_gemm_tc<128, 3>(A, lda, B, ldb, M, N, K, epi, m->err, st);
-        return launch_gemm_tc<64, 4>(A, lda, B, ldb, M, N, K, epi, m->err, st);
+        return gemm_tc<false>(A, lda, B, ldb, M, N, K, epi, m->err, st);
     }
     if (K % GBK != 0) return lrs_fail(LRS_ERR_ARG, "gemm: K=%d not a multiple of %d", K, GBK);
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
@@ -786,27 +823,29 @@ lrs_status mlp_backward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, f
         LRS_LAUNCH_CHECK("mean");
     }
     float* g = m->grad;
+    // weight gradient D^T Hin (D [Mp][Mo], Hin [Mp][No]): the tcgen05 kernel reads both
+    // operands MN-major straight from the activations; mma.sync goes through transposes
+    auto dW = [&](const bf16* D, int Mo, const bf16* Hin, int No, EpiStoreF32 e) -> lrs_status {
+        if (m->gemm == LRS_MLP_GEMM_TCGEN05) return gemm_tc<true>(D, Mo, Hin, No, Mo, No, Mp, e, m->err, st);
+        transpose(D, Mp, Mo, w.T1, st);
+        transpose(Hin, Mp, No, w.T2, st);
+        return gemm_tn(m, w.T1, Mp, w.T2, Mp, Mo, No, Mp, e, st);
+    };
     // dW3 = dZ3^T H2   [NP x H]
-    transpose(w.D3, Mp, NP, w.T1, st);
-    transpose(w.H2, Mp, H, w.T2, st);
-    if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, NP, H, Mp, EpiStoreF32{w.gW, H}, st)) != LRS_OK) return rc;
+    if ((rc = dW(w.D3, NP, w.H2, H, EpiStoreF32{w.gW, H})) != LRS_OK) return rc;
     k_copy_grad<<<(n * H + 255) / 256, 256, 0, st>>>(w.gW, n, H, H, g + m->off[4]);
     colsum(w.d3f, Mp, NP, n, w.colp, g + m->off[5], st);
     // dZ2 = (dZ3 W3) * [H2 > 0]
     if ((rc = gemm_tn(m, w.D3, NP, m->W3t, NP, Mp, H, NP, EpiReluGrad{w.H2, H, w.d2f, w.D2, H}, st)) != LRS_OK)
         return rc;
     // dW2 = dZ2^T H1   [H x H]
-    transpose(w.D2, Mp, H, w.T1, st);
-    transpose(w.H1, Mp, H, w.T2, st);
-    if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, H, H, Mp, EpiStoreF32{g + m->off[2], H}, st)) != LRS_OK) return rc;
+    if ((rc = dW(w.D2, H, w.H1, H, EpiStoreF32{g + m->off[2], H})) != LRS_OK) return rc;
     colsum(w.d2f, Mp, H, H, w.colp, g + m->off[3], st);
     // dZ1 = (dZ2 W2) * [H1 > 0]
     if ((rc = gemm_tn(m, w.D2, H, m->W2t, H, Mp, H, H, EpiReluGrad{w.H1, H, w.d1f, w.D1, H}, st)) != LRS_OK)
         return rc;
     // dW1 = dZ1^T X   [H x NP] -> packed [H x n]
-    transpose(w.D1, Mp, H, w.T1, st);
-    transpose(w.X, Mp, NP, w.T2, st);
-    if ((rc = gemm_tn(m, w.T1, Mp, w.T2, Mp, H, NP, Mp, EpiStoreF32{w.gW, NP}, st)) != LRS_OK) return rc;
+    if ((rc = dW(w.D1, H, w.X, NP, EpiStoreF32{w.gW, NP})) != LRS_OK) return rc;
     k_copy_grad<<<(H * n + 255) / 256, 256, 0, st>>>(w.gW, H, n, NP, g + m->off[0]);
     colsum(w.d1f, Mp, H, H, w.colp, g + m->off[1], st);
     k_apply_mask<<<(unsigned)((m->n_params + 255) / 256), 256, 0, st>>>(g, m->mask, m->n_params);

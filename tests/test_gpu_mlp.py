@@ -188,3 +188,29 @@ def test_gemm_kernels_agree_at_scale():
     want, _ = omlp.forward(params, omlp.bits_matrix(xs, n))
     assert _relfro(a[:: 512], want) <= 2e-3
     net.get_params()   # synchronises and reports a timed-out completion wait
+
+
+def test_gemm_kernels_agree_on_gradients_at_scale():
+    """Backward pass on 8192 rows, H = 1024: the tcgen05 weight gradients read
+    both operands MN-major (no transposed copies); mma.sync goes through
+    transposes.  Same exact products, different FP32 summation order."""
+    require_cuda()
+    n, H = 48, 1024
+    params = omlp.init_params(n, H, seed=8)
+    net = lrstab.MLP(n, H)
+    net.set_params(params)
+    x = _x(n, 8192, 17)
+    got = {}
+    for kind in GEMMS:
+        net.gemm = kind
+        loss = float(net.backward(x).cpu().numpy()[0])
+        _, g = net.get_params()
+        got[kind] = (loss, g)
+    (l0, g0), (l1, g1) = got[GEMMS[0]], got[GEMMS[1]]
+    assert l0 == pytest.approx(l1, rel=1e-5)
+    for k in g0:
+        assert _relfro(g0[k], g1[k]) <= 1e-3, k
+    xs = x.cpu().numpy().view(np.uint64)
+    _, want = omlp.loss_and_grads(params, omlp.bits_matrix(xs, n))
+    for k in want:
+        assert _relfro(g0[k], want[k]) <= 2e-3, k
