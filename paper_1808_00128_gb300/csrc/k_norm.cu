@@ -26,6 +26,15 @@ struct NormTerm {
     float2 coef;
 };
 
+// S <- S + m1 m2^T + m2 m1^T on the rows in m1 | m2 (one pass: row j gets m2 if j is
+// in m1 and m1 if j is in m2).
+__device__ __forceinline__ void rank2_update(uint64_t* sK, uint64_t m1, uint64_t m2) {
+    for (uint64_t r = m1 | m2; r; r &= r - 1) {
+        const int j = ffs64(r);
+        sK[j * NRM_TPB] ^= (m2 & (0ull - getb(m1, j))) ^ (m1 & (0ull - getb(m2, j)));
+    }
+}
+
 // Sum over variables of (-1)^(quadratic form), lifted from Z4 (Eq. (Q), (real)).
 // Rows S_j (j in v) live in sK[j * NRM_TPB]; X's neighbours are `odd`.
 // Returns Re, Im signs of Z (in {-1,0,1}) and e with |Re|,|Im| = 2^(e-1).
@@ -46,8 +55,7 @@ __device__ __forceinline__ void eliminate(uint64_t* sK, uint64_t v, uint64_t odd
         const uint64_t mm = m1 & m2;
         Lre ^= (getb(Lre, bq) ? m1 : 0ull) ^ mm;
         Lim ^= m2 ^ (getb(Lim, bq) ? m1 : 0ull) ^ mm;
-        for (uint64_t r = m1; r; r &= r - 1) sK[ffs64(r) * NRM_TPB] ^= m2;
-        for (uint64_t r = m2; r; r &= r - 1) sK[ffs64(r) * NRM_TPB] ^= m1;
+        rank2_update(sK, m1, m2);
         act &= ~bit64(bq);
     } else {
         e += 1;      // sum over x_X of (-1)^0 = 2 (Re), of (-1)^x_X = 0 (Im)
@@ -73,8 +81,7 @@ __device__ __forceinline__ void eliminate(uint64_t* sK, uint64_t v, uint64_t odd
         const uint64_t mm = m1 & m2;
         Lre ^= (m2 & (0ull - c1r)) ^ (m1 & (0ull - c2r)) ^ mm;
         Lim ^= (m2 & (0ull - c1i)) ^ (m1 & (0ull - c2i)) ^ mm;
-        for (uint64_t r = m1; r; r &= r - 1) sK[ffs64(r) * NRM_TPB] ^= m2;
-        for (uint64_t r = m2; r; r &= r - 1) sK[ffs64(r) * NRM_TPB] ^= m1;
+        rank2_update(sK, m1, m2);
         act &= ~ab;
         cand &= ~ab;
     }
@@ -97,24 +104,64 @@ __device__ __forceinline__ uint64_t fr_rows(const uint64_t* __restrict__ tab, ui
     return r;
 }
 
-// In-place transpose of the NT x NT bit matrix W[k * NRM_TPB] (bit b of row k).
-template <int NT>
-__device__ __forceinline__ void transpose_rows(uint64_t* W) {
-    uint64_t m = (NT == 64) ? 0x00000000FFFFFFFFull : 0x000000000000FFFFull;
+// Transpose of an 8 x 8 bit block held in one word (row r in byte r, column c in bit
+// c of that byte): three rounds exchanging bit groups across the diagonal (the
+// bit-matrix transposition of Warren, Hacker's Delight, ch. 7).
+__device__ __forceinline__ uint64_t tr8(uint64_t x) {
+    uint64_t t;
+    t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+    x ^= t ^ (t << 7);
+    t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+    x ^= t ^ (t << 14);
+    t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+    x ^= t ^ (t << 28);
+    return x;
+}
+
+// In-place transpose of the (8 NB) x (8 NB) bit matrix W[k * NRM_TPB] (bit b of row k)
+// by 8 x 8 blocks: block (i, j) transposed lands in block (j, i).  Needs no rows beyond
+// the matrix itself, so the work area is 8 ceil(n/8) words per thread.
+template <int NB>
+__device__ __forceinline__ void transpose_blocks(uint64_t* W) {
 #pragma unroll
-    for (int j = NT / 2; j != 0; j >>= 1) {
+    for (int bi = 0; bi < NB; ++bi) {
+        {
+            uint64_t row[8], x = 0;
 #pragma unroll
-        for (int k = 0; k < NT; k = (k + j + 1) & ~j) {
-            const uint64_t a = W[k * NRM_TPB], b = W[(k + j) * NRM_TPB];
-            const uint64_t t = ((a >> j) ^ b) & m;
-            W[(k + j) * NRM_TPB] = b ^ t;
-            W[k * NRM_TPB] = a ^ (t << j);
+            for (int r = 0; r < 8; ++r) {
+                row[r] = W[(8 * bi + r) * NRM_TPB];
+                x |= ((row[r] >> (8 * bi)) & 0xFFull) << (8 * r);
+            }
+            x = tr8(x);
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                W[(8 * bi + r) * NRM_TPB] =
+                    (row[r] & ~(0xFFull << (8 * bi))) | (((x >> (8 * r)) & 0xFFull) << (8 * bi));
         }
-        m ^= m << (j >> 1);
+#pragma unroll
+        for (int bj = bi + 1; bj < NB; ++bj) {
+            uint64_t ri[8], rj[8], x = 0, y = 0;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                ri[r] = W[(8 * bi + r) * NRM_TPB];
+                rj[r] = W[(8 * bj + r) * NRM_TPB];
+                x |= ((ri[r] >> (8 * bj)) & 0xFFull) << (8 * r);
+                y |= ((rj[r] >> (8 * bi)) & 0xFFull) << (8 * r);
+            }
+            x = tr8(x);
+            y = tr8(y);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                W[(8 * bi + r) * NRM_TPB] =
+                    (ri[r] & ~(0xFFull << (8 * bj))) | (((y >> (8 * r)) & 0xFFull) << (8 * bj));
+                W[(8 * bj + r) * NRM_TPB] =
+                    (rj[r] & ~(0xFFull << (8 * bi))) | (((x >> (8 * r)) & 0xFFull) << (8 * bi));
+            }
+        }
     }
 }
 
-template <int NCH, int NT>
+template <int NCH, int NB>
 __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64_t seed, int64_t tt,
                                                   float2* __restrict__ partial, int64_t n_tiles) {
     extern __shared__ uint64_t smem[];
@@ -127,7 +174,7 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64
     const int64_t l = (int64_t)blockIdx.y * NRM_TPB + tid;
     uint64_t* tab = smem;                                          // [NCH][16], shared
     uint64_t* sA = smem + NCH * 16 + tid;                          // A_c at sA[c * NRM_TPB]
-    uint64_t* sW = smem + NCH * 16 + (int64_t)n * NRM_TPB + tid;   // NT work rows
+    uint64_t* sW = smem + NCH * 16 + (int64_t)n * NRM_TPB + tid;   // 8 NB work rows
 
     // ---- A_l in M_n from the counter RNG
     const uint64_t key = sm64_key(seed, (uint64_t)(l < L ? l : 0));
@@ -209,8 +256,8 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64
             clo ^= Gc & m1;
             chi ^= Gc & m2;
         }
-        for (int c = n; c < NT; ++c) sW[c * NRM_TPB] = 0;
-        transpose_rows<NT>(sW);                // sW[k] = column k of P = D g_k
+        for (int c = n; c < 8 * NB; ++c) sW[c * NRM_TPB] = 0;
+        transpose_blocks<NB>(sW);              // sW[k] = column k of P = D g_k
         const uint64_t kdlo = clo;             // K_kk mod 2
         const uint64_t kdhi = chi ^ pacc;      // bit 1 of K_kk
         uint64_t lin = 0;
@@ -278,13 +325,13 @@ __global__ void k_norm_reduce(const float2* __restrict__ partial, int64_t n_tile
 template <int NCH>
 static lrs_status launch_norm_t(lrs_ctx* ctx, int64_t L, uint64_t seed, int64_t tt, float2* partial,
                                 int64_t n_tiles, cudaStream_t st) {
-    constexpr int NT = NCH <= 8 ? 32 : 64;
-    const size_t smem = ((size_t)NCH * 16 + (size_t)(ctx->n + NT) * NRM_TPB) * sizeof(uint64_t);
-    LRS_CUDA(cudaFuncSetAttribute(k_norm<NCH, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    constexpr int NB = (NCH + 1) / 2;   // 8 x 8 blocks per side of the transposed matrix
+    const size_t smem = ((size_t)NCH * 16 + (size_t)(ctx->n + 8 * NB) * NRM_TPB) * sizeof(uint64_t);
+    LRS_CUDA(cudaFuncSetAttribute(k_norm<NCH, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
     dim3 grid((unsigned)n_tiles, (unsigned)lblocks);
-    k_norm<NCH, NT><<<grid, NRM_TPB, smem, st>>>(ctx->view(), L, seed, tt, partial, n_tiles);
+    k_norm<NCH, NB><<<grid, NRM_TPB, smem, st>>>(ctx->view(), L, seed, tt, partial, n_tiles);
     LRS_LAUNCH_CHECK("norm kernel");
     return LRS_OK;
 }
