@@ -351,11 +351,20 @@ lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
  * per-term exact values.  The paper has no counterpart.
  *   LRS_TUNE_AMP_BLOCKS_PER_SM    amplitude grid target, blocks per SM (1..64, 8)
  *   LRS_TUNE_NORM_MAX_TILES       norm estimate, maximum term tiles (1..2^20, 2048)
- *   LRS_TUNE_MC_CHAINS_PER_BLOCK  Metropolis chains per block (1..64, 64)       */
+ *   LRS_TUNE_MC_CHAINS_PER_BLOCK  Metropolis chains per block (1..64, 64)
+ *   LRS_TUNE_NORM_MAX_FOLDS       norm estimate: a term with n - |v| <= this
+ *                                 value (-1..12, 12) evaluates its exponential
+ *                                 sum over y = G x, i.e. the form y^T (A+J) y
+ *                                 plus 2 (F s + (A+J) G s) . y restricted to the
+ *                                 n - |v| constraints (F^T y)_k = 0, k not in v,
+ *                                 instead of forming K = G^T (A+J) G; -1 forms
+ *                                 K for every term.  Both give the same exact
+ *                                 per-term value.                              */
 enum {
     LRS_TUNE_AMP_BLOCKS_PER_SM = 0,
     LRS_TUNE_NORM_MAX_TILES = 1,
-    LRS_TUNE_MC_CHAINS_PER_BLOCK = 2
+    LRS_TUNE_MC_CHAINS_PER_BLOCK = 2,
+    LRS_TUNE_NORM_MAX_FOLDS = 3
 };
 lrs_status lrs_set_tuning(lrs_ctx* ctx, int32_t param, int64_t value);
 lrs_status lrs_get_tuning(const lrs_ctx* ctx, int32_t param, int64_t* value);

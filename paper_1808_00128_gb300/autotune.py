@@ -14,6 +14,7 @@ CANDIDATES = {
     "amp_blocks_per_sm": [2, 4, 8, 16, 32],
     "norm_max_tiles": [256, 512, 1024, 2048, 4096],
     "mc_chains_per_block": [16, 32, 64],
+    "norm_max_folds": [-1, 4, 8, 12],
 }
 
 
@@ -63,6 +64,7 @@ def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_pat
     if L:
         eta = torch.empty(L, dtype=torch.float64, device=f"cuda:{sim.device}")
         jobs.append(("norm_max_tiles", L, lambda: sim.norm_estimate(L, seed=1, eta=eta)))
+        jobs.append(("norm_max_folds", L, lambda: sim.norm_estimate(L, seed=1, eta=eta)))
     if chains:
         jobs.append(("mc_chains_per_block", chains, lambda: sim.metropolis(8, seed=1)))
     for knob, batch, fn in jobs:

@@ -19,6 +19,7 @@
 namespace {
 
 constexpr int NRM_TPB = 64;   // A's per block
+constexpr int NRM_MFOLD = 12; // most constraints a change-of-variables term may carry
 
 struct NormTerm {
     uint64_t glo, ghi, v, s, z0;
@@ -26,13 +27,53 @@ struct NormTerm {
     float2 coef;
 };
 
-// S <- S + m1 m2^T + m2 m1^T on the rows in m1 | m2 (one pass: row j gets m2 if j is
-// in m1 and m1 if j is in m2).
-__device__ __forceinline__ void rank2_update(uint64_t* sK, uint64_t m1, uint64_t m2) {
-    for (uint64_t r = m1 | m2; r; r &= r - 1) {
-        const int j = ffs64(r);
-        sK[j * NRM_TPB] ^= (m2 & (0ull - getb(m1, j))) ^ (m1 & (0ull - getb(m2, j)));
+// S <- S + m1 m2^T + m2 m1^T (+ n1 n2^T + n2 n1^T) on the rows in `rows`: row j gets
+// m2 if j is in m1, m1 if j is in m2, and likewise for (n1, n2).  The rows are walked
+// as two 32-bit halves so that finding a row and testing its bits are 32-bit work.
+__device__ __forceinline__ void rank_update(uint64_t* sK, uint64_t rows, uint64_t m1, uint64_t m2, uint64_t n1,
+                                            uint64_t n2) {
+#pragma unroll
+    for (int hw = 0; hw < 2; ++hw) {
+        const uint32_t b1 = (uint32_t)(m1 >> (32 * hw)), b2 = (uint32_t)(m2 >> (32 * hw));
+        const uint32_t b3 = (uint32_t)(n1 >> (32 * hw)), b4 = (uint32_t)(n2 >> (32 * hw));
+        for (uint32_t r = (uint32_t)(rows >> (32 * hw)); r; r &= r - 1) {
+            const int j = __ffs(r) - 1;
+            sK[(j + 32 * hw) * NRM_TPB] ^= (m2 & (0ull - (uint64_t)((b1 >> j) & 1u))) ^
+                                           (m1 & (0ull - (uint64_t)((b2 >> j) & 1u))) ^
+                                           (n2 & (0ull - (uint64_t)((b3 >> j) & 1u))) ^
+                                           (n1 & (0ull - (uint64_t)((b4 >> j) & 1u)));
+        }
     }
+}
+
+// Row part of substituting y_p = h . y into the form (see the fold path in k_norm): row c
+// gets q if c is in h, h if c is in q (q = row p), and h if c is in h and the diagonal
+// of p is odd.  A row's own bit is left as it falls: every read masks it off.
+__device__ __forceinline__ void fold_rows(uint64_t* sK, uint64_t h, uint64_t q, uint64_t op) {
+    const uint64_t hq = q ^ (h & (0ull - op));
+#pragma unroll
+    for (int hw = 0; hw < 2; ++hw) {
+        const uint32_t bh = (uint32_t)(h >> (32 * hw)), bq = (uint32_t)(q >> (32 * hw));
+        for (uint32_t r = (uint32_t)((h | q) >> (32 * hw)); r; r &= r - 1) {
+            const int j = __ffs(r) - 1;
+            sK[(j + 32 * hw) * NRM_TPB] ^= (hq & (0ull - (uint64_t)((bh >> j) & 1u))) ^
+                                           (h & (0ull - (uint64_t)((bq >> j) & 1u)));
+        }
+    }
+}
+
+// Linear terms and signs of eliminating the pair (a, b) (neighbour sets m1 of a without
+// b, m2 of b without a): summing x_a, x_b out leaves the product of the two linear
+// forms, whose constant part goes to the sign and the rest to the linear vectors.
+__device__ __forceinline__ void pivot_terms(int a, int b, uint64_t m1, uint64_t m2, uint64_t& Lre, uint64_t& Lim,
+                                            uint32_t& sre, uint32_t& sim) {
+    const uint64_t c1r = getb(Lre, a), c2r = getb(Lre, b);
+    const uint64_t c1i = getb(Lim, a), c2i = getb(Lim, b);
+    sre ^= (uint32_t)(c1r & c2r);
+    sim ^= (uint32_t)(c1i & c2i);
+    const uint64_t mm = m1 & m2;
+    Lre ^= (m2 & (0ull - c1r)) ^ (m1 & (0ull - c2r)) ^ mm;
+    Lim ^= (m2 & (0ull - c1i)) ^ (m1 & (0ull - c2i)) ^ mm;
 }
 
 // Sum over variables of (-1)^(quadratic form), lifted from Z4 (Eq. (Q), (real)).
@@ -55,12 +96,15 @@ __device__ __forceinline__ void eliminate(uint64_t* sK, uint64_t v, uint64_t odd
         const uint64_t mm = m1 & m2;
         Lre ^= (getb(Lre, bq) ? m1 : 0ull) ^ mm;
         Lim ^= m2 ^ (getb(Lim, bq) ? m1 : 0ull) ^ mm;
-        rank2_update(sK, m1, m2);
+        rank_update(sK, m1 | m2, m1, m2, 0ull, 0ull);
         act &= ~bit64(bq);
     } else {
         e += 1;      // sum over x_X of (-1)^0 = 2 (Re), of (-1)^x_X = 0 (Im)
         zim = true;
     }
+    // Pivots are taken two at a time: the second pair (a2, b2) is found on the matrix
+    // as updated by the first, whose rows are read with that update applied on the
+    // fly, and one pass then applies both rank-2 updates to the remaining rows.
     uint64_t cand = act;
     while (cand) {
         const int a = ffs64(cand);
@@ -73,17 +117,30 @@ __device__ __forceinline__ void eliminate(uint64_t* sK, uint64_t v, uint64_t odd
         const uint64_t ab = bit64(a) | bit64(bq);
         const uint64_t m1 = ra & ~bit64(bq);
         const uint64_t m2 = sK[bq * NRM_TPB] & act & ~ab;
-        const uint64_t c1r = getb(Lre, a), c2r = getb(Lre, bq);
-        const uint64_t c1i = getb(Lim, a), c2i = getb(Lim, bq);
+        pivot_terms(a, bq, m1, m2, Lre, Lim, sre, sim);
         e += 1;
-        sre ^= (uint32_t)(c1r & c2r);
-        sim ^= (uint32_t)(c1i & c2i);
-        const uint64_t mm = m1 & m2;
-        Lre ^= (m2 & (0ull - c1r)) ^ (m1 & (0ull - c2r)) ^ mm;
-        Lim ^= (m2 & (0ull - c1i)) ^ (m1 & (0ull - c2i)) ^ mm;
-        rank2_update(sK, m1, m2);
         act &= ~ab;
         cand &= ~ab;
+        uint64_t n1 = 0, n2 = 0;
+        while (cand) {
+            const int a2 = ffs64(cand);
+            const uint64_t ra2 =
+                (sK[a2 * NRM_TPB] ^ (m2 & (0ull - getb(m1, a2))) ^ (m1 & (0ull - getb(m2, a2)))) & act & ~bit64(a2);
+            if (!ra2) {
+                cand &= ~bit64(a2);
+                continue;
+            }
+            const int b2 = ffs64(ra2);
+            const uint64_t ab2 = bit64(a2) | bit64(b2);
+            n1 = ra2 & ~bit64(b2);
+            n2 = (sK[b2 * NRM_TPB] ^ (m2 & (0ull - getb(m1, b2))) ^ (m1 & (0ull - getb(m2, b2)))) & act & ~ab2;
+            pivot_terms(a2, b2, n1, n2, Lre, Lim, sre, sim);
+            e += 1;
+            act &= ~ab2;
+            cand &= ~ab2;
+            break;
+        }
+        rank_update(sK, (m1 | m2 | n1 | n2) & act, m1, m2, n1, n2);
     }
     e += __popcll(act);
     if (Lre & act) zre = true;
@@ -161,13 +218,79 @@ __device__ __forceinline__ void transpose_blocks(uint64_t* W) {
     }
 }
 
+// Per-term quantities every A-block of the norm kernel needs, computed once per call
+// (one thread per term, struct-of-arrays over the term index alpha < cap):
+//   J[c][alpha]  row c of J = M F^T off the diagonal
+//   z0, u        z0 = G s (bit c = s . G_c) and u = F s (bit c = s . F_c)
+//   piv          for a term with n - |v| <= max_folds: the pivot set of the reduced
+//                echelon form of the constraints f_k = column k of F (k not in v),
+//                else 0; f[i][alpha] the i-th reduced constraint (it holds exactly
+//                one pivot, its own)
+struct NormPrep {
+    uint64_t *J, *z0, *u, *piv, *f;
+};
+
+__global__ void __launch_bounds__(NRM_TPB) k_norm_prep(TermsView T, int max_folds, NormPrep P) {
+    extern __shared__ uint64_t sF[];   // row c of this thread's F at sF[c * NRM_TPB + tid]
+    const int n = T.n, tid = threadIdx.x;
+    const int64_t alpha = (int64_t)blockIdx.x * NRM_TPB + tid;
+    if (alpha >= T.cap) return;        // no block-wide synchronisation below
+    uint64_t* F = sF + tid;
+    for (int c = 0; c < n; ++c) F[c * NRM_TPB] = T.F[(int64_t)c * T.cap + alpha];
+    const uint64_t s = T.s[alpha], v = T.v[alpha];
+    uint64_t z0 = 0, u = 0;
+    for (int c = 0; c < n; ++c) {
+        z0 |= (uint64_t)par64(s & T.G[(int64_t)c * T.cap + alpha]) << c;
+        u |= (uint64_t)par64(s & F[c * NRM_TPB]) << c;
+        const uint64_t Mc = T.M[(int64_t)c * T.cap + alpha];
+        uint64_t jrow = 0;
+        for (int d = 0; d < n; ++d) jrow |= (uint64_t)par64(Mc & F[d * NRM_TPB]) << d;
+        P.J[(int64_t)c * T.cap + alpha] = jrow & ~bit64(c);
+    }
+    P.z0[alpha] = z0;
+    P.u[alpha] = u;
+    const int mf = n - __popcll(v);
+    uint64_t piv = 0;
+    if (mf <= max_folds) {
+        uint64_t f[NRM_MFOLD];
+        uint64_t ks = ~v & T.nmask;
+#pragma unroll
+        for (int i = 0; i < NRM_MFOLD; ++i) {
+            f[i] = 0;
+            if (i < mf) {
+                const int k = ffs64(ks);
+                ks &= ks - 1;
+                for (int c = 0; c < n; ++c) f[i] |= getb(F[c * NRM_TPB], k) << c;
+            }
+        }
+        // reduced echelon form (the f_k are independent: F is invertible); pivot of f_i
+        // = its lowest bit when it is processed, then cleared from every other f_j
+#pragma unroll
+        for (int i = 0; i < NRM_MFOLD; ++i) {
+            if (i < mf) {
+                const int p = ffs64(f[i]);
+                piv |= bit64(p);
+#pragma unroll
+                for (int j = 0; j < NRM_MFOLD; ++j)
+                    if (j != i && j < mf && getb(f[j], p)) f[j] ^= f[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NRM_MFOLD; ++i)
+            if (i < mf) P.f[(int64_t)i * T.cap + alpha] = f[i];
+    }
+    P.piv[alpha] = piv;
+}
+
 template <int NCH, int NB>
-__global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64_t seed, int64_t tt,
-                                                  float2* __restrict__ partial, int64_t n_tiles) {
+__global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64_t L, uint64_t seed, int64_t tt,
+                                                  float2* __restrict__ partial, int64_t n_tiles,
+                                                  int max_folds) {
     extern __shared__ uint64_t smem[];
-    __shared__ uint64_t tG[64], tJ[64], tF[64], tM[64];
+    __shared__ uint64_t tG[64], tJ[64];
     __shared__ NormTerm tS;
-    __shared__ unsigned long long tz0;
+    __shared__ unsigned long long tz0, tU, tH[NRM_MFOLD];
+    __shared__ int tPiv[NRM_MFOLD];
     const int n = T.n;
     const uint64_t nmask = T.nmask;
     const int tid = threadIdx.x;
@@ -204,42 +327,85 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64
         const int64_t alpha = tile * tt + t;
         if (alpha >= T.cap) break;              // uniform across the block
         __syncthreads();
+        // Terms whose v misses at most max_folds qubits sum over y = G x directly: the
+        // form becomes y^T D y + 2 (F s + D G s) . y on the subspace F^T y = 0 off v.
+        const uint64_t vv = T.v[alpha];
+        const int mf = n - __popcll(vv);
+        const bool fold = mf <= max_folds;   // max_folds <= NRM_MFOLD
         if (tid < n) {
-            tG[tid] = T.G[(int64_t)tid * T.cap + alpha];
-            tF[tid] = T.F[(int64_t)tid * T.cap + alpha];
-            tM[tid] = T.M[(int64_t)tid * T.cap + alpha];
+            tJ[tid] = P.J[(int64_t)tid * T.cap + alpha];
+            if (!fold) tG[tid] = T.G[(int64_t)tid * T.cap + alpha];
+        }
+        if (fold && tid < mf) {
+            // constraint tid: y_p = h . y with p its pivot and h free of every pivot
+            const uint64_t pv = P.piv[alpha], f = P.f[(int64_t)tid * T.cap + alpha];
+            tPiv[tid] = ffs64(f & pv);
+            tH[tid] = f & ~pv;
         }
         if (tid == 0) {
             tS.glo = T.glo[alpha]; tS.ghi = T.ghi[alpha];
-            tS.v = T.v[alpha]; tS.s = T.s[alpha];
+            tS.v = vv; tS.s = T.s[alpha];
             tS.omega = T.omega[alpha]; tS.coef = T.coef[alpha];
-            tz0 = 0ull;
+            tz0 = P.z0[alpha];
+            tU = P.u[alpha];
         }
         __syncthreads();
-        if (tid < n) {
-            // row tid of J = (M F^T) off the diagonal; bit tid of z0 = s G^T
-            uint64_t jrow = 0;
-            const uint64_t Mc = tM[tid];
-            for (int c = 0; c < n; ++c)
-                if (c != tid) jrow |= (uint64_t)par64(Mc & tF[c]) << c;
-            tJ[tid] = jrow;
-            if (par64(tS.s & tG[tid])) atomicOr(&tz0, 1ull << tid);
-        }
-        for (int e = tid; e < NCH * 16; e += NRM_TPB) {    // Four-Russians table of G rows
-            const int ch = e >> 4, p = e & 15;
-            uint64_t r = 0;
+        if (!fold) {
+            for (int e = tid; e < NCH * 16; e += NRM_TPB) {    // Four-Russians table of G rows
+                const int ch = e >> 4, p = e & 15;
+                uint64_t r = 0;
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (((p >> b) & 1) && 4 * ch + b < n) r ^= tG[4 * ch + b];
-            tab[e] = r;
+                for (int b = 0; b < 4; ++b)
+                    if (((p >> b) & 1) && 4 * ch + b < n) r ^= tG[4 * ch + b];
+                tab[e] = r;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         const NormTerm S = tS;
         if ((S.omega >> 3) & 1u) continue;     // zero term (uniform)
         // diag(A + J) mod 4 as bit-planes: lo = adlo ^ glo, hi = adhi ^ ghi ^ (adlo & glo)
         const uint64_t dlo = adlo ^ S.glo;
         const uint64_t dhi = adhi ^ S.ghi ^ (adlo & S.glo);
         const uint64_t z0 = tz0;
+        uint64_t act, odd, Lb;
+        uint32_t sKs;
+        if (fold) {
+            // rows of D off the diagonal, D z0 (mod 2) and the pair parities of z0
+            uint64_t dz0 = 0, pz = 0;
+            for (int c = 0; c < n; ++c) {
+                const uint64_t Doff = sA[c * NRM_TPB] ^ tJ[c];
+                sW[c * NRM_TPB] = Doff;
+                if (getb(z0, c)) {
+                    dz0 ^= Doff;
+                    pz ^= Doff & z0 & ((c == 63) ? 0ull : (~0ull << (c + 1)));
+                }
+            }
+            dz0 ^= dlo & z0;
+            sKs = ((uint32_t)__popcll(z0 & dlo) + 2u * (uint32_t)__popcll(z0 & dhi) + 2u * par64(pz)) & 3u;
+            // Z4 form on y: diagonal D_cc + 2 (u + D z0)_c, off-diagonal D (mod 2)
+            odd = dlo;
+            Lb = dhi ^ tU ^ dz0;
+            act = nmask;
+            for (int i = 0; i < mf; ++i) {
+                // substitute y_p = h . y (h free of pivots): with y_p = sum_h y - 2 sum_pairs
+                // (mod 4), the diagonal of p spreads over h (with carry) and onto the
+                // pairs of h, and the row q of p couples h with q
+                const int p = tPiv[i];
+                const uint64_t h = tH[i];
+                const uint64_t q = sW[p * NRM_TPB] & act & ~bit64(p);
+                const uint64_t op = getb(odd, p), lp = getb(Lb, p);
+                Lb ^= h & ((0ull - lp) ^ (odd & (0ull - op)) ^ q);
+                odd ^= h & (0ull - op);
+                fold_rows(sW, h, q, op);
+                act &= ~bit64(p);
+            }
+            odd &= act;
+            Lb &= act;
+            for (uint64_t r = act; r; r &= r - 1) {
+                const int c = ffs64(r);
+                sW[c * NRM_TPB] = (sW[c * NRM_TPB] ^ (getb(odd, c) ? odd : 0ull)) & act & ~bit64(c);
+            }
+        } else {
         // P = D G row by row (D = (A + J) mod 2 with its diagonal), the pair
         // parities sum_{c<d in g_k} D_cd for every k at once, and those of z0.
         uint64_t pacc = 0, pz = 0, clo = 0, chi = 0;
@@ -267,18 +433,19 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, int64_t L, uint64
             sW[k * NRM_TPB] = Kr;
             lin |= (getb(S.s, k) ^ (uint64_t)par64(S.s & Kr)) << k;
         }
-        const uint32_t sKs = ((uint32_t)__popcll(z0 & dlo) + 2u * (uint32_t)__popcll(z0 & dhi) +
-                              2u * par64(pz)) & 3u;
+        sKs = ((uint32_t)__popcll(z0 & dlo) + 2u * (uint32_t)__popcll(z0 & dhi) + 2u * par64(pz)) & 3u;
         // B = K|_v + 2 diag(s + sK); lifted Z2 form: S_jk = B_jk + odd_j odd_k, X adjacent to odd
-        const uint64_t odd = kdlo & S.v;
-        const uint64_t Lb = (kdhi ^ lin) & S.v;
+        odd = kdlo & S.v;
+        Lb = (kdhi ^ lin) & S.v;
+        act = S.v;
         for (uint64_t vr = S.v; vr; vr &= vr - 1) {
             const int k = ffs64(vr);
             const uint64_t Kr = sW[k * NRM_TPB];
             sW[k * NRM_TPB] = (Kr ^ (getb(odd, k) ? odd : 0ull)) & S.v & ~bit64(k);
         }
+        }
         int re_s, im_s, e;
-        eliminate(sW, S.v, odd, Lb, re_s, im_s, e);
+        eliminate(sW, act, odd, Lb, re_s, im_s, e);
         if (re_s == 0 && im_s == 0) continue;
         // zeta = re_s + i im_s as sqrt2^{both} e^{i pi phz / 4}
         int phz;
@@ -323,15 +490,16 @@ __global__ void k_norm_reduce(const float2* __restrict__ partial, int64_t n_tile
 }  // namespace
 
 template <int NCH>
-static lrs_status launch_norm_t(lrs_ctx* ctx, int64_t L, uint64_t seed, int64_t tt, float2* partial,
-                                int64_t n_tiles, cudaStream_t st) {
+static lrs_status launch_norm_t(lrs_ctx* ctx, const NormPrep& P, int64_t L, uint64_t seed, int64_t tt,
+                                float2* partial, int64_t n_tiles, cudaStream_t st) {
     constexpr int NB = (NCH + 1) / 2;   // 8 x 8 blocks per side of the transposed matrix
     const size_t smem = ((size_t)NCH * 16 + (size_t)(ctx->n + 8 * NB) * NRM_TPB) * sizeof(uint64_t);
     LRS_CUDA(cudaFuncSetAttribute(k_norm<NCH, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
     dim3 grid((unsigned)n_tiles, (unsigned)lblocks);
-    k_norm<NCH, NB><<<grid, NRM_TPB, smem, st>>>(ctx->view(), L, seed, tt, partial, n_tiles);
+    k_norm<NCH, NB><<<grid, NRM_TPB, smem, st>>>(ctx->view(), P, L, seed, tt, partial, n_tiles,
+                                                  (int)ctx->tune_norm_folds);
     LRS_LAUNCH_CHECK("norm kernel");
     return LRS_OK;
 }
@@ -343,27 +511,40 @@ lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* 
     while ((ctx->cap + tt - 1) / tt > ctx->tune_norm_tiles) tt *= 2;
     const int64_t n_tiles = (ctx->cap + tt - 1) / tt;
     void* scr = nullptr;
-    lrs_status rc = lrs_scratch(ctx, (size_t)L * n_tiles * sizeof(float2), &scr);
+    // scratch: partial sums, then the per-term prep arrays
+    const size_t part_bytes = ((size_t)L * n_tiles * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t words = (size_t)ctx->cap * (size_t)(ctx->n + 3 + NRM_MFOLD);
+    lrs_status rc = lrs_scratch(ctx, part_bytes + words * sizeof(uint64_t), &scr);
     if (rc != LRS_OK) return rc;
     float2* partial = (float2*)scr;
+    NormPrep P;
+    P.J = (uint64_t*)((char*)scr + part_bytes);
+    P.z0 = P.J + (size_t)ctx->n * ctx->cap;
+    P.u = P.z0 + ctx->cap;
+    P.piv = P.u + ctx->cap;
+    P.f = P.piv + ctx->cap;
+    const int max_folds = (int)ctx->tune_norm_folds;
+    k_norm_prep<<<(unsigned)((ctx->cap + NRM_TPB - 1) / NRM_TPB), NRM_TPB,
+                  (size_t)ctx->n * NRM_TPB * sizeof(uint64_t), st>>>(ctx->view(), max_folds, P);
+    LRS_LAUNCH_CHECK("norm prep kernel");
     if ((L + NRM_TPB - 1) / NRM_TPB > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "L too large");
     switch ((ctx->n + 3) / 4) {
-        case 1: rc = launch_norm_t<1>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 2: rc = launch_norm_t<2>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 3: rc = launch_norm_t<3>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 4: rc = launch_norm_t<4>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 5: rc = launch_norm_t<5>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 6: rc = launch_norm_t<6>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 7: rc = launch_norm_t<7>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 8: rc = launch_norm_t<8>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 9: rc = launch_norm_t<9>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 10: rc = launch_norm_t<10>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 11: rc = launch_norm_t<11>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 12: rc = launch_norm_t<12>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 13: rc = launch_norm_t<13>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 14: rc = launch_norm_t<14>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        case 15: rc = launch_norm_t<15>(ctx, L, seed, tt, partial, n_tiles, st); break;
-        default: rc = launch_norm_t<16>(ctx, L, seed, tt, partial, n_tiles, st); break;
+        case 1: rc = launch_norm_t<1>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 2: rc = launch_norm_t<2>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 3: rc = launch_norm_t<3>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 4: rc = launch_norm_t<4>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 5: rc = launch_norm_t<5>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 6: rc = launch_norm_t<6>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 7: rc = launch_norm_t<7>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 8: rc = launch_norm_t<8>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 9: rc = launch_norm_t<9>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 10: rc = launch_norm_t<10>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 11: rc = launch_norm_t<11>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 12: rc = launch_norm_t<12>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 13: rc = launch_norm_t<13>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 14: rc = launch_norm_t<14>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 15: rc = launch_norm_t<15>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        default: rc = launch_norm_t<16>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
     }
     if (rc != LRS_OK) return rc;
     k_norm_reduce<<<(unsigned)L, 256, 0, st>>>(partial, n_tiles, L, eta);

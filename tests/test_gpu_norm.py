@@ -21,7 +21,25 @@ def _sim(n, ops, chi, mode, seed=0, ccz_mode="proj", alpha0=0, chi_total=None):
     return sim
 
 
+# per-term paths of the kernel: -1 forms K = G^T (A+J) G for every term; 0 sums over
+# y = G x for terms with v = all qubits; 12 for terms with up to 12 qubits outside v
+FOLDS = (-1, 0, 12)
+
+
+def _etas(sim, L, seed):
+    out = {}
+    for f in FOLDS:
+        sim.set_tuning("norm_max_folds", f)
+        out[f] = sim.norm_estimate(L, seed=seed).cpu().numpy()
+    sim.set_tuning("norm_max_folds", 12)
+    return out
+
+
 def _check(eta_gpu, overl, n, norm2):
+    if isinstance(eta_gpu, dict):
+        for f, e in eta_gpu.items():
+            _check(e, overl, n, norm2)
+        return
     want = (2.0 ** n) * np.abs(overl) ** 2
     tol = 1e-5 * np.maximum(want, norm2)
     bad = np.abs(eta_gpu - want) > tol
@@ -38,6 +56,7 @@ def test_tiny_config_eta_parity():
     terms, coefs, _ = oracle_terms(n, ops, chi, "exact")
     ov = oracle_overlaps(terms, coefs, n, 21, L, parallel=True)
     _check(eta.cpu().numpy(), ov, n, 1.0)
+    _check(_etas(sim, L, 21), ov, n, 1.0)
     assert mean == pytest.approx(float(np.mean(eta.cpu().numpy())), rel=1e-12)
     sim.close()
 
@@ -63,7 +82,7 @@ def test_edge_widths_eta_parity(n):
     chi = 4 * (2 if n >= 3 else 1)
     sim = _sim(n, ops, chi, "exact")
     L = 40
-    eta = sim.norm_estimate(L, seed=n).cpu().numpy()
+    eta = _etas(sim, L, n)
     terms, coefs, _ = oracle_terms(n, ops, chi, "exact", parallel=n > 30)
     ov = oracle_overlaps(terms, coefs, n, n, L, parallel=True)
     _check(eta, ov, n, 1.0)
@@ -77,7 +96,7 @@ def test_full_v_register():
     ops = [("H", q) for q in range(n)] + [("CZ", q, q + 1) for q in range(0, n - 1, 3)]
     ops += [("T", 7), ("S", 9)]
     sim = _sim(n, ops, 2, "exact")
-    eta = sim.norm_estimate(32, seed=4).cpu().numpy()
+    eta = _etas(sim, 32, 4)
     terms, coefs, _ = oracle_terms(n, ops, 2, "exact")
     ov = oracle_overlaps(terms, coefs, n, 4, 32, parallel=True)
     _check(eta, ov, n, 1.0)
@@ -92,7 +111,7 @@ def test_mid_slice_eta_parity():
     alpha0, chi = 777, 64
     sim = _sim(n, ops, chi, "sparsify", seed=seed, alpha0=alpha0, chi_total=chi_total)
     L = 64
-    eta = sim.norm_estimate(L, seed=99).cpu().numpy()
+    eta = _etas(sim, L, 99)
     terms, coefs, _ = oracle_terms(n, ops, chi_total, "sparsify", seed=seed,
                                    alphas=range(alpha0, alpha0 + chi), parallel=True)
     ov = oracle_overlaps(terms, coefs, n, 99, L, parallel=True)
@@ -111,4 +130,18 @@ def test_hidden_shift_norm_is_one():
     e = eta.cpu().numpy()
     assert np.all(np.abs(e - 1.0) <= 1e-5), e[np.abs(e - 1.0) > 1e-5][:5]
     assert mean == pytest.approx(1.0, abs=1e-5)
+    sim.close()
+
+
+def test_fold_paths_agree_at_scale():
+    """n=40 benchmark circuit, 4096 terms, L = 128: the change-of-variables path and
+    the K path give the same eta to FP32 summation order."""
+    require_cuda()
+    cfg = workloads.config_mid()
+    n, ops, seed = cfg["n"], cfg["ops"], cfg["seed"]
+    sim = _sim(n, ops, 4096, "sparsify", seed=seed, chi_total=cfg["chi"])
+    e = _etas(sim, 128, 7)
+    ref = e[-1]
+    for f in FOLDS[1:]:
+        assert np.all(np.abs(e[f] - ref) <= 1e-5 * np.maximum(np.abs(ref), 4096 / cfg["chi"])), f
     sim.close()
