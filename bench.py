@@ -195,6 +195,18 @@ def oracle_step_time(cfg, rates):
     return chi * (t_build + (B_X + C_CH * (T_MC + 1)) * t_amp + L_A * t_inner)
 
 
+def norm_ops_per_unit(n, vw, max_folds):
+    """32-bit integer ops per (A, term) of the norm estimate, by the path a term takes.
+    K path (n - |v| > max_folds): the two products of K = G^T (A+J) G, 8 n^2, plus the
+    pairwise elimination on |v| variables, 4 |v|^2.  Change-of-variables path: the rows
+    of A + J and the lifted rows, 8 n, one rank-2 update per folded constraint, 5 n
+    each, and the same elimination, 4 |v|^2."""
+    import numpy as np
+    vw = np.asarray(vw)
+    m = n - vw
+    return np.where(m <= max_folds, 8 * n + 5 * m * n + 4 * vw ** 2, 8 * n * n + 4 * vw ** 2)
+
+
 def units_per_step(chi):
     return chi * (B_X + C_CH * (T_MC + 1))
 
@@ -588,7 +600,7 @@ def main():
         sim.metropolis(T_MC, seed=3000 + step_idx, x_out=xo, p_out=po)
         mark(6)
 
-    launches_per_step = 1 + 1 + 2 + 2 + 1 + 2 + (1 + 2 * T_MC + 1)
+    launches_per_step = 1 + 1 + 2 + 3 + 1 + 2 + (1 + 2 * T_MC + 1)
 
     for w in range(args.warmup):
         step(step_idx=w)
@@ -632,8 +644,9 @@ def main():
     ops = {
         "apply_clifford": chi * clifford_ops_per_term(n, low),
         "amplitude": chi * B_X * (8 * ((n + 3) // 4) + 16),
-        "norm_estimate": chi * L_A * float(np.mean(8 * n * n + 4 * vw ** 2)),
+        "norm_estimate": chi * L_A * float(np.mean(norm_ops_per_unit(n, vw, sim.get_tuning("norm_max_folds")))),
     }
+    norm_formula = chi * L_A * float(np.mean(8 * n * n + 4 * vw ** 2))
     mc_bytes = T_MC * (chi * C_CH * (16 + 16 * 0.5) + chi * 16 * n)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -644,6 +657,9 @@ def main():
         ach = ops[p] / (phase_ms[p] * 1e-3)
         rows[p] = {"bound": "alu", "achieved": ach / 1e12, "peak": alu_measured / 1e12,
                    "unit": "Tops/s", "frac": ach / alu_measured, "ms": phase_ms[p]}
+    # the same phase counted with 8 n^2 + 4 |v|^2 per (A, term) for every term, as if
+    # K = G^T (A+J) G were formed (the change-of-variables path skips that product)
+    rows["norm_estimate"]["frac_k_formula"] = norm_formula / (phase_ms["norm_estimate"] * 1e-3) / alu_measured
     ach = mc_bytes / (phase_ms["metropolis"] * 1e-3) / 1e9
     rows["metropolis"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                           "frac": ach / hbm, "ms": phase_ms["metropolis"]}
@@ -651,9 +667,9 @@ def main():
     roof = dict(rows[dom])
     roof["kernel"] = dom
     # DRAM bytes per launch from ncu (profiles/): dram__bytes_read.sum + dram__bytes_write.sum
-    # of the n=40 chi=2^15 L=128 capture, scaled by the (term, A-block) units of a full
-    # chi=2^16 L=256 launch (4x); null for kernels changed since their capture.
-    traffic = {"norm_estimate": 4 * 32.957952e6}
+    # of the kernel's capture, scaled to a full launch; null for kernels changed since
+    # their capture.
+    traffic = {}
     roof["traffic"] = traffic.get(dom) if not args.small else None
     roof.pop("ms", None)
     roof["peak_source"] = ("measured LOP3 probe on this GPU" if roof["bound"] == "alu"

@@ -20,6 +20,7 @@ namespace {
 
 constexpr int NRM_TPB = 64;   // A's per block
 constexpr int NRM_MFOLD = 12; // most constraints a change-of-variables term may carry
+constexpr int NRM_PIVOTS = 4; // elimination pairs applied per pass over the rows
 
 struct NormTerm {
     uint64_t glo, ghi, v, s, z0;
@@ -29,35 +30,43 @@ struct NormTerm {
 
 // S <- S + m1 m2^T + m2 m1^T (+ n1 n2^T + n2 n1^T) on the rows in `rows`: row j gets
 // m2 if j is in m1, m1 if j is in m2, and likewise for (n1, n2).  The rows are walked
-// as two 32-bit halves so that finding a row and testing its bits are 32-bit work.
+// by their lowest set bit in two 32-bit halves, so each membership test is one AND
+// with that bit and each addition a predicated XOR.  Rows are stored unmasked: every
+// read of a row masks it with the active set (and drops its own bit).
 __device__ __forceinline__ void rank_update(uint64_t* sK, uint64_t rows, uint64_t m1, uint64_t m2, uint64_t n1,
                                             uint64_t n2) {
 #pragma unroll
     for (int hw = 0; hw < 2; ++hw) {
         const uint32_t b1 = (uint32_t)(m1 >> (32 * hw)), b2 = (uint32_t)(m2 >> (32 * hw));
         const uint32_t b3 = (uint32_t)(n1 >> (32 * hw)), b4 = (uint32_t)(n2 >> (32 * hw));
-        for (uint32_t r = (uint32_t)(rows >> (32 * hw)); r; r &= r - 1) {
-            const int j = __ffs(r) - 1;
-            sK[(j + 32 * hw) * NRM_TPB] ^= (m2 & (0ull - (uint64_t)((b1 >> j) & 1u))) ^
-                                           (m1 & (0ull - (uint64_t)((b2 >> j) & 1u))) ^
-                                           (n2 & (0ull - (uint64_t)((b3 >> j) & 1u))) ^
-                                           (n1 & (0ull - (uint64_t)((b4 >> j) & 1u)));
+        for (uint32_t r = (uint32_t)(rows >> (32 * hw)); r;) {
+            const uint32_t lb = r & (0u - r);
+            r ^= lb;
+            uint64_t x = 0;
+            if (b1 & lb) x ^= m2;
+            if (b2 & lb) x ^= m1;
+            if (b3 & lb) x ^= n2;
+            if (b4 & lb) x ^= n1;
+            sK[(__ffs(lb) - 1 + 32 * hw) * NRM_TPB] ^= x;
         }
     }
 }
 
 // Row part of substituting y_p = h . y into the form (see the fold path in k_norm): row c
 // gets q if c is in h, h if c is in q (q = row p), and h if c is in h and the diagonal
-// of p is odd.  A row's own bit is left as it falls: every read masks it off.
+// of p is odd.  Rows stay unmasked (see rank_update).
 __device__ __forceinline__ void fold_rows(uint64_t* sK, uint64_t h, uint64_t q, uint64_t op) {
     const uint64_t hq = q ^ (h & (0ull - op));
 #pragma unroll
     for (int hw = 0; hw < 2; ++hw) {
         const uint32_t bh = (uint32_t)(h >> (32 * hw)), bq = (uint32_t)(q >> (32 * hw));
-        for (uint32_t r = (uint32_t)((h | q) >> (32 * hw)); r; r &= r - 1) {
-            const int j = __ffs(r) - 1;
-            sK[(j + 32 * hw) * NRM_TPB] ^= (hq & (0ull - (uint64_t)((bh >> j) & 1u))) ^
-                                           (h & (0ull - (uint64_t)((bq >> j) & 1u)));
+        for (uint32_t r = (uint32_t)((h | q) >> (32 * hw)); r;) {
+            const uint32_t lb = r & (0u - r);
+            r ^= lb;
+            uint64_t x = 0;
+            if (bh & lb) x ^= hq;
+            if (bq & lb) x ^= h;
+            sK[(__ffs(lb) - 1 + 32 * hw) * NRM_TPB] ^= x;
         }
     }
 }
@@ -102,45 +111,68 @@ __device__ __forceinline__ void eliminate(uint64_t* sK, uint64_t v, uint64_t odd
         e += 1;      // sum over x_X of (-1)^0 = 2 (Re), of (-1)^x_X = 0 (Im)
         zim = true;
     }
-    // Pivots are taken two at a time: the second pair (a2, b2) is found on the matrix
-    // as updated by the first, whose rows are read with that update applied on the
-    // fly, and one pass then applies both rank-2 updates to the remaining rows.
+    // Pivots are taken NRM_PIVOTS at a time: pair k is found on the matrix as updated by
+    // pairs 0..k-1, whose rows are read with those updates applied on the fly, and one
+    // pass over the remaining rows then applies all the rank-2 updates together.
     uint64_t cand = act;
     while (cand) {
-        const int a = ffs64(cand);
-        const uint64_t ra = sK[a * NRM_TPB] & act & ~bit64(a);
-        if (!ra) {           // isolated: stays isolated
-            cand &= ~bit64(a);
-            continue;
-        }
-        const int bq = ffs64(ra);
-        const uint64_t ab = bit64(a) | bit64(bq);
-        const uint64_t m1 = ra & ~bit64(bq);
-        const uint64_t m2 = sK[bq * NRM_TPB] & act & ~ab;
-        pivot_terms(a, bq, m1, m2, Lre, Lim, sre, sim);
-        e += 1;
-        act &= ~ab;
-        cand &= ~ab;
-        uint64_t n1 = 0, n2 = 0;
-        while (cand) {
-            const int a2 = ffs64(cand);
-            const uint64_t ra2 =
-                (sK[a2 * NRM_TPB] ^ (m2 & (0ull - getb(m1, a2))) ^ (m1 & (0ull - getb(m2, a2)))) & act & ~bit64(a2);
-            if (!ra2) {
-                cand &= ~bit64(a2);
-                continue;
+        uint64_t P1[NRM_PIVOTS], P2[NRM_PIVOTS];
+        int np = 0;
+#pragma unroll
+        for (int k = 0; k < NRM_PIVOTS; ++k) {
+            P1[k] = 0;
+            P2[k] = 0;
+            if (np != k) continue;
+            while (cand) {
+                const int a = ffs64(cand);
+                uint64_t ra = sK[a * NRM_TPB];
+#pragma unroll
+                for (int i = 0; i < k; ++i) ra ^= (P2[i] & (0ull - getb(P1[i], a))) ^ (P1[i] & (0ull - getb(P2[i], a)));
+                ra &= act & ~bit64(a);
+                if (!ra) {       // isolated: stays isolated
+                    cand &= ~bit64(a);
+                    continue;
+                }
+                const int bq = ffs64(ra);
+                uint64_t rb = sK[bq * NRM_TPB];
+#pragma unroll
+                for (int i = 0; i < k; ++i)
+                    rb ^= (P2[i] & (0ull - getb(P1[i], bq))) ^ (P1[i] & (0ull - getb(P2[i], bq)));
+                const uint64_t ab = bit64(a) | bit64(bq);
+                P1[k] = ra & ~bit64(bq);
+                P2[k] = rb & act & ~ab;
+                pivot_terms(a, bq, P1[k], P2[k], Lre, Lim, sre, sim);
+                e += 1;
+                act &= ~ab;
+                cand &= ~ab;
+                ++np;
+                break;
             }
-            const int b2 = ffs64(ra2);
-            const uint64_t ab2 = bit64(a2) | bit64(b2);
-            n1 = ra2 & ~bit64(b2);
-            n2 = (sK[b2 * NRM_TPB] ^ (m2 & (0ull - getb(m1, b2))) ^ (m1 & (0ull - getb(m2, b2)))) & act & ~ab2;
-            pivot_terms(a2, b2, n1, n2, Lre, Lim, sre, sim);
-            e += 1;
-            act &= ~ab2;
-            cand &= ~ab2;
-            break;
         }
-        rank_update(sK, (m1 | m2 | n1 | n2) & act, m1, m2, n1, n2);
+        uint64_t rows = 0;
+#pragma unroll
+        for (int k = 0; k < NRM_PIVOTS; ++k) rows |= P1[k] | P2[k];
+        rows &= act;
+#pragma unroll
+        for (int hw = 0; hw < 2; ++hw) {
+            uint32_t B1[NRM_PIVOTS], B2[NRM_PIVOTS];
+#pragma unroll
+            for (int k = 0; k < NRM_PIVOTS; ++k) {
+                B1[k] = (uint32_t)(P1[k] >> (32 * hw));
+                B2[k] = (uint32_t)(P2[k] >> (32 * hw));
+            }
+            for (uint32_t r = (uint32_t)(rows >> (32 * hw)); r;) {
+                const uint32_t lb = r & (0u - r);
+                r ^= lb;
+                uint64_t x = 0;
+#pragma unroll
+                for (int k = 0; k < NRM_PIVOTS; ++k) {
+                    if (B1[k] & lb) x ^= P2[k];
+                    if (B2[k] & lb) x ^= P1[k];
+                }
+                sK[(__ffs(lb) - 1 + 32 * hw) * NRM_TPB] ^= x;
+            }
+        }
     }
     e += __popcll(act);
     if (Lre & act) zre = true;
@@ -370,18 +402,21 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64
         uint64_t act, odd, Lb;
         uint32_t sKs;
         if (fold) {
-            // rows of D off the diagonal, D z0 (mod 2) and the pair parities of z0
-            uint64_t dz0 = 0, pz = 0;
+            // rows of D off the diagonal, D z0 (mod 2), and sum_{c in z0} |D_c & z0| =
+            // twice the number of pairs of z0 joined in D
+            uint64_t dz0 = 0, zs = z0;
+            uint32_t pcnt = 0;
             for (int c = 0; c < n; ++c) {
                 const uint64_t Doff = sA[c * NRM_TPB] ^ tJ[c];
                 sW[c * NRM_TPB] = Doff;
-                if (getb(z0, c)) {
+                if (zs & 1ull) {
                     dz0 ^= Doff;
-                    pz ^= Doff & z0 & ((c == 63) ? 0ull : (~0ull << (c + 1)));
+                    pcnt += (uint32_t)__popcll(Doff & z0);
                 }
+                zs >>= 1;
             }
             dz0 ^= dlo & z0;
-            sKs = ((uint32_t)__popcll(z0 & dlo) + 2u * (uint32_t)__popcll(z0 & dhi) + 2u * par64(pz)) & 3u;
+            sKs = ((uint32_t)__popcll(z0 & dlo) + 2u * (uint32_t)__popcll(z0 & dhi) + pcnt) & 3u;
             // Z4 form on y: diagonal D_cc + 2 (u + D z0)_c, off-diagonal D (mod 2)
             odd = dlo;
             Lb = dhi ^ tU ^ dz0;
@@ -399,12 +434,10 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64
                 fold_rows(sW, h, q, op);
                 act &= ~bit64(p);
             }
+            // lift: S_c = Q_c + odd_c odd (rows stay unmasked, see rank_update)
             odd &= act;
             Lb &= act;
-            for (uint64_t r = act; r; r &= r - 1) {
-                const int c = ffs64(r);
-                sW[c * NRM_TPB] = (sW[c * NRM_TPB] ^ (getb(odd, c) ? odd : 0ull)) & act & ~bit64(c);
-            }
+            for (uint64_t r = odd; r; r &= r - 1) sW[ffs64(r) * NRM_TPB] ^= odd;
         } else {
         // P = D G row by row (D = (A + J) mod 2 with its diagonal), the pair
         // parities sum_{c<d in g_k} D_cd for every k at once, and those of z0.
