@@ -1,19 +1,28 @@
 // Norm estimation (Sec. 4.3): eta_l = 2^n |<phi_{A_l}|psi>|^2.
 //
-// One thread per equatorial state A_l; a block walks a tile of terms, so each
-// thread keeps its own FP32 Kahan sum over terms and no cross-thread reduction
-// is needed inside the tile.  Per (A, term), with D = (A + J) mod 2
-// (J_cd = (M F^T)_cd off the diagonal, gamma on it) and K = G^T (A+J) G
-// (Lemma (Inner Product)):
-//   P_c  = D_c G   : XOR of rows G_d over d in D_c, by Four-Russians lookups in a
-//                    per-term shared table of G (4 rows per nibble of D_c)
-//   R_k  = column k of P (an in-place bit transpose), K_k = R_k G (same table)
-//   K_kk = sum_{c in g_k} (A_cc + gamma_c) + 2 #{c<d in g_k : D_cd = 1}  (mod 4),
-//          bit-sliced over k (g_k = column k of G)
-// then the exponential sum of
-// B = K|_v + 2 diag(s + sK) by pairwise elimination on a symmetric adjacency
-// (Lemma (Exponential Sum), lifted to Z2 with one extra variable, Eq. (Q)).
-// Everything up to the chi-sum is exact integer arithmetic.
+// Three launches per call:
+//   k_norm_prep    per term: J = M F^T off the diagonal, z0 = G s, u = F s and, for a
+//                  term with n - |v| <= max_folds, the reduced echelon form of the
+//                  constraints f_k = column k of F, k not in v
+//   k_norm_draw_a  per l: A_l in M_n from the counter RNG
+//   k_norm         one thread per A_l, a block of 64 A's walks a tile of terms, each
+//                  thread keeping its own FP32 Kahan sum over the tile
+// then k_norm_reduce sums the tiles in FP64.
+//
+// Per (A, term), with D = A + J (diagonal A_cc + gamma_c in Z4) the paper's route
+// (Lemma (Inner Product)) forms K = G^T D G and sums i^(x^T B x) over x in Z2^v,
+// B = K|_v + 2 diag(s + sK).  The kernel has two exact routes to that sum:
+//   K path         P_c = D_c G by Four-Russians lookups in a per-term shared table of
+//                  G, an in-place bit transpose (R_k = D g_k), K_k = R_k G, and K_kk
+//                  mod 4 bit-sliced over k
+//   change of      with y = G x, x^T K x = y^T D y and s.x + s^T K x = (F s + D z0).y
+//   variables      (G^-1 = F^T since F G^T = I); x in Z2^v is the subspace
+//                  (F^T y)_k = 0 for k not in v, and each such constraint, in reduced
+//                  echelon form y_p = h . y, is substituted into the form (a rank-2
+//                  update of the rows of D plus diagonal carries).  No K is formed.
+// Either route ends in the exponential sum of a Z4 form by pairwise elimination on a
+// symmetric adjacency (Lemma (Exponential Sum), lifted to Z2 with one extra variable,
+// Eq. (Q)).  Everything up to the chi-sum is exact integer arithmetic.
 #include "lrs_device.cuh"
 
 namespace {
@@ -260,7 +269,37 @@ __device__ __forceinline__ void transpose_blocks(uint64_t* W) {
 //                one pivot, its own)
 struct NormPrep {
     uint64_t *J, *z0, *u, *piv, *f;
+    uint64_t *A, *adlo, *adhi;   // A_l: off-diagonal rows A[c][l], diagonal bit-planes (Z4)
 };
+
+// A_l in M_n from the counter RNG (one thread per l): the diagonal as two bit-planes
+// (words 0 and 1 of the stream of l), the upper triangle from words 2.. in the order
+// (0,1), (0,2), .., (0,n-1), (1,2), .., one bit each, mirrored below the diagonal.
+__global__ void __launch_bounds__(NRM_TPB) k_norm_draw_a(int n, uint64_t nmask, int64_t L, uint64_t seed,
+                                                         NormPrep P) {
+    extern __shared__ uint64_t sRow[];   // row c of this thread's A at sRow[c * NRM_TPB + tid]
+    const int tid = threadIdx.x;
+    const int64_t l = (int64_t)blockIdx.x * NRM_TPB + tid;
+    if (l >= L) return;
+    uint64_t* sA = sRow + tid;
+    const uint64_t key = sm64_key(seed, (uint64_t)l);
+    P.adlo[l] = sm64_at(key, 0) & nmask;
+    P.adhi[l] = sm64_at(key, 1) & nmask;
+    for (int c = 0; c < n; ++c) sA[c * NRM_TPB] = 0;
+    int64_t kbit = 0;
+    uint64_t word = sm64_at(key, 2);
+    for (int a = 0; a < n; ++a) {
+        uint64_t rowa = sA[a * NRM_TPB];
+        for (int b = a + 1; b < n; ++b) {
+            const uint64_t bt = (word >> (kbit & 63)) & 1ull;
+            rowa |= bt << b;
+            sA[b * NRM_TPB] |= bt << a;
+            ++kbit;
+            if ((kbit & 63) == 0) word = sm64_at(key, 2 + (uint64_t)(kbit >> 6));
+        }
+        P.A[(int64_t)a * L + l] = rowa;
+    }
+}
 
 __global__ void __launch_bounds__(NRM_TPB) k_norm_prep(TermsView T, int max_folds, NormPrep P) {
     extern __shared__ uint64_t sF[];   // row c of this thread's F at sF[c * NRM_TPB + tid]
@@ -315,7 +354,7 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm_prep(TermsView T, int max_fold
 }
 
 template <int NCH, int NB>
-__global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64_t L, uint64_t seed, int64_t tt,
+__global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64_t L, int64_t tt,
                                                   float2* __restrict__ partial, int64_t n_tiles,
                                                   int max_folds) {
     extern __shared__ uint64_t smem[];
@@ -331,26 +370,10 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64
     uint64_t* sA = smem + NCH * 16 + tid;                          // A_c at sA[c * NRM_TPB]
     uint64_t* sW = smem + NCH * 16 + (int64_t)n * NRM_TPB + tid;   // 8 NB work rows
 
-    // ---- A_l in M_n from the counter RNG
-    const uint64_t key = sm64_key(seed, (uint64_t)(l < L ? l : 0));
-    const uint64_t adlo = sm64_at(key, 0) & nmask;
-    const uint64_t adhi = sm64_at(key, 1) & nmask;
-    for (int c = 0; c < n; ++c) sA[c * NRM_TPB] = 0;
-    {
-        int64_t kbit = 0;
-        uint64_t word = sm64_at(key, 2);
-        for (int a = 0; a < n; ++a) {
-            uint64_t rowa = sA[a * NRM_TPB];
-            for (int b = a + 1; b < n; ++b) {
-                const uint64_t bt = (word >> (kbit & 63)) & 1ull;
-                rowa |= bt << b;
-                sA[b * NRM_TPB] |= bt << a;
-                ++kbit;
-                if ((kbit & 63) == 0) word = sm64_at(key, 2 + (uint64_t)(kbit >> 6));
-            }
-            sA[a * NRM_TPB] = rowa;
-        }
-    }
+    // ---- A_l (drawn once per call by k_norm_draw_a)
+    const int64_t la = l < L ? l : 0;
+    const uint64_t adlo = P.adlo[la], adhi = P.adhi[la];
+    for (int c = 0; c < n; ++c) sA[c * NRM_TPB] = P.A[(int64_t)c * L + la];
 
     KahanC acc;
     acc.init();
@@ -523,7 +546,7 @@ __global__ void k_norm_reduce(const float2* __restrict__ partial, int64_t n_tile
 }  // namespace
 
 template <int NCH>
-static lrs_status launch_norm_t(lrs_ctx* ctx, const NormPrep& P, int64_t L, uint64_t seed, int64_t tt,
+static lrs_status launch_norm_t(lrs_ctx* ctx, const NormPrep& P, int64_t L, int64_t tt,
                                 float2* partial, int64_t n_tiles, cudaStream_t st) {
     constexpr int NB = (NCH + 1) / 2;   // 8 x 8 blocks per side of the transposed matrix
     const size_t smem = ((size_t)NCH * 16 + (size_t)(ctx->n + 8 * NB) * NRM_TPB) * sizeof(uint64_t);
@@ -531,7 +554,7 @@ static lrs_status launch_norm_t(lrs_ctx* ctx, const NormPrep& P, int64_t L, uint
                                   (int)smem));
     const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
     dim3 grid((unsigned)n_tiles, (unsigned)lblocks);
-    k_norm<NCH, NB><<<grid, NRM_TPB, smem, st>>>(ctx->view(), P, L, seed, tt, partial, n_tiles,
+    k_norm<NCH, NB><<<grid, NRM_TPB, smem, st>>>(ctx->view(), P, L, tt, partial, n_tiles,
                                                   (int)ctx->tune_norm_folds);
     LRS_LAUNCH_CHECK("norm kernel");
     return LRS_OK;
@@ -546,7 +569,7 @@ lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* 
     void* scr = nullptr;
     // scratch: partial sums, then the per-term prep arrays
     const size_t part_bytes = ((size_t)L * n_tiles * sizeof(float2) + 255) & ~(size_t)255;
-    const size_t words = (size_t)ctx->cap * (size_t)(ctx->n + 3 + NRM_MFOLD);
+    const size_t words = (size_t)ctx->cap * (size_t)(ctx->n + 3 + NRM_MFOLD) + (size_t)L * (size_t)(ctx->n + 2);
     lrs_status rc = lrs_scratch(ctx, part_bytes + words * sizeof(uint64_t), &scr);
     if (rc != LRS_OK) return rc;
     float2* partial = (float2*)scr;
@@ -556,28 +579,34 @@ lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* 
     P.u = P.z0 + ctx->cap;
     P.piv = P.u + ctx->cap;
     P.f = P.piv + ctx->cap;
+    P.A = P.f + (size_t)NRM_MFOLD * ctx->cap;
+    P.adlo = P.A + (size_t)ctx->n * L;
+    P.adhi = P.adlo + L;
     const int max_folds = (int)ctx->tune_norm_folds;
     k_norm_prep<<<(unsigned)((ctx->cap + NRM_TPB - 1) / NRM_TPB), NRM_TPB,
                   (size_t)ctx->n * NRM_TPB * sizeof(uint64_t), st>>>(ctx->view(), max_folds, P);
     LRS_LAUNCH_CHECK("norm prep kernel");
+    k_norm_draw_a<<<(unsigned)((L + NRM_TPB - 1) / NRM_TPB), NRM_TPB, (size_t)ctx->n * NRM_TPB * sizeof(uint64_t),
+                    st>>>(ctx->n, ctx->nmask, L, seed, P);
+    LRS_LAUNCH_CHECK("equatorial state kernel");
     if ((L + NRM_TPB - 1) / NRM_TPB > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "L too large");
     switch ((ctx->n + 3) / 4) {
-        case 1: rc = launch_norm_t<1>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 2: rc = launch_norm_t<2>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 3: rc = launch_norm_t<3>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 4: rc = launch_norm_t<4>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 5: rc = launch_norm_t<5>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 6: rc = launch_norm_t<6>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 7: rc = launch_norm_t<7>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 8: rc = launch_norm_t<8>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 9: rc = launch_norm_t<9>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 10: rc = launch_norm_t<10>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 11: rc = launch_norm_t<11>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 12: rc = launch_norm_t<12>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 13: rc = launch_norm_t<13>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 14: rc = launch_norm_t<14>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        case 15: rc = launch_norm_t<15>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
-        default: rc = launch_norm_t<16>(ctx, P, L, seed, tt, partial, n_tiles, st); break;
+        case 1: rc = launch_norm_t<1>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 2: rc = launch_norm_t<2>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 3: rc = launch_norm_t<3>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 4: rc = launch_norm_t<4>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 5: rc = launch_norm_t<5>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 6: rc = launch_norm_t<6>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 7: rc = launch_norm_t<7>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 8: rc = launch_norm_t<8>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 9: rc = launch_norm_t<9>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 10: rc = launch_norm_t<10>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 11: rc = launch_norm_t<11>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 12: rc = launch_norm_t<12>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 13: rc = launch_norm_t<13>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 14: rc = launch_norm_t<14>(ctx, P, L, tt, partial, n_tiles, st); break;
+        case 15: rc = launch_norm_t<15>(ctx, P, L, tt, partial, n_tiles, st); break;
+        default: rc = launch_norm_t<16>(ctx, P, L, tt, partial, n_tiles, st); break;
     }
     if (rc != LRS_OK) return rc;
     k_norm_reduce<<<(unsigned)L, 256, 0, st>>>(partial, n_tiles, L, eta);
