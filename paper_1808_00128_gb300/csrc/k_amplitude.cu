@@ -23,10 +23,13 @@ struct AmpEntry {
     uint64_t u, w, z;
 };
 
-template <int NCH>
+// QOUT: also store every (x_i, term) Pauli as Q[i * cap + alpha] = (u | mu << 62, w),
+// zero terms included (the Metropolis chain state of Sec. 4.2).
+template <int NCH, bool QOUT>
 __global__ void __launch_bounds__(AMP_XT) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
                                                       int64_t batch, int64_t tt,
-                                                      float2* __restrict__ partial, int64_t n_tiles) {
+                                                      float2* __restrict__ partial, int64_t n_tiles,
+                                                      ulonglong2* __restrict__ Qout) {
     __shared__ AmpEntry tab[NCH][16];
     __shared__ uint64_t sF[64], sM[64];
     __shared__ float2 val8[8];              // b e^{i pi k/4} 2^{-(|v|+h)/2}, k = 0..7
@@ -98,7 +101,8 @@ __global__ void __launch_bounds__(AMP_XT) k_amplitude(TermsView T, const uint64_
             tab[c][q].z = z;
         }
         __syncthreads();
-        if (!sc_live) continue;             // zero term (uniform)
+        const bool live = sc_live != 0u;
+        if (!QOUT && !live) continue;       // zero term (uniform)
         const uint64_t glo = sc[0], ghi = sc[1], v = sc[2], s = sc[3];
         const uint64_t nv = ~v & T.nmask, sv = s & v;
 #pragma unroll
@@ -112,8 +116,12 @@ __global__ void __launch_bounds__(AMP_XT) k_amplitude(TermsView T, const uint64_
                 u ^= E.u;
                 w ^= E.w;
             }
-            if (((u ^ s) & nv) == 0) {
-                const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)par64(z);
+            const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)par64(z);
+            if (QOUT) {
+                const int64_t i = xb + tid + k * AMP_XT;
+                if (i < batch) Qout[i * T.cap + a] = make_ulonglong2(u | ((uint64_t)(mu & 3) << 62), w);
+            }
+            if (live && ((u ^ s) & nv) == 0) {
                 const int sign = (int)par64(u & (w ^ sv));
                 acc[k].add(val8[(2 * mu + 4 * sign) & 7]);
             }
@@ -174,34 +182,37 @@ AmpPlan amp_plan(const lrs_ctx* ctx, int64_t batch) {
 
 template <int NCH>
 lrs_status launch_amp_t(lrs_ctx* ctx, const uint64_t* x, int64_t batch, float2* partial,
-                        const AmpPlan& P, cudaStream_t st) {
+                        const AmpPlan& P, ulonglong2* Qout, cudaStream_t st) {
     dim3 grid((unsigned)P.n_tiles, (unsigned)P.xblocks);
-    k_amplitude<NCH><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles);
+    if (Qout)
+        k_amplitude<NCH, true><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles, Qout);
+    else
+        k_amplitude<NCH, false><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles, nullptr);
     LRS_LAUNCH_CHECK("amplitude kernel");
     return LRS_OK;
 }
 
 lrs_status launch_amp_kernels(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
-                              float2* partial, const AmpPlan& P, cudaStream_t st) {
+                              float2* partial, const AmpPlan& P, cudaStream_t st, ulonglong2* Qout) {
     if (P.xblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "amplitude batch too large");
     lrs_status rc;
     switch ((ctx->n + 3) / 4) {
-        case 1: rc = launch_amp_t<1>(ctx, x, batch, partial, P, st); break;
-        case 2: rc = launch_amp_t<2>(ctx, x, batch, partial, P, st); break;
-        case 3: rc = launch_amp_t<3>(ctx, x, batch, partial, P, st); break;
-        case 4: rc = launch_amp_t<4>(ctx, x, batch, partial, P, st); break;
-        case 5: rc = launch_amp_t<5>(ctx, x, batch, partial, P, st); break;
-        case 6: rc = launch_amp_t<6>(ctx, x, batch, partial, P, st); break;
-        case 7: rc = launch_amp_t<7>(ctx, x, batch, partial, P, st); break;
-        case 8: rc = launch_amp_t<8>(ctx, x, batch, partial, P, st); break;
-        case 9: rc = launch_amp_t<9>(ctx, x, batch, partial, P, st); break;
-        case 10: rc = launch_amp_t<10>(ctx, x, batch, partial, P, st); break;
-        case 11: rc = launch_amp_t<11>(ctx, x, batch, partial, P, st); break;
-        case 12: rc = launch_amp_t<12>(ctx, x, batch, partial, P, st); break;
-        case 13: rc = launch_amp_t<13>(ctx, x, batch, partial, P, st); break;
-        case 14: rc = launch_amp_t<14>(ctx, x, batch, partial, P, st); break;
-        case 15: rc = launch_amp_t<15>(ctx, x, batch, partial, P, st); break;
-        default: rc = launch_amp_t<16>(ctx, x, batch, partial, P, st); break;
+        case 1: rc = launch_amp_t<1>(ctx, x, batch, partial, P, Qout, st); break;
+        case 2: rc = launch_amp_t<2>(ctx, x, batch, partial, P, Qout, st); break;
+        case 3: rc = launch_amp_t<3>(ctx, x, batch, partial, P, Qout, st); break;
+        case 4: rc = launch_amp_t<4>(ctx, x, batch, partial, P, Qout, st); break;
+        case 5: rc = launch_amp_t<5>(ctx, x, batch, partial, P, Qout, st); break;
+        case 6: rc = launch_amp_t<6>(ctx, x, batch, partial, P, Qout, st); break;
+        case 7: rc = launch_amp_t<7>(ctx, x, batch, partial, P, Qout, st); break;
+        case 8: rc = launch_amp_t<8>(ctx, x, batch, partial, P, Qout, st); break;
+        case 9: rc = launch_amp_t<9>(ctx, x, batch, partial, P, Qout, st); break;
+        case 10: rc = launch_amp_t<10>(ctx, x, batch, partial, P, Qout, st); break;
+        case 11: rc = launch_amp_t<11>(ctx, x, batch, partial, P, Qout, st); break;
+        case 12: rc = launch_amp_t<12>(ctx, x, batch, partial, P, Qout, st); break;
+        case 13: rc = launch_amp_t<13>(ctx, x, batch, partial, P, Qout, st); break;
+        case 14: rc = launch_amp_t<14>(ctx, x, batch, partial, P, Qout, st); break;
+        case 15: rc = launch_amp_t<15>(ctx, x, batch, partial, P, Qout, st); break;
+        default: rc = launch_amp_t<16>(ctx, x, batch, partial, P, Qout, st); break;
     }
     if (rc != LRS_OK) return rc;
     k_amp_reduce<<<(unsigned)batch, 256, 0, st>>>(partial, P.n_tiles, batch, out);
@@ -211,6 +222,19 @@ lrs_status launch_amp_kernels(lrs_ctx* ctx, const uint64_t* x, int64_t batch, do
 
 }  // namespace
 
+// Amplitudes of x[0..batch) into scratch (*amp_out, 2 doubles per x) and the Pauli
+// state Q[i * cap + alpha] of every (x_i, term): the chain start of Sec. 4.2.
+lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, ulonglong2* Q, double** amp_out,
+                              cudaStream_t st) {
+    const AmpPlan P = amp_plan(ctx, batch);
+    const size_t part = ((size_t)batch * P.n_tiles * sizeof(float2) + 255) & ~(size_t)255;
+    void* scr = nullptr;
+    lrs_status rc = lrs_scratch(ctx, part + (size_t)batch * 2 * sizeof(double), &scr);
+    if (rc != LRS_OK) return rc;
+    *amp_out = (double*)((char*)scr + part);
+    return launch_amp_kernels(ctx, x, batch, *amp_out, (float2*)scr, P, st, Q);
+}
+
 lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
                             cudaStream_t st) {
     if (batch == 0) return LRS_OK;
@@ -218,7 +242,7 @@ lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, doub
     void* scr = nullptr;
     lrs_status rc = lrs_scratch(ctx, (size_t)batch * P.n_tiles * sizeof(float2), &scr);
     if (rc != LRS_OK) return rc;
-    return launch_amp_kernels(ctx, x, batch, out, (float2*)scr, P, st);
+    return launch_amp_kernels(ctx, x, batch, out, (float2*)scr, P, st, nullptr);
 }
 
 // ---------------------------------------------------------------------------------
@@ -272,5 +296,5 @@ extern "C" lrs_status lrs_amplitude_noalloc(lrs_ctx* ctx, const uint64_t* x, int
                         "lrs_amplitude_noalloc: %lld partial sums (batch x term tiles) exceed the "
                         "fixed buffer of %u; use a smaller batch or lrs_amplitude",
                         (long long)(batch * P.n_tiles), LRS_NOALLOC_PARTIALS);
-    return launch_amp_kernels(ctx, x, batch, out, partial, P, (cudaStream_t)stream);
+    return launch_amp_kernels(ctx, x, batch, out, partial, P, (cudaStream_t)stream, nullptr);
 }

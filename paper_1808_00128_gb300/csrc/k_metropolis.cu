@@ -35,55 +35,6 @@ __device__ __forceinline__ float2 block_sum(float2 v, float2 (*red)[MC_TPB / 32]
     return v;
 }
 
-// Q from scratch for x_c, and the block partial of <x_c|psi>.
-__global__ void __launch_bounds__(MC_TPB) k_chains_init(TermsView T, const uint64_t* __restrict__ xs,
-                                                        int64_t C, ulonglong2* __restrict__ Q,
-                                                        float2* __restrict__ partial, int64_t n_tiles,
-                                                        int cg) {
-    extern __shared__ uint64_t smem[];
-    __shared__ float2 red[MC_CG][MC_TPB / 32];
-    const int n = T.n;
-    const int tid = threadIdx.x;
-    const int64_t tile = blockIdx.x;
-    const int64_t a = tile * MC_TPB + tid;
-    uint64_t* sF = smem + tid;
-    uint64_t* sM = smem + (int64_t)n * MC_TPB + tid;
-    for (int p = 0; p < n; ++p) {
-        sF[p * MC_TPB] = T.F[(int64_t)p * T.cap + a];
-        sM[p * MC_TPB] = T.M[(int64_t)p * T.cap + a];
-    }
-    const uint64_t glo = T.glo[a], ghi = T.ghi[a], v = T.v[a], s = T.s[a];
-    const uint32_t om = T.omega[a];
-    const uint64_t nv = ~v & T.nmask, sv = s & v;
-    const bool live = ((om >> 3) & 1u) == 0u;
-    const int k0 = (int)(om & 7u), e0 = __popcll(v) + (int)(om >> 8);
-    const float2 b = T.coef[a];
-    const int64_t c0 = (int64_t)blockIdx.y * cg;
-    const int nc = (int)(C - c0 < cg ? C - c0 : cg);
-    for (int ci = 0; ci < nc; ++ci) {
-        const int64_t c = c0 + ci;
-        const uint64_t x = xs[c] & T.nmask;   // bits >= n are ignored
-        uint64_t u = 0, w = 0, z = 0;
-        for (uint64_t xr = x; xr; xr &= xr - 1) {
-            const int p = ffs64(xr);
-            const uint64_t Fp = sF[p * MC_TPB];
-            z ^= w & Fp;
-            u ^= Fp;
-            w ^= sM[p * MC_TPB];
-        }
-        const uint32_t mu = ((uint32_t)__popcll(x & glo) + 2u * (uint32_t)__popcll(x & ghi) +
-                             2u * par64(z)) & 3u;
-        Q[c * T.cap + a] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
-        block_sum(term_value(u, w, mu, s, nv, sv, live, k0, e0, b), red, ci);
-    }
-    __syncthreads();
-    if (tid < nc) {
-        float2 acc = red[tid][0];
-        for (int w2 = 1; w2 < MC_TPB / 32; ++w2) { acc.x += red[tid][w2].x; acc.y += red[tid][w2].y; }
-        partial[(c0 + tid) * n_tiles + tile] = acc;
-    }
-}
-
 // One proposal: apply the pending accepted flip, then form the amplitude of y.
 // Rows F_j, M_j come straight from global memory (the [row][term] layout makes
 // them one coalesced 256-byte read per warp and they stay in L2); the only
@@ -175,15 +126,14 @@ __device__ __forceinline__ int draw_j(uint64_t seed, int64_t c, int64_t step, in
     return (int)(((r >> 32) * (uint64_t)n) >> 32);
 }
 
-__global__ void k_chains_set(const float2* __restrict__ partial, int64_t n_tiles, const uint64_t* xs,
-                             uint64_t nmask, uint64_t* cx, double* cp, int32_t* pend) {
-    const int64_t c = blockIdx.x;
-    const double p = chain_reduce(partial, c, n_tiles);
-    if (threadIdx.x == 0) {
-        cx[c] = xs[c] & nmask;
-        cp[c] = p;
-        pend[c] = -1;
-    }
+__global__ void k_chains_set(const double* __restrict__ amp, int64_t C, const uint64_t* xs, uint64_t nmask,
+                             uint64_t* cx, double* cp, int32_t* pend) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const double re = amp[2 * c], im = amp[2 * c + 1];
+    cx[c] = xs[c] & nmask;
+    cp[c] = re * re + im * im;
+    pend[c] = -1;
 }
 
 // Per-call parameters live in device memory so that a captured graph of steps
@@ -266,29 +216,14 @@ __global__ void k_metro_out(int64_t C, const uint64_t* cx, const double* cp, uin
 
 }  // namespace
 
-static size_t mc_smem(const lrs_ctx* ctx) { return (size_t)2 * ctx->n * MC_TPB * sizeof(uint64_t); }
-
-static lrs_status mc_attrs() {
-    const int mx = 2 * 64 * MC_TPB * (int)sizeof(uint64_t);
-    LRS_CUDA(cudaFuncSetAttribute(k_chains_init, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    return LRS_OK;
-}
-
 lrs_status launch_chains_init(lrs_ctx* ctx, const uint64_t* x, cudaStream_t st) {
+    // Q of every (chain, term) and <x_c|psi> by the amplitude kernel (Four-Russians
+    // tables of the Pauli accumulator), then the chain scalars
     const int64_t C = ctx->n_chains;
-    const int64_t n_tiles = ctx->cap / MC_TPB;
-    void* scr = nullptr;
-    lrs_status rc = lrs_scratch(ctx, (size_t)C * n_tiles * sizeof(float2), &scr);
+    double* amp = nullptr;
+    lrs_status rc = launch_amplitude_q(ctx, x, C, ctx->Q, &amp, st);
     if (rc != LRS_OK) return rc;
-    rc = mc_attrs();
-    if (rc != LRS_OK) return rc;
-    float2* partial = (float2*)scr;
-    dim3 grid((unsigned)n_tiles, (unsigned)((C + ctx->tune_mc_cg - 1) / ctx->tune_mc_cg));
-    k_chains_init<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), x, C, ctx->Q, partial, n_tiles,
-                                                      (int)ctx->tune_mc_cg);
-    LRS_LAUNCH_CHECK("chains_init kernel");
-    k_chains_set<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, x, ctx->nmask, ctx->cx, ctx->cp,
-                                              ctx->pend);
+    k_chains_set<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(amp, C, x, ctx->nmask, ctx->cx, ctx->cp, ctx->pend);
     LRS_LAUNCH_CHECK("chains_set kernel");
     return LRS_OK;
 }
@@ -357,8 +292,6 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
     const size_t part_bytes = (size_t)C * n_tiles * sizeof(float2);
     lrs_status rc = lrs_scratch(ctx, part_bytes + (size_t)C * sizeof(int32_t) + 256, &scr);
     if (rc != LRS_OK) return rc;
-    rc = mc_attrs();
-    if (rc != LRS_OK) return rc;
     if (!ctx->mc_par) LRS_CUDA(cudaMalloc(&ctx->mc_par, sizeof(McParams)));
     float2* partial = (float2*)scr;
     int32_t* jprop = (int32_t*)((char*)scr + ((part_bytes + 255) & ~(size_t)255));
@@ -415,24 +348,18 @@ lrs_status launch_metropolis_learned(lrs_ctx* ctx, lrs_mlp* mlp, int64_t steps, 
     return LRS_OK;
 }
 
-// Rebuild Q for the chains' current strings (after learned moves).
+// Rebuild Q for the chains' current strings (after learned moves).  The strings are
+// copied into the learned proposal's buffer (free at this point) because chains_set
+// rewrites cx.
 lrs_status launch_chains_refresh(lrs_ctx* ctx, cudaStream_t st) {
-    void* scr = nullptr;
     const int64_t C = ctx->n_chains;
-    // copy cx aside: chains_init reads x and writes cx
-    lrs_status rc = lrs_scratch(ctx, (size_t)C * (ctx->cap / MC_TPB) * sizeof(float2) + (size_t)C * 8 + 512, &scr);
+    if (!ctx->ybuf || ctx->mh_cap < C) return lrs_fail(LRS_ERR_STATE, "chain refresh without a learned-move buffer");
+    LRS_CUDA(cudaMemcpyAsync(ctx->ybuf, ctx->cx, (size_t)C * 8, cudaMemcpyDeviceToDevice, st));
+    double* amp = nullptr;
+    lrs_status rc = launch_amplitude_q(ctx, ctx->ybuf, C, ctx->Q, &amp, st);
     if (rc != LRS_OK) return rc;
-    uint64_t* xcopy = (uint64_t*)((char*)scr + (((size_t)C * (ctx->cap / MC_TPB) * sizeof(float2) + 255) & ~(size_t)255));
-    LRS_CUDA(cudaMemcpyAsync(xcopy, ctx->cx, (size_t)C * 8, cudaMemcpyDeviceToDevice, st));
-    const int64_t n_tiles = ctx->cap / MC_TPB;
-    rc = mc_attrs();
-    if (rc != LRS_OK) return rc;
-    float2* partial = (float2*)scr;
-    dim3 grid((unsigned)n_tiles, (unsigned)((C + ctx->tune_mc_cg - 1) / ctx->tune_mc_cg));
-    k_chains_init<<<grid, MC_TPB, mc_smem(ctx), st>>>(ctx->view(), xcopy, C, ctx->Q, partial, n_tiles,
-                                                      (int)ctx->tune_mc_cg);
-    LRS_LAUNCH_CHECK("chains refresh kernel");
-    k_chains_set<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, xcopy, ctx->nmask, ctx->cx, ctx->cp, ctx->pend);
+    k_chains_set<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(amp, C, ctx->ybuf, ctx->nmask, ctx->cx, ctx->cp,
+                                                            ctx->pend);
     LRS_LAUNCH_CHECK("chains refresh set kernel");
     ctx->q_stale = false;
     return LRS_OK;

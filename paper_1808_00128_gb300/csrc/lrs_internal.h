@@ -153,6 +153,8 @@ lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_
                                  cudaStream_t st);
 lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
                             cudaStream_t st);
+lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, ulonglong2* Q, double** amp_out,
+                              cudaStream_t st);
 lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta,
                                 cudaStream_t st);
 lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint64_t* x,
