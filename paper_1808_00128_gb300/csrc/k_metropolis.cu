@@ -14,16 +14,10 @@
 
 namespace {
 
-constexpr int MC_TPB = 128;   // terms per block
+constexpr int MC_TPB = 128;   // threads per block
+constexpr int MC_TPT = 2;     // terms per thread
+constexpr int MC_TERMS = MC_TPB * MC_TPT;   // terms per block (cap is a multiple of 256)
 constexpr int MC_CG = 64;     // chains per block (grid.y groups)
-
-__device__ __forceinline__ float2 term_value(uint64_t u, uint64_t w, uint32_t mu, uint64_t s,
-                                             uint64_t nv, uint64_t sv, bool live, int k0, int e0,
-                                             float2 b) {
-    if (!live || ((u ^ s) & nv) != 0) return make_float2(0.f, 0.f);
-    const int sign = (int)(par64(u & w) ^ par64(u & sv));
-    return z8_scale(b, 2 * (int)mu + 4 * sign + k0, e0);
-}
 
 __device__ __forceinline__ float2 block_sum(float2 v, float2 (*red)[MC_TPB / 32], int slot) {
 #pragma unroll
@@ -35,10 +29,18 @@ __device__ __forceinline__ float2 block_sum(float2 v, float2 (*red)[MC_TPB / 32]
     return v;
 }
 
+// b e^{i pi k/4} 2^{-e/2} times i^m (m = mu + 2 sign): the Z8 factor of a term at a
+// string, with the term's part (coefficient, phase k, |v| + h) folded in once.
+__device__ __forceinline__ float2 times_i_pow(float2 z, uint32_t m) {
+    const float2 r = (m & 1u) ? make_float2(-z.y, z.x) : z;
+    return (m & 2u) ? make_float2(-r.x, -r.y) : r;
+}
+
 // One proposal: apply the pending accepted flip, then form the amplitude of y.
 // Rows F_j, M_j come straight from global memory (the [row][term] layout makes
 // them one coalesced 256-byte read per warp and they stay in L2); the only
-// per-(chain, term) HBM traffic is the 16-byte Q.
+// per-(chain, term) HBM traffic is the 16-byte Q.  Each thread owns MC_TPT terms
+// (tile * MC_TERMS + tid + k * MC_TPB) and sums them before the block reduction.
 __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C, ulonglong2* __restrict__ Q,
                                                           const int32_t* __restrict__ pend,
                                                           const int32_t* __restrict__ jprop,
@@ -47,48 +49,83 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     __shared__ float2 red[MC_CG][MC_TPB / 32];
     const int tid = threadIdx.x;
     const int64_t tile = blockIdx.x;
-    const int64_t a = tile * MC_TPB + tid;
-    const uint64_t glo = T.glo[a], ghi = T.ghi[a], v = T.v[a], s = T.s[a];
-    const uint32_t om = T.omega[a];
-    const uint64_t nv = ~v & T.nmask, sv = s & v;
-    const bool live = ((om >> 3) & 1u) == 0u;
-    const int k0 = (int)(om & 7u), e0 = __popcll(v) + (int)(om >> 8);
-    const float2 b = T.coef[a];
+    int64_t a[MC_TPT];
+    uint64_t glo[MC_TPT], ghi[MC_TPT], s[MC_TPT], nv[MC_TPT], sv[MC_TPT];
+    float2 base[MC_TPT];
+    bool live[MC_TPT];
+#pragma unroll
+    for (int k = 0; k < MC_TPT; ++k) {
+        a[k] = tile * MC_TERMS + tid + k * MC_TPB;
+        glo[k] = T.glo[a[k]];
+        ghi[k] = T.ghi[a[k]];
+        const uint64_t v = T.v[a[k]];
+        s[k] = T.s[a[k]];
+        nv[k] = ~v & T.nmask;
+        sv[k] = s[k] & v;
+        const uint32_t om = T.omega[a[k]];
+        live[k] = ((om >> 3) & 1u) == 0u;
+        base[k] = z8_scale(T.coef[a[k]], (int)(om & 7u), __popcll(v) + (int)(om >> 8));
+    }
     const uint64_t umask = (1ull << 62) - 1;
     const int64_t c0 = (int64_t)blockIdx.y * cg;
     const int nc = (int)(C - c0 < cg ? C - c0 : cg);
-    constexpr int U = 4;   // chains in flight per thread
+    // the block's chains' pending flips and proposals, staged once
+    __shared__ int32_t spj[MC_CG], sj[MC_CG];
+    if (tid < nc) {
+        spj[tid] = pend[c0 + tid];
+        sj[tid] = jprop[c0 + tid];
+    }
+    __syncthreads();
+    constexpr int U = 2;   // chains whose loads are in flight together
     for (int cb = 0; cb < nc; cb += U) {
-        ulonglong2 q[U];
+        ulonglong2 q[U][MC_TPT];
+        uint64_t Fp[U][MC_TPT], Mp[U][MC_TPT], Fj[U][MC_TPT], Mj[U][MC_TPT];
         int pj[U], jj[U];
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int ci = cb + k < nc ? cb + k : nc - 1;
-            q[k] = Q[(c0 + ci) * T.cap + a];
-            pj[k] = pend[c0 + ci];
-            jj[k] = jprop[c0 + ci];
+        for (int h = 0; h < U; ++h) {
+            const int ci = cb + h < nc ? cb + h : nc - 1;
+            const int64_t c = c0 + ci;
+            pj[h] = spj[ci];
+            jj[h] = sj[ci];
+#pragma unroll
+            for (int k = 0; k < MC_TPT; ++k) {
+                q[h][k] = Q[c * T.cap + a[k]];
+                const int r = pj[h] >= 0 ? pj[h] : 0;
+                Fp[h][k] = __ldg(&T.F[(int64_t)r * T.cap + a[k]]);
+                Mp[h][k] = __ldg(&T.M[(int64_t)r * T.cap + a[k]]);
+                Fj[h][k] = __ldg(&T.F[(int64_t)jj[h] * T.cap + a[k]]);
+                Mj[h][k] = __ldg(&T.M[(int64_t)jj[h] * T.cap + a[k]]);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int ci = cb + k;
+        for (int h = 0; h < U; ++h) {
+            const int ci = cb + h;
             if (ci >= nc) break;                       // uniform across the block
             const int64_t c = c0 + ci;
-            uint64_t u = q[k].x & umask, w = q[k].y;
-            uint32_t mu = (uint32_t)(q[k].x >> 62);
-            if (pj[k] >= 0) {   // commit the flip accepted at the previous step (uniform per chain)
-                const int p = pj[k];
-                const uint64_t Fp = __ldg(&T.F[(int64_t)p * T.cap + a]);
-                mu = (mu + (uint32_t)(getb(glo, p) | (getb(ghi, p) << 1)) + 2u * par64(w & Fp)) & 3u;
-                u ^= Fp;
-                w ^= __ldg(&T.M[(int64_t)p * T.cap + a]);
-                Q[c * T.cap + a] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < MC_TPT; ++k) {
+                uint64_t u = q[h][k].x & umask, w = q[h][k].y;
+                uint32_t mu = (uint32_t)(q[h][k].x >> 62);
+                if (pj[h] >= 0) {   // commit the flip accepted at the previous step
+                    const int p = pj[h];
+                    mu = (mu + (uint32_t)(getb(glo[k], p) | (getb(ghi[k], p) << 1)) + 2u * par64(w & Fp[h][k])) & 3u;
+                    u ^= Fp[h][k];
+                    w ^= Mp[h][k];
+                    Q[c * T.cap + a[k]] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
+                }
+                const int j = jj[h];
+                const uint32_t muy =
+                    (mu + (uint32_t)(getb(glo[k], j) | (getb(ghi[k], j) << 1)) + 2u * par64(w & Fj[h][k])) & 3u;
+                const uint64_t uy = u ^ Fj[h][k], wy = w ^ Mj[h][k];
+                if (live[k] && ((uy ^ s[k]) & nv[k]) == 0) {
+                    const uint32_t sign = par64(uy & wy) ^ par64(uy & sv[k]);
+                    const float2 t = times_i_pow(base[k], muy + 2u * sign);
+                    acc.x += t.x;
+                    acc.y += t.y;
+                }
             }
-            const int j = jj[k];
-            const uint64_t Fj = __ldg(&T.F[(int64_t)j * T.cap + a]);
-            const uint64_t Mj = __ldg(&T.M[(int64_t)j * T.cap + a]);
-            const uint32_t muy =
-                (mu + (uint32_t)(getb(glo, j) | (getb(ghi, j) << 1)) + 2u * par64(w & Fj)) & 3u;
-            block_sum(term_value(u ^ Fj, w ^ Mj, muy, s, nv, sv, live, k0, e0, b), red, ci);
+            block_sum(acc, red, ci);
         }
     }
     __syncthreads();
@@ -232,7 +269,7 @@ lrs_status launch_chains_init(lrs_ctx* ctx, const uint64_t* x, cudaStream_t st) 
 static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2* partial, int32_t* jprop,
                                 uint64_t* trace, cudaStream_t st) {
     const int64_t C = ctx->n_chains;
-    const int64_t n_tiles = ctx->cap / MC_TPB;
+    const int64_t n_tiles = ctx->cap / MC_TERMS;
     const int cg = (int)ctx->tune_mc_cg;
     dim3 grid((unsigned)n_tiles, (unsigned)((C + cg - 1) / cg));
     for (int64_t t = t0; t < t0 + count; ++t) {
@@ -287,7 +324,7 @@ static lrs_status mc_graph(lrs_ctx* ctx, float2* partial, int32_t* jprop, cudaGr
 lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t step0,
                              uint64_t* x_out, double* p_out, uint64_t* trace, cudaStream_t st) {
     const int64_t C = ctx->n_chains;
-    const int64_t n_tiles = ctx->cap / MC_TPB;
+    const int64_t n_tiles = ctx->cap / MC_TERMS;
     void* scr = nullptr;
     const size_t part_bytes = (size_t)C * n_tiles * sizeof(float2);
     lrs_status rc = lrs_scratch(ctx, part_bytes + (size_t)C * sizeof(int32_t) + 256, &scr);
