@@ -426,13 +426,19 @@ lrs_status launch_gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M,
 }
 
 // Tile width for an M x N output: the widest of 256, 128, 64 that divides N and still
-// gives every SM a tile.
+// gives every SM a tile; a single k-step takes a one-stage ring.
 template <bool MN, class Epi>
 lrs_status gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, Epi epi, int* err,
                    cudaStream_t st) {
     if (K % TC_BK != 0 || N % 64 != 0 || (MN && M % 64 != 0))
         return lrs_fail(LRS_ERR_ARG, "gemm: M=%d, N=%d, K=%d not multiples of 64", M, N, K);
     const int64_t mt = (M + TC_M - 1) / TC_M;
+    if (K == TC_BK) {
+        // one k-step: the tile is all epilogue, so a one-stage ring lets several CTAs
+        // share an SM and overlap their stores
+        if (N % 128 == 0) return launch_gemm_tc<128, 1, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
+        return launch_gemm_tc<64, 1, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
+    }
     if (N % 256 == 0 && mt * (N / 256) >= 148) return launch_gemm_tc<256, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
     if (N % 128 == 0 && mt * (N / 128) >= 148) return launch_gemm_tc<128, 3, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
     return launch_gemm_tc<64, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
