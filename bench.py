@@ -386,8 +386,9 @@ def _ev():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def qaoa_study(local=0, chi=1 << 20, B=4096, C=256, T=64, alu_peak=None, hbm_peak=6695.2):
-    """Config-4 shapes: n=50 Max-E3LIN2 QAOA (gamma 0.3, beta 0.2), chi = 2^20."""
+def qaoa_study(local=0, chi=1 << 20, B=4096, C=256, T=64, L=512, alu_peak=None, hbm_peak=6695.2):
+    """Config-4 shapes: n=50 Max-E3LIN2 QAOA (gamma 0.3, beta 0.2), chi = 2^20: gate
+    updates, amplitudes, Metropolis and the norm estimate with L = 512."""
     import numpy as np
     import torch
     from paper_1808_00128_gb300 import lrstab, workloads
@@ -433,6 +434,21 @@ def qaoa_study(local=0, chi=1 << 20, B=4096, C=256, T=64, alu_peak=None, hbm_pea
     ach = chi * B * (8 * ((n + 3) // 4) + 16) / t_amp
     res["amplitude"] = {"ms": t_amp * 1e3, "x_term_per_s": chi * B / t_amp, "achieved_Tops": ach / 1e12,
                         "frac": ach / alu_peak if alu_peak else None, "batch": B}
+    # norm estimate, L = 512 equatorial states
+    eta = torch.empty(L, dtype=torch.float64, device=dev)
+    sim.norm_estimate(L, seed=3, eta=eta)
+    a, b = _ev()
+    a.record()
+    sim.norm_estimate(L, seed=4, eta=eta)
+    b.record()
+    b.synchronize()
+    t_norm = a.elapsed_time(b) * 1e-3
+    ex = sim.export_terms(0, min(chi, 4096))
+    vw = np.array([bin(int(v)).count("1") for v in ex["v"]])
+    ach = chi * L * float(np.mean(norm_ops_per_unit(n, vw, sim.get_tuning("norm_max_folds")))) / t_norm
+    res["norm_estimate"] = {"ms": t_norm * 1e3, "A_term_per_s": chi * L / t_norm, "achieved_Tops": ach / 1e12,
+                            "frac": ach / alu_peak if alu_peak else None, "L": L,
+                            "mean_eta": float(eta.mean().item())}
     # Metropolis (flip chains), graph-replayed steps
     x0 = sim.sample_terms(C, seed=5)
     sim.chains_init(x0)

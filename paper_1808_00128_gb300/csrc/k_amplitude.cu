@@ -25,12 +25,17 @@ struct AmpEntry {
 
 // QOUT: also store every (x_i, term) Pauli as Q[i * cap + alpha] = (u | mu << 62, w),
 // zero terms included (the Metropolis chain state of Sec. 4.2).
-template <int NCH, bool QOUT>
+// PK (n <= 62): only parity(z) enters mu, and parity(z_after) = parity(z) +
+// parity(w & u_q) + parity(z_q), so a table entry keeps parity(z_q) in bit 63 of u_q
+// and the lookups count popc(w & u_q): two 8-byte tables (u_q, w_q) instead of three,
+// each a conflict-free 128-byte row per chunk.
+template <int NCH, bool QOUT, bool PK>
 __global__ void __launch_bounds__(AMP_XT) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
                                                       int64_t batch, int64_t tt,
                                                       float2* __restrict__ partial, int64_t n_tiles,
                                                       ulonglong2* __restrict__ Qout) {
-    __shared__ AmpEntry tab[NCH][16];
+    __shared__ AmpEntry tab[PK ? 1 : NCH][16];
+    __shared__ uint64_t tabU[PK ? NCH : 1][16], tabW[PK ? NCH : 1][16];
     __shared__ uint64_t sF[64], sM[64];
     __shared__ float2 val8[8];              // b e^{i pi k/4} 2^{-(|v|+h)/2}, k = 0..7
     __shared__ uint64_t sc[4];              // glo, ghi, v, s
@@ -96,9 +101,14 @@ __global__ void __launch_bounds__(AMP_XT) k_amplitude(TermsView T, const uint64_
                     w ^= sM[r];
                 }
             }
-            tab[c][q].u = u;
-            tab[c][q].w = w;
-            tab[c][q].z = z;
+            if (PK) {
+                tabU[c][q] = u | ((uint64_t)par64(z) << 63);
+                tabW[c][q] = w;
+            } else {
+                tab[c][q].u = u;
+                tab[c][q].w = w;
+                tab[c][q].z = z;
+            }
         }
         __syncthreads();
         const bool live = sc_live != 0u;
@@ -108,15 +118,32 @@ __global__ void __launch_bounds__(AMP_XT) k_amplitude(TermsView T, const uint64_
 #pragma unroll
         for (int k = 0; k < AMP_XP; ++k) {
             const uint64_t x = xv[k];
-            uint64_t u = 0, w = 0, z = 0;
+            uint64_t u = 0, w = 0;
+            uint32_t zpar;
+            if (PK) {
+                uint32_t zc = 0;
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                const AmpEntry& E = tab[c][(int)((x >> (4 * c)) & 15u)];
-                z ^= (w & E.u) ^ E.z;
-                u ^= E.u;
-                w ^= E.w;
+                for (int c = 0; c < NCH; ++c) {
+                    const int q = (int)((x >> (4 * c)) & 15u);
+                    const uint64_t Eu = tabU[c][q], Ew = tabW[c][q];
+                    zc += (uint32_t)__popcll(w & Eu);   // w has no bit 63
+                    u ^= Eu;
+                    w ^= Ew;
+                }
+                zpar = (zc + (uint32_t)(u >> 63)) & 1u;
+                u &= ~(1ull << 63);
+            } else {
+                uint64_t z = 0;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const AmpEntry& E = tab[c][(int)((x >> (4 * c)) & 15u)];
+                    z ^= (w & E.u) ^ E.z;
+                    u ^= E.u;
+                    w ^= E.w;
+                }
+                zpar = par64(z);
             }
-            const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)par64(z);
+            const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)zpar;
             if (QOUT) {
                 const int64_t i = xb + tid + k * AMP_XT;
                 if (i < batch) Qout[i * T.cap + a] = make_ulonglong2(u | ((uint64_t)(mu & 3) << 62), w);
@@ -184,10 +211,15 @@ template <int NCH>
 lrs_status launch_amp_t(lrs_ctx* ctx, const uint64_t* x, int64_t batch, float2* partial,
                         const AmpPlan& P, ulonglong2* Qout, cudaStream_t st) {
     dim3 grid((unsigned)P.n_tiles, (unsigned)P.xblocks);
-    if (Qout)
-        k_amplitude<NCH, true><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles, Qout);
+    const bool pk = ctx->n <= 62;
+    if (Qout)   // chains need n <= 62 (mu lives in bits 62-63 of Q), so the packed tables apply
+        k_amplitude<NCH, true, true><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles, Qout);
+    else if (pk)
+        k_amplitude<NCH, false, true><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles,
+                                                              nullptr);
     else
-        k_amplitude<NCH, false><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles, nullptr);
+        k_amplitude<NCH, false, false><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles,
+                                                               nullptr);
     LRS_LAUNCH_CHECK("amplitude kernel");
     return LRS_OK;
 }
