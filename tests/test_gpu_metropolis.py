@@ -86,3 +86,61 @@ def test_metropolis_continuation_and_errors():
     with pytest.raises(lrstab.LrsError):
         sim.metropolis(-1, seed=0)
     sim.close()
+
+
+def test_full_size_chains_match_amplitudes():
+    """n=40 benchmark decomposition at full size (2^16 terms), 64 chains x 32 steps
+    (two graph replays): every decision replayed with P = |<x|psi>|^2 from the
+    amplitude kernel (oracle-checked on slices), and the incremental P(x) of every
+    chain equal to the amplitude kernel's at the end."""
+    require_cuda()
+    cfg = workloads.config_mid()
+    n, ops, chi, seed = cfg["n"], cfg["ops"], cfg["chi"], cfg["seed"]
+    sim = _sim(n, ops, chi, "sparsify", seed)
+    C, T, mseed = 64, 32, 99
+    x0 = sim.sample_terms(C, seed=12)
+    sim.chains_init(x0)
+    xo = torch.empty(C, dtype=torch.int64, device="cuda:0")
+    po = torch.empty(C, dtype=torch.float64, device="cuda:0")
+    sim.metropolis(T, seed=mseed, x_out=xo, p_out=po)          # graph-replayed steps
+    sim.chains_init(x0)
+    trace = torch.empty((T, C), dtype=torch.int64, device="cuda:0")
+    sim.metropolis(T, seed=mseed, trace=trace)                  # direct steps
+    assert torch.equal(trace[-1], xo)
+    tr = trace.cpu().numpy().view(np.uint64)
+    xs = x0.cpu().numpy().view(np.uint64)
+    # proposals of every step, from the same draws as the kernels
+    props = np.zeros((T, C), np.uint64)
+    cur = xs.copy()
+    for t in range(T):
+        for c in range(C):
+            j, _ = E.metropolis_draws(n, mseed, c, t)
+            props[t, c] = np.uint64(int(cur[c]) ^ (1 << j))
+        cur = tr[t]
+    allx = np.concatenate([xs, props.reshape(-1)])
+    amp = sim.amplitude(torch.from_numpy(allx.view(np.int64)).cuda()).cpu().numpy()
+    P = amp[:, 0] ** 2 + amp[:, 1] ** 2
+    pmap = dict(zip(allx.tolist(), P.tolist()))
+    close = 0
+    cur = xs.copy()
+    for t in range(T):
+        for c in range(C):
+            x, y = int(cur[c]), int(props[t, c])
+            px, py = pmap[x], pmap[y]
+            _, r = E.metropolis_draws(n, mseed, c, t)
+            acc = int(tr[t, c]) == y
+            assert acc or int(tr[t, c]) == x
+            if px <= 0 or py >= px:
+                want = True
+            else:
+                want = r < py / px
+                if abs(py / px - r) <= 1e-4 * (py / px):
+                    close += 1
+                    want = acc
+            assert acc == want, (t, c)
+        cur = tr[t]
+    final = sim.amplitude(xo).cpu().numpy()
+    pf = final[:, 0] ** 2 + final[:, 1] ** 2
+    np.testing.assert_allclose(po.cpu().numpy(), pf, rtol=1e-5, atol=1e-12 * pf.max())
+    assert close < C * T // 50
+    sim.close()
