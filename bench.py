@@ -513,6 +513,36 @@ def batch_study(local=0, k=8, seed=0):
     return res
 
 
+def marginal_study(local=0, w=8, L=256, K=3):
+    """Chain-rule sampling of w bits by norm estimation (end of Sec. 4.3) on the n=40
+    hidden shift (exact 2^16-term decomposition of |s>): every bit must come out as
+    the shift's bit.  Each bit takes two median-of-means estimates (L K equatorial
+    states each, the same states for both branches) of the projected decomposition."""
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    cfg = workloads.config_hidden_shift()
+    n, chi = cfg["n"], cfg["chi"]
+    low = lrstab.lower_circuit(n, cfg["ops"])
+    sim = lrstab.Simulator(n, local)
+    sim.init_terms(low, chi, mode="exact")
+    sim.apply_clifford(low.gates)
+    work = (lrstab.Simulator(n, local), lrstab.Simulator(n, local))
+    qubits = list(range(0, n, n // w))[:w]
+    sim.marginal_sample(qubits[:1], L, K, seed=1, work=work)      # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bits, probs = sim.marginal_sample(qubits, L, K, seed=2, work=work)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ok = all(b == (cfg["shift"] >> q) & 1 for q, b in zip(qubits, bits))
+    units = 2.0 * w * L * K * chi
+    for s_ in (sim,) + work:
+        s_.close()
+    return {"workload": f"{cfg['name']}_w{w}", "w": w, "L": L, "K": K, "seconds": dt,
+            "bits_per_s": w / dt, "A_term_per_s": units / dt, "bits_are_the_shift": ok,
+            "max_wrong_branch_p": max(min(p) for p in probs)}
+
+
 def mlp_gemm_study(local=0, n=64, H=2048, batch=16384, reps=5, bf16_peak=None):
     """Tensor-core throughput of the learned proposal's products: forward pass and
     one AdamW training step of the MADE network (n=64, H=2048, 16384 rows), with the
@@ -741,14 +771,18 @@ def main():
                          "amplitude evals and 8 equatorial inner products per term; per-unit "
                          "times scaled to one full step",
                "seconds": round(time.perf_counter() - t0, 1)}
+    cert = None
+    if rank == 0 and not args.small:
+        cert = lrstab.sparsification_certificate(sim, low, L=L_A, K=3, seed=777)
     sim.close()
-    ess = qaoa = batch = gemm = None
+    ess = qaoa = batch = gemm = marg = None
     if rank == 0 and not args.small and not args.no_sampler_study:
         ess = sampler_study(local)
     if rank == 0 and not args.small and not args.no_extra:
         qaoa = qaoa_study(local, alu_peak=alu_measured, hbm_peak=hbm)
         batch = batch_study(local)
         gemm = mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops"))
+        marg = marginal_study(local)
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -759,7 +793,8 @@ def main():
                       "before every timed step", "parallelism": f"replicas x{world}", "tuned": tuned},
            "roofline": roof, "phases": rows, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "ess": ess,
-           "qaoa_n50": qaoa, "batch8": batch, "mlp_gemm": gemm}
+           "qaoa_n50": qaoa, "batch8": batch, "mlp_gemm": gemm, "marginals": marg,
+           "sparsification_certificate": cert}
     print(json.dumps(out))
 
 

@@ -256,6 +256,31 @@ lrs_status lrs_metropolis_step(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64
                                uint64_t* x_out_dev, double* p_out_dev, uint64_t* trace_dev,
                                void* stream);
 
+/* ---- median of means and marginal sampling (end of Sec. 4.3) ------------------ */
+/* Copy the terms of src (tableaux, gamma, v, s, omega, coefficients, slot choices
+ * and slot tables) into dst, which must have the same qubit count and device;
+ * dst's storage is reallocated when its capacity differs, and its chains are
+ * dropped.  Stream-ordered.                                                     */
+lrs_status lrs_copy_terms(lrs_ctx* dst, const lrs_ctx* src, void* stream);
+/* ||psi||^2 estimated as the median of K empirical means of eta_A, group g using
+ * the equatorial states l = g L .. g L + L - 1 of lrs_norm_estimate's stream
+ * `seed` (the median of an even K is the mean of the two middle means).  L, K >= 1,
+ * L K <= 2^22.  Writes *estimate_host; synchronises the stream.                  */
+lrs_status lrs_norm_median_of_means(lrs_ctx* ctx, int64_t L, int32_t K, uint64_t seed,
+                                    double* estimate_host, void* stream);
+/* Chain-rule sample of the bits on qubits[0..w) by norm estimation: step i fixes
+ * the bits drawn so far by the projectors (I + (-1)^x Z_q)/2 (Sec. 4.1, projective
+ * gates), estimates both branches p_b = ||Pi_{x_<i, b} psi||^2 by
+ * lrs_norm_median_of_means(L, K, seed_i) with seed_i = rand64(seed, 2^41 + i, 0)
+ * (the same equatorial states for both branches), and sets bits_host[i] = 1 iff
+ * uniform(seed, 2^42 + i, 0) < p_1 / (p_0 + p_1) (0 when p_0 + p_1 <= 0).
+ * probs_host (may be NULL) receives p_0, p_1 of every step.  work0 and work1 are
+ * two further contexts with the same qubit count (their terms are overwritten);
+ * ctx is not modified.  Distinct qubits, 0 <= w <= n.  Synchronises the stream. */
+lrs_status lrs_marginal_sample(lrs_ctx* ctx, lrs_ctx* work0, lrs_ctx* work1, const int32_t* qubits_host,
+                               int32_t w, int64_t L, int32_t K, uint64_t seed, uint8_t* bits_host,
+                               double* probs_host, void* stream);
+
 /* ---- learned proposal (MADE network; the paper proposes single flips only) ----- */
 /* The paper's Metropolis chain (Sec. 4.2) uses single bit flips and notes that
  * its mixing time is generally unknown.  These calls add an independent

@@ -223,6 +223,7 @@ extern "C" lrs_status lrs_destroy(lrs_ctx* c) {
     cudaFree(c->slots_dev); cudaFree(c->kgates_dev); cudaFree(c->gates_dev); cudaFree(c->scratch);
     cudaFree(c->mc_par);
     cudaFree(c->batch_buf);
+    cudaFree(c->eta_buf);
     if (c->mc_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->mc_exec);
     if (c->cap_stream) cudaStreamDestroy((cudaStream_t)c->cap_stream);
     delete c;
@@ -234,6 +235,35 @@ extern "C" lrs_status lrs_info(const lrs_ctx* c, int64_t* chi, int32_t* n, int64
     if (chi) *chi = c->chi;
     if (n) *n = c->n;
     if (n_slots) *n_slots = c->n_slots;
+    return LRS_OK;
+}
+
+// Term storage for `cap` terms and `n_slots` slot choices (reused when it fits the
+// same capacity; chains are dropped when it is reallocated).
+static lrs_status ensure_terms(lrs_ctx* c, int64_t cap, int64_t n_slots) {
+    if (cap == c->cap && n_slots <= c->choice_slots_cap) return LRS_OK;
+    free_terms(c);
+    free_chains(c);
+    const size_t rows = (size_t)c->n * cap * sizeof(uint64_t);
+    const size_t vec = (size_t)cap * sizeof(uint64_t);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&c->F, rows);
+    if (e == cudaSuccess) e = cudaMalloc(&c->G, rows);
+    if (e == cudaSuccess) e = cudaMalloc(&c->M, rows);
+    if (e == cudaSuccess) e = cudaMalloc(&c->glo, vec);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ghi, vec);
+    if (e == cudaSuccess) e = cudaMalloc(&c->v, vec);
+    if (e == cudaSuccess) e = cudaMalloc(&c->s, vec);
+    if (e == cudaSuccess) e = cudaMalloc(&c->omega, (size_t)cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->coef, (size_t)cap * sizeof(float2));
+    const int64_t cs = std::max<int64_t>(n_slots, 1);
+    if (e == cudaSuccess) e = cudaMalloc(&c->choice, (size_t)cs * cap);
+    if (e != cudaSuccess) {
+        free_terms(c);
+        return lrs_cuda_check(e, "term storage");
+    }
+    c->cap = cap;
+    c->choice_slots_cap = cs;
     return LRS_OK;
 }
 
@@ -315,30 +345,8 @@ extern "C" lrs_status lrs_init_terms(lrs_ctx* c, const lrs_slot* slots, int64_t 
 
     // (re)allocate term storage
     const int64_t cap = (chi + LRS_TERM_ALIGN - 1) / LRS_TERM_ALIGN * LRS_TERM_ALIGN;
-    if (cap != c->cap || n_slots > c->choice_slots_cap) {
-        free_terms(c);
-        free_chains(c);
-        const size_t rows = (size_t)c->n * cap * sizeof(uint64_t);
-        const size_t vec = (size_t)cap * sizeof(uint64_t);
-        cudaError_t e = cudaSuccess;
-        if (e == cudaSuccess) e = cudaMalloc(&c->F, rows);
-        if (e == cudaSuccess) e = cudaMalloc(&c->G, rows);
-        if (e == cudaSuccess) e = cudaMalloc(&c->M, rows);
-        if (e == cudaSuccess) e = cudaMalloc(&c->glo, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&c->ghi, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&c->v, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&c->s, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&c->omega, (size_t)cap * sizeof(uint32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&c->coef, (size_t)cap * sizeof(float2));
-        const int64_t cs = std::max<int64_t>(n_slots, 1);
-        if (e == cudaSuccess) e = cudaMalloc(&c->choice, (size_t)cs * cap);
-        if (e != cudaSuccess) {
-            free_terms(c);
-            return lrs_cuda_check(e, "term storage");
-        }
-        c->cap = cap;
-        c->choice_slots_cap = cs;
-    }
+    lrs_status rs = ensure_terms(c, cap, n_slots);
+    if (rs != LRS_OK) return rs;
     c->chi = chi;
     c->alpha0 = alpha0;
     c->chi_total = chi_total;
@@ -453,6 +461,133 @@ extern "C" lrs_status lrs_norm_estimate(lrs_ctx* c, int64_t L, uint64_t seed, do
         double m = 0.0;
         for (double x : h) m += x;
         *mean_host = m / (double)L;
+    }
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_copy_terms(lrs_ctx* dst, const lrs_ctx* src, void* stream) {
+    if (!dst || !src) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (dst == src) return LRS_OK;
+    if (!src->have_terms) return lrs_fail(LRS_ERR_STATE, "source has no terms");
+    if (dst->n != src->n || dst->device != src->device)
+        return lrs_fail(LRS_ERR_ARG, "contexts differ in qubit count or device");
+    LRS_CUDA(cudaSetDevice(dst->device));
+    cudaStream_t st = as_stream(stream);
+    lrs_status rc = ensure_terms(dst, src->cap, src->n_slots);
+    if (rc != LRS_OK) return rc;
+    const size_t rows = (size_t)src->n * src->cap * sizeof(uint64_t), vec = (size_t)src->cap * sizeof(uint64_t);
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    LRS_CUDA(cudaMemcpyAsync(dst->F, src->F, rows, dd, st));
+    LRS_CUDA(cudaMemcpyAsync(dst->G, src->G, rows, dd, st));
+    LRS_CUDA(cudaMemcpyAsync(dst->M, src->M, rows, dd, st));
+    LRS_CUDA(cudaMemcpyAsync(dst->glo, src->glo, vec, dd, st));
+    LRS_CUDA(cudaMemcpyAsync(dst->ghi, src->ghi, vec, dd, st));
+    LRS_CUDA(cudaMemcpyAsync(dst->v, src->v, vec, dd, st));
+    LRS_CUDA(cudaMemcpyAsync(dst->s, src->s, vec, dd, st));
+    LRS_CUDA(cudaMemcpyAsync(dst->omega, src->omega, (size_t)src->cap * sizeof(uint32_t), dd, st));
+    LRS_CUDA(cudaMemcpyAsync(dst->coef, src->coef, (size_t)src->cap * sizeof(float2), dd, st));
+    if (src->n_slots > 0)
+        LRS_CUDA(cudaMemcpyAsync(dst->choice, src->choice, (size_t)src->n_slots * src->cap, dd, st));
+    size_t have = (size_t)dst->slots_cap * sizeof(DevSlot);
+    rc = lrs_ensure((void**)&dst->slots_dev, &have, std::max<size_t>(1, (size_t)src->n_slots) * sizeof(DevSlot));
+    if (rc != LRS_OK) return rc;
+    dst->slots_cap = (int64_t)(have / sizeof(DevSlot));
+    have = (size_t)dst->kgates_cap * sizeof(lrs_gate);
+    rc = lrs_ensure((void**)&dst->kgates_dev, &have, std::max<size_t>(1, src->kgates_host.size()) * sizeof(lrs_gate));
+    if (rc != LRS_OK) return rc;
+    dst->kgates_cap = (int64_t)(have / sizeof(lrs_gate));
+    if (src->n_slots > 0)
+        LRS_CUDA(cudaMemcpyAsync(dst->slots_dev, src->slots_dev, (size_t)src->n_slots * sizeof(DevSlot), dd, st));
+    if (!src->kgates_host.empty())
+        LRS_CUDA(cudaMemcpyAsync(dst->kgates_dev, src->kgates_dev, src->kgates_host.size() * sizeof(lrs_gate), dd, st));
+    dst->n_slots = src->n_slots;
+    dst->slots_host = src->slots_host;
+    dst->kgates_host = src->kgates_host;
+    dst->chi = src->chi;
+    dst->alpha0 = src->alpha0;
+    dst->chi_total = src->chi_total;
+    dst->n_chains = 0;
+    dst->have_terms = true;
+    return LRS_OK;
+}
+
+// Median of the K means of consecutive groups of L values (even K: mean of the two
+// middle means).
+static double median_of_means(const double* eta, int64_t L, int32_t K) {
+    std::vector<double> m((size_t)K);
+    for (int32_t g = 0; g < K; ++g) {
+        double acc = 0.0;
+        for (int64_t l = 0; l < L; ++l) acc += eta[(size_t)g * L + l];
+        m[(size_t)g] = acc / (double)L;
+    }
+    std::sort(m.begin(), m.end());
+    return (K & 1) ? m[(size_t)K / 2] : 0.5 * (m[(size_t)K / 2 - 1] + m[(size_t)K / 2]);
+}
+
+static lrs_status norm_mom(lrs_ctx* c, int64_t L, int32_t K, uint64_t seed, double* out, cudaStream_t st) {
+    const int64_t LK = L * K;
+    size_t have = c->eta_bytes;
+    lrs_status rc = lrs_ensure((void**)&c->eta_buf, &have, (size_t)LK * sizeof(double));
+    if (rc != LRS_OK) return rc;
+    c->eta_bytes = have;
+    rc = launch_norm_estimate(c, LK, seed, c->eta_buf, st);
+    if (rc != LRS_OK) return rc;
+    std::vector<double> h((size_t)LK);
+    LRS_CUDA(cudaMemcpyAsync(h.data(), c->eta_buf, (size_t)LK * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LRS_CUDA(cudaStreamSynchronize(st));
+    *out = median_of_means(h.data(), L, K);
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_norm_median_of_means(lrs_ctx* c, int64_t L, int32_t K, uint64_t seed,
+                                               double* estimate_host, void* stream) {
+    if (!c || !estimate_host) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (L < 1 || K < 1 || L * (int64_t)K > (1ll << 22)) return lrs_fail(LRS_ERR_ARG, "need L, K >= 1 and L K <= 2^22");
+    LRS_CUDA(cudaSetDevice(c->device));
+    return norm_mom(c, L, K, seed, estimate_host, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_marginal_sample(lrs_ctx* c, lrs_ctx* work0, lrs_ctx* work1, const int32_t* qubits,
+                                          int32_t w, int64_t L, int32_t K, uint64_t seed, uint8_t* bits_host,
+                                          double* probs_host, void* stream) {
+    if (!c || !work0 || !work1 || (w > 0 && (!qubits || !bits_host))) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (work0 == work1 || work0 == c || work1 == c) return lrs_fail(LRS_ERR_ARG, "contexts must be distinct");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (w < 0 || w > c->n) return lrs_fail(LRS_ERR_ARG, "w must be in 0..n");
+    if (L < 1 || K < 1 || L * (int64_t)K > (1ll << 22)) return lrs_fail(LRS_ERR_ARG, "need L, K >= 1 and L K <= 2^22");
+    for (int32_t i = 0; i < w; ++i) {
+        if (qubits[i] < 0 || qubits[i] >= c->n) return lrs_fail(LRS_ERR_ARG, "qubit %d out of range", qubits[i]);
+        for (int32_t j = 0; j < i; ++j)
+            if (qubits[j] == qubits[i]) return lrs_fail(LRS_ERR_ARG, "qubit %d listed twice", qubits[i]);
+    }
+    LRS_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    lrs_status rc = lrs_copy_terms(work0, c, stream);      // prefix Pi_{x_<i} psi
+    if (rc != LRS_OK) return rc;
+    lrs_ctx* pref = work0;
+    lrs_ctx* alt = work1;
+    for (int32_t i = 0; i < w; ++i) {
+        // both branches from the prefix, the same equatorial states for both
+        if ((rc = lrs_copy_terms(alt, pref, stream)) != LRS_OK) return rc;
+        lrs_gate g0, g1;
+        g0.op = LRS_OP_P0; g0.q = (uint8_t)qubits[i]; g0.r = 0;
+        g1.op = LRS_OP_P1; g1.q = (uint8_t)qubits[i]; g1.r = 0;
+        if ((rc = lrs_apply_clifford(alt, &g0, 1, stream)) != LRS_OK) return rc;
+        if ((rc = lrs_apply_clifford(pref, &g1, 1, stream)) != LRS_OK) return rc;
+        const uint64_t s_i = sm64_at(sm64_key(seed, (1ull << 41) + (uint64_t)i), 0);
+        double p0 = 0.0, p1 = 0.0;
+        if ((rc = norm_mom(alt, L, K, s_i, &p0, st)) != LRS_OK) return rc;
+        if ((rc = norm_mom(pref, L, K, s_i, &p1, st)) != LRS_OK) return rc;
+        const double u = sm64_unit(sm64_at(sm64_key(seed, (1ull << 42) + (uint64_t)i), 0));
+        const double tot = p0 + p1;
+        const int x = (tot > 0.0 && u < p1 / tot) ? 1 : 0;
+        bits_host[i] = (uint8_t)x;
+        if (probs_host) {
+            probs_host[2 * i] = p0;
+            probs_host[2 * i + 1] = p1;
+        }
+        if (x == 0) std::swap(pref, alt);   // the prefix holds the chosen branch
     }
     return LRS_OK;
 }

@@ -94,6 +94,9 @@ struct lrs_ctx {
     int64_t tune_norm_tiles = 2048; // norm: maximum term tiles per A-block column
     int64_t tune_mc_cg = 64;        // Metropolis: chains per block (1..64)
     int64_t tune_norm_folds = 12;   // norm: terms with n - |v| <= this sum over y = G x (-1..12)
+    // equatorial samples of median-of-means estimates
+    double* eta_buf = nullptr;
+    size_t eta_bytes = 0;
     // work table of batched launches led by this context
     void* batch_buf = nullptr;
     size_t batch_buf_bytes = 0;

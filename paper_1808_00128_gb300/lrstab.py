@@ -38,7 +38,8 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_alu_probe", "lrs_amplitude_noalloc", "lrs_mlp_create", "lrs_mlp_destroy",
             "lrs_mlp_info", "lrs_mlp_set_gemm", "lrs_mlp_get_gemm", "lrs_mlp_set_params", "lrs_mlp_get_params", "lrs_mlp_forward",
             "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned",
-            "lrs_apply_clifford_batch", "lrs_set_tuning", "lrs_get_tuning"]
+            "lrs_apply_clifford_batch", "lrs_set_tuning", "lrs_get_tuning", "lrs_copy_terms",
+            "lrs_norm_median_of_means", "lrs_marginal_sample"]
 
 
 class LrsError(RuntimeError):
@@ -90,6 +91,9 @@ def lib():
         "lrs_metropolis_learned": [vp, vp, i64, u64, i64, vp, vp, vp, vp, vp],
         "lrs_apply_clifford_batch": [vp, vp, vp, i32, vp],
         "lrs_set_tuning": [vp, i32, i64],
+        "lrs_copy_terms": [vp, vp, vp],
+        "lrs_norm_median_of_means": [vp, i64, i32, u64, vp, vp],
+        "lrs_marginal_sample": [vp, vp, vp, vp, i32, i64, i32, u64, vp, vp, vp],
         "lrs_get_tuning": [vp, i32, vp],
     }
     for name, args in sigs.items():
@@ -152,6 +156,27 @@ class Lowered:
                                       (s["c_im"][: s["n_choices"]] != 0)))
             out *= nz
         return out
+
+
+    @property
+    def l1_norm(self) -> float:
+        """||c||_1 of the whole decomposition: the product over slots of sum_j |c_j|
+        (Sec. 5.2; the sparsification error is delta^2 = ||c||_1^2 / chi)."""
+        out = 1.0
+        for s in self.slots:
+            k = s["n_choices"]
+            out *= float(np.sum(np.hypot(s["c_re"][:k], s["c_im"][:k])))
+        return out
+
+
+def sparsification_certificate(sim: "Simulator", lowered: Lowered, L: int, K: int, seed: int) -> dict:
+    """Lemma (Sparsification tail bound): for Omega the sparsified state on sim's chi
+    terms, ||psi - Omega||^2 <= <Omega|Omega> - 1 + delta^2 with high probability,
+    delta^2 = ||c||_1^2 / chi; <Omega|Omega> is estimated by the median of K means of L
+    equatorial samples."""
+    omega2 = sim.norm_median_of_means(L, K, seed)
+    delta2 = lowered.l1_norm ** 2 / sim.chi_total
+    return {"omega_norm2": omega2, "delta2": delta2, "bound": omega2 - 1.0 + delta2, "L": L, "K": K}
 
 
 def lower_circuit(n: int, ops, ccz_mode: str = "proj") -> Lowered:
@@ -257,6 +282,38 @@ class Simulator:
         _check(lib().lrs_norm_estimate(self._h, L, seed & (2 ** 64 - 1), _ptr(eta),
                                        C.byref(mean) if want_mean else None, _stream(stream)))
         return (eta, mean.value) if want_mean else eta
+
+    def norm_median_of_means(self, L: int, K: int, seed: int, stream=None) -> float:
+        est = C.c_double(0.0)
+        _check(lib().lrs_norm_median_of_means(self._h, L, K, seed & (2 ** 64 - 1), C.byref(est),
+                                              _stream(stream)))
+        return est.value
+
+    def copy_terms_from(self, src: "Simulator", stream=None):
+        _check(lib().lrs_copy_terms(self._h, src._h, _stream(stream)))
+        chi, ns = C.c_int64(0), C.c_int64(0)
+        _check(lib().lrs_info(self._h, C.byref(chi), None, C.byref(ns)))
+        self.chi, self.n_slots = chi.value, ns.value
+        self.chi_total = getattr(src, "chi_total", chi.value)
+
+    def marginal_sample(self, qubits, L: int, K: int, seed: int, work=None, stream=None):
+        """Chain-rule sample of the bits on `qubits` (lrs_marginal_sample).  Returns
+        (bits, probs) with probs[i] = (p0, p1) of step i.  `work`: two Simulators with
+        the same n (created and closed here when None)."""
+        own = work is None
+        if own:
+            work = (Simulator(self.n, self.device), Simulator(self.n, self.device))
+        try:
+            q = np.ascontiguousarray(qubits, dtype=np.int32)
+            bits = np.zeros(len(q), np.uint8)
+            probs = np.zeros((len(q), 2), np.float64)
+            _check(lib().lrs_marginal_sample(self._h, work[0]._h, work[1]._h, _ptr(q), len(q), L, K,
+                                             seed & (2 ** 64 - 1), _ptr(bits), _ptr(probs), _stream(stream)))
+        finally:
+            if own:
+                work[0].close()
+                work[1].close()
+        return bits.tolist(), [tuple(p) for p in probs]
 
     def sample_terms(self, count: int, seed: int, x=None, alpha=None, stream=None):
         import torch

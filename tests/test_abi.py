@@ -86,3 +86,13 @@ def test_create_without_device_is_an_error(lib):
         lrstab.Simulator(4, 0)
     with pytest.raises(lrstab.LrsError):
         lrstab.Simulator(0, 0)
+
+
+def test_lowered_l1_norm_matches_oracle_tables():
+    """||c||_1 of the lowered slots (the sparsification certificate's delta^2 =
+    ||c||_1^2 / chi) equals the oracle's product of slot l1 norms."""
+    from oracle import decomp
+    for cfg in (workloads.config_tiny(), workloads.config_mid()):
+        low = lrstab.lower_circuit(cfg["n"], cfg["ops"])
+        _, slots = decomp.lower(cfg["ops"])
+        assert low.l1_norm == pytest.approx(decomp.l1_norm(slots), rel=1e-12)
