@@ -174,9 +174,13 @@ def sparsification_certificate(sim: "Simulator", lowered: Lowered, L: int, K: in
     terms, ||psi - Omega||^2 <= <Omega|Omega> - 1 + delta^2 with high probability,
     delta^2 = ||c||_1^2 / chi; <Omega|Omega> is estimated by the median of K means of L
     equatorial samples."""
-    omega2 = sim.norm_median_of_means(L, K, seed)
+    eta = sim.norm_estimate(L * K, seed).cpu().numpy()
+    means = eta.reshape(K, L).mean(axis=1)
+    omega2 = float(np.median(means))            # as lrs_norm_median_of_means
+    stderr = float(eta.std(ddof=1) / np.sqrt(eta.size)) if eta.size > 1 else float("nan")
     delta2 = lowered.l1_norm ** 2 / sim.chi_total
-    return {"omega_norm2": omega2, "delta2": delta2, "bound": omega2 - 1.0 + delta2, "L": L, "K": K}
+    return {"omega_norm2": omega2, "stderr": stderr, "delta2": delta2, "bound": omega2 - 1.0 + delta2,
+            "bound_plus_2_stderr": omega2 + 2 * stderr - 1.0 + delta2, "L": L, "K": K}
 
 
 def lower_circuit(n: int, ops, ccz_mode: str = "proj") -> Lowered:
