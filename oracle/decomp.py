@@ -82,6 +82,53 @@ def lower(ops, ccz_mode: str = "proj"):
     return gates, slots
 
 
+def lower_gadget(n: int, ops, ccz_mode: str = "proj"):
+    """Fixed-sample gadget form (Sec. 2.3.1, Eqs. (singlegate), (Uidentity)).
+
+    Every non-Clifford gate V_j on t_j qubits gets t_j ancilla qubits (numbered from
+    n on, in the order of the gates) holding the magic state |V_j> = V_j |+^t_j>; the
+    gate itself becomes CNOT(q_k -> a_k) for its qubits q_k and ancillas a_k, and
+    every ancilla is post-selected on 0 by the projector (I + Z)/2.  Then
+    U|0^n> = 2^{tau/2} (1 x <0^tau|) C |0^n>|Psi>; the factor 2^{t_j/2} of each gadget
+    is folded into the coefficients of its magic-state slot, so that the final
+    (n + tau)-qubit state is exactly U|0^n> (x) |0^tau>.  The magic states take the
+    sum-over-Cliffords decompositions of V_j applied to |+^t_j>.
+
+    Returns (n_total, gates, slots) in the form of lower().
+    """
+    gadgets, a = [], n
+    for op in ops:
+        if op[0] in ("T", "RZ"):
+            gadgets.append((op, [a]))
+            a += 1
+        elif op[0] == "CCZ":
+            gadgets.append((op, [a, a + 1, a + 2]))
+            a += 3
+    gates, slots = [], []
+    for op, anc in gadgets:
+        for q in anc:
+            gates.append(("H", q))
+        if op[0] == "CCZ":
+            vop = ("CCZ_PROJ" if ccz_mode == "proj" else "CCZ_SUM8",) + tuple(anc)
+        else:
+            vop = (op[0], anc[0]) + tuple(op[2:])
+        scale = 2.0 ** (len(anc) / 2)
+        gates.append(("SLOT", len(slots)))
+        slots.append([(c * scale, K) for c, K in gate_decomposition(vop)])
+    k = 0
+    for op in ops:
+        if op[0] in ("T", "RZ", "CCZ"):
+            anc = gadgets[k][1]
+            k += 1
+            for qk, ak in zip(op[1:1 + len(anc)], anc):
+                gates.append(("CX", qk, ak))
+        else:
+            gates.append(op)
+    for q in range(n, a):
+        gates.append(("P0", q))
+    return a, gates, slots
+
+
 def l1_norm(slots) -> float:
     """||c||_1 of the product decomposition = prod_p ||c^(p)||_1 (Sec. 2.3.2)."""
     out = 1.0
@@ -162,13 +209,17 @@ def term_choices(slots, alpha: int, mode: str, seed: int):
 
 
 def build_decomposition(n: int, ops, chi: int, mode: str, seed: int = 0, ccz_mode: str = "proj",
-                        alphas=None):
+                        alphas=None, method: str = "sum"):
     """Terms (CHForm) and coefficients b_alpha of the stabilizer decomposition.
 
     `alphas` restricts the work to a subset of term indices (the other terms
-    are not built); chi is still the total number of terms.
+    are not built); chi is still the total number of terms.  method "gadget" builds
+    the fixed-sample gadget form on n + tau qubits (lower_gadget).
     """
-    gates, slots = lower(ops, ccz_mode)
+    if method == "gadget":
+        n, gates, slots = lower_gadget(n, ops, ccz_mode)
+    else:
+        gates, slots = lower(ops, ccz_mode)
     if mode == "exact" and chi != exact_chi(slots):
         raise ValueError(f"exact mode needs chi = {exact_chi(slots)}")
     alphas = range(chi) if alphas is None else alphas

@@ -102,3 +102,39 @@ def test_sparsified_norm_concentrates():
     amps = np.array([amplitude(terms, coefs, x) for x in range(1 << n)])
     assert np.linalg.norm(amps) ** 2 == pytest.approx(1.0, abs=0.05)
     assert np.linalg.norm(amps - psi) ** 2 < 3 * (decomp.l1_norm(decomp.lower(ops)[1]) ** 2) / 2000
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gadget_form_equals_circuit_state(seed):
+    """Fixed-sample gadgets (Eq. (Uidentity)): the exact decomposition on n + tau
+    qubits is U|0^n> (x) |0^tau> (ancillas in the high bits), for T, RZ and CCZ in
+    both CCZ forms."""
+    rng = random.Random(600 + seed)
+    n = rng.randint(3, 4)
+    ops = []
+    for _ in range(12):
+        r = rng.random()
+        if r < 0.3:
+            ops.append(("H", rng.randrange(n)))
+        elif r < 0.5:
+            a, b = rng.sample(range(n), 2)
+            ops.append(("CX", a, b))
+        elif r < 0.6:
+            ops.append(("S", rng.randrange(n)))
+        elif r < 0.7:
+            a, b = rng.sample(range(n), 2)
+            ops.append(("CZ", a, b))
+    pos = rng.sample(range(len(ops) + 1), 3)
+    extra = [("T", rng.randrange(n)), ("RZ", rng.randrange(n), rng.uniform(-2.0, 2.0)),
+             ("CCZ",) + tuple(rng.sample(range(n), 3))]
+    for p_, e in sorted(zip(pos, extra), reverse=True):
+        ops.insert(p_, e)
+    want = dense.run(n, ops)
+    for ccz_mode in ("proj", "sum8"):
+        n_total, gates, slots = decomp.lower_gadget(n, ops, ccz_mode)
+        assert n_total == n + 1 + 1 + 3
+        chi = decomp.exact_chi(slots)
+        terms, coefs, _ = decomp.build_decomposition(n, ops, chi, "exact", ccz_mode=ccz_mode, method="gadget")
+        psi = sum(b * np.array([t.amplitude(x) for x in range(1 << n_total)]) for t, b in zip(terms, coefs))
+        np.testing.assert_allclose(psi[: 1 << n], want, atol=1e-10)
+        assert np.abs(psi[1 << n:]).max() < 1e-10
