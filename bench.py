@@ -513,6 +513,47 @@ def batch_study(local=0, k=8, seed=0):
     return res
 
 
+def gadget_study(local=0, n=30, n_t=14, B=4096):
+    """Fixed-sample gadgets (Sec. 2.3.1) against sum-over-Cliffords on the same
+    circuit (n=30, 600 Cliffords + 14 T, both exact with 2^14 terms): the gadget form
+    works on n + 14 = 44 qubits.  Times apply_clifford and a B-string amplitude batch
+    for each, and checks the amplitudes agree."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    ops = workloads.random_clifford_t(n, 600, n_t, seed=workloads.SEED_BASE + 61)
+    dev = torch.device(f"cuda:{local}")
+    x = torch.from_numpy(workloads.random_bitstrings(n, B, workloads.SEED_BASE + 63).view(np.int64)).to(dev)
+    res, amps = {}, {}
+    for method in ("sum", "gadget"):
+        low = lrstab.lower_circuit(n, ops, method=method)
+        chi = low.exact_chi
+        sim = lrstab.Simulator(low.n_total, local)
+        ts, ta = [], []
+        for rep in range(3):
+            sim.init_terms(low, chi, mode="exact")
+            a, b = _ev()
+            a.record()
+            sim.apply_clifford(low.gates)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            a.record()
+            out = sim.amplitude(x)
+            b.record()
+            b.synchronize()
+            ta.append(a.elapsed_time(b))
+        amps[method] = out.cpu().numpy()
+        res[method] = {"qubits": low.n_total, "chi": chi, "gates": len(low.gates),
+                       "apply_ms": min(ts), "amplitude_ms": min(ta)}
+        sim.close()
+    d = amps["sum"] - amps["gadget"]
+    res["max_amplitude_difference"] = float(np.abs(d[:, 0] + 1j * d[:, 1]).max())
+    res["gadget_over_sum_time"] = ((res["gadget"]["apply_ms"] + res["gadget"]["amplitude_ms"]) /
+                                   (res["sum"]["apply_ms"] + res["sum"]["amplitude_ms"]))
+    return res
+
+
 def marginal_study(local=0, w=8, L=256, K=3):
     """Chain-rule sampling of w bits by norm estimation (end of Sec. 4.3) on the n=40
     hidden shift (exact 2^16-term decomposition of |s>): every bit must come out as
@@ -775,7 +816,7 @@ def main():
     if rank == 0 and not args.small:
         cert = lrstab.sparsification_certificate(sim, low, L=L_A, K=3, seed=777)
     sim.close()
-    ess = qaoa = batch = gemm = marg = None
+    ess = qaoa = batch = gemm = marg = gadget = None
     if rank == 0 and not args.small and not args.no_sampler_study:
         ess = sampler_study(local)
     if rank == 0 and not args.small and not args.no_extra:
@@ -783,6 +824,7 @@ def main():
         batch = batch_study(local)
         gemm = mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops"))
         marg = marginal_study(local)
+        gadget = gadget_study(local)
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -794,7 +836,7 @@ def main():
            "roofline": roof, "phases": rows, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "ess": ess,
            "qaoa_n50": qaoa, "batch8": batch, "mlp_gemm": gemm, "marginals": marg,
-           "sparsification_certificate": cert}
+           "sparsification_certificate": cert, "gadget_vs_sum": gadget}
     print(json.dumps(out))
 
 

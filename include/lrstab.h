@@ -134,6 +134,20 @@ lrs_status lrs_lower_circuit(int32_t n_qubits, const lrs_circuit_op* ops_host, i
                              lrs_slot* slots_host, int64_t slots_cap, int64_t* n_slots,
                              lrs_gate* k_gates_host, int64_t k_cap, int64_t* n_k_gates);
 
+/* Fixed-sample gadget form of the same circuit (Sec. 2.3.1, Eqs. (singlegate),
+ * (Uidentity)): each non-Clifford op V_j on t_j qubits (T, RZ: 1; CCZ: 3) gets t_j
+ * ancillas, numbered from n on in the order of the ops, prepared in the magic state
+ * V_j |+^t_j> (H on each ancilla, then V_j's sum-over-Cliffords slot on the
+ * ancillas with every coefficient times 2^{t_j/2}); V_j itself becomes
+ * CX(q_k, a_k) for its qubits q_k and ancillas a_k; at the end every ancilla is
+ * post-selected on 0 by the projector (I + Z)/2.  The state on *n_total = n + tau
+ * <= 64 qubits is then exactly (U|0^n>) (x) |0^tau> (ancilla bits of x are 0).
+ * Outputs as lrs_lower_circuit.                                                  */
+lrs_status lrs_lower_gadget(int32_t n_qubits, const lrs_circuit_op* ops_host, int64_t n_ops, int32_t ccz_mode,
+                            int32_t* n_total, lrs_gate* gates_host, int64_t gates_cap, int64_t* n_gates,
+                            lrs_slot* slots_host, int64_t slots_cap, int64_t* n_slots,
+                            lrs_gate* k_gates_host, int64_t k_cap, int64_t* n_k_gates);
+
 /* ---- context ------------------------------------------------------------------ */
 /* Create a context for n_qubits (1..64) on CUDA device `device`.
  * Errors: LRS_ERR_ARG (n out of range), LRS_ERR_CUDA (bad device).           */

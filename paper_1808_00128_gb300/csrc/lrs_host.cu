@@ -80,24 +80,56 @@ lrs_gate mk(int op, int q, int r = 0) {
 }
 }  // namespace
 
-extern "C" lrs_status lrs_lower_circuit(int32_t n, const lrs_circuit_op* ops, int64_t n_ops,
-                                        int32_t ccz_mode, lrs_gate* gates, int64_t gates_cap,
-                                        int64_t* n_gates, lrs_slot* slots, int64_t slots_cap,
-                                        int64_t* n_slots, lrs_gate* k_gates, int64_t k_cap,
-                                        int64_t* n_k_gates) {
+// The sum-over-Cliffords slot of one non-Clifford op acting on qubits q[0..t) (the
+// op's own qubits, or its gadget's ancillas), every coefficient times `scale`.
+static void push_slot(Lowering& L, const lrs_circuit_op& o, const int* q, int32_t ccz_mode, double scale) {
+    lrs_slot s;
+    memset(&s, 0, sizeof(s));
+    if (o.kind == LRS_C_T || o.kind == LRS_C_RZ) {
+        // R(theta) = (cos(th/2) - sin(th/2)) I + sqrt2 e^{-i pi/4} sin(th/2) S, th >= 0;
+        // conjugate on (I, S^dagger) for theta < 0.  T = e^{i pi/8} R(pi/4).
+        const double theta = (o.kind == LRS_C_T) ? M_PI / 4 : o.theta;
+        const double th = fabs(theta);
+        const double c0 = cos(th / 2) - sin(th / 2);
+        const double sn = sin(th / 2);
+        // sqrt2 e^{-i pi/4} = 1 - i
+        const double c1re = sn, c1im = (theta >= 0) ? -sn : sn;
+        double g_re = 1.0, g_im = 0.0;
+        if (o.kind == LRS_C_T) { g_re = cos(M_PI / 8); g_im = sin(M_PI / 8); }
+        L.add_choice(s, scale * (g_re * c0), scale * (g_im * c0), {});
+        L.add_choice(s, scale * (g_re * c1re - g_im * c1im), scale * (g_re * c1im + g_im * c1re),
+                     {mk(theta >= 0 ? LRS_OP_S : LRS_OP_SDG, q[0])});
+    } else {
+        const int a = q[0], b = q[1], c = q[2];
+        if (ccz_mode == LRS_CCZ_PROJECTOR) {
+            L.add_choice(s, scale * 1.0, 0.0, {});
+            L.add_choice(s, scale * -2.0, 0.0, {mk(LRS_OP_P1, a), mk(LRS_OP_P1, b), mk(LRS_OP_P1, c)});
+        } else {
+            const double w = scale * (1.0 / 6.0);
+            L.add_choice(s, w, 0, {});
+            L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b)});
+            L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, c)});
+            L.add_choice(s, w, 0, {mk(LRS_OP_CZ, b, c)});
+            L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, a, c), mk(LRS_OP_Z, a)});
+            L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, b, c), mk(LRS_OP_Z, b)});
+            L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, c), mk(LRS_OP_CZ, b, c), mk(LRS_OP_Z, c)});
+            L.add_choice(s, -w, 0,
+                         {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, a, c), mk(LRS_OP_CZ, b, c), mk(LRS_OP_Z, a),
+                          mk(LRS_OP_Z, b), mk(LRS_OP_Z, c)});
+        }
+    }
+    L.gates.push_back(mk(LRS_OP_SLOT, 0, (int)L.slots.size()));
+    L.slots.push_back(s);
+}
+
+static lrs_status check_ops(int32_t n, const lrs_circuit_op* ops, int64_t n_ops) {
     if (n < 1 || n > 64) return lrs_fail(LRS_ERR_ARG, "n_qubits must be in 1..64 (got %d)", n);
     if (n_ops < 0 || (n_ops > 0 && !ops)) return lrs_fail(LRS_ERR_ARG, "bad ops array");
-    if (ccz_mode != LRS_CCZ_PROJECTOR && ccz_mode != LRS_CCZ_SUM8)
-        return lrs_fail(LRS_ERR_ARG, "unknown ccz_mode %d", ccz_mode);
-    Lowering L;
-    const double r2 = sqrt(2.0);
     for (int64_t i = 0; i < n_ops; ++i) {
         const lrs_circuit_op& o = ops[i];
-        int nq = 1;
-        if (o.kind == LRS_C_CX || o.kind == LRS_C_CZ) nq = 2;
-        if (o.kind == LRS_C_CCZ) nq = 3;
         if (o.kind < LRS_C_H || o.kind > LRS_C_CCZ)
             return lrs_fail(LRS_ERR_ARG, "op %lld: unknown kind %d", (long long)i, o.kind);
+        const int nq = (o.kind == LRS_C_CX || o.kind == LRS_C_CZ) ? 2 : (o.kind == LRS_C_CCZ ? 3 : 1);
         for (int t = 0; t < nq; ++t) {
             if (o.q[t] < 0 || o.q[t] >= n)
                 return lrs_fail(LRS_ERR_ARG, "op %lld: qubit %d out of range", (long long)i, o.q[t]);
@@ -105,62 +137,13 @@ extern "C" lrs_status lrs_lower_circuit(int32_t n, const lrs_circuit_op* ops, in
                 if (o.q[t] == o.q[t2])
                     return lrs_fail(LRS_ERR_ARG, "op %lld: repeated qubit %d", (long long)i, o.q[t]);
         }
-        switch (o.kind) {
-            case LRS_C_H: L.gates.push_back(mk(LRS_OP_H, o.q[0])); break;
-            case LRS_C_S: L.gates.push_back(mk(LRS_OP_S, o.q[0])); break;
-            case LRS_C_SDG: L.gates.push_back(mk(LRS_OP_SDG, o.q[0])); break;
-            case LRS_C_Z: L.gates.push_back(mk(LRS_OP_Z, o.q[0])); break;
-            case LRS_C_CX: L.gates.push_back(mk(LRS_OP_CX, o.q[0], o.q[1])); break;
-            case LRS_C_CZ: L.gates.push_back(mk(LRS_OP_CZ, o.q[0], o.q[1])); break;
-            case LRS_C_T:
-            case LRS_C_RZ: {
-                // R(theta) = (cos(th/2) - sin(th/2)) I + sqrt2 e^{-i pi/4} sin(th/2) S, th >= 0;
-                // conjugate on (I, S^dagger) for theta < 0.  T = e^{i pi/8} R(pi/4).
-                const double theta = (o.kind == LRS_C_T) ? M_PI / 4 : o.theta;
-                const double th = fabs(theta);
-                const double c0 = cos(th / 2) - sin(th / 2);
-                const double sn = sin(th / 2);
-                // sqrt2 e^{-i pi/4} = 1 - i
-                double c1re = sn, c1im = (theta >= 0) ? -sn : sn;
-                double g_re = 1.0, g_im = 0.0;
-                if (o.kind == LRS_C_T) { g_re = cos(M_PI / 8); g_im = sin(M_PI / 8); }
-                lrs_slot s;
-                memset(&s, 0, sizeof(s));
-                L.add_choice(s, g_re * c0, g_im * c0, {});
-                L.add_choice(s, g_re * c1re - g_im * c1im, g_re * c1im + g_im * c1re,
-                             {mk(theta >= 0 ? LRS_OP_S : LRS_OP_SDG, o.q[0])});
-                (void)r2;
-                L.gates.push_back(mk(LRS_OP_SLOT, 0, (int)L.slots.size()));
-                L.slots.push_back(s);
-                break;
-            }
-            case LRS_C_CCZ: {
-                const int a = o.q[0], b = o.q[1], c = o.q[2];
-                lrs_slot s;
-                memset(&s, 0, sizeof(s));
-                if (ccz_mode == LRS_CCZ_PROJECTOR) {
-                    L.add_choice(s, 1.0, 0.0, {});
-                    L.add_choice(s, -2.0, 0.0, {mk(LRS_OP_P1, a), mk(LRS_OP_P1, b), mk(LRS_OP_P1, c)});
-                } else {
-                    const double w = 1.0 / 6.0;
-                    L.add_choice(s, w, 0, {});
-                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b)});
-                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, c)});
-                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, b, c)});
-                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, a, c), mk(LRS_OP_Z, a)});
-                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, b, c), mk(LRS_OP_Z, b)});
-                    L.add_choice(s, w, 0, {mk(LRS_OP_CZ, a, c), mk(LRS_OP_CZ, b, c), mk(LRS_OP_Z, c)});
-                    L.add_choice(s, -w, 0,
-                                 {mk(LRS_OP_CZ, a, b), mk(LRS_OP_CZ, a, c), mk(LRS_OP_CZ, b, c),
-                                  mk(LRS_OP_Z, a), mk(LRS_OP_Z, b), mk(LRS_OP_Z, c)});
-                }
-                L.gates.push_back(mk(LRS_OP_SLOT, 0, (int)L.slots.size()));
-                L.slots.push_back(s);
-                break;
-            }
-        }
-        if (L.slots.size() > 65535) return lrs_fail(LRS_ERR_ARG, "more than 65535 slots");
     }
+    return LRS_OK;
+}
+
+static lrs_status emit(const Lowering& L, lrs_gate* gates, int64_t gates_cap, int64_t* n_gates, lrs_slot* slots,
+                       int64_t slots_cap, int64_t* n_slots, lrs_gate* k_gates, int64_t k_cap, int64_t* n_k_gates) {
+    if (L.slots.size() > 65535) return lrs_fail(LRS_ERR_ARG, "more than 65535 slots");
     if (n_gates) *n_gates = (int64_t)L.gates.size();
     if (n_slots) *n_slots = (int64_t)L.slots.size();
     if (n_k_gates) *n_k_gates = (int64_t)L.kg.size();
@@ -172,6 +155,87 @@ extern "C" lrs_status lrs_lower_circuit(int32_t n, const lrs_circuit_op* ops, in
     if (!L.slots.empty()) memcpy(slots, L.slots.data(), L.slots.size() * sizeof(lrs_slot));
     if (!L.kg.empty()) memcpy(k_gates, L.kg.data(), L.kg.size() * sizeof(lrs_gate));
     return LRS_OK;
+}
+
+extern "C" lrs_status lrs_lower_gadget(int32_t n, const lrs_circuit_op* ops, int64_t n_ops, int32_t ccz_mode,
+                                       int32_t* n_total, lrs_gate* gates, int64_t gates_cap, int64_t* n_gates,
+                                       lrs_slot* slots, int64_t slots_cap, int64_t* n_slots, lrs_gate* k_gates,
+                                       int64_t k_cap, int64_t* n_k_gates) {
+    lrs_status rc = check_ops(n, ops, n_ops);
+    if (rc != LRS_OK) return rc;
+    if (ccz_mode != LRS_CCZ_PROJECTOR && ccz_mode != LRS_CCZ_SUM8)
+        return lrs_fail(LRS_ERR_ARG, "unknown ccz_mode %d", ccz_mode);
+    // ancillas from qubit n on, in the order of the non-Clifford ops
+    int64_t tau = 0;
+    for (int64_t i = 0; i < n_ops; ++i)
+        tau += ops[i].kind == LRS_C_CCZ ? 3 : ((ops[i].kind == LRS_C_T || ops[i].kind == LRS_C_RZ) ? 1 : 0);
+    if (n + tau > 64)
+        return lrs_fail(LRS_ERR_ARG, "gadget form needs %lld qubits (more than 64)", (long long)(n + tau));
+    if (n_total) *n_total = (int32_t)(n + tau);
+    Lowering L;
+    // magic states |V_j> = V_j |+^t>: H on the ancillas, then V_j's slot on them with its
+    // coefficients times 2^{t/2} (the post-selection renormalisation of Eq. (Uidentity))
+    int a = n;
+    for (int64_t i = 0; i < n_ops; ++i) {
+        const lrs_circuit_op& o = ops[i];
+        const int t = o.kind == LRS_C_CCZ ? 3 : ((o.kind == LRS_C_T || o.kind == LRS_C_RZ) ? 1 : 0);
+        if (t == 0) continue;
+        const int anc[3] = {a, a + 1, a + 2};
+        for (int k = 0; k < t; ++k) L.gates.push_back(mk(LRS_OP_H, anc[k]));
+        push_slot(L, o, anc, ccz_mode, (t == 1) ? sqrt(2.0) : 2.0 * sqrt(2.0));
+        a += t;
+    }
+    // the circuit with V_j replaced by CX(q_k, a_k), then post-selection on 0^tau
+    a = n;
+    for (int64_t i = 0; i < n_ops; ++i) {
+        const lrs_circuit_op& o = ops[i];
+        switch (o.kind) {
+            case LRS_C_H: L.gates.push_back(mk(LRS_OP_H, o.q[0])); break;
+            case LRS_C_S: L.gates.push_back(mk(LRS_OP_S, o.q[0])); break;
+            case LRS_C_SDG: L.gates.push_back(mk(LRS_OP_SDG, o.q[0])); break;
+            case LRS_C_Z: L.gates.push_back(mk(LRS_OP_Z, o.q[0])); break;
+            case LRS_C_CX: L.gates.push_back(mk(LRS_OP_CX, o.q[0], o.q[1])); break;
+            case LRS_C_CZ: L.gates.push_back(mk(LRS_OP_CZ, o.q[0], o.q[1])); break;
+            case LRS_C_T:
+            case LRS_C_RZ: L.gates.push_back(mk(LRS_OP_CX, o.q[0], a)); a += 1; break;
+            case LRS_C_CCZ:
+                for (int k = 0; k < 3; ++k) L.gates.push_back(mk(LRS_OP_CX, o.q[k], a + k));
+                a += 3;
+                break;
+        }
+    }
+    for (int q = n; q < a; ++q) L.gates.push_back(mk(LRS_OP_P0, q));
+    return emit(L, gates, gates_cap, n_gates, slots, slots_cap, n_slots, k_gates, k_cap, n_k_gates);
+}
+
+extern "C" lrs_status lrs_lower_circuit(int32_t n, const lrs_circuit_op* ops, int64_t n_ops,
+                                        int32_t ccz_mode, lrs_gate* gates, int64_t gates_cap,
+                                        int64_t* n_gates, lrs_slot* slots, int64_t slots_cap,
+                                        int64_t* n_slots, lrs_gate* k_gates, int64_t k_cap,
+                                        int64_t* n_k_gates) {
+    lrs_status rc = check_ops(n, ops, n_ops);
+    if (rc != LRS_OK) return rc;
+    if (ccz_mode != LRS_CCZ_PROJECTOR && ccz_mode != LRS_CCZ_SUM8)
+        return lrs_fail(LRS_ERR_ARG, "unknown ccz_mode %d", ccz_mode);
+    Lowering L;
+    for (int64_t i = 0; i < n_ops; ++i) {
+        const lrs_circuit_op& o = ops[i];
+        switch (o.kind) {
+            case LRS_C_H: L.gates.push_back(mk(LRS_OP_H, o.q[0])); break;
+            case LRS_C_S: L.gates.push_back(mk(LRS_OP_S, o.q[0])); break;
+            case LRS_C_SDG: L.gates.push_back(mk(LRS_OP_SDG, o.q[0])); break;
+            case LRS_C_Z: L.gates.push_back(mk(LRS_OP_Z, o.q[0])); break;
+            case LRS_C_CX: L.gates.push_back(mk(LRS_OP_CX, o.q[0], o.q[1])); break;
+            case LRS_C_CZ: L.gates.push_back(mk(LRS_OP_CZ, o.q[0], o.q[1])); break;
+            default: {
+                const int q[3] = {o.q[0], o.q[1], o.q[2]};
+                push_slot(L, o, q, ccz_mode, 1.0);
+                break;
+            }
+        }
+        if (L.slots.size() > 65535) return lrs_fail(LRS_ERR_ARG, "more than 65535 slots");
+    }
+    return emit(L, gates, gates_cap, n_gates, slots, slots_cap, n_slots, k_gates, k_cap, n_k_gates);
 }
 
 // ---------------------------------------------------------------------------------

@@ -39,7 +39,7 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_mlp_info", "lrs_mlp_set_gemm", "lrs_mlp_get_gemm", "lrs_mlp_set_params", "lrs_mlp_get_params", "lrs_mlp_forward",
             "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned",
             "lrs_apply_clifford_batch", "lrs_set_tuning", "lrs_get_tuning", "lrs_copy_terms",
-            "lrs_norm_median_of_means", "lrs_marginal_sample"]
+            "lrs_norm_median_of_means", "lrs_marginal_sample", "lrs_lower_gadget"]
 
 
 class LrsError(RuntimeError):
@@ -92,6 +92,7 @@ def lib():
         "lrs_apply_clifford_batch": [vp, vp, vp, i32, vp],
         "lrs_set_tuning": [vp, i32, i64],
         "lrs_copy_terms": [vp, vp, vp],
+        "lrs_lower_gadget": [i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, vp, vp, i64, vp],
         "lrs_norm_median_of_means": [vp, i64, i32, u64, vp, vp],
         "lrs_marginal_sample": [vp, vp, vp, vp, i32, i64, i32, u64, vp, vp, vp],
         "lrs_get_tuning": [vp, i32, vp],
@@ -143,10 +144,12 @@ def circuit_ops(ops) -> np.ndarray:
 
 
 class Lowered:
-    """Lowered circuit: gates (with SLOT entries), slot tables and K_j gate lists."""
+    """Lowered circuit: gates (with SLOT entries), slot tables and K_j gate lists, on
+    n_total qubits (the circuit's own n, or n + tau for the gadget form)."""
 
-    def __init__(self, gates, slots, kgates):
+    def __init__(self, gates, slots, kgates, n_total=None):
         self.gates, self.slots, self.kgates = gates, slots, kgates
+        self.n_total = n_total
 
     @property
     def exact_chi(self) -> int:
@@ -183,18 +186,26 @@ def sparsification_certificate(sim: "Simulator", lowered: Lowered, L: int, K: in
             "bound_plus_2_stderr": omega2 + 2 * stderr - 1.0 + delta2, "L": L, "K": K}
 
 
-def lower_circuit(n: int, ops, ccz_mode: str = "proj") -> Lowered:
+def lower_circuit(n: int, ops, ccz_mode: str = "proj", method: str = "sum") -> Lowered:
+    """lrs_lower_circuit (method "sum": sum-over-Cliffords slots on n qubits) or
+    lrs_lower_gadget (method "gadget": fixed-sample gadgets on n + tau qubits)."""
     cops = circuit_ops(ops)
-    ng, ns, nk = C.c_int64(0), C.c_int64(0), C.c_int64(0)
-    # first call sizes the outputs
-    gates = np.zeros(max(1, 2 * len(ops)), GATE_DT)
+    ng, ns, nk, nt = C.c_int64(0), C.c_int64(0), C.c_int64(0), C.c_int32(n)
+    gates = np.zeros(max(1, 8 * len(ops) + 8), GATE_DT)
     slots = np.zeros(max(1, len(ops)), SLOT_DT)
     kg = np.zeros(max(1, 8 * len(ops)), GATE_DT)
-    rc = lib().lrs_lower_circuit(n, _ptr(cops), len(ops), CCZ_MODE[ccz_mode], _ptr(gates), len(gates),
-                                 C.byref(ng), _ptr(slots), len(slots), C.byref(ns), _ptr(kg), len(kg),
-                                 C.byref(nk))
+    if method == "gadget":
+        rc = lib().lrs_lower_gadget(n, _ptr(cops), len(ops), CCZ_MODE[ccz_mode], C.byref(nt), _ptr(gates),
+                                    len(gates), C.byref(ng), _ptr(slots), len(slots), C.byref(ns), _ptr(kg),
+                                    len(kg), C.byref(nk))
+    elif method == "sum":
+        rc = lib().lrs_lower_circuit(n, _ptr(cops), len(ops), CCZ_MODE[ccz_mode], _ptr(gates), len(gates),
+                                     C.byref(ng), _ptr(slots), len(slots), C.byref(ns), _ptr(kg), len(kg),
+                                     C.byref(nk))
+    else:
+        raise ValueError(f"unknown lowering method {method!r}")
     _check(rc)
-    return Lowered(gates[: ng.value].copy(), slots[: ns.value].copy(), kg[: nk.value].copy())
+    return Lowered(gates[: ng.value].copy(), slots[: ns.value].copy(), kg[: nk.value].copy(), nt.value)
 
 
 def gates_array(gates) -> np.ndarray:

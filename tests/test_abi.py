@@ -41,11 +41,17 @@ def test_struct_layouts():
 
 
 @pytest.mark.parametrize("ccz_mode", ["proj", "sum8"])
-def test_lowering_matches_oracle_tables(lib, ccz_mode):
+@pytest.mark.parametrize("method", ["sum", "gadget"])
+def test_lowering_matches_oracle_tables(lib, ccz_mode, method):
     ops = workloads.random_clifford_t(7, 60, 5, seed=3)
     ops += [("RZ", 2, 0.3), ("RZ", 4, -0.7), ("CCZ", 1, 3, 5), ("SDG", 0), ("Z", 6)]
-    low = lrstab.lower_circuit(7, ops, ccz_mode)
-    gates, slots = decomp.lower(ops, ccz_mode)
+    low = lrstab.lower_circuit(7, ops, ccz_mode, method=method)
+    if method == "gadget":
+        n_total, gates, slots = decomp.lower_gadget(7, ops, ccz_mode)
+        assert low.n_total == n_total == 7 + 5 + 2 + 3
+    else:
+        gates, slots = decomp.lower(ops, ccz_mode)
+        assert low.n_total == 7
     assert len(low.gates) == len(gates)
     inv = {v: k for k, v in lrstab.OP.items()}
     for g, og in zip(low.gates, gates):
@@ -60,7 +66,7 @@ def test_lowering_matches_oracle_tables(lib, ccz_mode):
     for s, dec in zip(low.slots, slots):
         assert s["n_choices"] == len(dec)
         for j, (c, kg) in enumerate(dec):
-            assert complex(s["c_re"][j], s["c_im"][j]) == pytest.approx(c, abs=1e-15)
+            assert complex(s["c_re"][j], s["c_im"][j]) == pytest.approx(c, abs=4e-15)
             sub = low.kgates[s["k_off"][j]: s["k_off"][j] + s["k_len"][j]]
             got = []
             for g in sub:
@@ -76,6 +82,8 @@ def test_lowering_rejects_bad_input(lib):
         lrstab.lower_circuit(3, [("H", 3)])
     with pytest.raises(lrstab.LrsError):
         lrstab.lower_circuit(65, [])
+    with pytest.raises(lrstab.LrsError):      # 40 + 25 ancillas > 64 qubits
+        lrstab.lower_circuit(40, [("T", q % 40) for q in range(25)], method="gadget")
 
 
 def test_create_without_device_is_an_error(lib):
