@@ -554,6 +554,42 @@ def gadget_study(local=0, n=30, n_t=14, B=4096):
     return res
 
 
+def prefix_study(local=0, sizes=(16, 20)):
+    """Prefix sharing on exact n=40 hidden shifts (16 and 20 CCZ slots, chi = 2^16 and
+    2^20): the whole circuit per term (the paper's way) vs lrs_apply_circuit_shared,
+    which runs each Clifford segment once per distinct choice prefix.  Same terms bit
+    for bit (compared on the first and last 4096 terms)."""
+    import numpy as np
+    from paper_1808_00128_gb300 import lrstab, workloads
+    out = []
+    for n_ccz in sizes:
+        n = 40
+        ops, _ = workloads.hidden_shift_circuit(n, n_ccz, workloads.SEED_BASE + 3)
+        chi = 1 << n_ccz
+        low = lrstab.lower_circuit(n, ops)
+        sim = lrstab.Simulator(n, local)
+        res = {"workload": f"hidden_shift_n{n}_ccz{n_ccz}", "chi": chi, "gates": len(low.gates)}
+        ex = {}
+        for name, fn in (("per_term", sim.apply_clifford), ("shared_prefixes", sim.apply_circuit_shared)):
+            ts = []
+            for rep in range(3):
+                sim.init_terms(low, chi, mode="exact")
+                a, b = _ev()
+                a.record()
+                fn(low.gates)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            res[name] = {"ms": min(ts), "term_gates_per_s": chi * len(low.gates) / (min(ts) * 1e-3)}
+            ex[name] = (sim.export_terms(0, 4096), sim.export_terms(chi - 4096, 4096))
+        res["speedup"] = res["per_term"]["ms"] / res["shared_prefixes"]["ms"]
+        res["identical_terms"] = all(np.array_equal(x[k], y[k]) for x, y in zip(ex["per_term"], ex["shared_prefixes"])
+                                     for k in x)
+        sim.close()
+        out.append(res)
+    return out
+
+
 def marginal_study(local=0, w=8, L=256, K=3):
     """Chain-rule sampling of w bits by norm estimation (end of Sec. 4.3) on the n=40
     hidden shift (exact 2^16-term decomposition of |s>): every bit must come out as
@@ -816,7 +852,7 @@ def main():
     if rank == 0 and not args.small:
         cert = lrstab.sparsification_certificate(sim, low, L=L_A, K=3, seed=777)
     sim.close()
-    ess = qaoa = batch = gemm = marg = gadget = None
+    ess = qaoa = batch = gemm = marg = gadget = prefix = None
     if rank == 0 and not args.small and not args.no_sampler_study:
         ess = sampler_study(local)
     if rank == 0 and not args.small and not args.no_extra:
@@ -825,6 +861,7 @@ def main():
         gemm = mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops"))
         marg = marginal_study(local)
         gadget = gadget_study(local)
+        prefix = prefix_study(local)
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -836,7 +873,7 @@ def main():
            "roofline": roof, "phases": rows, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "ess": ess,
            "qaoa_n50": qaoa, "batch8": batch, "mlp_gemm": gemm, "marginals": marg,
-           "sparsification_certificate": cert, "gadget_vs_sum": gadget}
+           "sparsification_certificate": cert, "gadget_vs_sum": gadget, "prefix_sharing": prefix}
     print(json.dumps(out))
 
 

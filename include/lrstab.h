@@ -193,6 +193,21 @@ lrs_status lrs_init_terms(lrs_ctx* ctx, const lrs_slot* slots_host, int64_t n_sl
 lrs_status lrs_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates,
                               void* stream);
 
+/* The same as lrs_apply_clifford with the lowered circuit on freshly initialised
+ * EXACT-mode terms (the whole decomposition, alpha0 = 0), sharing the work of common
+ * choice prefixes: term alpha takes choice digit j_p = (alpha / R_p) mod r_p of slot p
+ * (r_q its number of nonzero choices, R_p = r_0 ... r_{p-1}; the enumeration of
+ * lrs_init_terms), so before slot p only R_p distinct states exist.  Each Clifford
+ * segment runs on those R_p states; at a run of consecutive slots p..p+k-1 they are
+ * copied out to R_{p+k} terms, which take the run's slots and the next segment in
+ * one launch.  The gate list must hold every slot exactly once, in order 0, 1, ..
+ * The resulting terms equal lrs_apply_clifford's bit for bit; the work of segment p
+ * falls from chi to R_p terms (the paper applies each term's gates separately).
+ * LRS_ERR_STATE if the terms are not fresh EXACT-mode terms of the whole
+ * decomposition or the slots' radices do not multiply to chi (checked before any
+ * launch).  Synchronises the stream after the gate upload.                         */
+lrs_status lrs_apply_circuit_shared(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, void* stream);
+
 /* Batched form of lrs_apply_clifford for several circuits (contexts on one
  * device, e.g. decompositions of uneven chi): context i receives gate list i
  * (copied before return).  All tiles of all circuits run in one launch (up to

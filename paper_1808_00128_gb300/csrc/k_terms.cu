@@ -155,7 +155,31 @@ __global__ void k_sample_terms(TermsView T, int64_t count, uint64_t seed, uint64
     if (alpha_out) alpha_out[i] = a;
 }
 
+// Prefix sharing: terms [R, Rn) become copies of term (alpha mod R) -- the state of
+// their common choice prefix (exact mode, slot 0 the least significant digit).
+__global__ void k_expand_terms(TermsView T, int64_t R, int64_t Rn) {
+    const int64_t a = R + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= Rn) return;
+    const int64_t src = a % R;
+    for (int p = 0; p < T.n; ++p) {
+        T.F[(int64_t)p * T.cap + a] = T.F[(int64_t)p * T.cap + src];
+        T.G[(int64_t)p * T.cap + a] = T.G[(int64_t)p * T.cap + src];
+        T.M[(int64_t)p * T.cap + a] = T.M[(int64_t)p * T.cap + src];
+    }
+    T.glo[a] = T.glo[src]; T.ghi[a] = T.ghi[src];
+    T.v[a] = T.v[src]; T.s[a] = T.s[src];
+    T.omega[a] = T.omega[src];
+}
+
 }  // namespace
+
+lrs_status launch_expand_terms(lrs_ctx* ctx, int64_t R, int64_t Rn, cudaStream_t st) {
+    if (Rn <= R) return LRS_OK;
+    const int tpb = 256;
+    k_expand_terms<<<(unsigned)((Rn - R + tpb - 1) / tpb), tpb, 0, st>>>(ctx->view(), R, Rn);
+    LRS_LAUNCH_CHECK("expand terms kernel");
+    return LRS_OK;
+}
 
 lrs_status launch_init_terms(lrs_ctx* ctx, int32_t mode, uint64_t seed, double scale,
                              cudaStream_t st) {
@@ -168,6 +192,12 @@ lrs_status launch_init_terms(lrs_ctx* ctx, int32_t mode, uint64_t seed, double s
 
 lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates,
                                  cudaStream_t st) {
+    return launch_apply_clifford_range(ctx, gates_dev, n_gates, ctx->cap, st);
+}
+
+// The gate list on the terms of the first ceil(n_terms / APPLY_TPB) tiles only.
+lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates, int64_t n_terms,
+                                       cudaStream_t st) {
     const size_t smem = (size_t)3 * ctx->n * APPLY_TPB * sizeof(uint64_t);
     static int configured_dev = -1;
     if (configured_dev != ctx->device) {
@@ -175,7 +205,9 @@ lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_
                                       3 * 64 * APPLY_TPB * (int)sizeof(uint64_t)));
         configured_dev = ctx->device;
     }
-    const int64_t blocks = ctx->cap / APPLY_TPB;
+    if (n_terms > ctx->cap) n_terms = ctx->cap;
+    const int64_t blocks = (n_terms + APPLY_TPB - 1) / APPLY_TPB;
+    if (blocks == 0 || n_gates == 0) return LRS_OK;
     k_apply_clifford<<<(unsigned)blocks, APPLY_TPB, smem, st>>>(ctx->view(), gates_dev, n_gates);
     LRS_LAUNCH_CHECK("apply_clifford kernel");
     return LRS_OK;

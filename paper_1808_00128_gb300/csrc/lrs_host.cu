@@ -438,6 +438,8 @@ extern "C" lrs_status lrs_init_terms(lrs_ctx* c, const lrs_slot* slots, int64_t 
     rc = launch_init_terms(c, mode, seed, l1 / (double)chi_total, st);
     if (rc != LRS_OK) return rc;
     c->have_terms = true;
+    c->mode = mode;
+    c->fresh = true;
     return LRS_OK;
 }
 
@@ -461,7 +463,72 @@ extern "C" lrs_status lrs_apply_clifford(lrs_ctx* c, const lrs_gate* gates, int6
                              cudaMemcpyHostToDevice, st));
     LRS_CUDA(cudaStreamSynchronize(st));   // pageable source: keep the copy complete on return
     c->n_chains = 0;                        // chain states refer to the old terms
+    c->fresh = false;
     return launch_apply_clifford(c, c->gates_dev, n_gates, st);
+}
+
+extern "C" lrs_status lrs_apply_circuit_shared(lrs_ctx* c, const lrs_gate* gates, int64_t n_gates, void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "lrs_init_terms has not been called");
+    if (!c->fresh) return lrs_fail(LRS_ERR_STATE, "terms are not as lrs_init_terms left them");
+    if (c->mode != LRS_MODE_EXACT || c->alpha0 != 0 || c->chi != c->chi_total)
+        return lrs_fail(LRS_ERR_STATE, "prefix sharing needs the whole exact decomposition in one context");
+    if (n_gates < 0 || (n_gates > 0 && !gates)) return lrs_fail(LRS_ERR_ARG, "bad gate array");
+    // Nonzero choices of the slot that gate i names: its digit's radix.
+    auto radix = [&](int64_t i) {
+        const lrs_slot& sl = c->slots_host[(size_t)gates[i].r];
+        int64_t r = 0;
+        for (int j = 0; j < sl.n_choices; ++j) r += (sl.c_re[j] != 0.0 || sl.c_im[j] != 0.0) ? 1 : 0;
+        return r;
+    };
+    int64_t next_slot = 0, prod = 1;
+    for (int64_t i = 0; i < n_gates; ++i) {
+        lrs_status rc = check_gate(c, gates[i], c->n_slots, true, i, "gate");
+        if (rc != LRS_OK) return rc;
+        if (gates[i].op == LRS_OP_SLOT) {
+            if (gates[i].r != next_slot)
+                return lrs_fail(LRS_ERR_ARG, "gate %lld: slots must appear once each, in order 0..%lld",
+                                (long long)i, (long long)c->n_slots - 1);
+            ++next_slot;
+            const int64_t r = radix(i);
+            if (r < 1 || prod > c->chi / r)
+                return lrs_fail(LRS_ERR_STATE, "gate %lld: slot radices give more than %lld terms", (long long)i,
+                                (long long)c->chi);
+            prod *= r;
+        }
+    }
+    if (next_slot != c->n_slots) return lrs_fail(LRS_ERR_ARG, "the gate list misses slots");
+    if (prod != c->chi)
+        return lrs_fail(LRS_ERR_STATE, "slot radices give %lld terms, not %lld", (long long)prod, (long long)c->chi);
+    LRS_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    if (n_gates > 0) {
+        size_t have = (size_t)c->gates_cap * sizeof(lrs_gate);
+        lrs_status rc = lrs_ensure((void**)&c->gates_dev, &have, (size_t)n_gates * sizeof(lrs_gate));
+        if (rc != LRS_OK) return rc;
+        c->gates_cap = (int64_t)(have / sizeof(lrs_gate));
+        LRS_CUDA(cudaMemcpyAsync(c->gates_dev, gates, (size_t)n_gates * sizeof(lrs_gate), cudaMemcpyHostToDevice, st));
+        LRS_CUDA(cudaStreamSynchronize(st));
+    }
+    c->n_chains = 0;
+    c->fresh = false;
+    // Term alpha has digit j_p = (alpha / R_p) mod r_p over the nonzero choices of slot
+    // p (R_p = r_0 ... r_{p-1}), so the R_p distinct states before slot p are terms
+    // 0..R_p-1.  Each Clifford segment runs on those only; at a run of consecutive
+    // slots the R_p states are copied out to R_{p+k} terms at once, and the run's slots
+    // (each term its own choices) go into the same launch as the segment after them.
+    int64_t R = 1, start = 0, i = 0;
+    lrs_status rc;
+    while (i < n_gates) {
+        if (gates[i].op != LRS_OP_SLOT) { ++i; continue; }
+        if ((rc = launch_apply_clifford_range(c, c->gates_dev + start, i - start, R, st)) != LRS_OK) return rc;
+        int64_t Rn = R;
+        start = i;
+        for (; i < n_gates && gates[i].op == LRS_OP_SLOT; ++i) Rn *= radix(i);
+        if ((rc = launch_expand_terms(c, R, Rn, st)) != LRS_OK) return rc;
+        R = Rn;
+    }
+    return launch_apply_clifford_range(c, c->gates_dev + start, n_gates - start, R, st);
 }
 
 extern "C" lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_gate* const* gates,
@@ -494,6 +561,7 @@ extern "C" lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_g
                                      cudaMemcpyHostToDevice, st));
         c->batch_n_gates = n_gates[i];
         c->n_chains = 0;
+        c->fresh = false;
     }
     return launch_apply_clifford_batch(ctxs, count, st, &ctxs[0]->batch_buf, &ctxs[0]->batch_buf_bytes);
 }
@@ -572,6 +640,8 @@ extern "C" lrs_status lrs_copy_terms(lrs_ctx* dst, const lrs_ctx* src, void* str
     dst->chi_total = src->chi_total;
     dst->n_chains = 0;
     dst->have_terms = true;
+    dst->mode = src->mode;
+    dst->fresh = src->fresh;
     return LRS_OK;
 }
 

@@ -66,6 +66,8 @@ struct lrs_ctx {
     int64_t chi_total = 0;
     int64_t cap = 0;
     bool have_terms = false;
+    int32_t mode = -1;              // lrs_init_terms mode of the current terms
+    bool fresh = false;             // terms as lrs_init_terms left them (|0^n>, no gate applied)
 
     uint64_t *F = nullptr, *G = nullptr, *M = nullptr;
     uint64_t *glo = nullptr, *ghi = nullptr, *v = nullptr, *s = nullptr;
@@ -154,6 +156,9 @@ lrs_status launch_init_terms(lrs_ctx* ctx, int32_t mode, uint64_t seed, double s
                              cudaStream_t st);
 lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates,
                                  cudaStream_t st);
+lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates, int64_t n_terms,
+                                       cudaStream_t st);
+lrs_status launch_expand_terms(lrs_ctx* ctx, int64_t R, int64_t Rn, cudaStream_t st);
 lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
                             cudaStream_t st);
 lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, ulonglong2* Q, double** amp_out,

@@ -39,7 +39,8 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_mlp_info", "lrs_mlp_set_gemm", "lrs_mlp_get_gemm", "lrs_mlp_set_params", "lrs_mlp_get_params", "lrs_mlp_forward",
             "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned",
             "lrs_apply_clifford_batch", "lrs_set_tuning", "lrs_get_tuning", "lrs_copy_terms",
-            "lrs_norm_median_of_means", "lrs_marginal_sample", "lrs_lower_gadget"]
+            "lrs_norm_median_of_means", "lrs_marginal_sample", "lrs_lower_gadget",
+            "lrs_apply_circuit_shared"]
 
 
 class LrsError(RuntimeError):
@@ -92,6 +93,7 @@ def lib():
         "lrs_apply_clifford_batch": [vp, vp, vp, i32, vp],
         "lrs_set_tuning": [vp, i32, i64],
         "lrs_copy_terms": [vp, vp, vp],
+        "lrs_apply_circuit_shared": [vp, vp, i64, vp],
         "lrs_lower_gadget": [i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, vp, vp, i64, vp],
         "lrs_norm_median_of_means": [vp, i64, i32, u64, vp, vp],
         "lrs_marginal_sample": [vp, vp, vp, vp, i32, i64, i32, u64, vp, vp, vp],
@@ -274,6 +276,11 @@ class Simulator:
 
     def apply_clifford(self, gates: np.ndarray, stream=None):
         _check(lib().lrs_apply_clifford(self._h, _ptr(gates), len(gates), _stream(stream)))
+
+    def apply_circuit_shared(self, gates: np.ndarray, stream=None):
+        """lrs_apply_circuit_shared: the lowered circuit on fresh exact-mode terms,
+        sharing the work of common choice prefixes."""
+        _check(lib().lrs_apply_circuit_shared(self._h, _ptr(gates), len(gates), _stream(stream)))
 
     def amplitude(self, x, out=None, stream=None):
         """x: int64/uint64 CUDA tensor [B] -> float64 CUDA tensor [B, 2] (Re, Im)."""
