@@ -64,27 +64,58 @@ __global__ void k_init_terms(TermsView T, int32_t mode, uint64_t seed, double sc
 }
 
 // ---- apply_clifford: one thread per term, tableau rows in shared memory -----------
-// Shared layout [row][thread] makes every per-thread row index conflict-free.
+// Shared layout [row][thread] makes every per-thread row index conflict-free.  A row
+// is kept as its low 32 bits plus, for n > 32, its next HB bits (8, 16 or 32; bits at
+// or above n are zero in every row): a 40-qubit tableau takes 15n bytes per term
+// instead of 24n, so five 64-term blocks fit on an SM instead of three.
+constexpr int APPLY_TPB = 64;
+
+template <int HB> struct HiWord { typedef uint32_t T; };
+template <> struct HiWord<8> { typedef uint8_t T; };
+template <> struct HiWord<16> { typedef uint16_t T; };
+
+template <int HB>
 struct SmemRows {
-    uint64_t* base;
+    typedef typename HiWord<HB>::T Hi;
+    uint32_t* lo;   // 3n rows (F, G, M) of APPLY_TPB words; this thread's column
+    Hi* hi;
     int n;
-    __device__ __forceinline__ uint64_t& F(int p) { return base[(p) * APPLY_TPB_STRIDE]; }
-    __device__ __forceinline__ uint64_t& G(int p) { return base[(n + p) * APPLY_TPB_STRIDE]; }
-    __device__ __forceinline__ uint64_t& M(int p) { return base[(2 * n + p) * APPLY_TPB_STRIDE]; }
-    static constexpr int APPLY_TPB_STRIDE = 64;
+    __device__ __forceinline__ SmemRows(uint64_t* smem, int n_) : n(n_) {
+        lo = reinterpret_cast<uint32_t*>(smem) + threadIdx.x;
+        hi = reinterpret_cast<Hi*>(reinterpret_cast<uint32_t*>(smem) + 3 * n_ * APPLY_TPB) + threadIdx.x;
+    }
+    __device__ __forceinline__ uint64_t get(int r) const {
+        uint64_t x = lo[r * APPLY_TPB];
+        if (HB > 0) x |= (uint64_t)hi[r * APPLY_TPB] << 32;
+        return x;
+    }
+    __device__ __forceinline__ void set(int r, uint64_t x) {
+        lo[r * APPLY_TPB] = (uint32_t)x;
+        if (HB > 0) hi[r * APPLY_TPB] = (Hi)(x >> 32);
+    }
+    __device__ __forceinline__ uint64_t F(int p) const { return get(p); }
+    __device__ __forceinline__ uint64_t G(int p) const { return get(n + p); }
+    __device__ __forceinline__ uint64_t M(int p) const { return get(2 * n + p); }
+    __device__ __forceinline__ void setF(int p, uint64_t x) { set(p, x); }
+    __device__ __forceinline__ void setG(int p, uint64_t x) { set(n + p, x); }
+    __device__ __forceinline__ void setM(int p, uint64_t x) { set(2 * n + p, x); }
+    static size_t bytes(int n) { return (size_t)3 * n * APPLY_TPB * (4 + HB / 8); }
 };
-constexpr int APPLY_TPB = SmemRows::APPLY_TPB_STRIDE;
+
+// High-word width for n qubits.
+inline int apply_hb(int n) { return n <= 32 ? 0 : n <= 40 ? 8 : n <= 48 ? 16 : 32; }
 
 // One tile of APPLY_TPB terms through the whole gate list.
+template <int HB>
 __device__ __forceinline__ void apply_tile(const TermsView T, const lrs_gate* __restrict__ gates,
                                            int64_t n_gates, int64_t tile, uint64_t* smem) {
     const int n = T.n;
     const int64_t a = tile * APPLY_TPB + threadIdx.x;   // cap % APPLY_TPB == 0
-    SmemRows R{smem + threadIdx.x, n};
+    SmemRows<HB> R(smem, n);
     for (int p = 0; p < n; ++p) {
-        R.F(p) = T.F[(int64_t)p * T.cap + a];
-        R.G(p) = T.G[(int64_t)p * T.cap + a];
-        R.M(p) = T.M[(int64_t)p * T.cap + a];
+        R.setF(p, T.F[(int64_t)p * T.cap + a]);
+        R.setG(p, T.G[(int64_t)p * T.cap + a]);
+        R.setM(p, T.M[(int64_t)p * T.cap + a]);
     }
     TermRegs S;
     S.glo = T.glo[a]; S.ghi = T.ghi[a]; S.v = T.v[a]; S.s = T.s[a];
@@ -111,10 +142,11 @@ __device__ __forceinline__ void apply_tile(const TermsView T, const lrs_gate* __
     T.omega[a] = omega_pack(S.k, S.zero, S.h);
 }
 
+template <int HB>
 __global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford(TermsView T, const lrs_gate* __restrict__ gates,
                                                               int64_t n_gates) {
     extern __shared__ uint64_t smem[];
-    apply_tile(T, gates, n_gates, blockIdx.x, smem);
+    apply_tile<HB>(T, gates, n_gates, blockIdx.x, smem);
 }
 
 // Several circuits of uneven chi in one launch: block b runs global tile b; the
@@ -130,6 +162,7 @@ struct ApplyBatch {
     int64_t n_gates[LRS_APPLY_BATCH_MAX];
 };
 
+template <int HB>
 __global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford_batch(const __grid_constant__ ApplyBatch B) {
     extern __shared__ uint64_t smem[];
     const int64_t tile = blockIdx.x;
@@ -137,7 +170,7 @@ __global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford_batch(const __grid
 #pragma unroll 1
     for (int i = 1; i < B.count; ++i)
         if (B.first_tile[i] <= tile) c = i;
-    apply_tile(B.T[c], B.gates[c], B.n_gates[c], tile - B.first_tile[c], smem);
+    apply_tile<HB>(B.T[c], B.gates[c], B.n_gates[c], tile - B.first_tile[c], smem);
 }
 
 // ---- sample x from single terms (Sec. 4.1, "Simulating measurements") --------------
@@ -195,22 +228,29 @@ lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_
     return launch_apply_clifford_range(ctx, gates_dev, n_gates, ctx->cap, st);
 }
 
+template <int HB>
+static lrs_status launch_apply_hb(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates, int64_t blocks,
+                                  cudaStream_t st) {
+    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford<HB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SmemRows<HB>::bytes(64)));
+    k_apply_clifford<HB><<<(unsigned)blocks, APPLY_TPB, SmemRows<HB>::bytes(ctx->n), st>>>(ctx->view(), gates_dev,
+                                                                                           n_gates);
+    LRS_LAUNCH_CHECK("apply_clifford kernel");
+    return LRS_OK;
+}
+
 // The gate list on the terms of the first ceil(n_terms / APPLY_TPB) tiles only.
 lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates, int64_t n_terms,
                                        cudaStream_t st) {
-    const size_t smem = (size_t)3 * ctx->n * APPLY_TPB * sizeof(uint64_t);
-    static int configured_dev = -1;
-    if (configured_dev != ctx->device) {
-        LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      3 * 64 * APPLY_TPB * (int)sizeof(uint64_t)));
-        configured_dev = ctx->device;
-    }
     if (n_terms > ctx->cap) n_terms = ctx->cap;
     const int64_t blocks = (n_terms + APPLY_TPB - 1) / APPLY_TPB;
     if (blocks == 0 || n_gates == 0) return LRS_OK;
-    k_apply_clifford<<<(unsigned)blocks, APPLY_TPB, smem, st>>>(ctx->view(), gates_dev, n_gates);
-    LRS_LAUNCH_CHECK("apply_clifford kernel");
-    return LRS_OK;
+    switch (apply_hb(ctx->n)) {
+        case 0: return launch_apply_hb<0>(ctx, gates_dev, n_gates, blocks, st);
+        case 8: return launch_apply_hb<8>(ctx, gates_dev, n_gates, blocks, st);
+        case 16: return launch_apply_hb<16>(ctx, gates_dev, n_gates, blocks, st);
+        default: return launch_apply_hb<32>(ctx, gates_dev, n_gates, blocks, st);
+    }
 }
 
 lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint64_t* x,
@@ -223,12 +263,21 @@ lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint6
     return LRS_OK;
 }
 
+// The circuits of one batch share the layout of the widest one (a narrower tableau
+// keeps zero high bits).
+template <int HB>
+static lrs_status launch_apply_batch_hb(const ApplyBatch& B, int64_t tiles, int nmax, cudaStream_t st) {
+    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford_batch<HB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SmemRows<HB>::bytes(64)));
+    k_apply_clifford_batch<HB><<<(unsigned)tiles, APPLY_TPB, SmemRows<HB>::bytes(nmax), st>>>(B);
+    LRS_LAUNCH_CHECK("batched apply_clifford kernel");
+    return LRS_OK;
+}
+
 lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cudaStream_t st,
                                        void** dev_buf, size_t* dev_buf_bytes) {
     (void)dev_buf;
     (void)dev_buf_bytes;
-    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  3 * 64 * APPLY_TPB * (int)sizeof(uint64_t)));
     for (int32_t base = 0; base < count; base += LRS_APPLY_BATCH_MAX) {
         ApplyBatch B;
         memset(&B, 0, sizeof(B));
@@ -245,9 +294,14 @@ lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cuda
             if (c->n > nmax) nmax = c->n;
         }
         B.first_tile[B.count] = tiles;
-        const size_t smem = (size_t)3 * nmax * APPLY_TPB * sizeof(uint64_t);
-        k_apply_clifford_batch<<<(unsigned)tiles, APPLY_TPB, smem, st>>>(B);
-        LRS_LAUNCH_CHECK("batched apply_clifford kernel");
+        lrs_status rc;
+        switch (apply_hb(nmax)) {
+            case 0: rc = launch_apply_batch_hb<0>(B, tiles, nmax, st); break;
+            case 8: rc = launch_apply_batch_hb<8>(B, tiles, nmax, st); break;
+            case 16: rc = launch_apply_batch_hb<16>(B, tiles, nmax, st); break;
+            default: rc = launch_apply_batch_hb<32>(B, tiles, nmax, st); break;
+        }
+        if (rc != LRS_OK) return rc;
     }
     return LRS_OK;
 }

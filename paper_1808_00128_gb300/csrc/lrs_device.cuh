@@ -120,7 +120,7 @@ __device__ __forceinline__ void prop_h_rows(Rows& R, int n, int q, uint64_t mA, 
                                             uint64_t& sub1) {
 #pragma unroll 2
     for (int p = 0; p < n; ++p) {
-        uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
+        const uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
         const uint64_t fq = getb(Fp, q);
         uint64_t Gn = Gp, Fn = Fp, Mn = Mp;
         if (MODE != 2 && MODE != 3) {
@@ -139,9 +139,9 @@ __device__ __forceinline__ void prop_h_rows(Rows& R, int n, int q, uint64_t mA, 
         const uint64_t fs = a & getb(Fn, q);
         Mn ^= fs << q;
         sub1 |= fs << p;
-        R.G(p) = Gn;
-        R.F(p) = Fn;
-        R.M(p) = Mn;
+        R.setG(p, Gn);
+        R.setF(p, Fn);
+        R.setM(p, Mn);
     }
 }
 
@@ -245,7 +245,7 @@ __device__ __forceinline__ void gate_proj(Rows& R, TermRegs& T, int n, uint64_t 
 template <class Rows>
 __device__ __forceinline__ void gate_s(Rows& R, TermRegs& T, int q, uint32_t dg) {
     // S: dg = 3 (gamma_q -= 1); S^dagger: dg = 1; both M_q ^= G_q.
-    R.M(q) ^= R.G(q);
+    R.setM(q, R.M(q) ^ R.G(q));
     gamma_set(T, q, (gamma_get(T, q) + dg) & 3u);
 }
 template <class Rows>
@@ -257,17 +257,17 @@ template <class Rows>
 __device__ __forceinline__ void gate_cz(Rows& R, TermRegs& T, int q, int r) {
     (void)T;
     const uint64_t Gq = R.G(q), Gr = R.G(r);
-    R.M(q) ^= Gr;
-    R.M(r) ^= Gq;
+    R.setM(q, R.M(q) ^ Gr);
+    R.setM(r, R.M(r) ^ Gq);
 }
 template <class Rows>
 __device__ __forceinline__ void gate_cx(Rows& R, TermRegs& T, int q, int r) {
     const uint64_t Mq = R.M(q), Fr = R.F(r);
     const uint32_t g = (gamma_get(T, q) + gamma_get(T, r) + 2u * par64(Mq & Fr)) & 3u;
     gamma_set(T, q, g);
-    R.G(r) ^= R.G(q);
-    R.F(q) ^= Fr;
-    R.M(q) = Mq ^ R.M(r);
+    R.setG(r, R.G(r) ^ R.G(q));
+    R.setF(q, R.F(q) ^ Fr);
+    R.setM(q, Mq ^ R.M(r));
 }
 
 template <class Rows>
