@@ -67,8 +67,14 @@ __global__ void k_init_terms(TermsView T, int32_t mode, uint64_t seed, double sc
 // Shared layout [row][thread] makes every per-thread row index conflict-free.  A row
 // is kept as its low 32 bits plus, for n > 32, its next HB bits (8, 16 or 32; bits at
 // or above n are zero in every row): a 40-qubit tableau takes 15n bytes per term
-// instead of 24n, so five 64-term blocks fit on an SM instead of three.
-constexpr int APPLY_TPB = 64;
+// instead of 24n, so five 64-term blocks fit on an SM instead of three.  The Hadamard
+// row pass reads F and G through per-term pointers; the 8- and 16-bit high rows of G
+// and M sit 64 bytes further on, so that a warp reading row p of F for some terms and
+// of G for others hits other banks.
+#ifndef LRS_APPLY_TPB
+#define LRS_APPLY_TPB 64
+#endif
+constexpr int APPLY_TPB = LRS_APPLY_TPB;
 
 template <int HB> struct HiWord { typedef uint32_t T; };
 template <> struct HiWord<8> { typedef uint8_t T; };
@@ -77,29 +83,40 @@ template <> struct HiWord<16> { typedef uint16_t T; };
 template <int HB>
 struct SmemRows {
     typedef typename HiWord<HB>::T Hi;
-    uint32_t* lo;   // 3n rows (F, G, M) of APPLY_TPB words; this thread's column
-    Hi* hi;
-    int n;
-    __device__ __forceinline__ SmemRows(uint64_t* smem, int n_) : n(n_) {
-        lo = reinterpret_cast<uint32_t*>(smem) + threadIdx.x;
-        hi = reinterpret_cast<Hi*>(reinterpret_cast<uint32_t*>(smem) + 3 * n_ * APPLY_TPB) + threadIdx.x;
+    static constexpr int HI_PAD = (HB == 8 || HB == 16) ? 64 / (int)sizeof(Hi) : 0;
+    struct Mat {   // one matrix: row p is lo[p * APPLY_TPB] | hi[p * APPLY_TPB] << 32
+        uint32_t* lo;
+        Hi* hi;
+    };
+    Mat f, g, m;
+    __device__ __forceinline__ SmemRows(uint64_t* smem, int n) {
+        uint32_t* lo = reinterpret_cast<uint32_t*>(smem) + threadIdx.x;
+        Hi* hi = reinterpret_cast<Hi*>(reinterpret_cast<uint32_t*>(smem) + 3 * n * APPLY_TPB) + threadIdx.x;
+        f = Mat{lo, hi};
+        g = Mat{lo + n * APPLY_TPB, hi + n * APPLY_TPB + HI_PAD};
+        m = Mat{lo + 2 * n * APPLY_TPB, hi + 2 * n * APPLY_TPB + HI_PAD};
     }
-    __device__ __forceinline__ uint64_t get(int r) const {
-        uint64_t x = lo[r * APPLY_TPB];
-        if (HB > 0) x |= (uint64_t)hi[r * APPLY_TPB] << 32;
-        return x;
+    __device__ __forceinline__ uint64_t get(const Mat& x, int p) const {
+        uint64_t v = x.lo[p * APPLY_TPB];
+        if (HB > 0) v |= (uint64_t)x.hi[p * APPLY_TPB] << 32;
+        return v;
     }
-    __device__ __forceinline__ void set(int r, uint64_t x) {
-        lo[r * APPLY_TPB] = (uint32_t)x;
-        if (HB > 0) hi[r * APPLY_TPB] = (Hi)(x >> 32);
+    __device__ __forceinline__ void set(const Mat& x, int p, uint64_t v) {
+        x.lo[p * APPLY_TPB] = (uint32_t)v;
+        if (HB > 0) x.hi[p * APPLY_TPB] = (Hi)(v >> 32);
     }
-    __device__ __forceinline__ uint64_t F(int p) const { return get(p); }
-    __device__ __forceinline__ uint64_t G(int p) const { return get(n + p); }
-    __device__ __forceinline__ uint64_t M(int p) const { return get(2 * n + p); }
-    __device__ __forceinline__ void setF(int p, uint64_t x) { set(p, x); }
-    __device__ __forceinline__ void setG(int p, uint64_t x) { set(n + p, x); }
-    __device__ __forceinline__ void setM(int p, uint64_t x) { set(2 * n + p, x); }
-    static size_t bytes(int n) { return (size_t)3 * n * APPLY_TPB * (4 + HB / 8); }
+    __device__ __forceinline__ Mat matF() const { return f; }
+    __device__ __forceinline__ Mat matG() const { return g; }
+    __device__ __forceinline__ Mat matM() const { return m; }
+    __device__ __forceinline__ uint64_t F(int p) const { return get(f, p); }
+    __device__ __forceinline__ uint64_t G(int p) const { return get(g, p); }
+    __device__ __forceinline__ uint64_t M(int p) const { return get(m, p); }
+    __device__ __forceinline__ void setF(int p, uint64_t x) { set(f, p, x); }
+    __device__ __forceinline__ void setG(int p, uint64_t x) { set(g, p, x); }
+    __device__ __forceinline__ void setM(int p, uint64_t x) { set(m, p, x); }
+    static size_t bytes(int n) {
+        return (size_t)3 * n * APPLY_TPB * (4 + HB / 8) + (size_t)HI_PAD * sizeof(Hi);
+    }
 };
 
 // High-word width for n qubits.

@@ -108,41 +108,87 @@ __device__ __forceinline__ uint32_t sq_entry(int vq, int d) {
 }
 
 // Row pass of the Hadamard fan-out (proof of Prop. (prop:H)) followed by R[S_q]^a.
+// With V0 = d \ v nonempty (q = min V0, mA = V0 \ q, m1 = V1):
 //   R[CX_{q,i}], i in mA:  G[p,q] ^= G[p,i]; F[p,i] ^= F[p,q]; M[p,q] ^= M[p,i]
 //   R[CZ_{q,i}], i in m1:  M[p,q] ^= F[p,i]; M[p,i] ^= F[p,q]; gamma_p += 2 F[p,q] F[p,i]
+// otherwise (q = min V1, mB = V1 \ q):
 //   R[CX_{i,q}], i in mB:  G[p,i] ^= G[p,q]; F[p,q] ^= F[p,i]; M[p,i] ^= M[p,q]
-//   R[S_q] (a = 1):        M[p,q] ^= F[p,q]; gamma_p -= F[p,q]
-// MODE 1 assumes mB = 0, MODE 2 assumes mA = m1 = 0, MODE 3 assumes no fan-out
-// (mA = m1 = mB = 0: only R[S_q]), MODE 0 is general.
-template <int MODE, class Rows>
-__device__ __forceinline__ void prop_h_rows(Rows& R, int n, int q, uint64_t mA, uint64_t m1,
-                                            uint64_t mB, uint64_t a, uint64_t& add2,
-                                            uint64_t& sub1) {
-#pragma unroll 2
-    for (int p = 0; p < n; ++p) {
-        const uint64_t Gp = R.G(p), Fp = R.F(p), Mp = R.M(p);
-        const uint64_t fq = getb(Fp, q);
-        uint64_t Gn = Gp, Fn = Fp, Mn = Mp;
-        if (MODE != 2 && MODE != 3) {
-            const uint64_t f1 = par64(Fp & m1);
-            Gn ^= (uint64_t)par64(Gp & mA) << q;
-            Fn ^= mA & (0ull - fq);
-            Mn ^= ((uint64_t)par64((Mp & mA) ^ (Fp & m1)) << q) ^ (m1 & (0ull - fq));
-            add2 |= (fq & f1) << p;
-        }
-        if (MODE != 1 && MODE != 3) {
-            const uint64_t gq = getb(Gp, q), mq = getb(Mp, q);
-            Gn ^= mB & (0ull - gq);
-            Fn ^= (uint64_t)par64(Fp & mB) << q;
-            Mn ^= mB & (0ull - mq);
-        }
-        const uint64_t fs = a & getb(Fn, q);
-        Mn ^= fs << q;
-        sub1 |= fs << p;
-        R.setG(p, Gn);
-        R.setF(p, Fn);
-        R.setM(p, Mn);
+// and then, when a = 1,    R[S_q]: M[p,q] ^= F[p,q]; gamma_p -= F[p,q].
+// Both fan-outs have one matrix X that takes a parity into column q (G, resp. F) and
+// one matrix Y that copies its column q out over the mask (F, resp. G), so each term
+// works on X and Y through row pointers chosen once per gate, and only M differs:
+// parity over mA plus the CZ terms (first case) or a copy of M[p,q] over mB (second).
+// Rows are worked on as 32-bit halves: bit q of a row is taken from the half that holds
+// it (sign-extended to a whole-word mask), a parity is placed at q through the one-bit
+// masks qml/qmh, and the bits of add2 / sub1 are shifted in from the top row down.
+struct HRowMasks {
+    uint32_t qs, sh, qml, qmh, aql, aqh, a;
+    uint32_t ml, mh;     // mA or mB
+    uint32_t m1l, m1h;   // m1 (0 in the second case)
+    uint32_t mPl, mPh;   // parity mask of M: mA (0 in the second case)
+    uint32_t mFl, mFh;   // mask of the copy into M: m1, or mB
+    bool qh, first;      // q >= 32; the first case
+};
+
+template <bool FAN, class Rows, class Mat>
+__device__ __forceinline__ void prop_h_row(Rows& R, const Mat& X, const Mat& Y, const Mat& Mm, int p,
+                                           const HRowMasks& k, uint32_t& add2, uint32_t& sub1) {
+    const uint64_t Xp = R.get(X, p), Yp = R.get(Y, p), Mp = R.get(Mm, p);
+    const uint32_t Xl = (uint32_t)Xp, Xh = (uint32_t)(Xp >> 32);
+    const uint32_t Yl = (uint32_t)Yp, Yh = (uint32_t)(Yp >> 32);
+    const uint32_t Ml = (uint32_t)Mp, Mh = (uint32_t)(Mp >> 32);
+    uint32_t Xnl = Xl, Xnh = Xh, Ynl = Yl, Ynh = Yh, Mnl = Ml, Mnh = Mh;
+    uint32_t f2 = 0;
+    if (FAN) {
+        const uint32_t my = (uint32_t)((int32_t)((k.qh ? Yh : Yl) << k.sh) >> 31);   // Y[p,q]
+        const uint32_t mm = (uint32_t)((int32_t)((k.qh ? Mh : Ml) << k.sh) >> 31);   // M[p,q]
+        const uint32_t c1 = __popc((Yl & k.m1l) ^ (Yh & k.m1h));
+        const uint32_t tx = __popc((Xl & k.ml) ^ (Xh & k.mh)) << k.qs;
+        const uint32_t tm = (__popc((Ml & k.mPl) ^ (Mh & k.mPh)) ^ c1) << k.qs;
+        const uint32_t ms = k.first ? my : mm;
+        Xnl ^= tx & k.qml;
+        Xnh ^= tx & k.qmh;
+        Ynl ^= k.ml & my;
+        Ynh ^= k.mh & my;
+        Mnl ^= (tm & k.qml) ^ (k.mFl & ms);
+        Mnh ^= (tm & k.qmh) ^ (k.mFh & ms);
+        f2 = c1 & my & 1u;
     }
+    // a F'[p,q]: F is Y in the first case (column q unchanged), X in the second
+    const uint32_t fl = k.first ? Ynl : Xnl, fh = k.first ? Ynh : Xnh;
+    const uint32_t fs = ((k.qh ? fh : fl) >> k.qs) & k.a;
+    Mnl ^= fl & k.aql;
+    Mnh ^= fh & k.aqh;
+    add2 = 2u * add2 + f2;
+    sub1 = 2u * sub1 + fs;
+    if (FAN) {
+        R.set(X, p, ((uint64_t)Xnh << 32) | Xnl);
+        R.set(Y, p, ((uint64_t)Ynh << 32) | Ynl);
+    }
+    R.set(Mm, p, ((uint64_t)Mnh << 32) | Mnl);
+}
+
+// QLO: q < 32 for every term of the warp (the usual case: q is the lowest bit of a
+// mask), so column q lies in the low halves and the high halves only take part in the
+// parities and the fan-out copies.
+template <bool FAN, bool QLO, class Rows>
+__device__ __forceinline__ void prop_h_rows(Rows& R, int n, const HRowMasks& k0, uint64_t& add2, uint64_t& sub1) {
+    HRowMasks k = k0;
+    if (QLO) {
+        k.qh = false;
+        k.qmh = 0u;
+        k.aqh = 0u;
+    }
+    const auto X = k.first ? R.matG() : R.matF();
+    const auto Y = k.first ? R.matF() : R.matG();
+    const auto Mm = R.matM();
+    uint32_t ah = 0, sh = 0, al = 0, sl = 0;
+#pragma unroll 2
+    for (int p = n - 1; p >= 32; --p) prop_h_row<FAN>(R, X, Y, Mm, p, k, ah, sh);
+#pragma unroll 2
+    for (int p = (n < 32 ? n : 32) - 1; p >= 0; --p) prop_h_row<FAN>(R, X, Y, Mm, p, k, al, sl);
+    add2 = ((uint64_t)ah << 32) | al;
+    sub1 = ((uint64_t)sh << 32) | sl;
 }
 
 // Prop. (prop:H): U_H(|t> + i^delta |u>) = sqrt2 e^{i pi k1/4} W_C W_H |s'> for t != u.
@@ -154,19 +200,12 @@ __device__ __forceinline__ void prop_h(Rows& R, TermRegs& T, int n, uint64_t t, 
     const uint64_t d = t ^ u;
     const uint64_t V0 = d & ~T.v;
     const uint64_t V1 = d & T.v;
-    int q;
-    uint64_t mA, m1, mB;
-    if (V0) {  // V_C = prod_{i in V0\q} CX_{q,i} prod_{i in V1} CZ_{q,i}
-        q = ffs64(V0);
-        mA = V0 & ~bit64(q);
-        m1 = V1;
-        mB = 0;
-    } else {   // V_C = prod_{i in V1\q} CX_{i,q}
-        q = ffs64(V1);
-        mA = 0;
-        m1 = 0;
-        mB = V1 & ~bit64(q);
-    }
+    // V_C = prod_{i in V0\q} CX_{q,i} prod_{i in V1} CZ_{q,i} when V0 is nonempty,
+    // else prod_{i in V1\q} CX_{i,q}
+    const bool first = V0 != 0;
+    const int q = ffs64(first ? V0 : V1);
+    const uint64_t m = (first ? V0 : V1) & ~bit64(q);
+    const uint64_t m1 = first ? V1 : 0ull;
     uint64_t y;
     if (getb(t, q)) y = u ^ bit64(q); else y = t;
     const int yq = (int)getb(y, q);
@@ -180,20 +219,29 @@ __device__ __forceinline__ void prop_h(Rows& R, TermRegs& T, int n, uint64_t t, 
     const uint64_t a = e & 1u, b = (e >> 1) & 1u, c = (e >> 2) & 1u;
     T.k += e >> 3;
 
+    HRowMasks k;
+    k.qs = (uint32_t)q & 31u;
+    k.sh = 31u - k.qs;
+    k.qh = q >= 32;
+    k.first = first;
+    k.qml = k.qh ? 0u : (1u << k.qs);
+    k.qmh = k.qh ? (1u << k.qs) : 0u;
+    k.a = (uint32_t)a;
+    k.aql = a ? k.qml : 0u;
+    k.aqh = a ? k.qmh : 0u;
+    k.ml = (uint32_t)m; k.mh = (uint32_t)(m >> 32);
+    k.m1l = (uint32_t)m1; k.m1h = (uint32_t)(m1 >> 32);
+    k.mPl = first ? k.ml : 0u; k.mPh = first ? k.mh : 0u;
+    k.mFl = first ? k.m1l : k.ml; k.mFh = first ? k.m1h : k.mh;
     uint64_t add2 = 0, sub1 = 0;
-    // The warp takes the cheapest row pass that covers all of its active terms:
-    // MODE 2 when no term has a V0 fan-out (only CX_{i,q}), MODE 1 when none has a
-    // V1-only fan-out, MODE 0 otherwise.
+    // The warp skips the fan-out when no active term has one (e.g. H on |0>), and the
+    // row pass altogether when no term needs R[S_q] either.
     const unsigned am = __activemask();
-    if (__all_sync(am, (mA | m1 | mB) == 0)) {
-        // no fan-out anywhere in the warp (e.g. H on |0>): only R[S_q], if any term needs it
-        if (__any_sync(am, a != 0)) prop_h_rows<3>(R, n, q, mA, m1, mB, a, add2, sub1);
-    } else if (__all_sync(am, (mA | m1) == 0)) {
-        prop_h_rows<2>(R, n, q, mA, m1, mB, a, add2, sub1);
-    } else if (__all_sync(am, mB == 0)) {
-        prop_h_rows<1>(R, n, q, mA, m1, mB, a, add2, sub1);
-    } else {
-        prop_h_rows<0>(R, n, q, mA, m1, mB, a, add2, sub1);
+    if (__any_sync(am, (m | m1) != 0)) {
+        if (__all_sync(am, q < 32)) prop_h_rows<true, true>(R, n, k, add2, sub1);
+        else prop_h_rows<true, false>(R, n, k, add2, sub1);
+    } else if (__any_sync(am, a != 0)) {
+        prop_h_rows<false, false>(R, n, k, add2, sub1);
     }
     // gamma += 2 add2, then gamma -= sub1 (bit-plane Z4 arithmetic)
     T.ghi ^= add2;
