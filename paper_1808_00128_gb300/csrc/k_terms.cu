@@ -64,37 +64,46 @@ __global__ void k_init_terms(TermsView T, int32_t mode, uint64_t seed, double sc
 }
 
 // ---- apply_clifford: one thread per term, tableau rows in shared memory -----------
-// Shared layout [row][thread] makes every per-thread row index conflict-free.  A row
-// is kept as its low 32 bits plus, for n > 32, its next HB bits (8, 16 or 32; bits at
+// Shared layout [row][thread] makes every per-thread row index conflict-free.  For
+// n <= 48 a row is kept as its low 32 bits plus its next HB bits (0, 8 or 16; bits at
 // or above n are zero in every row): a 40-qubit tableau takes 15n bytes per term
-// instead of 24n, so five 64-term blocks fit on an SM instead of three.  The Hadamard
-// row pass reads F and G through per-term pointers; the 8- and 16-bit high rows of G
-// and M sit 64 bytes further on, so that a warp reading row p of F for some terms and
-// of G for others hits other banks.
-#ifndef LRS_APPLY_TPB
-#define LRS_APPLY_TPB 64
-#endif
-constexpr int APPLY_TPB = LRS_APPLY_TPB;
+// instead of 24n, so five 64-term blocks fit on an SM instead of three.  Wider
+// tableaux keep each row as one 64-bit word (HB = 64): at n = 50 the single 64-bit
+// access per row beats the extra block per SM that 16 + 8-bit high words would give.
+// The Hadamard row pass reads F and G through per-term pointers; the narrow high rows
+// of G and M are padded so that a warp reading row p of F for some terms and of G for
+// others hits other banks.
+constexpr int APPLY_TPB = 64;
 
 template <int HB> struct HiWord { typedef uint32_t T; };
 template <> struct HiWord<8> { typedef uint8_t T; };
 template <> struct HiWord<16> { typedef uint16_t T; };
 
+// Elements of padding after the F rows of an array of esz-byte entries, so that
+// row p of G starts 16 banks away from row p of F (the warp's entries of one row
+// cover at most 16 banks when esz < 4; 4-byte entries are conflict-free anyway).
+__host__ __device__ __forceinline__ int rows_pad(int n, int esz) {
+    if (esz >= 4) return 0;
+    const int offw = (n * APPLY_TPB * esz / 4) & 31;
+    return ((16 - offw) & 31) * 4 / esz;
+}
+
 template <int HB>
 struct SmemRows {
     typedef typename HiWord<HB>::T Hi;
-    static constexpr int HI_PAD = (HB == 8 || HB == 16) ? 64 / (int)sizeof(Hi) : 0;
-    struct Mat {   // one matrix: row p is lo[p * APPLY_TPB] | hi[p * APPLY_TPB] << 32
+    struct Mat {
         uint32_t* lo;
         Hi* hi;
     };
     Mat f, g, m;
     __device__ __forceinline__ SmemRows(uint64_t* smem, int n) {
+        const int rows = 3 * n * APPLY_TPB;
+        const int hp = HB > 0 ? rows_pad(n, (int)sizeof(Hi)) : 0;
         uint32_t* lo = reinterpret_cast<uint32_t*>(smem) + threadIdx.x;
-        Hi* hi = reinterpret_cast<Hi*>(reinterpret_cast<uint32_t*>(smem) + 3 * n * APPLY_TPB) + threadIdx.x;
+        Hi* hi = reinterpret_cast<Hi*>(reinterpret_cast<uint32_t*>(smem) + rows) + threadIdx.x;
         f = Mat{lo, hi};
-        g = Mat{lo + n * APPLY_TPB, hi + n * APPLY_TPB + HI_PAD};
-        m = Mat{lo + 2 * n * APPLY_TPB, hi + 2 * n * APPLY_TPB + HI_PAD};
+        g = Mat{lo + n * APPLY_TPB, hi + n * APPLY_TPB + hp};
+        m = Mat{lo + 2 * n * APPLY_TPB, hi + 2 * n * APPLY_TPB + hp};
     }
     __device__ __forceinline__ uint64_t get(const Mat& x, int p) const {
         uint64_t v = x.lo[p * APPLY_TPB];
@@ -115,12 +124,41 @@ struct SmemRows {
     __device__ __forceinline__ void setG(int p, uint64_t x) { set(g, p, x); }
     __device__ __forceinline__ void setM(int p, uint64_t x) { set(m, p, x); }
     static size_t bytes(int n) {
-        return (size_t)3 * n * APPLY_TPB * (4 + HB / 8) + (size_t)HI_PAD * sizeof(Hi);
+        const size_t rows = (size_t)3 * n * APPLY_TPB;
+        size_t b = rows * 4;
+        if (HB > 0) b += (rows + rows_pad(n, (int)sizeof(Hi))) * sizeof(Hi);
+        return b;
     }
 };
 
-// High-word width for n qubits.
-inline int apply_hb(int n) { return n <= 32 ? 0 : n <= 40 ? 8 : n <= 48 ? 16 : 32; }
+template <>
+struct SmemRows<64> {
+    struct Mat {
+        uint64_t* r;
+    };
+    Mat f, g, m;
+    __device__ __forceinline__ SmemRows(uint64_t* smem, int n) {
+        uint64_t* b = smem + threadIdx.x;
+        f = Mat{b};
+        g = Mat{b + n * APPLY_TPB};
+        m = Mat{b + 2 * n * APPLY_TPB};
+    }
+    __device__ __forceinline__ uint64_t get(const Mat& x, int p) const { return x.r[p * APPLY_TPB]; }
+    __device__ __forceinline__ void set(const Mat& x, int p, uint64_t v) { x.r[p * APPLY_TPB] = v; }
+    __device__ __forceinline__ Mat matF() const { return f; }
+    __device__ __forceinline__ Mat matG() const { return g; }
+    __device__ __forceinline__ Mat matM() const { return m; }
+    __device__ __forceinline__ uint64_t F(int p) const { return get(f, p); }
+    __device__ __forceinline__ uint64_t G(int p) const { return get(g, p); }
+    __device__ __forceinline__ uint64_t M(int p) const { return get(m, p); }
+    __device__ __forceinline__ void setF(int p, uint64_t x) { set(f, p, x); }
+    __device__ __forceinline__ void setG(int p, uint64_t x) { set(g, p, x); }
+    __device__ __forceinline__ void setM(int p, uint64_t x) { set(m, p, x); }
+    static size_t bytes(int n) { return (size_t)3 * n * APPLY_TPB * 8; }
+};
+
+// Row layout for n qubits.
+inline int apply_hb(int n) { return n <= 32 ? 0 : n <= 40 ? 8 : n <= 48 ? 16 : 64; }
 
 // One tile of APPLY_TPB terms through the whole gate list.
 template <int HB>
@@ -180,7 +218,7 @@ struct ApplyBatch {
 };
 
 template <int HB>
-__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford_batch(const __grid_constant__ ApplyBatch B) {
+__global__ void __maxnreg__(168) k_apply_clifford_batch(const __grid_constant__ ApplyBatch B) {
     extern __shared__ uint64_t smem[];
     const int64_t tile = blockIdx.x;
     int c = 0;
@@ -266,7 +304,7 @@ lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_dev, 
         case 0: return launch_apply_hb<0>(ctx, gates_dev, n_gates, blocks, st);
         case 8: return launch_apply_hb<8>(ctx, gates_dev, n_gates, blocks, st);
         case 16: return launch_apply_hb<16>(ctx, gates_dev, n_gates, blocks, st);
-        default: return launch_apply_hb<32>(ctx, gates_dev, n_gates, blocks, st);
+        default: return launch_apply_hb<64>(ctx, gates_dev, n_gates, blocks, st);
     }
 }
 
@@ -316,7 +354,7 @@ lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cuda
             case 0: rc = launch_apply_batch_hb<0>(B, tiles, nmax, st); break;
             case 8: rc = launch_apply_batch_hb<8>(B, tiles, nmax, st); break;
             case 16: rc = launch_apply_batch_hb<16>(B, tiles, nmax, st); break;
-            default: rc = launch_apply_batch_hb<32>(B, tiles, nmax, st); break;
+            default: rc = launch_apply_batch_hb<64>(B, tiles, nmax, st); break;
         }
         if (rc != LRS_OK) return rc;
     }

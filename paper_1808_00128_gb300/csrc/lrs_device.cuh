@@ -171,13 +171,21 @@ __device__ __forceinline__ void prop_h_row(Rows& R, const Mat& X, const Mat& Y, 
 // QLO: q < 32 for every term of the warp (the usual case: q is the lowest bit of a
 // mask), so column q lies in the low halves and the high halves only take part in the
 // parities and the fan-out copies.
-template <bool FAN, bool QLO, class Rows>
+// SECOND: every term of the warp has V0 empty (e.g. all of v set, as after a layer of
+// Hadamards on |0>), so no CZ part and no parity into M.
+template <bool FAN, bool QLO, bool SECOND, class Rows>
 __device__ __forceinline__ void prop_h_rows(Rows& R, int n, const HRowMasks& k0, uint64_t& add2, uint64_t& sub1) {
     HRowMasks k = k0;
     if (QLO) {
         k.qh = false;
         k.qmh = 0u;
         k.aqh = 0u;
+    }
+    if (SECOND) {
+        k.first = false;
+        k.m1l = k.m1h = k.mPl = k.mPh = 0u;
+        k.mFl = k.ml;
+        k.mFh = k.mh;
     }
     const auto X = k.first ? R.matG() : R.matF();
     const auto Y = k.first ? R.matF() : R.matG();
@@ -238,10 +246,14 @@ __device__ __forceinline__ void prop_h(Rows& R, TermRegs& T, int n, uint64_t t, 
     // row pass altogether when no term needs R[S_q] either.
     const unsigned am = __activemask();
     if (__any_sync(am, (m | m1) != 0)) {
-        if (__all_sync(am, q < 32)) prop_h_rows<true, true>(R, n, k, add2, sub1);
-        else prop_h_rows<true, false>(R, n, k, add2, sub1);
+        if (__all_sync(am, q < 32)) {
+            if (__all_sync(am, !first)) prop_h_rows<true, true, true>(R, n, k, add2, sub1);
+            else prop_h_rows<true, true, false>(R, n, k, add2, sub1);
+        } else {
+            prop_h_rows<true, false, false>(R, n, k, add2, sub1);
+        }
     } else if (__any_sync(am, a != 0)) {
-        prop_h_rows<false, false>(R, n, k, add2, sub1);
+        prop_h_rows<false, false, false>(R, n, k, add2, sub1);
     }
     // gamma += 2 add2, then gamma -= sub1 (bit-plane Z4 arithmetic)
     T.ghi ^= add2;

@@ -56,7 +56,7 @@ def _random_circuit(n, n_gates, n_t, n_ccz, rng):
     return ops
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 32, 33, 62, 63, 64])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 32, 33, 39, 40, 41, 48, 49, 50, 56, 57, 62, 63, 64])
 def test_edge_widths_bit_exact(n):
     """Exact decompositions with T and projector-form CCZ at edge register widths."""
     require_cuda()
@@ -156,6 +156,21 @@ def test_mid_config_full_size_sampled_terms():
     for a, t in zip(pick, terms):
         ex = sim.export_terms(a, 1)
         compare_term(ex, 0, t, f"term {a}")
+    sim.close()
+
+
+def test_qaoa_full_size_sampled_terms():
+    """n=50 QAOA circuit sparsified to chi = 2^20 (the 24-bit high-word tableau layout);
+    sampled terms bit-exact."""
+    require_cuda()
+    cfg = workloads.config_qaoa()
+    n, ops, chi = cfg["n"], cfg["ops"], cfg["chi"]
+    sim, low = _run(n, ops, chi, "sparsify", seed=cfg["seed"])
+    rng = random.Random(5)
+    pick = sorted(rng.sample(range(chi), 5)) + [chi - 1]
+    terms, _, _ = oracle_terms(n, ops, chi, "sparsify", seed=cfg["seed"], alphas=pick, parallel=True)
+    for a, t in zip(pick, terms):
+        compare_term(sim.export_terms(a, 1), 0, t, f"term {a}")
     sim.close()
 
 
