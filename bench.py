@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--mlp-gemm-only", action="store_true",
                     help="run only the MADE network tensor-core study (n=64, H=2048, 16384 rows) and "
                          "print its JSON (for ncu captures of the GEMM kernels; not a bench line)")
+    ap.add_argument("--qaoa-apply-only", action="store_true",
+                    help="run only apply_clifford on the n=50 QAOA circuit at chi = 2^16, twice, and "
+                         "print its times (for ncu captures of the 64-bit-row layout; not a bench line)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: chi = 2^15 terms of the same decomposition, B = 2048, "
                          "L = 128, C = 128, T = 2 (for ncu captures; not a bench line)")
@@ -386,6 +389,26 @@ def _ev():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def qaoa_apply_only(local=0, chi=1 << 16):
+    """apply_clifford alone on the n=50 QAOA circuit, chi = 2^16, two launches (the
+    second is the one to capture)."""
+    from paper_1808_00128_gb300 import lrstab, workloads
+    cfg = workloads.config_qaoa(chi=chi)
+    low = lrstab.lower_circuit(cfg["n"], cfg["ops"])
+    sim = lrstab.Simulator(cfg["n"], local)
+    ms = []
+    for rep in range(2):
+        sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"])
+        a, b = _ev()
+        a.record()
+        sim.apply_clifford(low.gates)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    sim.close()
+    return {"workload": f"qaoa_e3lin2_n50_chi{chi}", "apply_ms": ms}
+
+
 def qaoa_study(local=0, chi=1 << 20, B=4096, C=256, T=64, L=512, alu_peak=None, hbm_peak=6695.2):
     """Config-4 shapes: n=50 Max-E3LIN2 QAOA (gamma 0.3, beta 0.2), chi = 2^20: gate
     updates, amplitudes, Metropolis and the norm estimate with L = 512."""
@@ -677,6 +700,9 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         print(json.dumps(mlp_gemm_study(0, reps=2, bf16_peak=peaks.get("bf16_tflops"))))
+        return
+    if args.qaoa_apply_only:
+        print(json.dumps(qaoa_apply_only(0)))
         return
     import numpy as np
     import torch

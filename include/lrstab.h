@@ -185,7 +185,8 @@ lrs_status lrs_init_terms(lrs_ctx* ctx, const lrs_slot* slots_host, int64_t n_sl
 /* Apply the lowered gate list to every term (left multiplications for
  * S, S^dagger, Z, CX, CZ; Eqs. (H1)-(H7) with Prop. (prop:H) for H; the
  * projective-gate rule of Sec. 4.1 for P0/P1; each term's own K_j for
- * LRS_OP_SLOT).  The gate list is copied to the device before return.
+ * LRS_OP_SLOT).  The gate list is read before return (it travels as kernel launch
+ * parameters, 7680 gates per launch); the work runs asynchronously on `stream`.
  * Readings: rules of one gate are simultaneous; "the first qubit" of V_b is
  * the lowest index; the single-qubit rewrite takes a = 0 when b = 0.
  * Errors: LRS_ERR_ARG (qubit >= n, q == r, unknown op, slot index out of
@@ -205,7 +206,7 @@ lrs_status lrs_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t 
  * falls from chi to R_p terms (the paper applies each term's gates separately).
  * LRS_ERR_STATE if the terms are not fresh EXACT-mode terms of the whole
  * decomposition or the slots' radices do not multiply to chi (checked before any
- * launch).  Synchronises the stream after the gate upload.                         */
+ * launch).  The gate list is read before return; the work runs asynchronously.      */
 lrs_status lrs_apply_circuit_shared(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, void* stream);
 
 /* Batched form of lrs_apply_clifford for several circuits (contexts on one

@@ -2,6 +2,8 @@
 // Clifford-circuit kernel.
 #include <string.h>
 
+#include <algorithm>
+
 #include <vector>
 
 #include "lrs_device.cuh"
@@ -161,9 +163,9 @@ struct SmemRows<64> {
 inline int apply_hb(int n) { return n <= 32 ? 0 : n <= 40 ? 8 : n <= 48 ? 16 : 64; }
 
 // One tile of APPLY_TPB terms through the whole gate list.
-template <int HB>
-__device__ __forceinline__ void apply_tile(const TermsView T, const lrs_gate* __restrict__ gates,
-                                           int64_t n_gates, int64_t tile, uint64_t* smem) {
+template <int HB, class Gates>
+__device__ __forceinline__ void apply_tile(const TermsView T, const Gates gates, int64_t n_gates, int64_t tile,
+                                           uint64_t* smem) {
     const int n = T.n;
     const int64_t a = tile * APPLY_TPB + threadIdx.x;   // cap % APPLY_TPB == 0
     SmemRows<HB> R(smem, n);
@@ -197,11 +199,27 @@ __device__ __forceinline__ void apply_tile(const TermsView T, const lrs_gate* __
     T.omega[a] = omega_pack(S.k, S.zero, S.h);
 }
 
+// The gate list of one launch is a kernel parameter (at most APPLY_PARAM_GATES gates;
+// longer lists take several launches): every thread reads the same gate, which the
+// parameter space serves from the constant cache without a global-memory round trip.
+constexpr int APPLY_PARAM_GATES = 7680;
+struct GateList {
+    lrs_gate g[APPLY_PARAM_GATES];
+};
+struct GatesParam {
+    const GateList* p;
+    __device__ __forceinline__ lrs_gate operator[](int64_t i) const { return p->g[i]; }
+};
+struct GatesGlobal {
+    const lrs_gate* __restrict__ p;
+    __device__ __forceinline__ lrs_gate operator[](int64_t i) const { return p[i]; }
+};
+
 template <int HB>
-__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford(TermsView T, const lrs_gate* __restrict__ gates,
-                                                              int64_t n_gates) {
+__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford(TermsView T, const __grid_constant__ GateList G,
+                                                              int n_gates) {
     extern __shared__ uint64_t smem[];
-    apply_tile<HB>(T, gates, n_gates, blockIdx.x, smem);
+    apply_tile<HB>(T, GatesParam{&G}, n_gates, blockIdx.x, smem);
 }
 
 // Several circuits of uneven chi in one launch: block b runs global tile b; the
@@ -225,7 +243,7 @@ __global__ void __maxnreg__(168) k_apply_clifford_batch(const __grid_constant__ 
 #pragma unroll 1
     for (int i = 1; i < B.count; ++i)
         if (B.first_tile[i] <= tile) c = i;
-    apply_tile<HB>(B.T[c], B.gates[c], B.n_gates[c], tile - B.first_tile[c], smem);
+    apply_tile<HB>(B.T[c], GatesGlobal{B.gates[c]}, B.n_gates[c], tile - B.first_tile[c], smem);
 }
 
 // ---- sample x from single terms (Sec. 4.1, "Simulating measurements") --------------
@@ -278,33 +296,37 @@ lrs_status launch_init_terms(lrs_ctx* ctx, int32_t mode, uint64_t seed, double s
     return LRS_OK;
 }
 
-lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates,
-                                 cudaStream_t st) {
-    return launch_apply_clifford_range(ctx, gates_dev, n_gates, ctx->cap, st);
+lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, cudaStream_t st) {
+    return launch_apply_clifford_range(ctx, gates_host, n_gates, ctx->cap, st);
 }
 
 template <int HB>
-static lrs_status launch_apply_hb(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates, int64_t blocks,
+static lrs_status launch_apply_hb(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, int64_t blocks,
                                   cudaStream_t st) {
     LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford<HB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)SmemRows<HB>::bytes(64)));
-    k_apply_clifford<HB><<<(unsigned)blocks, APPLY_TPB, SmemRows<HB>::bytes(ctx->n), st>>>(ctx->view(), gates_dev,
-                                                                                           n_gates);
-    LRS_LAUNCH_CHECK("apply_clifford kernel");
+    static thread_local GateList G;
+    for (int64_t i0 = 0; i0 < n_gates; i0 += APPLY_PARAM_GATES) {
+        const int len = (int)std::min<int64_t>(APPLY_PARAM_GATES, n_gates - i0);
+        memcpy(G.g, gates_host + i0, (size_t)len * sizeof(lrs_gate));
+        k_apply_clifford<HB><<<(unsigned)blocks, APPLY_TPB, SmemRows<HB>::bytes(ctx->n), st>>>(ctx->view(), G, len);
+        LRS_LAUNCH_CHECK("apply_clifford kernel");
+    }
     return LRS_OK;
 }
 
-// The gate list on the terms of the first ceil(n_terms / APPLY_TPB) tiles only.
-lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates, int64_t n_terms,
+// The gate list (host memory, read before return) on the terms of the first
+// ceil(n_terms / APPLY_TPB) tiles only.
+lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, int64_t n_terms,
                                        cudaStream_t st) {
     if (n_terms > ctx->cap) n_terms = ctx->cap;
     const int64_t blocks = (n_terms + APPLY_TPB - 1) / APPLY_TPB;
     if (blocks == 0 || n_gates == 0) return LRS_OK;
     switch (apply_hb(ctx->n)) {
-        case 0: return launch_apply_hb<0>(ctx, gates_dev, n_gates, blocks, st);
-        case 8: return launch_apply_hb<8>(ctx, gates_dev, n_gates, blocks, st);
-        case 16: return launch_apply_hb<16>(ctx, gates_dev, n_gates, blocks, st);
-        default: return launch_apply_hb<64>(ctx, gates_dev, n_gates, blocks, st);
+        case 0: return launch_apply_hb<0>(ctx, gates_host, n_gates, blocks, st);
+        case 8: return launch_apply_hb<8>(ctx, gates_host, n_gates, blocks, st);
+        case 16: return launch_apply_hb<16>(ctx, gates_host, n_gates, blocks, st);
+        default: return launch_apply_hb<64>(ctx, gates_host, n_gates, blocks, st);
     }
 }
 

@@ -454,17 +454,9 @@ extern "C" lrs_status lrs_apply_clifford(lrs_ctx* c, const lrs_gate* gates, int6
         if (rc != LRS_OK) return rc;
     }
     LRS_CUDA(cudaSetDevice(c->device));
-    size_t have = (size_t)c->gates_cap * sizeof(lrs_gate);
-    lrs_status rc = lrs_ensure((void**)&c->gates_dev, &have, (size_t)n_gates * sizeof(lrs_gate));
-    if (rc != LRS_OK) return rc;
-    c->gates_cap = (int64_t)(have / sizeof(lrs_gate));
-    cudaStream_t st = as_stream(stream);
-    LRS_CUDA(cudaMemcpyAsync(c->gates_dev, gates, (size_t)n_gates * sizeof(lrs_gate),
-                             cudaMemcpyHostToDevice, st));
-    LRS_CUDA(cudaStreamSynchronize(st));   // pageable source: keep the copy complete on return
     c->n_chains = 0;                        // chain states refer to the old terms
     c->fresh = false;
-    return launch_apply_clifford(c, c->gates_dev, n_gates, st);
+    return launch_apply_clifford(c, gates, n_gates, as_stream(stream));   // gates go in as launch parameters
 }
 
 extern "C" lrs_status lrs_apply_circuit_shared(lrs_ctx* c, const lrs_gate* gates, int64_t n_gates, void* stream) {
@@ -502,14 +494,6 @@ extern "C" lrs_status lrs_apply_circuit_shared(lrs_ctx* c, const lrs_gate* gates
         return lrs_fail(LRS_ERR_STATE, "slot radices give %lld terms, not %lld", (long long)prod, (long long)c->chi);
     LRS_CUDA(cudaSetDevice(c->device));
     cudaStream_t st = as_stream(stream);
-    if (n_gates > 0) {
-        size_t have = (size_t)c->gates_cap * sizeof(lrs_gate);
-        lrs_status rc = lrs_ensure((void**)&c->gates_dev, &have, (size_t)n_gates * sizeof(lrs_gate));
-        if (rc != LRS_OK) return rc;
-        c->gates_cap = (int64_t)(have / sizeof(lrs_gate));
-        LRS_CUDA(cudaMemcpyAsync(c->gates_dev, gates, (size_t)n_gates * sizeof(lrs_gate), cudaMemcpyHostToDevice, st));
-        LRS_CUDA(cudaStreamSynchronize(st));
-    }
     c->n_chains = 0;
     c->fresh = false;
     // Term alpha has digit j_p = (alpha / R_p) mod r_p over the nonzero choices of slot
@@ -521,14 +505,14 @@ extern "C" lrs_status lrs_apply_circuit_shared(lrs_ctx* c, const lrs_gate* gates
     lrs_status rc;
     while (i < n_gates) {
         if (gates[i].op != LRS_OP_SLOT) { ++i; continue; }
-        if ((rc = launch_apply_clifford_range(c, c->gates_dev + start, i - start, R, st)) != LRS_OK) return rc;
+        if ((rc = launch_apply_clifford_range(c, gates + start, i - start, R, st)) != LRS_OK) return rc;
         int64_t Rn = R;
         start = i;
         for (; i < n_gates && gates[i].op == LRS_OP_SLOT; ++i) Rn *= radix(i);
         if ((rc = launch_expand_terms(c, R, Rn, st)) != LRS_OK) return rc;
         R = Rn;
     }
-    return launch_apply_clifford_range(c, c->gates_dev + start, n_gates - start, R, st);
+    return launch_apply_clifford_range(c, gates + start, n_gates - start, R, st);
 }
 
 extern "C" lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_gate* const* gates,

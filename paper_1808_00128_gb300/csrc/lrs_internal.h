@@ -154,9 +154,10 @@ lrs_status lrs_scratch(lrs_ctx* ctx, size_t bytes, void** out);
 // ---- launchers implemented in the kernel translation units --------------------
 lrs_status launch_init_terms(lrs_ctx* ctx, int32_t mode, uint64_t seed, double scale,
                              cudaStream_t st);
-lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates,
-                                 cudaStream_t st);
-lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_dev, int64_t n_gates, int64_t n_terms,
+// Gate lists are host arrays, read before the call returns (passed to the kernel as
+// launch parameters).
+lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, cudaStream_t st);
+lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, int64_t n_terms,
                                        cudaStream_t st);
 lrs_status launch_expand_terms(lrs_ctx* ctx, int64_t R, int64_t Rn, cudaStream_t st);
 lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,

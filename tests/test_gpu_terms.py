@@ -72,6 +72,22 @@ def test_edge_widths_bit_exact(n):
     sim.close()
 
 
+def test_gate_list_longer_than_one_launch():
+    """More gates than one launch carries (7680): the list is split over launches."""
+    require_cuda()
+    rng = random.Random(77)
+    n = 9
+    ops = _random_circuit(n, 16000, 2, 1, rng)
+    chi = 2 ** 3
+    sim, low = _run(n, ops, chi, "exact")
+    assert len(low.gates) > 2 * 7680
+    ex = sim.export_terms()
+    terms, _, _ = oracle_terms(n, ops, chi, "exact", parallel=True)
+    for a in range(chi):
+        compare_term(ex, a, terms[a], f"term {a}")
+    sim.close()
+
+
 def test_all_hadamard_v_full():
     """|v| = 64: H on every qubit of a 64-qubit register."""
     require_cuda()
