@@ -29,8 +29,12 @@ struct AmpEntry {
 // parity(w & u_q) + parity(z_q), so a table entry keeps parity(z_q) in bit 63 of u_q
 // and the lookups count popc(w & u_q): two 8-byte tables (u_q, w_q) instead of three,
 // each a conflict-free 128-byte row per chunk.
+// Register budget: eight blocks per SM (64 registers) for the plain amplitude batch,
+// six for the variant that also writes the Pauli states (it spills at 64).  More
+// resident warps hide the shared-table lookups and the per-term barriers.
+constexpr int amp_min_blocks(bool qout) { return qout ? 6 : 8; }
 template <int NCH, bool QOUT, bool PK>
-__global__ void __launch_bounds__(AMP_XT) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
+__global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
                                                       int64_t batch, int64_t tt,
                                                       float2* __restrict__ partial, int64_t n_tiles,
                                                       ulonglong2* __restrict__ Qout) {

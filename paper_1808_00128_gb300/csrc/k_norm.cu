@@ -353,8 +353,12 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm_prep(TermsView T, int max_fold
     P.piv[alpha] = piv;
 }
 
+// Blocks per SM the register budget is sized for: eight at n <= 40 (shared memory
+// allows eight there), fewer for wider tableaux, whose elimination keeps more rows live.
+constexpr int norm_min_blocks(int nch) { return nch <= 10 ? 8 : nch <= 14 ? 6 : 5; }
+
 template <int NCH, int NB>
-__global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64_t L, int64_t tt,
+__global__ void __launch_bounds__(NRM_TPB, norm_min_blocks(NCH)) k_norm(TermsView T, NormPrep P, int64_t L, int64_t tt,
                                                   float2* __restrict__ partial, int64_t n_tiles,
                                                   int max_folds) {
     extern __shared__ uint64_t smem[];
@@ -367,13 +371,15 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64
     const int tid = threadIdx.x;
     const int64_t l = (int64_t)blockIdx.y * NRM_TPB + tid;
     uint64_t* tab = smem;                                          // [NCH][16], shared
-    uint64_t* sA = smem + NCH * 16 + tid;                          // A_c at sA[c * NRM_TPB]
-    uint64_t* sW = smem + NCH * 16 + (int64_t)n * NRM_TPB + tid;   // 8 NB work rows
+    uint64_t* sW = smem + NCH * 16 + tid;                          // 8 NB work rows
 
-    // ---- A_l (drawn once per call by k_norm_draw_a)
+    // ---- A_l (drawn once per call by k_norm_draw_a).  Its rows are read from global
+    // memory for every term: the block's 64 A's (n rows each) stay in L1, and keeping
+    // them out of shared memory lets eight blocks share an SM instead of five.
     const int64_t la = l < L ? l : 0;
     const uint64_t adlo = P.adlo[la], adhi = P.adhi[la];
-    for (int c = 0; c < n; ++c) sA[c * NRM_TPB] = P.A[(int64_t)c * L + la];
+    const uint64_t* gA = P.A + la;
+#define NRM_AROW(c) __ldg(gA + (int64_t)(c) * L)
 
     KahanC acc;
     acc.init();
@@ -430,7 +436,7 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64
             uint64_t dz0 = 0, zs = z0;
             uint32_t pcnt = 0;
             for (int c = 0; c < n; ++c) {
-                const uint64_t Doff = sA[c * NRM_TPB] ^ tJ[c];
+                const uint64_t Doff = NRM_AROW(c) ^ tJ[c];
                 sW[c * NRM_TPB] = Doff;
                 if (zs & 1ull) {
                     dz0 ^= Doff;
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm(TermsView T, NormPrep P, int64
         // parities sum_{c<d in g_k} D_cd for every k at once, and those of z0.
         uint64_t pacc = 0, pz = 0, clo = 0, chi = 0;
         for (int c = 0; c < n; ++c) {
-            const uint64_t Doff = sA[c * NRM_TPB] ^ tJ[c];
+            const uint64_t Doff = NRM_AROW(c) ^ tJ[c];
             const uint64_t above = (c == 63) ? 0ull : (~0ull << (c + 1));
             const uint64_t Gc = tG[c];
             sW[c * NRM_TPB] = fr_rows<NCH>(tab, Doff ^ (getb(dlo, c) << c));
@@ -549,7 +555,7 @@ template <int NCH>
 static lrs_status launch_norm_t(lrs_ctx* ctx, const NormPrep& P, int64_t L, int64_t tt,
                                 float2* partial, int64_t n_tiles, cudaStream_t st) {
     constexpr int NB = (NCH + 1) / 2;   // 8 x 8 blocks per side of the transposed matrix
-    const size_t smem = ((size_t)NCH * 16 + (size_t)(ctx->n + 8 * NB) * NRM_TPB) * sizeof(uint64_t);
+    const size_t smem = ((size_t)NCH * 16 + (size_t)(8 * NB) * NRM_TPB) * sizeof(uint64_t);
     LRS_CUDA(cudaFuncSetAttribute(k_norm<NCH, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
