@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--qaoa-apply-only", action="store_true",
                     help="run only apply_clifford on the n=50 QAOA circuit at chi = 2^16, twice, and "
                          "print its times (for ncu captures of the 64-bit-row layout; not a bench line)")
+    ap.add_argument("--metropolis-only", action="store_true",
+                    help="run only chain starts and 2 x 16 Metropolis steps on the n=40 workload at "
+                         "chi = 2^16, C = 256, and print their times (for ncu captures of the propose "
+                         "kernel; not a bench line)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: chi = 2^15 terms of the same decomposition, B = 2048, "
                          "L = 128, C = 128, T = 2 (for ncu captures; not a bench line)")
@@ -389,6 +393,32 @@ def _ev():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def metropolis_only(local=0, C=256, T=16):
+    """Chain starts and two calls of T Metropolis steps on the n=40 benchmark workload
+    (chi = 2^16, C chains); propose launches 17..32 are the second call's."""
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    cfg = workloads.config_mid()
+    n, chi = cfg["n"], cfg["chi"]
+    low = lrstab.lower_circuit(n, cfg["ops"])
+    sim = lrstab.Simulator(n, local)
+    sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"])
+    sim.apply_clifford(low.gates)
+    x0 = sim.sample_terms(C, seed=5)
+    sim.chains_init(x0)
+    ms = []
+    for rep in range(2):
+        a, b = _ev()
+        a.record()
+        sim.metropolis(T, seed=6, step0=rep * T)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    sim.close()
+    return {"workload": f"clifford_t_n40_chi{chi}_C{C}", "steps": T, "ms": ms}
+
+
 def qaoa_apply_only(local=0, chi=1 << 16):
     """apply_clifford alone on the n=50 QAOA circuit, chi = 2^16, two launches (the
     second is the one to capture)."""
@@ -703,6 +733,9 @@ def main():
         return
     if args.qaoa_apply_only:
         print(json.dumps(qaoa_apply_only(0)))
+        return
+    if args.metropolis_only:
+        print(json.dumps(metropolis_only(0)))
         return
     import numpy as np
     import torch

@@ -36,99 +36,171 @@ __device__ __forceinline__ float2 times_i_pow(float2 z, uint32_t m) {
     return (m & 2u) ? make_float2(-r.x, -r.y) : r;
 }
 
+// ---- bulk-copy pipeline helpers (1-D cp.async.bulk completing on an mbarrier) ----------
+constexpr unsigned long long MC_WAIT_NS = 1000000000ull;   // 1 s
+__device__ __forceinline__ uint32_t mc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long mc_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mc_bar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mc_bar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mc_bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ bool mc_bar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase of the given parity; false after MC_WAIT_NS.
+__device__ __forceinline__ bool mc_bar_wait(uint32_t bar, uint32_t parity) {
+    if (mc_bar_try(bar, parity)) return true;
+    const unsigned long long t0 = mc_ns();
+    while (!mc_bar_try(bar, parity))
+        if (mc_ns() - t0 > MC_WAIT_NS) return false;
+    return true;
+}
+
+// One chain's inputs for the block's MC_TERMS terms: its Pauli states and the rows
+// F_j, M_j of its proposal and F_p, M_p of its pending accepted flip.
+// Chains in flight per block: two stages (24 KB) leave room for eight blocks per SM,
+// which beats deeper per-block pipelines with fewer blocks.
+constexpr int MC_ST = 2;
+struct McStage {
+    ulonglong2 q[MC_TERMS];
+    uint64_t fj[MC_TERMS], mj[MC_TERMS], fp[MC_TERMS], mp[MC_TERMS];
+};
+constexpr size_t MC_SMEM = sizeof(McStage) * MC_ST;
+
 // One proposal: apply the pending accepted flip, then form the amplitude of y.
-// Rows F_j, M_j come straight from global memory (the [row][term] layout makes
-// them one coalesced 256-byte read per warp and they stay in L2); the only
-// per-(chain, term) HBM traffic is the 16-byte Q.  Each thread owns MC_TPT terms
-// (tile * MC_TERMS + tid + k * MC_TPB) and sums them before the block reduction.
+// The block owns MC_TERMS consecutive terms; for each of its chains thread 0 copies
+// the 4 KB of Q and the 2 KB row segments (coalesced [row][term] layout) into a
+// shared stage with cp.async.bulk, MC_ST chains ahead, so the HBM stream does not
+// depend on how many loads the threads keep in flight.  Q is written back only
+// where a pending flip is committed.  Each thread owns MC_TPT terms
+// (tid + k * MC_TPB) and sums them before the block reduction.  A stage wait that
+// gives up (1 s) sets *err, stops the block and leaves its partial sums unwritten.
 __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C, ulonglong2* __restrict__ Q,
                                                           const int32_t* __restrict__ pend,
                                                           const int32_t* __restrict__ jprop,
                                                           float2* __restrict__ partial, int64_t n_tiles,
-                                                          int cg) {
+                                                          int cg, int* err) {
+    extern __shared__ __align__(128) unsigned char mc_dyn[];
+    McStage* stage = reinterpret_cast<McStage*>(mc_dyn);
     __shared__ float2 red[MC_CG][MC_TPB / 32];
+    __shared__ int32_t spj[MC_CG], sj[MC_CG];
+    __shared__ __align__(8) uint64_t full[MC_ST];
+    __shared__ int abort_flag;
     const int tid = threadIdx.x;
     const int64_t tile = blockIdx.x;
-    int64_t a[MC_TPT];
+    const int64_t c0 = (int64_t)blockIdx.y * cg;
+    const int nc = (int)(C - c0 < cg ? C - c0 : cg);
+    const int64_t a0 = tile * MC_TERMS;
+    if (tid < nc) {
+        spj[tid] = pend[c0 + tid];
+        sj[tid] = jprop[c0 + tid];
+    }
+    if (tid < MC_ST) mc_bar_init(mc_smem(&full[tid]));
+    if (tid == 0) abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    auto issue = [&](int ci) {   // thread 0
+        McStage& S = stage[ci % MC_ST];
+        const uint32_t bar = mc_smem(&full[ci % MC_ST]);
+        const int pj = spj[ci], j = sj[ci];
+        const int64_t c = c0 + ci;
+        mc_bar_expect(bar, (uint32_t)(sizeof(S.q) + 2 * sizeof(S.fj) + (pj >= 0 ? 2 * sizeof(S.fp) : 0)));
+        mc_bulk_load(mc_smem(S.q), Q + c * T.cap + a0, sizeof(S.q), bar);
+        mc_bulk_load(mc_smem(S.fj), T.F + (int64_t)j * T.cap + a0, sizeof(S.fj), bar);
+        mc_bulk_load(mc_smem(S.mj), T.M + (int64_t)j * T.cap + a0, sizeof(S.mj), bar);
+        if (pj >= 0) {
+            mc_bulk_load(mc_smem(S.fp), T.F + (int64_t)pj * T.cap + a0, sizeof(S.fp), bar);
+            mc_bulk_load(mc_smem(S.mp), T.M + (int64_t)pj * T.cap + a0, sizeof(S.mp), bar);
+        }
+    };
+    if (tid == 0)
+        for (int ci = 0; ci < nc && ci < MC_ST; ++ci) issue(ci);
+
+    int tl[MC_TPT];
     uint64_t glo[MC_TPT], ghi[MC_TPT], s[MC_TPT], nv[MC_TPT], sv[MC_TPT];
     float2 base[MC_TPT];
     bool live[MC_TPT];
 #pragma unroll
     for (int k = 0; k < MC_TPT; ++k) {
-        a[k] = tile * MC_TERMS + tid + k * MC_TPB;
-        glo[k] = T.glo[a[k]];
-        ghi[k] = T.ghi[a[k]];
-        const uint64_t v = T.v[a[k]];
-        s[k] = T.s[a[k]];
+        tl[k] = tid + k * MC_TPB;
+        const int64_t a = a0 + tl[k];
+        glo[k] = T.glo[a];
+        ghi[k] = T.ghi[a];
+        const uint64_t v = T.v[a];
+        s[k] = T.s[a];
         nv[k] = ~v & T.nmask;
         sv[k] = s[k] & v;
-        const uint32_t om = T.omega[a[k]];
+        const uint32_t om = T.omega[a];
         live[k] = ((om >> 3) & 1u) == 0u;
-        base[k] = z8_scale(T.coef[a[k]], (int)(om & 7u), __popcll(v) + (int)(om >> 8));
+        base[k] = z8_scale(T.coef[a], (int)(om & 7u), __popcll(v) + (int)(om >> 8));
     }
     const uint64_t umask = (1ull << 62) - 1;
-    const int64_t c0 = (int64_t)blockIdx.y * cg;
-    const int nc = (int)(C - c0 < cg ? C - c0 : cg);
-    // the block's chains' pending flips and proposals, staged once
-    __shared__ int32_t spj[MC_CG], sj[MC_CG];
-    if (tid < nc) {
-        spj[tid] = pend[c0 + tid];
-        sj[tid] = jprop[c0 + tid];
-    }
-    __syncthreads();
-    constexpr int U = 2;   // chains whose loads are in flight together
-    for (int cb = 0; cb < nc; cb += U) {
-        ulonglong2 q[U][MC_TPT];
-        uint64_t Fp[U][MC_TPT], Mp[U][MC_TPT], Fj[U][MC_TPT], Mj[U][MC_TPT];
-        int pj[U], jj[U];
+    int ci = 0;
+    for (; ci < nc; ++ci) {
+        const McStage& S = stage[ci % MC_ST];
+        if (!mc_bar_wait(mc_smem(&full[ci % MC_ST]), (uint32_t)(ci / MC_ST) & 1u)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;   // uniform: read after the barrier
+        const int64_t c = c0 + ci;
+        const int pj = spj[ci], j = sj[ci];
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int h = 0; h < U; ++h) {
-            const int ci = cb + h < nc ? cb + h : nc - 1;
-            const int64_t c = c0 + ci;
-            pj[h] = spj[ci];
-            jj[h] = sj[ci];
-#pragma unroll
-            for (int k = 0; k < MC_TPT; ++k) {
-                q[h][k] = Q[c * T.cap + a[k]];
-                const int r = pj[h] >= 0 ? pj[h] : 0;
-                Fp[h][k] = __ldg(&T.F[(int64_t)r * T.cap + a[k]]);
-                Mp[h][k] = __ldg(&T.M[(int64_t)r * T.cap + a[k]]);
-                Fj[h][k] = __ldg(&T.F[(int64_t)jj[h] * T.cap + a[k]]);
-                Mj[h][k] = __ldg(&T.M[(int64_t)jj[h] * T.cap + a[k]]);
+        for (int k = 0; k < MC_TPT; ++k) {
+            const ulonglong2 q = S.q[tl[k]];
+            uint64_t u = q.x & umask, w = q.y;
+            uint32_t mu = (uint32_t)(q.x >> 62);
+            if (pj >= 0) {   // commit the flip accepted at the previous step
+                const uint64_t Fp = S.fp[tl[k]];
+                mu = (mu + (uint32_t)(getb(glo[k], pj) | (getb(ghi[k], pj) << 1)) + 2u * par64(w & Fp)) & 3u;
+                u ^= Fp;
+                w ^= S.mp[tl[k]];
+                Q[c * T.cap + a0 + tl[k]] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
+            }
+            const uint64_t Fj = S.fj[tl[k]];
+            const uint32_t muy =
+                (mu + (uint32_t)(getb(glo[k], j) | (getb(ghi[k], j) << 1)) + 2u * par64(w & Fj)) & 3u;
+            const uint64_t uy = u ^ Fj, wy = w ^ S.mj[tl[k]];
+            if (live[k] && ((uy ^ s[k]) & nv[k]) == 0) {
+                const uint32_t sign = par64(uy & wy) ^ par64(uy & sv[k]);
+                const float2 t = times_i_pow(base[k], muy + 2u * sign);
+                acc.x += t.x;
+                acc.y += t.y;
             }
         }
-#pragma unroll
-        for (int h = 0; h < U; ++h) {
-            const int ci = cb + h;
-            if (ci >= nc) break;                       // uniform across the block
-            const int64_t c = c0 + ci;
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < MC_TPT; ++k) {
-                uint64_t u = q[h][k].x & umask, w = q[h][k].y;
-                uint32_t mu = (uint32_t)(q[h][k].x >> 62);
-                if (pj[h] >= 0) {   // commit the flip accepted at the previous step
-                    const int p = pj[h];
-                    mu = (mu + (uint32_t)(getb(glo[k], p) | (getb(ghi[k], p) << 1)) + 2u * par64(w & Fp[h][k])) & 3u;
-                    u ^= Fp[h][k];
-                    w ^= Mp[h][k];
-                    Q[c * T.cap + a[k]] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
-                }
-                const int j = jj[h];
-                const uint32_t muy =
-                    (mu + (uint32_t)(getb(glo[k], j) | (getb(ghi[k], j) << 1)) + 2u * par64(w & Fj[h][k])) & 3u;
-                const uint64_t uy = u ^ Fj[h][k], wy = w ^ Mj[h][k];
-                if (live[k] && ((uy ^ s[k]) & nv[k]) == 0) {
-                    const uint32_t sign = par64(uy & wy) ^ par64(uy & sv[k]);
-                    const float2 t = times_i_pow(base[k], muy + 2u * sign);
-                    acc.x += t.x;
-                    acc.y += t.y;
-                }
-            }
-            block_sum(acc, red, ci);
+        block_sum(acc, red, ci);
+        __syncthreads();   // every thread is done with this stage
+        if (tid == 0 && ci + MC_ST < nc) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(ci + MC_ST);
         }
     }
-    __syncthreads();
+    if (ci < nc) {
+        // gave up: wait (bounded) for the copies still in flight into this block's
+        // stages, report, and leave the partial sums unwritten
+        if (tid == 0) {
+            for (int cj = ci; cj < nc && cj < ci + MC_ST; ++cj)
+                mc_bar_wait(mc_smem(&full[cj % MC_ST]), (uint32_t)(cj / MC_ST) & 1u);
+            atomicExch(err, 1);
+        }
+        return;
+    }
     if (tid < nc) {
         float2 acc = red[tid][0];
         for (int w2 = 1; w2 < MC_TPB / 32; ++w2) { acc.x += red[tid][w2].x; acc.y += red[tid][w2].y; }
@@ -273,8 +345,8 @@ static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2*
     const int cg = (int)ctx->tune_mc_cg;
     dim3 grid((unsigned)n_tiles, (unsigned)((C + cg - 1) / cg));
     for (int64_t t = t0; t < t0 + count; ++t) {
-        k_metro_propose<<<grid, MC_TPB, 0, st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop, partial,
-                                                 n_tiles, cg);
+        k_metro_propose<<<grid, MC_TPB, MC_SMEM, st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop, partial,
+                                                       n_tiles, cg, ctx->mc_err_d);
         LRS_LAUNCH_CHECK("metropolis propose kernel");
         k_metro_accept<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, ctx->mc_par, t, ctx->n, ctx->cx,
                                                      ctx->cp, ctx->pend, jprop,
@@ -330,6 +402,16 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
     lrs_status rc = lrs_scratch(ctx, part_bytes + (size_t)C * sizeof(int32_t) + 256, &scr);
     if (rc != LRS_OK) return rc;
     if (!ctx->mc_par) LRS_CUDA(cudaMalloc(&ctx->mc_par, sizeof(McParams)));
+    if (!ctx->mc_err_h) {
+        LRS_CUDA(cudaHostAlloc((void**)&ctx->mc_err_h, sizeof(int), cudaHostAllocMapped));
+        *ctx->mc_err_h = 0;
+        LRS_CUDA(cudaHostGetDevicePointer((void**)&ctx->mc_err_d, ctx->mc_err_h, 0));
+    }
+    if (*(volatile int*)ctx->mc_err_h) {   // set by an earlier propose launch that gave up waiting
+        *(volatile int*)ctx->mc_err_h = 0;
+        return lrs_fail(LRS_ERR_TIMEOUT, "a Metropolis propose kernel gave up waiting for its copies");
+    }
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MC_SMEM));
     float2* partial = (float2*)scr;
     int32_t* jprop = (int32_t*)((char*)scr + ((part_bytes + 255) & ~(size_t)255));
     k_mc_set<<<1, 1, 0, st>>>(ctx->mc_par, seed, step0);

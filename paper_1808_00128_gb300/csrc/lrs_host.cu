@@ -290,6 +290,7 @@ extern "C" lrs_status lrs_destroy(lrs_ctx* c) {
     cudaFree(c->eta_buf);
     if (c->mc_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->mc_exec);
     if (c->cap_stream) cudaStreamDestroy((cudaStream_t)c->cap_stream);
+    if (c->mc_err_h) cudaFreeHost(c->mc_err_h);
     delete c;
     return LRS_OK;
 }

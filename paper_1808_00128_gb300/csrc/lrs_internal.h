@@ -113,6 +113,8 @@ struct lrs_ctx {
     int64_t chains_cap = 0;
     bool q_stale = false;           // x moved by learned proposals: Q must be rebuilt
     McParams* mc_par = nullptr;     // device parameters of the flip-chain kernels
+    int* mc_err_h = nullptr;        // mapped host flag: a propose kernel gave up waiting
+    int* mc_err_d = nullptr;        // its device address
     void* mc_exec = nullptr;        // cudaGraphExec_t of LRS_MC_GRAPH_STEPS steps
     const void* mc_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     void* cap_stream = nullptr;     // cudaStream_t used for graph capture
