@@ -502,8 +502,10 @@ def qaoa_study(local=0, chi=1 << 20, B=4096, C=256, T=64, L=512, alu_peak=None, 
     res["norm_estimate"] = {"ms": t_norm * 1e3, "A_term_per_s": chi * L / t_norm, "achieved_Tops": ach / 1e12,
                             "frac": ach / alu_peak if alu_peak else None, "L": L,
                             "mean_eta": float(eta.mean().item())}
-    # Metropolis (flip chains), graph-replayed steps
+    # Metropolis (flip chains), graph-replayed steps, launch shape autotuned for C chains
     x0 = sim.sample_terms(C, seed=5)
+    sim.chains_init(x0)
+    res["tuned"].update({k: v for k, (v, ms) in autotune.tune(sim, chains=C).items()})
     sim.chains_init(x0)
     sim.metropolis(T, seed=6)
     torch.cuda.synchronize()

@@ -414,12 +414,16 @@ lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
  *                                 n - |v| constraints (F^T y)_k = 0, k not in v,
  *                                 instead of forming K = G^T (A+J) G; -1 forms
  *                                 K for every term.  Both give the same exact
- *                                 per-term value.                              */
+ *                                 per-term value.
+ *   LRS_TUNE_MC_STAGES            Metropolis: chains whose inputs a block keeps
+ *                                 in flight in shared memory (1..4, 2; 12 KB each)
+ */
 enum {
     LRS_TUNE_AMP_BLOCKS_PER_SM = 0,
     LRS_TUNE_NORM_MAX_TILES = 1,
     LRS_TUNE_MC_CHAINS_PER_BLOCK = 2,
-    LRS_TUNE_NORM_MAX_FOLDS = 3
+    LRS_TUNE_NORM_MAX_FOLDS = 3,
+    LRS_TUNE_MC_STAGES = 4
 };
 lrs_status lrs_set_tuning(lrs_ctx* ctx, int32_t param, int64_t value);
 lrs_status lrs_get_tuning(const lrs_ctx* ctx, int32_t param, int64_t* value);

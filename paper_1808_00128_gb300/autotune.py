@@ -13,22 +13,33 @@ import os
 CANDIDATES = {
     "amp_blocks_per_sm": [2, 4, 8, 16, 32],
     "norm_max_tiles": [256, 512, 1024, 2048, 4096],
-    "mc_chains_per_block": [16, 32, 64],
+    # fewer than 32 chains per block re-read each term's scalars (44 bytes) for too few
+    # chains; the knob itself accepts 1..64
+    "mc_chains_per_block": [32, 64],
     "norm_max_folds": [-1, 4, 8, 12],
+    "mc_stages": [1, 2, 3, 4],
 }
 
 
-def _time_ms(fn, reps: int = 3) -> float:
+def _time_ms(fn, reps: int = 3, flush=None) -> float:
+    """Median of `reps` timed calls; with `flush` (a device buffer larger than L2) the
+    buffer is rewritten before each call, outside the timed interval, so every call
+    starts from a cold L2 as a step of a long job does."""
+    import statistics
     import torch
     fn()                                   # warm-up (and any lazy set-up)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    ts = []
     for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         fn()
-    e1.record()
-    e1.synchronize()
-    return e0.elapsed_time(e1) / reps
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
 
 
 def _load(path):
@@ -47,17 +58,21 @@ def _save(path, cache):
 
 
 def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_path: str | None = None,
-         reps: int = 3) -> dict:
+         reps: int = 3, flush_l2: int = 256 << 20) -> dict:
     """Pick the fastest knob values for the given workload and set them on `sim`.
 
     x: amplitude batch (CUDA int64 tensor); L: number of equatorial states for
     norm estimation; chains: the chain count (chains must already be
-    initialised on `sim`).  Returns {knob: (value, ms)}.
+    initialised on `sim`); flush_l2: bytes of a buffer rewritten before every timed
+    call (0: time with a warm L2).  Returns {knob: (value, ms)}.
     """
     import torch
     cache = _load(cache_path)
     chosen = {}
     jobs = []
+    flush = None
+    if flush_l2:
+        flush = torch.empty(flush_l2 // 4, dtype=torch.float32, device=f"cuda:{sim.device}")
     if x is not None:
         out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
         jobs.append(("amp_blocks_per_sm", x.numel(), lambda: sim.amplitude(x, out=out)))
@@ -66,7 +81,8 @@ def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_pat
         jobs.append(("norm_max_tiles", L, lambda: sim.norm_estimate(L, seed=1, eta=eta)))
         jobs.append(("norm_max_folds", L, lambda: sim.norm_estimate(L, seed=1, eta=eta)))
     if chains:
-        jobs.append(("mc_chains_per_block", chains, lambda: sim.metropolis(8, seed=1)))
+        jobs.append(("mc_chains_per_block", chains, lambda: sim.metropolis(16, seed=1)))
+        jobs.append(("mc_stages", chains, lambda: sim.metropolis(16, seed=1)))
     for knob, batch, fn in jobs:
         key = f"{knob}|n={sim.n}|chi={sim.chi}|batch={batch}"
         if key in cache:
@@ -76,7 +92,7 @@ def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_pat
         best = None
         for v in CANDIDATES[knob]:
             sim.set_tuning(knob, v)
-            ms = _time_ms(fn, reps)
+            ms = _time_ms(fn, reps, flush)
             if best is None or ms < best[1]:
                 best = (v, ms)
         sim.set_tuning(knob, best[0])

@@ -60,8 +60,10 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
 
     const int64_t a0 = tile * tt;
     const int64_t a1 = (a0 + tt < T.cap) ? a0 + tt : T.cap;
-    // register prefetch of the next term: threads < n hold rows, threads 64..69 scalars
-    uint64_t pf = 0, pm = 0;
+    // register prefetch of the next term: threads < n hold rows, threads 64..66 scalars
+    // (thread 66 keeps its own copy of v: it must not read sc[2], which thread 65
+    // writes in the same barrier interval)
+    uint64_t pf = 0, pm = 0, pv = 0;
     auto prefetch = [&](int64_t a) {
         if (tid < n) {
             pf = T.F[(int64_t)tid * T.cap + a];
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
             pf = T.omega[a];
             const float2 b = T.coef[a];
             pm = (uint64_t)__float_as_uint(b.x) | ((uint64_t)__float_as_uint(b.y) << 32);
+            pv = T.v[a];
         }
     };
     if (a0 < a1) prefetch(a0);
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
             const uint32_t om = (uint32_t)pf;
             const float2 b = make_float2(__uint_as_float((uint32_t)pm), __uint_as_float((uint32_t)(pm >> 32)));
             sc_live = ((om >> 3) & 1u) ? 0u : 1u;
-            const int e0 = __popcll(sc[2]) + (int)(om >> 8);
+            const int e0 = __popcll(pv) + (int)(om >> 8);
 #pragma unroll
             for (int k = 0; k < 8; ++k) val8[k] = z8_scale(b, k + (int)(om & 7u), e0);
         }

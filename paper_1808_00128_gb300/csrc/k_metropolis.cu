@@ -75,19 +75,19 @@ __device__ __forceinline__ bool mc_bar_wait(uint32_t bar, uint32_t parity) {
 
 // One chain's inputs for the block's MC_TERMS terms: its Pauli states and the rows
 // F_j, M_j of its proposal and F_p, M_p of its pending accepted flip.
-// Chains in flight per block: two stages (24 KB) leave room for eight blocks per SM,
-// which beats deeper per-block pipelines with fewer blocks.
-constexpr int MC_ST = 2;
+// At most MC_ST chains in flight per block; the launch takes nst <= MC_ST stages
+// (a tuning knob: two stages, 24 KB, leave room for eight blocks per SM at n = 40,
+// four suit the n = 50 workload).
+constexpr int MC_ST = 4;
 struct McStage {
     ulonglong2 q[MC_TERMS];
     uint64_t fj[MC_TERMS], mj[MC_TERMS], fp[MC_TERMS], mp[MC_TERMS];
 };
-constexpr size_t MC_SMEM = sizeof(McStage) * MC_ST;
 
 // One proposal: apply the pending accepted flip, then form the amplitude of y.
 // The block owns MC_TERMS consecutive terms; for each of its chains thread 0 copies
 // the 4 KB of Q and the 2 KB row segments (coalesced [row][term] layout) into a
-// shared stage with cp.async.bulk, MC_ST chains ahead, so the HBM stream does not
+// shared stage with cp.async.bulk, nst chains ahead, so the HBM stream does not
 // depend on how many loads the threads keep in flight.  Q is written back only
 // where a pending flip is committed.  Each thread owns MC_TPT terms
 // (tid + k * MC_TPB) and sums them before the block reduction.  A stage wait that
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
                                                           const int32_t* __restrict__ pend,
                                                           const int32_t* __restrict__ jprop,
                                                           float2* __restrict__ partial, int64_t n_tiles,
-                                                          int cg, int* err) {
+                                                          int cg, int nst, int* err) {
     extern __shared__ __align__(128) unsigned char mc_dyn[];
     McStage* stage = reinterpret_cast<McStage*>(mc_dyn);
     __shared__ float2 red[MC_CG][MC_TPB / 32];
@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     auto issue = [&](int ci) {   // thread 0
-        McStage& S = stage[ci % MC_ST];
-        const uint32_t bar = mc_smem(&full[ci % MC_ST]);
+        McStage& S = stage[ci % nst];
+        const uint32_t bar = mc_smem(&full[ci % nst]);
         const int pj = spj[ci], j = sj[ci];
         const int64_t c = c0 + ci;
         mc_bar_expect(bar, (uint32_t)(sizeof(S.q) + 2 * sizeof(S.fj) + (pj >= 0 ? 2 * sizeof(S.fp) : 0)));
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         }
     };
     if (tid == 0)
-        for (int ci = 0; ci < nc && ci < MC_ST; ++ci) issue(ci);
+        for (int ci = 0; ci < nc && ci < nst; ++ci) issue(ci);
 
     int tl[MC_TPT];
     uint64_t glo[MC_TPT], ghi[MC_TPT], s[MC_TPT], nv[MC_TPT], sv[MC_TPT];
@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     const uint64_t umask = (1ull << 62) - 1;
     int ci = 0;
     for (; ci < nc; ++ci) {
-        const McStage& S = stage[ci % MC_ST];
-        if (!mc_bar_wait(mc_smem(&full[ci % MC_ST]), (uint32_t)(ci / MC_ST) & 1u)) abort_flag = 1;
+        const McStage& S = stage[ci % nst];
+        if (!mc_bar_wait(mc_smem(&full[ci % nst]), (uint32_t)(ci / nst) & 1u)) abort_flag = 1;
         __syncthreads();
         if (abort_flag) break;   // uniform: read after the barrier
         const int64_t c = c0 + ci;
@@ -186,17 +186,17 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         }
         block_sum(acc, red, ci);
         __syncthreads();   // every thread is done with this stage
-        if (tid == 0 && ci + MC_ST < nc) {
+        if (tid == 0 && ci + nst < nc) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(ci + MC_ST);
+            issue(ci + nst);
         }
     }
     if (ci < nc) {
         // gave up: wait (bounded) for the copies still in flight into this block's
         // stages, report, and leave the partial sums unwritten
         if (tid == 0) {
-            for (int cj = ci; cj < nc && cj < ci + MC_ST; ++cj)
-                mc_bar_wait(mc_smem(&full[cj % MC_ST]), (uint32_t)(cj / MC_ST) & 1u);
+            for (int cj = ci; cj < nc && cj < ci + nst; ++cj)
+                mc_bar_wait(mc_smem(&full[cj % nst]), (uint32_t)(cj / nst) & 1u);
             atomicExch(err, 1);
         }
         return;
@@ -345,8 +345,9 @@ static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2*
     const int cg = (int)ctx->tune_mc_cg;
     dim3 grid((unsigned)n_tiles, (unsigned)((C + cg - 1) / cg));
     for (int64_t t = t0; t < t0 + count; ++t) {
-        k_metro_propose<<<grid, MC_TPB, MC_SMEM, st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop, partial,
-                                                       n_tiles, cg, ctx->mc_err_d);
+        const int nst = (int)ctx->tune_mc_stages;
+        k_metro_propose<<<grid, MC_TPB, nst * sizeof(McStage), st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop,
+                                                                     partial, n_tiles, cg, nst, ctx->mc_err_d);
         LRS_LAUNCH_CHECK("metropolis propose kernel");
         k_metro_accept<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, ctx->mc_par, t, ctx->n, ctx->cx,
                                                      ctx->cp, ctx->pend, jprop,
@@ -360,7 +361,7 @@ static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2*
 // rebuilt whenever the buffers it was captured with change.
 static lrs_status mc_graph(lrs_ctx* ctx, float2* partial, int32_t* jprop, cudaGraphExec_t* out) {
     const void* key[6] = {partial, jprop, ctx->Q, ctx->F,
-                          (void*)(intptr_t)(ctx->n_chains * 128 + ctx->tune_mc_cg),
+                          (void*)(intptr_t)((ctx->n_chains * 128 + ctx->tune_mc_cg) * 8 + ctx->tune_mc_stages),
                           (void*)(intptr_t)ctx->cap};
     if (ctx->mc_exec && memcmp(key, ctx->mc_key, sizeof(key)) == 0) {
         *out = (cudaGraphExec_t)ctx->mc_exec;
@@ -411,7 +412,8 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
         *(volatile int*)ctx->mc_err_h = 0;
         return lrs_fail(LRS_ERR_TIMEOUT, "a Metropolis propose kernel gave up waiting for its copies");
     }
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MC_SMEM));
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(MC_ST * sizeof(McStage))));
     float2* partial = (float2*)scr;
     int32_t* jprop = (int32_t*)((char*)scr + ((part_bytes + 255) & ~(size_t)255));
     k_mc_set<<<1, 1, 0, st>>>(ctx->mc_par, seed, step0);

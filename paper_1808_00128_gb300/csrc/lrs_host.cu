@@ -832,6 +832,10 @@ extern "C" lrs_status lrs_set_tuning(lrs_ctx* c, int32_t param, int64_t value) {
             if (value < 1 || value > 64) return lrs_fail(LRS_ERR_ARG, "chains per block in 1..64");
             c->tune_mc_cg = value;
             return LRS_OK;
+        case LRS_TUNE_MC_STAGES:
+            if (value < 1 || value > 4) return lrs_fail(LRS_ERR_ARG, "Metropolis stages in 1..4");
+            c->tune_mc_stages = value;
+            return LRS_OK;
         case LRS_TUNE_NORM_MAX_FOLDS:
             if (value < -1 || value > 12) return lrs_fail(LRS_ERR_ARG, "norm max folds in -1..12");
             c->tune_norm_folds = value;
@@ -847,6 +851,7 @@ extern "C" lrs_status lrs_get_tuning(const lrs_ctx* c, int32_t param, int64_t* v
         case LRS_TUNE_AMP_BLOCKS_PER_SM: *value = c->tune_amp_bps; return LRS_OK;
         case LRS_TUNE_NORM_MAX_TILES: *value = c->tune_norm_tiles; return LRS_OK;
         case LRS_TUNE_MC_CHAINS_PER_BLOCK: *value = c->tune_mc_cg; return LRS_OK;
+        case LRS_TUNE_MC_STAGES: *value = c->tune_mc_stages; return LRS_OK;
         case LRS_TUNE_NORM_MAX_FOLDS: *value = c->tune_norm_folds; return LRS_OK;
         default: return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
     }

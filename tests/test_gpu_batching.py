@@ -69,7 +69,8 @@ def test_tuning_knobs_keep_results():
         outs.append(xo.cpu())
     assert torch.equal(outs[0], outs[1])
     chosen = autotune.tune(sim, x=x, L=64, chains=100)
-    assert set(chosen) == {"amp_blocks_per_sm", "norm_max_tiles", "norm_max_folds", "mc_chains_per_block"}
+    assert set(chosen) == {"amp_blocks_per_sm", "norm_max_tiles", "norm_max_folds", "mc_chains_per_block",
+                           "mc_stages"}
     for k, (v, ms) in chosen.items():
         assert v in autotune.CANDIDATES[k] and ms > 0
         assert sim.get_tuning(k) == v
