@@ -21,6 +21,9 @@ CANDIDATES = {
 }
 
 
+MARGIN = 0.03
+
+
 def _time_ms(fn, reps: int = 3, flush=None) -> float:
     """Median of `reps` timed calls; with `flush` (a device buffer larger than L2) the
     buffer is rewritten before each call, outside the timed interval, so every call
@@ -58,7 +61,7 @@ def _save(path, cache):
 
 
 def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_path: str | None = None,
-         reps: int = 3, flush_l2: int = 256 << 20) -> dict:
+         reps: int = 5, flush_l2: int = 256 << 20) -> dict:
     """Pick the fastest knob values for the given workload and set them on `sim`.
 
     x: amplitude batch (CUDA int64 tensor); L: number of equatorial states for
@@ -89,11 +92,15 @@ def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_pat
             sim.set_tuning(knob, cache[key]["value"])
             chosen[knob] = (cache[key]["value"], cache[key]["ms"])
             continue
+        # the current value is the incumbent; another candidate must beat it by more
+        # than MARGIN (timing noise must not move a knob)
+        cur = sim.get_tuning(knob)
+        order = [cur] + [v for v in CANDIDATES[knob] if v != cur]
         best = None
-        for v in CANDIDATES[knob]:
+        for v in order:
             sim.set_tuning(knob, v)
             ms = _time_ms(fn, reps, flush)
-            if best is None or ms < best[1]:
+            if best is None or ms < best[1] * (1.0 - MARGIN):
                 best = (v, ms)
         sim.set_tuning(knob, best[0])
         cache[key] = {"value": best[0], "ms": best[1]}
