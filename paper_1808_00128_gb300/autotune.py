@@ -92,10 +92,10 @@ def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_pat
             sim.set_tuning(knob, cache[key]["value"])
             chosen[knob] = (cache[key]["value"], cache[key]["ms"])
             continue
-        # the current value is the incumbent; another candidate must beat it by more
-        # than MARGIN (timing noise must not move a knob)
+        # the current value, if it is a candidate, is the incumbent; another candidate
+        # must beat it by more than MARGIN (timing noise must not move a knob)
         cur = sim.get_tuning(knob)
-        order = [cur] + [v for v in CANDIDATES[knob] if v != cur]
+        order = ([cur] if cur in CANDIDATES[knob] else []) + [v for v in CANDIDATES[knob] if v != cur]
         best = None
         for v in order:
             sim.set_tuning(knob, v)
