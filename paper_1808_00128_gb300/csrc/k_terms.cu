@@ -93,6 +93,7 @@ __host__ __device__ __forceinline__ int rows_pad(int n, int esz) {
 template <int HB>
 struct SmemRows {
     typedef typename HiWord<HB>::T Hi;
+    static constexpr int kRowUnroll = 2;   // rows per step of the Hadamard row pass
     struct Mat {
         uint32_t* lo;
         Hi* hi;
@@ -138,6 +139,7 @@ struct SmemRows {
 // (4% faster at n = 50 than generic pointers).
 template <>
 struct SmemRows<64> {
+    static constexpr int kRowUnroll = 2;
     struct Mat {
         uint32_t a;
     };

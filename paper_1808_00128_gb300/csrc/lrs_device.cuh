@@ -191,9 +191,9 @@ __device__ __forceinline__ void prop_h_rows(Rows& R, int n, const HRowMasks& k0,
     const auto Y = k.first ? R.matF() : R.matG();
     const auto Mm = R.matM();
     uint32_t ah = 0, sh = 0, al = 0, sl = 0;
-#pragma unroll 2
+#pragma unroll (Rows::kRowUnroll)
     for (int p = n - 1; p >= 32; --p) prop_h_row<FAN>(R, X, Y, Mm, p, k, ah, sh);
-#pragma unroll 2
+#pragma unroll (Rows::kRowUnroll)
     for (int p = (n < 32 ? n : 32) - 1; p >= 0; --p) prop_h_row<FAN>(R, X, Y, Mm, p, k, al, sl);
     add2 = ((uint64_t)ah << 32) | al;
     sub1 = ((uint64_t)sh << 32) | sl;
