@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     if (tid == 0) abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
-    auto issue = [&](int ci) {   // thread 0
-        McStage& S = stage[ci % nst];
-        const uint32_t bar = mc_smem(&full[ci % nst]);
+    auto issue = [&](int ci, int si) {   // thread 0: chain ci into stage si
+        McStage& S = stage[si];
+        const uint32_t bar = mc_smem(&full[si]);
         const int pj = spj[ci], j = sj[ci];
         const int64_t c = c0 + ci;
         mc_bar_expect(bar, (uint32_t)(sizeof(S.q) + 2 * sizeof(S.fj) + (pj >= 0 ? 2 * sizeof(S.fp) : 0)));
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         }
     };
     if (tid == 0)
-        for (int ci = 0; ci < nc && ci < nst; ++ci) issue(ci);
+        for (int ci = 0; ci < nc && ci < nst; ++ci) issue(ci, ci);
 
     int tl[MC_TPT];
     uint64_t glo[MC_TPT], ghi[MC_TPT], s[MC_TPT], nv[MC_TPT], sv[MC_TPT];
@@ -152,10 +152,11 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         base[k] = z8_scale(T.coef[a], (int)(om & 7u), __popcll(v) + (int)(om >> 8));
     }
     const uint64_t umask = (1ull << 62) - 1;
-    int ci = 0;
+    int ci = 0, si = 0;       // chain, its stage
+    uint32_t ph = 0;          // parity of the stage's current phase
     for (; ci < nc; ++ci) {
-        const McStage& S = stage[ci % nst];
-        if (!mc_bar_wait(mc_smem(&full[ci % nst]), (uint32_t)(ci / nst) & 1u)) abort_flag = 1;
+        const McStage& S = stage[si];
+        if (!mc_bar_wait(mc_smem(&full[si]), ph)) abort_flag = 1;
         __syncthreads();
         if (abort_flag) break;   // uniform: read after the barrier
         const int64_t c = c0 + ci;
@@ -188,15 +189,24 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         __syncthreads();   // every thread is done with this stage
         if (tid == 0 && ci + nst < nc) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(ci + nst);
+            issue(ci + nst, si);
+        }
+        if (++si == nst) {
+            si = 0;
+            ph ^= 1u;
         }
     }
     if (ci < nc) {
         // gave up: wait (bounded) for the copies still in flight into this block's
         // stages, report, and leave the partial sums unwritten
         if (tid == 0) {
-            for (int cj = ci; cj < nc && cj < ci + nst; ++cj)
-                mc_bar_wait(mc_smem(&full[cj % nst]), (uint32_t)(cj / nst) & 1u);
+            for (int cj = ci; cj < nc && cj < ci + nst; ++cj) {
+                mc_bar_wait(mc_smem(&full[si]), ph);
+                if (++si == nst) {
+                    si = 0;
+                    ph ^= 1u;
+                }
+            }
             atomicExch(err, 1);
         }
         return;
