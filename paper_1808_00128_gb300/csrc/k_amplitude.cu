@@ -27,8 +27,9 @@ struct AmpEntry {
 // zero terms included (the Metropolis chain state of Sec. 4.2).
 // PK (n <= 62): only parity(z) enters mu, and parity(z_after) = parity(z) +
 // parity(w & u_q) + parity(z_q), so a table entry keeps parity(z_q) in bit 63 of u_q
-// and the lookups count popc(w & u_q): two 8-byte tables (u_q, w_q) instead of three,
-// each a conflict-free 128-byte row per chunk.
+// and the lookups XOR-accumulate w & u_q (one popcount per string at the end): two
+// 8-byte tables (u_q, w_q) instead of three, each a conflict-free 128-byte row per
+// chunk.
 // Register budget: eight blocks per SM (64 registers) for the plain amplitude batch,
 // six for the variant that also writes the Pauli states (it spills at 64).  More
 // resident warps hide the shared-table lookups and the per-term barriers.
@@ -128,16 +129,18 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
             uint64_t u = 0, w = 0;
             uint32_t zpar;
             if (PK) {
-                uint32_t zc = 0;
+                // only the parity of sum_c popc(w_c & u_q) enters, and that is the
+                // parity of the XOR of the terms: one popcount per string
+                uint64_t zx = 0;
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) {
                     const int q = (int)((x >> (4 * c)) & 15u);
                     const uint64_t Eu = tabU[c][q], Ew = tabW[c][q];
-                    zc += (uint32_t)__popcll(w & Eu);   // w has no bit 63
+                    zx ^= w & Eu;   // w has no bit 63
                     u ^= Eu;
                     w ^= Ew;
                 }
-                zpar = (zc + (uint32_t)(u >> 63)) & 1u;
+                zpar = ((uint32_t)__popcll(zx) + (uint32_t)(u >> 63)) & 1u;
                 u &= ~(1ull << 63);
             } else {
                 uint64_t z = 0;
