@@ -353,9 +353,10 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm_prep(TermsView T, int max_fold
     P.piv[alpha] = piv;
 }
 
-// Blocks per SM the register budget is sized for: eight at n <= 40 (shared memory
-// allows eight there), fewer for wider tableaux, whose elimination keeps more rows live.
-constexpr int norm_min_blocks(int nch) { return nch <= 10 ? 8 : nch <= 14 ? 6 : 5; }
+// Blocks per SM the register budget is sized for: at n <= 40 96 registers (shared
+// memory then fits nine blocks; the few spilled values cost less than the extra
+// warps gain), fewer blocks for wider tableaux, whose elimination keeps more rows live.
+constexpr int norm_min_blocks(int nch) { return nch <= 10 ? 10 : nch <= 14 ? 6 : 5; }
 
 template <int NCH, int NB>
 __global__ void __launch_bounds__(NRM_TPB, norm_min_blocks(NCH)) k_norm(TermsView T, NormPrep P, int64_t L, int64_t tt,
