@@ -58,16 +58,22 @@ def test_tuning_knobs_keep_results():
         assert np.all(np.abs(eta - eta0) <= 1e-5 * np.maximum(eta0, 0.25))
     with pytest.raises(lrstab.LrsError):
         sim.set_tuning("mc_chains_per_block", 65)
-    # chains per block: same trajectory
+    # chains per block and chains in flight per block: same trajectory
     x0 = sim.sample_terms(100, seed=9)
     outs = []
-    for cg in (64, 7):
+    for cg, st in ((64, 2), (7, 2), (64, 1), (13, 3), (64, 4)):
         sim.set_tuning("mc_chains_per_block", cg)
+        sim.set_tuning("mc_stages", st)
         sim.chains_init(x0)
         xo = torch.empty(100, dtype=torch.int64, device="cuda:0")
         sim.metropolis(40, seed=2, x_out=xo)     # 40 steps: two graph replays + 8 direct steps
         outs.append(xo.cpu())
-    assert torch.equal(outs[0], outs[1])
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
+    with pytest.raises(lrstab.LrsError):
+        sim.set_tuning("mc_stages", 5)
+    sim.set_tuning("mc_chains_per_block", 7)
+    sim.set_tuning("mc_stages", 2)
     chosen = autotune.tune(sim, x=x, L=64, chains=100)
     assert set(chosen) == {"amp_blocks_per_sm", "norm_max_tiles", "norm_max_folds", "mc_chains_per_block",
                            "mc_stages"}
