@@ -23,8 +23,9 @@ struct AmpEntry {
     uint64_t u, w, z;
 };
 
-// QOUT: also store every (x_i, term) Pauli as Q[i * cap + alpha] = (u | mu << 62, w),
-// zero terms included (the Metropolis chain state of Sec. 4.2).
+// QOUT: also store every (x_i, term) Pauli state at entry i * cap + alpha of Qout
+// (q_store: 12 bytes for n <= 40, i.e. NCH <= 10, else 16), zero terms included (the
+// Metropolis chain state of Sec. 4.2).
 // PK (n <= 62): only parity(z) enters mu, and parity(z_after) = parity(z) +
 // parity(w & u_q) + parity(z_q), so a table entry keeps parity(z_q) in bit 63 of u_q
 // and the lookups XOR-accumulate w & u_q (one popcount per string at the end): two
@@ -38,7 +39,7 @@ template <int NCH, bool QOUT, bool PK>
 __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
                                                       int64_t batch, int64_t tt,
                                                       float2* __restrict__ partial, int64_t n_tiles,
-                                                      ulonglong2* __restrict__ Qout) {
+                                                      void* __restrict__ Qout) {
     __shared__ AmpEntry tab[PK ? 1 : NCH][16];
     __shared__ uint64_t tabU[PK ? NCH : 1][16], tabW[PK ? NCH : 1][16];
     __shared__ uint64_t sF[64], sM[64];
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
             const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)zpar;
             if (QOUT) {
                 const int64_t i = xb + tid + k * AMP_XT;
-                if (i < batch) Qout[i * T.cap + a] = make_ulonglong2(u | ((uint64_t)(mu & 3) << 62), w);
+                if (i < batch) q_store<(NCH <= 10)>(Qout, batch * T.cap, i * T.cap + a, u, w, (uint32_t)mu);
             }
             if (live && ((u ^ s) & nv) == 0) {
                 const int sign = (int)par64(u & (w ^ sv));
@@ -219,7 +220,7 @@ AmpPlan amp_plan(const lrs_ctx* ctx, int64_t batch) {
 
 template <int NCH>
 lrs_status launch_amp_t(lrs_ctx* ctx, const uint64_t* x, int64_t batch, float2* partial,
-                        const AmpPlan& P, ulonglong2* Qout, cudaStream_t st) {
+                        const AmpPlan& P, void* Qout, cudaStream_t st) {
     dim3 grid((unsigned)P.n_tiles, (unsigned)P.xblocks);
     const bool pk = ctx->n <= 62;
     if (Qout)   // chains need n <= 62 (mu lives in bits 62-63 of Q), so the packed tables apply
@@ -235,7 +236,7 @@ lrs_status launch_amp_t(lrs_ctx* ctx, const uint64_t* x, int64_t batch, float2* 
 }
 
 lrs_status launch_amp_kernels(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
-                              float2* partial, const AmpPlan& P, cudaStream_t st, ulonglong2* Qout) {
+                              float2* partial, const AmpPlan& P, cudaStream_t st, void* Qout) {
     if (P.xblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "amplitude batch too large");
     lrs_status rc;
     switch ((ctx->n + 3) / 4) {
@@ -266,7 +267,7 @@ lrs_status launch_amp_kernels(lrs_ctx* ctx, const uint64_t* x, int64_t batch, do
 
 // Amplitudes of x[0..batch) into scratch (*amp_out, 2 doubles per x) and the Pauli
 // state Q[i * cap + alpha] of every (x_i, term): the chain start of Sec. 4.2.
-lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, ulonglong2* Q, double** amp_out,
+lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, void* Q, double** amp_out,
                               cudaStream_t st) {
     const AmpPlan P = amp_plan(ctx, batch);
     const size_t part = ((size_t)batch * P.n_tiles * sizeof(float2) + 255) & ~(size_t)255;

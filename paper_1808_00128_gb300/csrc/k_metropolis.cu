@@ -1,7 +1,8 @@
 // Metropolis chains with the incremental Pauli update of Sec. 4.2.
 //
 // State per (chain c, term alpha): Q = i^mu X(u) Z(w) = U_C^{-1} X(x_c) U_C,
-// packed in 16 bytes as (u | mu << 62, w) (needs n <= 62), layout [chain][term].
+// packed in 12 bytes for n <= 40 and 16 bytes up to n = 62 (q_store), layout
+// [chain][term].
 // A step proposes y = x ^ e_j; every term updates Q_y = Q_x P_j with
 // P_j = U_C^{-1} X_j U_C = i^{gamma_j} X(F_j) Z(M_j):
 //     mu += gamma_j + 2 parity(w & F_j);  u ^= F_j;  w ^= M_j
@@ -80,7 +81,9 @@ __device__ __forceinline__ bool mc_bar_wait(uint32_t bar, uint32_t parity) {
 // four suit the n = 50 workload).
 constexpr int MC_ST = 4;
 struct McStage {
-    ulonglong2 q[MC_TERMS];
+    // the chain's Pauli states: MC_TERMS 16-byte pairs, or (compact) MC_TERMS 64-bit
+    // words followed by MC_TERMS 32-bit words
+    __align__(16) unsigned char q[MC_TERMS * 16];
     uint64_t fj[MC_TERMS], mj[MC_TERMS], fp[MC_TERMS], mp[MC_TERMS];
 };
 
@@ -92,7 +95,8 @@ struct McStage {
 // where a pending flip is committed.  Each thread owns MC_TPT terms
 // (tid + k * MC_TPB) and sums them before the block reduction.  A stage wait that
 // gives up (1 s) sets *err, stops the block and leaves its partial sums unwritten.
-__global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C, ulonglong2* __restrict__ Q,
+template <bool CQ>
+__global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C, void* __restrict__ Q,
                                                           const int32_t* __restrict__ pend,
                                                           const int32_t* __restrict__ jprop,
                                                           float2* __restrict__ partial, int64_t n_tiles,
@@ -108,6 +112,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     const int64_t c0 = (int64_t)blockIdx.y * cg;
     const int nc = (int)(C - c0 < cg ? C - c0 : cg);
     const int64_t a0 = tile * MC_TERMS;
+    const int64_t pairs = C * T.cap;   // entries of the Pauli-state arrays
     if (tid < nc) {
         spj[tid] = pend[c0 + tid];
         sj[tid] = jprop[c0 + tid];
@@ -121,8 +126,16 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         const uint32_t bar = mc_smem(&full[si]);
         const int pj = spj[ci], j = sj[ci];
         const int64_t c = c0 + ci;
-        mc_bar_expect(bar, (uint32_t)(sizeof(S.q) + 2 * sizeof(S.fj) + (pj >= 0 ? 2 * sizeof(S.fp) : 0)));
-        mc_bulk_load(mc_smem(S.q), Q + c * T.cap + a0, sizeof(S.q), bar);
+        const uint32_t qb = CQ ? MC_TERMS * 12 : MC_TERMS * 16;
+        mc_bar_expect(bar, (uint32_t)(qb + 2 * sizeof(S.fj) + (pj >= 0 ? 2 * sizeof(S.fp) : 0)));
+        if (CQ) {
+            mc_bulk_load(mc_smem(S.q), reinterpret_cast<const uint64_t*>(Q) + c * T.cap + a0, MC_TERMS * 8, bar);
+            mc_bulk_load(mc_smem(S.q + MC_TERMS * 8),
+                         reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint64_t*>(Q) + pairs) + c * T.cap + a0,
+                         MC_TERMS * 4, bar);
+        } else {
+            mc_bulk_load(mc_smem(S.q), reinterpret_cast<const ulonglong2*>(Q) + c * T.cap + a0, MC_TERMS * 16, bar);
+        }
         mc_bulk_load(mc_smem(S.fj), T.F + (int64_t)j * T.cap + a0, sizeof(S.fj), bar);
         mc_bulk_load(mc_smem(S.mj), T.M + (int64_t)j * T.cap + a0, sizeof(S.mj), bar);
         if (pj >= 0) {
@@ -151,7 +164,6 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         live[k] = ((om >> 3) & 1u) == 0u;
         base[k] = z8_scale(T.coef[a], (int)(om & 7u), __popcll(v) + (int)(om >> 8));
     }
-    const uint64_t umask = (1ull << 62) - 1;
     int ci = 0, si = 0;       // chain, its stage
     uint32_t ph = 0;          // parity of the stage's current phase
     for (; ci < nc; ++ci) {
@@ -164,15 +176,20 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < MC_TPT; ++k) {
-            const ulonglong2 q = S.q[tl[k]];
-            uint64_t u = q.x & umask, w = q.y;
-            uint32_t mu = (uint32_t)(q.x >> 62);
+            uint64_t u, w;
+            uint32_t mu;
+            if (CQ)
+                q_unpack<true>(reinterpret_cast<const uint64_t*>(S.q)[tl[k]],
+                               reinterpret_cast<const uint32_t*>(S.q + MC_TERMS * 8)[tl[k]], u, w, mu);
+            else
+                q_unpack<false>(reinterpret_cast<const ulonglong2*>(S.q)[tl[k]].x,
+                                reinterpret_cast<const ulonglong2*>(S.q)[tl[k]].y, u, w, mu);
             if (pj >= 0) {   // commit the flip accepted at the previous step
                 const uint64_t Fp = S.fp[tl[k]];
                 mu = (mu + (uint32_t)(getb(glo[k], pj) | (getb(ghi[k], pj) << 1)) + 2u * par64(w & Fp)) & 3u;
                 u ^= Fp;
                 w ^= S.mp[tl[k]];
-                Q[c * T.cap + a0 + tl[k]] = make_ulonglong2(u | ((uint64_t)mu << 62), w);
+                q_store<CQ>(Q, pairs, c * T.cap + a0 + tl[k], u, w, mu);
             }
             const uint64_t Fj = S.fj[tl[k]];
             const uint32_t muy =
@@ -356,8 +373,12 @@ static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2*
     dim3 grid((unsigned)n_tiles, (unsigned)((C + cg - 1) / cg));
     for (int64_t t = t0; t < t0 + count; ++t) {
         const int nst = (int)ctx->tune_mc_stages;
-        k_metro_propose<<<grid, MC_TPB, nst * sizeof(McStage), st>>>(ctx->view(), C, ctx->Q, ctx->pend, jprop,
-                                                                     partial, n_tiles, cg, nst, ctx->mc_err_d);
+        if (q_compact(ctx->n))
+            k_metro_propose<true><<<grid, MC_TPB, nst * sizeof(McStage), st>>>(
+                ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d);
+        else
+            k_metro_propose<false><<<grid, MC_TPB, nst * sizeof(McStage), st>>>(
+                ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d);
         LRS_LAUNCH_CHECK("metropolis propose kernel");
         k_metro_accept<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, ctx->mc_par, t, ctx->n, ctx->cx,
                                                      ctx->cp, ctx->pend, jprop,
@@ -422,7 +443,9 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
         *(volatile int*)ctx->mc_err_h = 0;
         return lrs_fail(LRS_ERR_TIMEOUT, "a Metropolis propose kernel gave up waiting for its copies");
     }
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(MC_ST * sizeof(McStage))));
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(MC_ST * sizeof(McStage))));
     float2* partial = (float2*)scr;
     int32_t* jprop = (int32_t*)((char*)scr + ((part_bytes + 255) & ~(size_t)255));

@@ -345,6 +345,36 @@ __device__ __forceinline__ void apply_gate(Rows& R, TermRegs& T, int n, uint64_t
     }
 }
 
+// Pauli state Q = i^mu X(u) Z(w) of a (chain, term) pair (Sec. 4.2), entry idx of
+// `pairs` entries.  For n <= 40 it takes 12 bytes: the 64-bit word u | w << 40 in an
+// array of pairs words, followed by an array of 32-bit words (w >> 24) | mu << 16;
+// wider registers (n <= 62) take 16 bytes, (u | mu << 62, w).
+__host__ __device__ constexpr bool q_compact(int n) { return n <= 40; }
+__host__ __device__ constexpr size_t q_bytes(int n) { return q_compact(n) ? 12 : 16; }
+template <bool CQ>
+__device__ __forceinline__ void q_store(void* Q, int64_t pairs, int64_t idx, uint64_t u, uint64_t w, uint32_t mu) {
+    if (CQ) {
+        reinterpret_cast<uint64_t*>(Q)[idx] = u | (w << 40);
+        reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(Q) + pairs)[idx] =
+            (uint32_t)(w >> 24) | ((mu & 3u) << 16);
+    } else {
+        reinterpret_cast<ulonglong2*>(Q)[idx] = make_ulonglong2(u | ((uint64_t)(mu & 3u) << 62), w);
+    }
+}
+// Unpack from the two words (compact) or the 16-byte pair.
+template <bool CQ>
+__device__ __forceinline__ void q_unpack(uint64_t a, uint64_t b, uint64_t& u, uint64_t& w, uint32_t& mu) {
+    if (CQ) {   // a = u | w << 40, b = (w >> 24) | mu << 16
+        u = a & ((1ull << 40) - 1);
+        w = (a >> 40) | ((b & 0xFFFFull) << 24);
+        mu = (uint32_t)(b >> 16) & 3u;
+    } else {
+        u = a & ((1ull << 62) - 1);
+        w = b;
+        mu = (uint32_t)(a >> 62);
+    }
+}
+
 __host__ __device__ __forceinline__ uint32_t omega_pack(uint32_t k, uint32_t zero, uint32_t h) {
     return (k & 7u) | ((zero & 1u) << 3) | (h << 8);
 }

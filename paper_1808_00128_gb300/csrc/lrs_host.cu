@@ -727,7 +727,7 @@ extern "C" lrs_status lrs_chains_init(lrs_ctx* c, int64_t n_chains, const uint64
     if (n_chains < 1 || !x) return lrs_fail(LRS_ERR_ARG, "bad chains");
     if (n_chains > 65535) return lrs_fail(LRS_ERR_ARG, "at most 65535 chains");
     LRS_CUDA(cudaSetDevice(c->device));
-    const size_t qb = (size_t)n_chains * c->cap * sizeof(ulonglong2);
+    const size_t qb = (size_t)n_chains * c->cap * q_bytes(c->n);
     lrs_status rc = lrs_ensure((void**)&c->Q, &c->Q_bytes, qb);
     if (rc != LRS_OK) return rc;
     if (n_chains > c->chains_cap) {

@@ -106,7 +106,7 @@ struct lrs_ctx {
 
     // Metropolis chains
     int64_t n_chains = 0;
-    ulonglong2* Q = nullptr;        // [chain][cap]: (u | mu << 62, w)
+    void* Q = nullptr;              // [chain][cap] Pauli states (q_store layout)
     size_t Q_bytes = 0;
     uint64_t* cx = nullptr;         // [chain] current x
     double* cp = nullptr;           // [chain] P(x) (unnormalised)
@@ -165,7 +165,7 @@ lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_host,
 lrs_status launch_expand_terms(lrs_ctx* ctx, int64_t R, int64_t Rn, cudaStream_t st);
 lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
                             cudaStream_t st);
-lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, ulonglong2* Q, double** amp_out,
+lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, void* Q, double** amp_out,
                               cudaStream_t st);
 lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta,
                                 cudaStream_t st);

@@ -21,17 +21,22 @@ def _sim(n, ops, chi, mode, seed=0):
     return sim
 
 
-@pytest.mark.parametrize("case", ["tiny_exact", "sparse_ragged"])
+@pytest.mark.parametrize("case", ["tiny_exact", "sparse_ragged", "wide_16_byte_states"])
 def test_chain_replay(case):
+    """Chains on 12-byte Pauli states (n <= 40) and on 16-byte ones (n = 44)."""
     require_cuda()
+    C, T, mseed = 70, 25, 1234
     if case == "tiny_exact":
         cfg = workloads.config_tiny()
         n, ops, chi, mode, seed = cfg["n"], cfg["ops"], cfg["chi"], "exact", 0
-    else:
+    elif case == "sparse_ragged":
         n, chi, mode, seed = 12, 600, "sparsify", 3
         ops = workloads.random_clifford_t(n, 220, 10, seed=71)
+    else:
+        n, chi, mode, seed = 44, 32, "exact", 0
+        ops = workloads.random_clifford_t(n, 300, 5, seed=72)
+        C, T = 24, 12
     sim = _sim(n, ops, chi, mode, seed)
-    C, T, mseed = 70, 25, 1234
     x0 = sim.sample_terms(C, seed=8)
     sim.chains_init(x0)
     trace = torch.empty((T, C), dtype=torch.int64, device="cuda:0")
