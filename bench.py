@@ -866,7 +866,7 @@ def main():
     # DRAM bytes per launch from ncu (profiles/): dram__bytes_read.sum + dram__bytes_write.sum
     # of the kernel's capture on this workload (the timed step's launch; one pass); null
     # for kernels changed since their capture.
-    traffic = {"norm_estimate": 27.02e6}   # k_norm DRAM bytes per launch (ncu), re-taken after each change of the kernel
+    traffic = {"norm_estimate": 27.16e6}   # k_norm DRAM bytes per launch (ncu), re-taken after each change of the kernel
     roof["traffic"] = traffic.get(dom) if not args.small else None
     roof.pop("ms", None)
     roof["peak_source"] = ("measured LOP3 probe on this GPU" if roof["bound"] == "alu"
