@@ -46,6 +46,12 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
     __shared__ float2 val8[8];              // b e^{i pi k/4} 2^{-(|v|+h)/2}, k = 0..7
     __shared__ uint64_t sc[4];              // glo, ghi, v, s
     __shared__ uint32_t sc_live;
+    // compact Pauli states of the last QG terms for each of the block's strings, private
+    // to the thread that owns the string: written out as 16-byte vectors every QG terms
+    constexpr bool CQ = QOUT && NCH <= 10;
+    constexpr int QG = 4;
+    __shared__ uint64_t qb8[CQ ? QG : 1][CQ ? AMP_XB : 1];
+    __shared__ uint32_t qb4[CQ ? QG : 1][CQ ? AMP_XB : 1];
     const int n = T.n;
     const int tid = threadIdx.x;
     const int64_t tile = blockIdx.x;
@@ -155,13 +161,34 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
                 zpar = par64(z);
             }
             const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)zpar;
-            if (QOUT) {
+            if (CQ) {
+                const int g = (int)((a - a0) & (QG - 1));
+                qb8[g][tid + k * AMP_XT] = u | (w << 40);
+                qb4[g][tid + k * AMP_XT] = (uint32_t)(w >> 24) | ((uint32_t)(mu & 3) << 16);
+            } else if (QOUT) {
                 const int64_t i = xb + tid + k * AMP_XT;
-                if (i < batch) q_store<(NCH <= 10)>(Qout, batch * T.cap, i * T.cap + a, u, w, (uint32_t)mu);
+                if (i < batch) q_store<false>(Qout, batch * T.cap, i * T.cap + a, u, w, (uint32_t)mu);
             }
             if (live && ((u ^ s) & nv) == 0) {
                 const int sign = (int)par64(u & (w ^ sv));
                 acc[k].add(val8[(2 * mu + 4 * sign) & 7]);
+            }
+        }
+        if (CQ && ((a - a0) & (QG - 1)) == QG - 1) {
+            // terms a-3 .. a of each of the thread's strings: 32 bytes of u | w << 40 and
+            // 16 bytes of (w >> 24) | mu << 16, contiguous and 16-byte aligned (a0 and
+            // the tile length are multiples of QG, cap of 256)
+            uint64_t* q8 = reinterpret_cast<uint64_t*>(Qout);
+            uint32_t* q4 = reinterpret_cast<uint32_t*>(q8 + batch * T.cap);
+#pragma unroll
+            for (int k = 0; k < AMP_XP; ++k) {
+                const int sl = tid + k * AMP_XT;
+                const int64_t i = xb + sl;
+                if (i >= batch) continue;
+                const int64_t e = i * T.cap + a - (QG - 1);
+                reinterpret_cast<ulonglong2*>(q8 + e)[0] = make_ulonglong2(qb8[0][sl], qb8[1][sl]);
+                reinterpret_cast<ulonglong2*>(q8 + e)[1] = make_ulonglong2(qb8[2][sl], qb8[3][sl]);
+                *reinterpret_cast<uint4*>(q4 + e) = make_uint4(qb4[0][sl], qb4[1][sl], qb4[2][sl], qb4[3][sl]);
             }
         }
     }
@@ -213,7 +240,7 @@ AmpPlan amp_plan(const lrs_ctx* ctx, int64_t batch) {
     const int64_t maxt = (ctx->cap + 31) / 32;
     if (nt > maxt) nt = maxt;
     if (nt < 1) nt = 1;
-    P.tt = (ctx->cap + nt - 1) / nt;
+    P.tt = ((ctx->cap + nt - 1) / nt + 7) & ~(int64_t)7;   // tiles start at multiples of 8 terms
     P.n_tiles = (ctx->cap + P.tt - 1) / P.tt;
     return P;
 }
