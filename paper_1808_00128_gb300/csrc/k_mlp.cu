@@ -13,6 +13,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "lrs_device.cuh"
 
 typedef __nv_bfloat16 bf16;
@@ -370,6 +372,194 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TN) : "memory");
 }
 
+// Persistent variant for products with several k-steps.  A grid of at most one CTA
+// per SM slot walks the output tiles (tile t, t + gridDim.x, ...); 192 threads:
+//   warp 0, lane 0   TMA producer for every tile; k-steps are counted across tiles, so
+//                    the ring of ST stages runs on from one tile into the next
+//   warp 1, lane 0   MMA issuer; tile j accumulates into tensor-memory buffer j & 1
+//                    (2 TN columns in all) and commits to accf[j & 1]
+//   warps 2-5        epilogue: wait accf[b], read the 32 lanes of their quadrant
+//                    (warp & 3), run the fused epilogue, release the buffer (acce[b])
+// so a tile's epilogue overlaps the next tile's loads and MMAs.  Every wait is bounded
+// (1 s); a wait that gives up stops all roles, the MMAs and copies in flight are waited
+// for, and *err is set.
+template <int TN, int ST, bool MN, class Epi>
+__global__ void __launch_bounds__(192, 1) k_gemm_tcp(const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+                                                     Epi epi, int* err) {
+    using S = TcShape<TN, ST>;
+    extern __shared__ uint8_t tc_dyn[];
+    __shared__ __align__(8) uint64_t full[ST], empty[ST], accf[2], acce[2], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag, s_issued, s_consumed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_n = N / TN;
+    const int tiles = tiles_n * ((M + TC_M - 1) / TC_M);
+    const int nk = K / TC_BK;
+    const uint32_t sbase = (smem_u32(tc_dyn) + 1023u) & ~1023u;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "n"(2 * TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int i = 0; i < ST; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[i])) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&accf[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(&acce[b])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        abort_flag = 0;
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int g = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            const int m0 = (t / tiles_n) * TC_M, n0 = (t % tiles_n) * TN;
+            bool ok = true;
+            for (int kt = 0; kt < nk; ++kt, ++g) {
+                const int s = g % ST;
+                if (g >= ST && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((g / ST) - 1) & 1u)) {
+                    atomicExch(&abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                if (*(volatile int*)&abort_flag) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t fb = smem_u32(&full[s]);
+                const uint32_t sa = sbase + (uint32_t)(s * S::STAGE), sb = sa + (uint32_t)S::A_BYTES;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(S::STAGE)
+                             : "memory");
+                if constexpr (!MN) {
+                    tma_load_2d(sa, &tmA, kt * TC_BK, m0, fb);
+                    tma_load_2d(sb, &tmB, kt * TC_BK, n0, fb);
+                } else {
+#pragma unroll
+                    for (int h = 0; h < TC_M / 64; ++h) tma_load_2d(sa + h * 8192, &tmA, m0 + 64 * h, kt * TC_BK, fb);
+#pragma unroll
+                    for (int jj = 0; jj < TN / 64; ++jj) tma_load_2d(sb + jj * 8192, &tmB, n0 + 64 * jj, kt * TC_BK, fb);
+                }
+                s_issued = g + 1;
+            }
+            if (!ok) break;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = tc_idesc(TC_M, TN, MN);
+        int g = 0, j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            const int b = j & 1;
+            if (j >= 2 && !mbar_wait(smem_u32(&acce[b]), (uint32_t)((j >> 1) - 1) & 1u)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)(b * TN);
+            bool ok = true;
+            for (int kt = 0; kt < nk; ++kt, ++g) {
+                const int s = g % ST;
+                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(g / ST) & 1u)) {
+                    atomicExch(&abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t sa = sbase + (uint32_t)(s * S::STAGE), sb = sa + (uint32_t)S::A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    const uint64_t da = MN ? tc_desc_mn_sw128(sa + kk * 2048) : tc_desc_sw128(sa + kk * 32);
+                    const uint64_t db = MN ? tc_desc_mn_sw128(sb + kk * 2048) : tc_desc_sw128(sb + kk * 32);
+                    const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                        "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&empty[s]))
+                             : "memory");
+                s_consumed = g + 1;
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&accf[b]))
+                         : "memory");
+        }
+        // arrives once every MMA issued above has completed (also after an abort)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
+    } else if (warp >= 2) {
+        // epilogue: lanes 32 q .. 32 q + 31 of the accumulator
+        const int q = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            const int b = j & 1;
+            const bool ok = mbar_wait(smem_u32(&accf[b]), (uint32_t)(j >> 1) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int m0 = (t / tiles_n) * TC_M, n0 = (t % tiles_n) * TN;
+            const int row = m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < TN; c0 += 16) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TN + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (row < M) {
+                    float v[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+                    epi.row16(row, n0 + c0, v);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&acce[b])) : "memory");
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    // every MMA issued has completed before the accumulators are freed
+    const bool mma_done = mbar_wait(smem_u32(&done), 0u);
+    if (tid == 0 && (*(volatile int*)&abort_flag || !mma_done)) {
+        atomicExch(err, 1);
+        // let the producer's copies that no MMA waited for land before the CTA exits
+        for (int g = s_consumed; g < s_issued; ++g)
+            if (!mbar_wait(smem_u32(&full[g % ST]), (uint32_t)(g / ST) & 1u)) break;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(2 * TN) : "memory");
+}
+
 // Host side: cuTensorMapEncodeTiled through the runtime's driver entry point.
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -425,6 +615,34 @@ lrs_status launch_gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M,
     return LRS_OK;
 }
 
+// Persistent launch: grid = resident CTAs (at most one per tile).
+template <int TN, int ST, bool MN, class Epi>
+lrs_status launch_gemm_tcp(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, Epi epi, int* err,
+                           cudaStream_t st) {
+    CUtensorMap ta, tb;
+    lrs_status rc;
+    if (!MN) {
+        if ((rc = tmap_2d(&ta, A, M, K, lda, TC_M)) != LRS_OK) return rc;
+        if ((rc = tmap_2d(&tb, B, N, K, ldb, TN)) != LRS_OK) return rc;
+    } else {
+        if ((rc = tmap_2d(&ta, A, K, M, lda, 64)) != LRS_OK) return rc;
+        if ((rc = tmap_2d(&tb, B, K, N, ldb, 64)) != LRS_OK) return rc;
+    }
+    constexpr int smem = TcShape<TN, ST>::SMEM;
+    LRS_CUDA(cudaFuncSetAttribute(k_gemm_tcp<TN, ST, MN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    LRS_CUDA(cudaGetDevice(&dev));
+    LRS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LRS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm_tcp<TN, ST, MN, Epi>, 192, smem));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm * 2 * TN > 512) per_sm = 512 / (2 * TN);   // tensor memory: 512 columns per SM
+    const int tiles = (N / TN) * ((M + TC_M - 1) / TC_M);
+    const int grid = std::min(tiles, sms * per_sm);
+    k_gemm_tcp<TN, ST, MN, Epi><<<grid, 192, smem, st>>>(ta, tb, M, N, K, epi, err);
+    LRS_LAUNCH_CHECK("persistent tcgen05 gemm");
+    return LRS_OK;
+}
+
 // Tile width for an M x N output: the widest of 256, 128, 64 that divides N and still
 // gives every SM a tile; a single k-step takes a one-stage ring.
 template <bool MN, class Epi>
@@ -439,9 +657,9 @@ lrs_status gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M, int N,
         if (N % 128 == 0) return launch_gemm_tc<128, 1, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
         return launch_gemm_tc<64, 1, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
     }
-    if (N % 256 == 0 && mt * (N / 256) >= 148) return launch_gemm_tc<256, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
-    if (N % 128 == 0 && mt * (N / 128) >= 148) return launch_gemm_tc<128, 3, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
-    return launch_gemm_tc<64, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
+    if (N % 256 == 0 && mt * (N / 256) >= 148) return launch_gemm_tcp<256, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
+    if (N % 128 == 0 && mt * (N / 128) >= 148) return launch_gemm_tcp<128, 3, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
+    return launch_gemm_tcp<64, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
 }
 
 // ---- epilogues ------------------------------------------------------------------------
