@@ -149,3 +149,25 @@ def test_full_size_chains_match_amplitudes():
     np.testing.assert_allclose(po.cpu().numpy(), pf, rtol=1e-5, atol=1e-12 * pf.max())
     assert close < C * T // 50
     sim.close()
+
+
+def test_hidden_shift_chains_stay_at_the_shift():
+    """The n=40 hidden shift with its exact 2^16-term decomposition and 1024 chains (the
+    chain count of that workload) started at the shift s: |<x|psi>|^2 is 1 at s and 0
+    elsewhere, so every proposal is rejected, and the chains keep x = s, P(s) = 1."""
+    require_cuda()
+    cfg = workloads.config_hidden_shift()
+    n, ops, chi, s = cfg["n"], cfg["ops"], cfg["chi"], cfg["shift"]
+    C = cfg["chains"]
+    assert C == 1024
+    sim = _sim(n, ops, chi, "exact")
+    x0 = torch.full((C,), np.int64(np.uint64(s).view(np.int64)), dtype=torch.int64, device="cuda:0")
+    sim.chains_init(x0)
+    xo = torch.empty(C, dtype=torch.int64, device="cuda:0")
+    po = torch.empty(C, dtype=torch.float64, device="cuda:0")
+    sim.metropolis(32, seed=4, x_out=xo, p_out=po)
+    xo = xo.cpu().numpy().view(np.uint64)
+    po = po.cpu().numpy()
+    assert np.all(xo == np.uint64(s))
+    assert np.all(np.abs(po - 1.0) <= 1e-5)
+    sim.close()
