@@ -161,7 +161,7 @@ def test_hidden_shift_chains_stay_at_the_shift():
     C = cfg["chains"]
     assert C == 1024
     sim = _sim(n, ops, chi, "exact")
-    x0 = torch.full((C,), np.int64(np.uint64(s).view(np.int64)), dtype=torch.int64, device="cuda:0")
+    x0 = torch.full((C,), int(s), dtype=torch.int64, device="cuda:0")   # s < 2^40
     sim.chains_init(x0)
     xo = torch.empty(C, dtype=torch.int64, device="cuda:0")
     po = torch.empty(C, dtype=torch.float64, device="cuda:0")
