@@ -386,16 +386,18 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
 template <int TN, int ST, bool MN, class Epi>
 __global__ void __launch_bounds__(192, 1) k_gemm_tcp(const __grid_constant__ CUtensorMap tmA,
                                                      const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-                                                     Epi epi, int* err) {
+                                                     int ksplit, Epi epi, int* err) {
     using S = TcShape<TN, ST>;
     extern __shared__ uint8_t tc_dyn[];
     __shared__ __align__(8) uint64_t full[ST], empty[ST], accf[2], acce[2], done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag, s_issued, s_consumed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // work unit u: output tile u % tiles, k-steps [kc (u / tiles), kc (u / tiles + 1))
     const int tiles_n = N / TN;
     const int tiles = tiles_n * ((M + TC_M - 1) / TC_M);
-    const int nk = K / TC_BK;
+    const int units = tiles * ksplit;
+    const int nk = K / TC_BK / ksplit;
     const uint32_t sbase = (smem_u32(tc_dyn) + 1023u) & ~1023u;
 
     if (warp == 0) {
@@ -427,10 +429,11 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tcp(const __grid_constant__ CUt
     if (warp == 0 && lane == 0) {
         // TMA producer
         int g = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        for (int u = blockIdx.x; u < units; u += gridDim.x) {
+            const int t = u % tiles, k0 = (u / tiles) * nk;
             const int m0 = (t / tiles_n) * TC_M, n0 = (t % tiles_n) * TN;
             bool ok = true;
-            for (int kt = 0; kt < nk; ++kt, ++g) {
+            for (int kt = k0; kt < k0 + nk; ++kt, ++g) {
                 const int s = g % ST;
                 if (g >= ST && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((g / ST) - 1) & 1u)) {
                     atomicExch(&abort_flag, 1);
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tcp(const __grid_constant__ CUt
         // MMA issuer
         constexpr uint32_t idesc = tc_idesc(TC_M, TN, MN);
         int g = 0, j = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++j) {
             const int b = j & 1;
             if (j >= 2 && !mbar_wait(smem_u32(&acce[b]), (uint32_t)((j >> 1) - 1) & 1u)) {
                 atomicExch(&abort_flag, 1);
@@ -509,7 +512,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tcp(const __grid_constant__ CUt
         // epilogue: lanes 32 q .. 32 q + 31 of the accumulator
         const int q = warp & 3;
         int j = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++j) {
+            const int t = u % tiles;
             const int b = j & 1;
             const bool ok = mbar_wait(smem_u32(&accf[b]), (uint32_t)(j >> 1) & 1u);
             if (!__all_sync(0xffffffffu, ok)) {
@@ -618,7 +622,7 @@ lrs_status launch_gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M,
 // Persistent launch: grid = resident CTAs (at most one per tile).
 template <int TN, int ST, bool MN, class Epi>
 lrs_status launch_gemm_tcp(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, Epi epi, int* err,
-                           cudaStream_t st) {
+                           cudaStream_t st, int ksplit = 1) {
     CUtensorMap ta, tb;
     lrs_status rc;
     if (!MN) {
@@ -636,9 +640,9 @@ lrs_status launch_gemm_tcp(const bf16* A, int lda, const bf16* B, int ldb, int M
     LRS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm_tcp<TN, ST, MN, Epi>, 192, smem));
     if (per_sm < 1) per_sm = 1;
     if (per_sm * 2 * TN > 512) per_sm = 512 / (2 * TN);   // tensor memory: 512 columns per SM
-    const int tiles = (N / TN) * ((M + TC_M - 1) / TC_M);
-    const int grid = std::min(tiles, sms * per_sm);
-    k_gemm_tcp<TN, ST, MN, Epi><<<grid, 192, smem, st>>>(ta, tb, M, N, K, epi, err);
+    const int units = (N / TN) * ((M + TC_M - 1) / TC_M) * ksplit;
+    const int grid = std::min(units, sms * per_sm);
+    k_gemm_tcp<TN, ST, MN, Epi><<<grid, 192, smem, st>>>(ta, tb, M, N, K, ksplit, epi, err);
     LRS_LAUNCH_CHECK("persistent tcgen05 gemm");
     return LRS_OK;
 }
@@ -660,6 +664,27 @@ lrs_status gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int M, int N,
     if (N % 256 == 0 && mt * (N / 256) >= 148) return launch_gemm_tcp<256, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
     if (N % 128 == 0 && mt * (N / 128) >= 148) return launch_gemm_tcp<128, 3, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
     return launch_gemm_tcp<64, 4, MN>(A, lda, B, ldb, M, N, K, epi, err, st);
+}
+
+// Weight gradients: C[M x N] = A . B^T with K = the batch (MN-major operands), few
+// output tiles and many k-steps.  The k-steps are split over up to 16 chunks so that
+// up to four work units per SM exist; the chunks' partial products are added into
+// the output, which is zeroed first.  Uses the persistent kernel.
+template <class EpiAdd>
+lrs_status gemm_tc_splitk(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, float* out, int ldo,
+                          int* err, cudaStream_t st) {
+    if (K % TC_BK != 0 || N % 64 != 0 || M % 64 != 0)
+        return lrs_fail(LRS_ERR_ARG, "gemm: M=%d, N=%d, K=%d not multiples of 64", M, N, K);
+    LRS_CUDA(cudaMemsetAsync(out, 0, (size_t)M * ldo * sizeof(float), st));
+    const int64_t mt = (M + TC_M - 1) / TC_M;
+    const int tn = (N % 128 == 0 && mt * (N / 128) >= 64) ? 128 : 64;
+    const int tiles = (int)(mt * (N / tn));
+    const int nk = K / TC_BK;
+    int ks = 1;
+    while (ks < 16 && tiles * ks * 2 <= 4 * 152 && nk % (ks * 2) == 0 && nk / (ks * 2) >= 4) ks *= 2;
+    const EpiAdd e{out, ldo};
+    if (tn == 128) return launch_gemm_tcp<128, 3, true>(A, lda, B, ldb, M, N, K, e, err, st, ks);
+    return launch_gemm_tcp<64, 4, true>(A, lda, B, ldb, M, N, K, e, err, st, ks);
 }
 
 // ---- epilogues ------------------------------------------------------------------------
@@ -739,6 +764,16 @@ struct EpiReluGrad {         // dZ = acc * [H > 0]; FP32 and BF16 copies
         uint4* o16 = reinterpret_cast<uint4*>(out16 + (size_t)r * ldo + c0);
         o16[0] = make_uint4(p[0], p[1], p[2], p[3]);
         o16[1] = make_uint4(p[4], p[5], p[6], p[7]);
+    }
+};
+struct EpiAddF32 {           // out += acc (split-K partial products into a zeroed output)
+    float* out;
+    int ldo;
+    __device__ __forceinline__ void operator()(int r, int c, float v) const { atomicAdd(out + (size_t)r * ldo + c, v); }
+    __device__ __forceinline__ void row16(int r, int c0, const float (&v)[16]) const {
+        float* o = out + (size_t)r * ldo + c0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) atomicAdd(o + q, v[q]);
     }
 };
 struct EpiStoreF32 {
@@ -1050,7 +1085,8 @@ lrs_status mlp_backward(lrs_mlp* m, const uint64_t* xs, int M, const MlpWS& w, f
     // weight gradient D^T Hin (D [Mp][Mo], Hin [Mp][No]): the tcgen05 kernel reads both
     // operands MN-major straight from the activations; mma.sync goes through transposes
     auto dW = [&](const bf16* D, int Mo, const bf16* Hin, int No, EpiStoreF32 e) -> lrs_status {
-        if (m->gemm == LRS_MLP_GEMM_TCGEN05) return gemm_tc<true>(D, Mo, Hin, No, Mo, No, Mp, e, m->err, st);
+        if (m->gemm == LRS_MLP_GEMM_TCGEN05)
+            return gemm_tc_splitk<EpiAddF32>(D, Mo, Hin, No, Mo, No, Mp, e.out, e.ldo, m->err, st);
         transpose(D, Mp, Mo, w.T1, st);
         transpose(Hin, Mp, No, w.T2, st);
         return gemm_tn(m, w.T1, Mp, w.T2, Mp, Mo, No, Mp, e, st);
