@@ -270,8 +270,9 @@ lrs_status lrs_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint64_t
 
 /* ---- Metropolis (Sec. 4.2) ------------------------------------------------------ */
 /* Start n_chains chains at x_dev[c]: computes Q_x for every (chain, term) and
- * P(x) = |<x|psi>|^2.  Needs n <= 62 (Q is packed in 16 bytes).  Storage is
- * n_chains * chi * 16 bytes, owned by the context.
+ * P(x) = |<x|psi>|^2.  Needs n <= 62 (Q = i^mu X(u) Z(w) is packed in 12 bytes for
+ * n <= 40, 16 bytes above).  Storage is n_chains * chi_padded * 12 (or 16) bytes,
+ * owned by the context.
  * Errors: LRS_ERR_ARG, LRS_ERR_STATE, LRS_ERR_UNSUPPORTED (n > 62), LRS_ERR_OOM. */
 lrs_status lrs_chains_init(lrs_ctx* ctx, int64_t n_chains, const uint64_t* x_dev, void* stream);
 
@@ -280,8 +281,10 @@ lrs_status lrs_chains_init(lrs_ctx* ctx, int64_t n_chains, const uint64_t* x_dev
  * 2t)) * n) >> 32 and accepts if P(y) >= P(x), else iff
  * uniform(seed, c, 2t+1) < P(y)/P(x) (FP64).  Optional outputs (device, may
  * be NULL): x_out_dev[c] and p_out_dev[c] after the last step, trace_dev
- * [t * n_chains + c] = x after step t.
- * Errors: LRS_ERR_ARG (steps < 0), LRS_ERR_STATE (chains not initialised).  */
+ * [t * n_chains + c] = x after step t.  Runs asynchronously on `stream`.
+ * Errors: LRS_ERR_ARG (steps < 0), LRS_ERR_STATE (chains not initialised),
+ * LRS_ERR_TIMEOUT (an earlier call's propose kernel gave up waiting, after 1 s, for
+ * the copies of its inputs into shared memory; that call's results are invalid).  */
 lrs_status lrs_metropolis_step(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t step0,
                                uint64_t* x_out_dev, double* p_out_dev, uint64_t* trace_dev,
                                void* stream);
