@@ -61,21 +61,23 @@ def _save(path, cache):
 
 
 def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_path: str | None = None,
-         reps: int = 5, flush_l2: int = 256 << 20) -> dict:
+         reps: int = 5, flush_l2: int = 256 << 20, timer=None) -> dict:
     """Pick the fastest knob values for the given workload and set them on `sim`.
 
     x: amplitude batch (CUDA int64 tensor); L: number of equatorial states for
     norm estimation; chains: the chain count (chains must already be
     initialised on `sim`); flush_l2: bytes of a buffer rewritten before every timed
-    call (0: time with a warm L2).  Returns {knob: (value, ms)}.
+    call (0: time with a warm L2); timer: replaces the CUDA-event timing, a function
+    of the job's callable returning milliseconds.  Returns {knob: (value, ms)}.
     """
     import torch
     cache = _load(cache_path)
     chosen = {}
     jobs = []
     flush = None
-    if flush_l2:
+    if flush_l2 and timer is None:
         flush = torch.empty(flush_l2 // 4, dtype=torch.float32, device=f"cuda:{sim.device}")
+    time_fn = timer if timer is not None else (lambda fn: _time_ms(fn, reps, flush))
     if x is not None:
         out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
         jobs.append(("amp_blocks_per_sm", x.numel(), lambda: sim.amplitude(x, out=out)))
@@ -99,7 +101,7 @@ def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_pat
         best = None
         for v in order:
             sim.set_tuning(knob, v)
-            ms = _time_ms(fn, reps, flush)
+            ms = time_fn(fn)
             if best is None or ms < best[1] * (1.0 - MARGIN):
                 best = (v, ms)
         sim.set_tuning(knob, best[0])
