@@ -236,9 +236,10 @@ lrs_status lrs_amplitude(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch, dou
  * a fixed 16 MiB array in the library's device memory (2^21 float2 entries),
  * present on every GPU that loads the library until the process exits.
  * Limit: batch * n_tiles <= 2^21 partial sums, where n_tiles, the number of
- * term tiles the kernel uses, is min(ceil(b * SMs / ceil(batch / 512)),
- * ceil(chi_padded / 32)) with b = LRS_TUNE_AMP_BLOCKS_PER_SM (default 8: 152
- * tiles for batch 4096 on a 152-SM GPU); larger requests return LRS_ERR_ARG.
+ * term tiles the kernel uses, is at most min(ceil(b * SMs / ceil(batch / 1024)),
+ * ceil(chi_padded / 32)) with b = LRS_TUNE_AMP_BLOCKS_PER_SM (default 8: 304
+ * tiles for batch 4096 on a 152-SM GPU; tiles are whole multiples of 8 terms);
+ * larger requests return LRS_ERR_ARG.
  * Any batch above 2^21 is rejected.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

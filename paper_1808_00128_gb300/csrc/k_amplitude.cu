@@ -16,8 +16,11 @@
 namespace {
 
 constexpr int AMP_XT = 128;   // threads per block
-constexpr int AMP_XP = 4;     // strings per thread (independent chains for ILP)
-constexpr int AMP_XB = AMP_XT * AMP_XP;
+// strings per thread (independent chains for ILP): eight for the plain batch (each
+// term's tables and barrier serve 1024 strings), four for the chain start (its
+// per-string state buffers)
+__host__ __device__ constexpr int amp_xp(bool qout) { return qout ? 4 : 8; }
+__host__ __device__ constexpr int amp_xb(bool qout) { return AMP_XT * amp_xp(qout); }
 
 struct AmpEntry {
     uint64_t u, w, z;
@@ -31,10 +34,10 @@ struct AmpEntry {
 // and the lookups XOR-accumulate w & u_q (one popcount per string at the end): two
 // 8-byte tables (u_q, w_q) instead of three, each a conflict-free 128-byte row per
 // chunk.
-// Register budget: eight blocks per SM (64 registers) for the plain amplitude batch,
-// six for the variant that also writes the Pauli states (it spills at 64).  More
-// resident warps hide the shared-table lookups and the per-term barriers.
-constexpr int amp_min_blocks(bool qout) { return qout ? 6 : 8; }
+// Register budget: five blocks per SM (96 registers, eight strings per thread) for the
+// plain amplitude batch, six (80 registers, four strings) for the variant that also
+// writes the Pauli states.
+constexpr int amp_min_blocks(bool qout) { return qout ? 6 : 5; }
 template <int NCH, bool QOUT, bool PK>
 __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
                                                       int64_t batch, int64_t tt,
@@ -48,6 +51,7 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
     __shared__ uint32_t sc_live;
     // compact Pauli states of the last QG terms for each of the block's strings, private
     // to the thread that owns the string: written out as 16-byte vectors every QG terms
+    constexpr int AMP_XP = amp_xp(QOUT), AMP_XB = amp_xb(QOUT);
     constexpr bool CQ = QOUT && NCH <= 10;
     constexpr int QG = 4;
     __shared__ uint64_t qb8[CQ ? QG : 1][CQ ? AMP_XB : 1];
@@ -232,9 +236,9 @@ struct AmpPlan {
 };
 
 // Term tiles so that the grid covers every SM several times.
-AmpPlan amp_plan(const lrs_ctx* ctx, int64_t batch) {
+AmpPlan amp_plan(const lrs_ctx* ctx, int64_t batch, bool qout) {
     AmpPlan P;
-    P.xblocks = (batch + AMP_XB - 1) / AMP_XB;
+    P.xblocks = (batch + amp_xb(qout) - 1) / amp_xb(qout);
     const int64_t target = (int64_t)ctx->sm_count * ctx->tune_amp_bps;
     int64_t nt = (target + P.xblocks - 1) / P.xblocks;
     const int64_t maxt = (ctx->cap + 31) / 32;
@@ -296,7 +300,7 @@ lrs_status launch_amp_kernels(lrs_ctx* ctx, const uint64_t* x, int64_t batch, do
 // state Q[i * cap + alpha] of every (x_i, term): the chain start of Sec. 4.2.
 lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, void* Q, double** amp_out,
                               cudaStream_t st) {
-    const AmpPlan P = amp_plan(ctx, batch);
+    const AmpPlan P = amp_plan(ctx, batch, true);
     const size_t part = ((size_t)batch * P.n_tiles * sizeof(float2) + 255) & ~(size_t)255;
     void* scr = nullptr;
     lrs_status rc = lrs_scratch(ctx, part + (size_t)batch * 2 * sizeof(double), &scr);
@@ -308,7 +312,7 @@ lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, vo
 lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
                             cudaStream_t st) {
     if (batch == 0) return LRS_OK;
-    const AmpPlan P = amp_plan(ctx, batch);
+    const AmpPlan P = amp_plan(ctx, batch, false);
     void* scr = nullptr;
     lrs_status rc = lrs_scratch(ctx, (size_t)batch * P.n_tiles * sizeof(float2), &scr);
     if (rc != LRS_OK) return rc;
@@ -360,7 +364,7 @@ extern "C" lrs_status lrs_amplitude_noalloc(lrs_ctx* ctx, const uint64_t* x, int
     lrs_status rc = noalloc_address(ctx->device, &partial);   // first call on a device: set-up
     if (rc != LRS_OK) return rc;
     if (batch == 0) return LRS_OK;
-    const AmpPlan P = amp_plan(ctx, batch);
+    const AmpPlan P = amp_plan(ctx, batch, false);
     if ((uint64_t)batch * (uint64_t)P.n_tiles > (uint64_t)LRS_NOALLOC_PARTIALS)
         return lrs_fail(LRS_ERR_ARG,
                         "lrs_amplitude_noalloc: %lld partial sums (batch x term tiles) exceed the "
