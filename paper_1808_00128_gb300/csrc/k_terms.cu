@@ -70,8 +70,9 @@ __global__ void k_init_terms(TermsView T, int32_t mode, uint64_t seed, double sc
 // n <= 48 a row is kept as its low 32 bits plus its next HB bits (0, 8 or 16; bits at
 // or above n are zero in every row): a 40-qubit tableau takes 15n bytes per term
 // instead of 24n, so five 64-term blocks fit on an SM instead of three.  Wider
-// tableaux keep each row as one 64-bit word (HB = 64): at n = 50 the single 64-bit
-// access per row beats the extra block per SM that 16 + 8-bit high words would give.
+// tableaux keep each row as one 64-bit word (HB = 64): at n = 50 one 64-bit access
+// per row beats a 16 + 8-bit split of the high word (three accesses per row for the
+// same three blocks per SM).
 // The Hadamard row pass reads F and G through per-term pointers; the narrow high rows
 // of G and M are padded so that a warp reading row p of F for some terms and of G for
 // others hits other banks.
