@@ -221,8 +221,9 @@ lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_gate* const*
 
 /* out_dev[2i], out_dev[2i+1] = Re, Im of <x_i|psi> = sum_alpha b_alpha
  * <x_i|phi_alpha> for i < batch (Eq. (amplitude1) per term).  Per-term values
- * are exact Z8 phases times powers of sqrt2 times b_alpha; the chi-sum is
- * accumulated in FP32 (pairwise within a block), then in FP64 across blocks.
+ * are exact Z8 phases times powers of sqrt2 times b_alpha; the chi-sum is a
+ * per-thread compensated (Kahan) FP32 sum over a tile of terms, then an FP64
+ * tree sum across tiles.
  * x_dev: batch uint64 basis strings.  batch = 0 is a no-op.
  * Errors: LRS_ERR_ARG (batch < 0, NULL pointers), LRS_ERR_STATE.            */
 lrs_status lrs_amplitude(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch, double* out_dev,

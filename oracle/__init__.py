@@ -18,6 +18,11 @@ Modules
             (Sec. 3.3.2, Lemma 6 "Sparsification")
   estimators  amplitudes, equatorial inner products, norm estimation
             (Sec. 4.3) and Metropolis chains (Sec. 4.2)
+  exact     exact chi-sums in Z[zeta8] (integer coordinates, one final
+            conversion): the pin against which FP64 and FP32 sums state their
+            error per result
+  marginals median of means and chain-rule marginal sampling (end of Sec. 4.3)
+  mlp       the learned proposal's MADE network (not in the paper)
 
 Parity pins live in tests/ (dense brute force, closed forms, invariants).
 Functions without such a pin say "parity unpinned" in their docstring.

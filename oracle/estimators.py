@@ -67,6 +67,14 @@ def inner_equatorial(ch: CHForm, A: np.ndarray) -> complex:
     """<phi|phi_A> for the omega = 1 part of `ch` (Lemma (Inner Product),
     Eq. (inner_explicit)), with Z(B) from Lemma (Exponential Sum)."""
     n = ch.n
+    sKs, sv, nvars, re, im = inner_equatorial_parts(ch, A)
+    return (2.0 ** (-(n + nvars) / 2)) * (1j ** sKs) * ((-1) ** sv) * complex(re, im)
+
+
+def inner_equatorial_parts(ch: CHForm, A: np.ndarray):
+    """The exact ingredients of <phi|phi_A> = 2^{-(n+|v|)/2} i^{sKs} (-1)^{s.v} Z(B)
+    (Lemma (Inner Product)): (sKs mod 4, s.v mod 2, |v|, Re Z(B), Im Z(B))."""
+    n = ch.n
     G, F, M = _mat(ch.G, n), _mat(ch.F, n), _mat(ch.M, n)
     # J in M_n: diag(J) = gamma, J_ab = (M F^T)_ab mod 2 for a != b
     J = (M @ F.T) % 2
@@ -82,7 +90,7 @@ def inner_equatorial(ch: CHForm, A: np.ndarray) -> complex:
     B = [[int(Bfull[a, b]) % (4 if a == b else 2) for b in idx] for a in idx]
     re, im = expsum(B)
     sv = int(s @ v) % 2
-    return (2.0 ** (-(n + len(idx)) / 2)) * (1j ** sKs) * ((-1) ** sv) * complex(re, im)
+    return sKs, sv, len(idx), re, im
 
 
 def overlap_A(terms, coefs, A: np.ndarray) -> complex:

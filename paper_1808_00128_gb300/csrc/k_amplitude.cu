@@ -11,6 +11,8 @@
 // One thread owns XP strings x and walks the block's tile of terms, so its
 // chi-sum is a private FP32 Kahan sum (no cross-thread reduction); the tile
 // partials are summed in FP64 by k_amp_reduce.
+#include <atomic>
+
 #include "lrs_device.cuh"
 
 namespace {
@@ -336,20 +338,20 @@ static __device__ __align__(256) float2 g_noalloc_partials[LRS_NOALLOC_PARTIALS]
 
 // Device address of g_noalloc_partials, looked up once per device.  In host
 // code the symbol name is only a host-side stand-in, so it is never passed to a
-// kernel directly.
-static void* g_noalloc_addr[128];
-static bool g_noalloc_ready[128];
+// kernel directly.  The address is published through an atomic, so first calls
+// racing from several host threads each look it up (same value) without a data
+// race; a failed lookup publishes nothing and the next call tries again.
+static std::atomic<void*> g_noalloc_addr[128];
 
 static lrs_status noalloc_address(int device, float2** out) {
     if (device < 0 || device >= 128) return lrs_fail(LRS_ERR_UNSUPPORTED, "device index %d", device);
-    if (!g_noalloc_ready[device]) {
-        void* p = nullptr;
+    void* p = g_noalloc_addr[device].load(std::memory_order_acquire);
+    if (!p) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess) return lrs_cuda_check(e, "cudaGetSymbolAddress(g_noalloc_partials)");
-        g_noalloc_addr[device] = p;
-        g_noalloc_ready[device] = true;
+        g_noalloc_addr[device].store(p, std::memory_order_release);
     }
-    *out = (float2*)g_noalloc_addr[device];
+    *out = (float2*)p;
     return LRS_OK;
 }
 

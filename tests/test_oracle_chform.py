@@ -117,3 +117,27 @@ def test_sampling_support_and_uniformity():
         assert set(seen) == support
         assert len(set(seen.values())) == 1
         assert len(support) == 1 << popcount(ch.v)
+
+
+@pytest.mark.parametrize("n", [10, 11, 12])
+def test_chform_matches_dense_up_to_12_qubits(n):
+    """The same brute-force pin at n = 10..12 (all 2^n amplitudes), with a check after
+    every gate on one circuit at n = 10."""
+    rng = random.Random(100 + n)
+    for trial in range(3):
+        ops = rand_clifford(n, 80, rng, proj=False)
+        q = rng.randrange(n)
+        # a projector that keeps part of the state (one of P0, P1 always does)
+        proj = "P0" if np.abs(dense.run(n, ops + [("P0", q)])).max() > 0 else "P1"
+        ops += [(proj, q), ("H", rng.randrange(n))]
+        ch = run_gates(n, ops)
+        psi = dense.run(n, ops)
+        assert np.abs(psi).max() > 0
+        np.testing.assert_allclose(_all_amps(ch, n), psi, atol=1e-12)
+    if n == 10:
+        ch = CHForm(n)
+        psi = dense.zero_state(n)
+        for g in rand_clifford(n, 40, rng, proj=True):
+            run_gates(n, [g], ch)
+            psi = dense.apply_gate(psi, n, g)
+            np.testing.assert_allclose(_all_amps(ch, n), psi, atol=1e-12, err_msg=str(g))
