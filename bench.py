@@ -1,20 +1,23 @@
 #!/usr/bin/env python
 """Benchmark of the low-rank stabilizer-decomposition hot path on GB300.
 
-One step = one pass of the whole path over one batch of the n=40 workload
-(2000 random Cliffords + 24 T gates, sparsified to chi = 2^16 terms):
-  init_terms -> apply_clifford -> amplitude (B = 4096 x) -> norm_estimate
-  (L = 256) -> sample chain starts -> chains_init (C = 256) -> Metropolis
-  (T = 16 steps).
+One step = one pass of the whole path over one batch of the QAOA workload: n = 50
+qubits, QAOA p = 1 on a seeded degree-4 Max-E3LIN2 instance (gamma = 0.3, beta = 0.2;
+264 CX, 150 H and 116 rotation slots), sparsified to chi = 2^20 terms:
+  init_terms -> apply_clifford -> amplitude (B = 4096 uniform x) -> norm_estimate
+  (L = 512) -> sample chain starts -> chains_init (C = 256) -> Metropolis (T = 64
+  steps of the workload's 10^4 per chain).
 Units per step: chi-term amplitude evaluations = chi * (B + C * (T + 1)).
-`value` is device-resident throughput (inputs already in HBM); `e2e` runs the
-same step through the public API with host buffers and the host<->device
-copies inside the timed region.  L2 is flushed (256 MB write) before every
-timed step.  Prints one JSON line (rank 0).
+`value` is device-resident throughput (inputs already in HBM); `e2e` runs the same
+step through the public API with host buffers and the host<->device copies inside
+the timed region.  L2 is flushed (256 MB write) before every timed step.  The same
+step on the n = 40 random Clifford+T workload (chi = 2^16) is a side study.  Prints
+one JSON line (rank 0).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -28,34 +31,42 @@ sys.path.insert(0, ROOT)
 
 METRIC = "χ-term amplitude evals/s"
 UNIT = "term-amplitude evals/s"
-B_X, L_A, C_CH, T_MC = 4096, 256, 256, 16
+
+# step shapes: batch B, equatorial states L, chains C, Metropolis steps T per step
+SHAPES = {
+    "qaoa": dict(B=4096, L=512, C=256, T=64),
+    "mid": dict(B=4096, L=256, C=256, T=16),
+    "qaoa_small": dict(B=2048, L=64, C=64, T=2, chi=1 << 16),   # profiling case
+}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lrstab", choices=["lrstab", "reference"])
+    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "mid"],
+                    help="headline workload (default: the n=50 QAOA step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sampler-study", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the QAOA n=50 and batching studies")
+                    help="skip the side studies (n=40 step, batching, gadgets, prefixes, marginals, GEMMs)")
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: chi = 2^16 terms of the QAOA decomposition, B = 2048, L = 64, "
+                         "C = 64, T = 2 (for ncu captures; not a bench line)")
     ap.add_argument("--mlp-gemm-only", action="store_true",
                     help="run only the MADE network tensor-core study (n=64, H=2048, 16384 rows) and "
                          "print its JSON (for ncu captures of the GEMM kernels; not a bench line)")
     ap.add_argument("--qaoa-apply-only", action="store_true",
                     help="run only apply_clifford on the n=50 QAOA circuit at chi = 2^16, twice, and "
-                         "print its times (for ncu captures of the 64-bit-row layout; not a bench line)")
+                         "print its times (for ncu captures; not a bench line)")
     ap.add_argument("--metropolis-only", action="store_true",
-                    help="run only chain starts and 2 x 16 Metropolis steps on the n=40 workload at "
-                         "chi = 2^16, C = 256, and print their times (for ncu captures of the propose "
-                         "kernel; not a bench line)")
-    ap.add_argument("--small", action="store_true",
-                    help="profiling case: chi = 2^15 terms of the same decomposition, B = 2048, "
-                         "L = 128, C = 128, T = 2 (for ncu captures; not a bench line)")
-    return ap.parse_args()
+                    help="run only chain starts and 2 x 16 Metropolis steps at chi = 2^16 (n = 40, or "
+                         "n = 50 with --workload qaoa), and print their times (for ncu captures; not a "
+                         "bench line)")
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------------
@@ -64,12 +75,13 @@ def parse():
 GATE_OPS = {"S": 4, "SDG": 4, "Z": 2, "CZ": 4, "CX": 12}
 
 
-def clifford_ops_per_term(n, low):
+def clifford_ops_per_term(n, low, formula=False):
     """Expected integer ops per term of the lowered circuit.
 
-    An H on a qubit no earlier gate has touched acts on |0> and needs no row pass
-    (no fan-out, a = 0): it is counted at its constant part (40), every other
-    H or projector at 30n + 40."""
+    formula=False (the kernel's count): an H on a qubit no earlier gate has touched
+    acts on |0> and needs no row pass (no fan-out, a = 0), so it is counted at its
+    constant part (40); every other H or projector at 30n + 40.  formula=True: every
+    H and projector at 30 n + 40, the per-gate figure of the hot-path table."""
     import numpy as np
     from paper_1808_00128_gb300 import lrstab
     inv = {v: k for k, v in lrstab.OP.items()}
@@ -80,7 +92,7 @@ def clifford_ops_per_term(n, low):
         name = inv[int(g["op"])]
         q = int(g["q"])
         if name in ("H", "P0", "P1"):
-            cost = h_ops if (q in touched or name != "H") else 40
+            cost = h_ops if (formula or q in touched or name != "H") else 40
             touched.add(q)
             return cost
         touched.add(q)
@@ -111,6 +123,68 @@ def clifford_ops_per_term(n, low):
         else:
             total += gate_cost(g)
     return total
+
+
+def amplitude_ops_per_unit(n, mean_popcount_x, formula=False):
+    """Integer ops per (x, term).  Kernel count: Four-Russians lookups, 4 word ops per
+    4-row chunk, 8 ceil(n/4) + 16.  Formula of the hot-path table: 10 |x| + 30 (one
+    row step per set bit of x)."""
+    if formula:
+        return 10.0 * mean_popcount_x + 30.0
+    return 8.0 * ((n + 3) // 4) + 16.0
+
+
+def norm_ops_per_unit(n, vw, max_folds):
+    """32-bit integer ops per (A, term) of the norm estimate, by the path a term takes.
+    K path (n - |v| > max_folds): the two products of K = G^T (A+J) G, 8 n^2, plus the
+    pairwise elimination on |v| variables, 4 |v|^2.  Change-of-variables path: the rows
+    of A + J and the lifted rows, 8 n, one rank-2 update per folded constraint, 5 n
+    each, and the same elimination, 4 |v|^2.  max_folds = -1 gives the hot-path
+    table's formula 8 n^2 + 4 |v|^2 for every term."""
+    import numpy as np
+    vw = np.asarray(vw)
+    m = n - vw
+    return np.where(m <= max_folds, 8 * n + 5 * m * n + 4 * vw ** 2, 8 * n * n + 4 * vw ** 2)
+
+
+def metropolis_bytes(chi, C, T, n, accept=0.5):
+    """Algorithmic HBM bytes of T steps of C chains: the 16-byte state of every (chain,
+    term) read, written back for accepted moves, and the rows F_j, M_j of every term
+    (16 n bytes per term per step)."""
+    return T * (chi * C * (16 + 16 * accept) + chi * 16 * n)
+
+
+def units_per_step(chi, B, C, T):
+    return chi * (B + C * (T + 1))
+
+
+def launches_per_step(T):
+    """Library kernels one step launches: init, apply, amplitude + reduce, norm (prep,
+    equatorial draws, norm, reduce), chain starts, chains_init (amplitude with Pauli
+    states, reduce, chain scalars), Metropolis (set, first, graphs of 16 steps with
+    2 launches per step and an advance node, the remaining steps, out)."""
+    g, r = divmod(T, 16)
+    return 1 + 1 + 2 + 4 + 1 + 3 + (2 + g * (2 * 16 + 1) + 2 * r + 1)
+
+
+# DRAM bytes per launch of the dominant kernel (ncu: dram__bytes_read.sum +
+# dram__bytes_write.sum), per unit of work, with the hash of the kernel source the
+# capture ran; `traffic` is reported only while that source is unchanged.
+TRAFFIC = {}
+
+
+def source_sha16(path):
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_for(phase, units):
+    t = TRAFFIC.get(phase)
+    if not t:
+        return None, None
+    if source_sha16(t["source"]) != t["sha16"]:
+        return None, f"{t['profile']} (kernel changed since the capture)"
+    return t["bytes_per_unit"] * units, t["profile"]
 
 
 # ---------------------------------------------------------------------------------
@@ -171,54 +245,80 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------
-# CPU oracle timing (bounded sample)
+# CPU oracle timing: a bounded sample of the step, spread over the host cores
 # ---------------------------------------------------------------------------------
-def oracle_sample_rates(cfg, n_terms=24, n_x=256, n_a=8, seed_alpha=0):
-    """Per-unit oracle times on a bounded sample of the workload."""
+def _oracle_worker(args):
+    """One host process: build `k` terms of the decomposition (from term alpha0),
+    evaluate their amplitudes at n_x strings and their equatorial inner products with
+    n_a states; returns the seconds of each phase and its unit counts."""
+    cfg_name, alpha0, k, n_x, n_a = args
     from oracle import decomp
     from oracle import estimators as E
     from paper_1808_00128_gb300 import workloads
+    cfg = workload_config(cfg_name)
     n, ops = cfg["n"], cfg["ops"]
-    xs = [int(x) for x in workloads.random_bitstrings(n, n_x, seed=workloads.SEED_BASE + 50)]
+    xs = [int(x) for x in workloads.random_bitstrings(n, n_x, seed=workloads.SEED_BASE + 50 + alpha0)]
     t0 = time.perf_counter()
-    terms, coefs, _ = decomp.build_decomposition(n, ops, chi=cfg["chi"], mode=cfg["mode"],
-                                                 seed=cfg["seed"],
-                                                 alphas=range(seed_alpha, seed_alpha + n_terms))
-    t_build = (time.perf_counter() - t0) / n_terms
-    t0 = time.perf_counter()
+    terms, coefs, _ = decomp.build_decomposition(n, ops, chi=cfg["chi"], mode=cfg["mode"], seed=cfg["seed"],
+                                                 alphas=range(alpha0, alpha0 + k))
+    t1 = time.perf_counter()
     for t, b in zip(terms, coefs):
         for x in xs:
             b * t.amplitude(x)
-    t_amp = (time.perf_counter() - t0) / (n_terms * n_x)
-    t0 = time.perf_counter()
+    t2 = time.perf_counter()
     for l in range(n_a):
-        A = E.draw_A(n, 7, l)
+        A = E.draw_A(n, 7 + alpha0, l)
         for t in terms:
             E.inner_equatorial(t, A)
-    t_inner = (time.perf_counter() - t0) / (n_terms * n_a)
-    return t_build, t_amp, t_inner
+    t3 = time.perf_counter()
+    return t1 - t0, t2 - t1, t3 - t2, k, k * n_x, k * n_a
 
 
-def oracle_step_time(cfg, rates):
-    t_build, t_amp, t_inner = rates
-    chi = cfg["chi"]
-    return chi * (t_build + (B_X + C_CH * (T_MC + 1)) * t_amp + L_A * t_inner)
+def workload_config(name):
+    from paper_1808_00128_gb300 import workloads
+    if name == "qaoa":
+        return workloads.config_qaoa()
+    return workloads.config_mid()
 
 
-def norm_ops_per_unit(n, vw, max_folds):
-    """32-bit integer ops per (A, term) of the norm estimate, by the path a term takes.
-    K path (n - |v| > max_folds): the two products of K = G^T (A+J) G, 8 n^2, plus the
-    pairwise elimination on |v| variables, 4 |v|^2.  Change-of-variables path: the rows
-    of A + J and the lifted rows, 8 n, one rank-2 update per folded constraint, 5 n
-    each, and the same elimination, 4 |v|^2."""
-    import numpy as np
-    vw = np.asarray(vw)
-    m = n - vw
-    return np.where(m <= max_folds, 8 * n + 5 * m * n + 4 * vw ** 2, 8 * n * n + 4 * vw ** 2)
+class OracleTimer:
+    """The oracle as it stands, run on all host cores by a spawn-started process
+    pool (safe after CUDA initialisation).  A sample gives per-unit single-core times
+    of term building, amplitude evaluation and equatorial inner products; the step's
+    oracle time is the step's units times those, divided by the parallelism the pool
+    achieved (busy seconds / wall seconds)."""
+
+    def __init__(self, workers=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workers = workers or max(1, os.cpu_count() or 1)
+        self.pool = cf.ProcessPoolExecutor(max_workers=self.workers, mp_context=mp.get_context("spawn"))
+        list(self.pool.map(_noop, range(self.workers)))          # start the workers
+
+    def sample(self, cfg_name, k, n_x, n_a, alpha0=0):
+        t0 = time.perf_counter()
+        res = list(self.pool.map(_oracle_worker, [(cfg_name, alpha0 + w * k, k, n_x, n_a)
+                                                  for w in range(self.workers)]))
+        wall = time.perf_counter() - t0
+        tb = sum(r[0] for r in res) / sum(r[3] for r in res)
+        ta = sum(r[1] for r in res) / sum(r[4] for r in res)
+        ti = sum(r[2] for r in res) / sum(r[5] for r in res)
+        busy = sum(r[0] + r[1] + r[2] for r in res)
+        return {"t_build": tb, "t_amp": ta, "t_inner": ti, "parallel": busy / wall, "wall": wall, "busy": busy}
+
+    def close(self):
+        self.pool.shutdown()
 
 
-def units_per_step(chi):
-    return chi * (B_X + C_CH * (T_MC + 1))
+def _noop(_):
+    import oracle.estimators  # noqa: F401  (import cost paid before timing)
+    return 0
+
+
+def oracle_step_seconds(chi, shape, rates):
+    serial = chi * (rates["t_build"] + (shape["B"] + shape["C"] * (shape["T"] + 1)) * rates["t_amp"]
+                    + shape["L"] * rates["t_inner"])
+    return serial / max(rates["parallel"], 1.0)
 
 
 def run_reference(args):
@@ -226,36 +326,253 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_1808_00128_gb300 import workloads
-    cfg = workloads.config_mid()
+    name = args.workload
+    cfg, shape = workload_config(name), SHAPES[name]
+    chi = cfg["chi"]
+    units = units_per_step(chi, shape["B"], shape["C"], shape["T"])
+    timer = OracleTimer()
+    per = dict(k=2, n_x=256, n_a=2)
     for w in range(args.warmup):
-        oracle_sample_rates(cfg, n_terms=1, n_x=128, n_a=2, seed_alpha=w)
+        timer.sample(name, alpha0=1000 * w, **per)
     times, vals = [], []
     for k in range(args.steps):
         t0 = time.perf_counter()
-        r = oracle_sample_rates(cfg, n_terms=1, n_x=128, n_a=2, seed_alpha=100 + k)
+        r = timer.sample(name, alpha0=100000 + 1000 * k, **per)
         times.append(time.perf_counter() - t0)
-        vals.append(units_per_step(cfg["chi"]) / oracle_step_time(cfg, r))
+        vals.append(units / oracle_step_seconds(chi, shape, r))
+    timer.close()
     value = statistics.median(vals)
-    sample = ("per step: 1 term of the 2^16-term n=40 decomposition built by the oracle, "
-              "128 amplitude evaluations and 2 equatorial inner products; per-unit times "
-              "scaled to one full step (chi*(B + C*(T+1)) amplitude evals, chi*L inner products)")
+    sample = (f"per step: {per['k']} term per core ({timer.workers} cores) of the {cfg['name']} decomposition "
+              f"built by the oracle, {per['n_x']} amplitude evaluations and {per['n_a']} equatorial inner "
+              "product per term; per-unit times scaled to one full step (chi (B + C (T+1)) amplitude "
+              "evaluations, chi L inner products) and divided by the parallelism achieved")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": cfg["name"], "n": cfg["n"], "chi": cfg["chi"], "batch": B_X,
-                      "L": L_A, "chains": C_CH, "metropolis_steps": T_MC},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "config": {"workload": cfg["name"], "n": cfg["n"], "chi": chi, "batch": shape["B"],
+                      "L": shape["L"], "chains": shape["C"], "metropolis_steps": shape["T"]},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": timer.workers, "kind": "oracle",
                             "sample": sample},
-           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": 0}}
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
 # ---------------------------------------------------------------------------------
-# learned proposal vs single-flip Metropolis (ESS/s at matched accuracy)
+# the step
 # ---------------------------------------------------------------------------------
+class StepRunner:
+    """One workload's step on one GPU: the context, device buffers and the timed
+    phases."""
+
+    PHASES = ["init_terms", "apply_clifford", "amplitude", "norm_estimate", "chains_init", "metropolis"]
+
+    def __init__(self, name, local=0, rank=0, small=False):
+        import numpy as np
+        import torch
+        from paper_1808_00128_gb300 import lrstab, workloads
+        self.name = name
+        self.cfg = workload_config(name)
+        self.shape = dict(SHAPES["qaoa_small" if small else name])
+        self.n = self.cfg["n"]
+        self.chi_total = self.cfg["chi"]
+        self.chi = self.shape.pop("chi", self.chi_total)
+        self.seed = self.cfg["seed"] + 1000 * rank          # rank r: its own instance
+        self.low = lrstab.lower_circuit(self.n, self.cfg["ops"])
+        self.dev = torch.device(f"cuda:{local}")
+        B, L, C = self.shape["B"], self.shape["L"], self.shape["C"]
+        self.x_host = torch.from_numpy(workloads.random_bitstrings(self.n, B, seed=workloads.SEED_BASE + 40)
+                                       .view(np.int64)).pin_memory()
+        self.x_dev = self.x_host.to(self.dev)
+        self.amp = torch.empty((B, 2), dtype=torch.float64, device=self.dev)
+        self.eta = torch.empty(L, dtype=torch.float64, device=self.dev)
+        self.x0 = torch.empty(C, dtype=torch.int64, device=self.dev)
+        self.xo = torch.empty(C, dtype=torch.int64, device=self.dev)
+        self.po = torch.empty(C, dtype=torch.float64, device=self.dev)
+        self.sim = lrstab.Simulator(self.n, local)
+        self.stream = torch.cuda.current_stream()
+
+    def units(self):
+        s = self.shape
+        return units_per_step(self.chi, s["B"], s["C"], s["T"])
+
+    def step(self, ev=None, idx=0):
+        st = self.stream
+
+        def mark(i):
+            if ev is not None:
+                ev[i].record(st)
+        s = self.shape
+        mark(0)
+        self.sim.init_terms(self.low, self.chi, mode="sparsify", seed=self.seed, chi_total=self.chi_total)
+        mark(1)
+        self.sim.apply_clifford(self.low.gates)
+        mark(2)
+        self.sim.amplitude(self.x_dev, out=self.amp)
+        mark(3)
+        self.sim.norm_estimate(s["L"], seed=1000 + idx, eta=self.eta)
+        mark(4)
+        self.sim.sample_terms(s["C"], seed=2000 + idx, x=self.x0)
+        self.sim.chains_init(self.x0)
+        mark(5)
+        self.sim.metropolis(s["T"], seed=3000 + idx, x_out=self.xo, p_out=self.po)
+        mark(6)
+
+    def tune(self, cache_path=None):
+        from paper_1808_00128_gb300 import autotune
+        s = self.shape
+        return {k: v for k, (v, ms) in autotune.tune(self.sim, x=self.x_dev, L=s["L"], chains=s["C"],
+                                                       cache_path=cache_path).items()}
+
+    def timed(self, steps, idx0, flush, world=1):
+        import torch
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            self.step(evs[k], idx=idx0 + k)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        per_phase = {p: [] for p in self.PHASES}
+        step_ms = []
+        for e in evs:
+            for i, p in enumerate(self.PHASES):
+                per_phase[p].append(e[i].elapsed_time(e[i + 1]))
+            step_ms.append(e[0].elapsed_time(e[6]))
+        return step_ms, {p: statistics.mean(v) for p, v in per_phase.items()}
+
+    def e2e(self, steps, idx0, flush):
+        import torch
+        s = self.shape
+        amp_h = torch.empty((s["B"], 2), dtype=torch.float64).pin_memory()
+        eta_h = torch.empty(s["L"], dtype=torch.float64).pin_memory()
+        xo_h = torch.empty(s["C"], dtype=torch.int64).pin_memory()
+        po_h = torch.empty(s["C"], dtype=torch.float64).pin_memory()
+        ms = []
+        for k in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            self.x_dev.copy_(self.x_host, non_blocking=True)
+            self.step(idx=idx0 + k)
+            amp_h.copy_(self.amp, non_blocking=True)
+            eta_h.copy_(self.eta, non_blocking=True)
+            xo_h.copy_(self.xo, non_blocking=True)
+            po_h.copy_(self.po, non_blocking=True)
+            e1.record(self.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        h2d = self.x_host.numel() * 8 + len(self.low.gates) * 4
+        d2h = amp_h.numel() * 8 + eta_h.numel() * 8 + xo_h.numel() * 8 + po_h.numel() * 8
+        return statistics.mean(ms), h2d, d2h
+
+    def rooflines(self, phase_ms, alu_peak, hbm_peak):
+        """Per phase: achieved and fraction of the roofline on the kernel's own op count
+        and on the hot-path table's formula."""
+        import numpy as np
+        n, chi, s = self.n, self.chi, self.shape
+        ex = self.sim.export_terms(0, min(chi, 4096))
+        vw = np.array([bin(int(v)).count("1") for v in ex["v"]])
+        xs = self.x_host.numpy().view(np.uint64)
+        xpop = float(np.mean([bin(int(x)).count("1") for x in xs]))
+        folds = self.sim.get_tuning("norm_max_folds")
+        ops = {
+            "apply_clifford": (chi * clifford_ops_per_term(n, self.low), chi * clifford_ops_per_term(n, self.low, True)),
+            "amplitude": (chi * s["B"] * amplitude_ops_per_unit(n, xpop),
+                          chi * s["B"] * amplitude_ops_per_unit(n, xpop, True)),
+            "norm_estimate": (chi * s["L"] * float(np.mean(norm_ops_per_unit(n, vw, folds))),
+                              chi * s["L"] * float(np.mean(norm_ops_per_unit(n, vw, -1)))),
+        }
+        units = {"apply_clifford": ("term-gates", chi * len(self.low.gates)),
+                 "amplitude": ("(x, term)", chi * s["B"]), "norm_estimate": ("(A, term)", chi * s["L"]),
+                 "metropolis": ("chain-term-steps", chi * s["C"] * s["T"])}
+        rows = {}
+        for p, (k_ops, f_ops) in ops.items():
+            t = phase_ms[p] * 1e-3
+            rows[p] = {"bound": "alu", "achieved": k_ops / t / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
+                       "frac": k_ops / t / alu_peak, "frac_formula": f_ops / t / alu_peak, "ms": phase_ms[p],
+                       "rate": units[p][1] / t, "rate_unit": units[p][0] + "/s"}
+        t = phase_ms["metropolis"] * 1e-3
+        byts = metropolis_bytes(chi, s["C"], s["T"], n)
+        rows["metropolis"] = {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": byts / t / 1e9 / hbm_peak, "frac_formula": byts / t / 1e9 / hbm_peak,
+                              "ms": phase_ms["metropolis"], "ms_per_metropolis_step": phase_ms["metropolis"] / s["T"],
+                              "rate": units["metropolis"][1] / t, "rate_unit": units["metropolis"][0] + "/s"}
+        return rows
+
+    def error_statement(self):
+        """The kernel's per-result bound on |a_gpu - exact chi-sum| over the step's
+        batch, relative to max(|a|, ||psi|| 2^{-n/2}) with ||psi||^2 the step's norm
+        estimate."""
+        import numpy as np
+        import torch
+        err = torch.empty(self.shape["B"], dtype=torch.float32, device=self.dev)
+        a = self.sim.amplitude(self.x_dev, err=err).cpu().numpy()
+        err = err.cpu().numpy().astype(np.float64)
+        mag = np.hypot(a[:, 0], a[:, 1])
+        norm = float(np.sqrt(max(self.eta.mean().item(), 0.0)))
+        rel = err / np.maximum(mag, norm * 2.0 ** (-self.n / 2))
+        return {"bound_max_rel": float(rel.max()), "bound_median_rel": float(np.median(rel)),
+                "norm_estimate": norm ** 2, "relative_to": "max(|a|, ||psi|| 2^{-n/2})"}
+
+    def close(self):
+        self.sim.close()
+
+
+def slice_parity(name, local=0, chi=128, alpha0=31337, n_x=64, timer=None):
+    """Measured error of the CUDA amplitudes against the oracle's exact Z[zeta8]
+    chi-sums on a `chi`-term slice of the workload's decomposition, at strings drawn
+    from the slice's terms and uniform strings; also checks the kernel's stated
+    bound.  The oracle's terms are built on the host pool."""
+    import numpy as np
+    import torch
+    from oracle import exact
+    from paper_1808_00128_gb300 import lrstab, workloads
+    cfg = workload_config(name)
+    n, ops = cfg["n"], cfg["ops"]
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, local)
+    sim.init_terms(low, chi, mode=cfg["mode"], seed=cfg["seed"], alpha0=alpha0, chi_total=cfg["chi"])
+    sim.apply_clifford(low.gates)
+    xs_t = sim.sample_terms(n_x, seed=77).cpu().numpy().view(np.uint64)
+    xs = np.concatenate([xs_t, workloads.random_bitstrings(n, n_x, seed=78)])
+    x = torch.from_numpy(xs.view(np.int64)).to(f"cuda:{local}")
+    err = torch.empty(len(xs), dtype=torch.float32, device=x.device)
+    a = sim.amplitude(x, err=err).cpu().numpy()
+    sim.close()
+    got = a[:, 0] + 1j * a[:, 1]
+    err = err.cpu().numpy().astype(np.float64)
+    k = max(1, chi // timer.workers) if timer else chi
+    jobs = [(name, alpha0 + i, min(k, alpha0 + chi - (alpha0 + i)), [int(v) for v in xs]) for i in range(0, chi, k)]
+    parts = list(timer.pool.map(_exact_slice_worker, jobs)) if timer else [_exact_slice_worker(j) for j in jobs]
+    ex = exact.ExactDecomposition(n, ops, cfg["chi"], cfg["mode"])
+    want = np.array([exact.to_complex(ex.finish_parts([p[i] for p in parts])) for i in range(len(xs))])
+    d = np.abs(got - want)
+    coef = ex.l1 / cfg["chi"]
+    scale = np.maximum(np.abs(want), coef * np.sqrt(chi) * 2.0 ** (-n / 2))
+    return {"workload": f"{cfg['name']} terms {alpha0}..{alpha0 + chi - 1}", "strings": int(len(xs)),
+            "max_abs_err": float(d.max()), "max_rel_err": float((d / scale).max()),
+            "relative_to": "max(|a|, |b| sqrt(chi_slice) 2^{-n/2})",
+            "bound_holds": bool(np.all(d <= err)), "max_err_over_bound": float(np.max(d / np.maximum(err, 1e-300)))}
+
+
+def _exact_slice_worker(args):
+    name, a0, k, xs = args
+    from oracle import decomp, exact
+    cfg = workload_config(name)
+    terms, _, chs = decomp.build_decomposition(cfg["n"], cfg["ops"], chi=cfg["chi"], mode=cfg["mode"],
+                                               seed=cfg["seed"], alphas=range(a0, a0 + k))
+    ex = exact.ExactDecomposition(cfg["n"], cfg["ops"], cfg["chi"], cfg["mode"])
+    return [ex.amplitude_parts(terms, chs, x) for x in xs]
+
+
+# ---------------------------------------------------------------------------------
+# side studies
+# ---------------------------------------------------------------------------------
+
 def tau_int(series):
     """Integrated autocorrelation time of a [T][C] series (chain-averaged
     autocorrelation, Sokal's automatic window with c = 5)."""
@@ -384,25 +701,22 @@ def sampler_study(local=0, n=20, chi=1 << 14, C=1024, T_plain=2000, T_learned=20
             "ess_ratio_learned_over_plain": ess_learned / ess_plain}
 
 
-# ---------------------------------------------------------------------------------
-# QAOA n=50 at chi = 2^20 (gate updates, amplitudes, Metropolis) and batching of
-# 8 circuits of uneven chi in one persistent launch
-# ---------------------------------------------------------------------------------
 def _ev():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def metropolis_only(local=0, C=256, T=16):
-    """Chain starts and two calls of T Metropolis steps on the n=40 benchmark workload
-    (chi = 2^16, C chains); propose launches 17..32 are the second call's."""
+def metropolis_only(local=0, C=256, T=16, workload="mid"):
+    """Chain starts and two calls of T Metropolis steps at chi = 2^16 terms of the n=40
+    workload (or the n=50 QAOA one), C chains; propose launches 17..32 are the second
+    call's."""
     import torch
-    from paper_1808_00128_gb300 import lrstab, workloads
-    cfg = workloads.config_mid()
-    n, chi = cfg["n"], cfg["chi"]
+    from paper_1808_00128_gb300 import lrstab
+    cfg = workload_config(workload)
+    n, chi = cfg["n"], 1 << 16
     low = lrstab.lower_circuit(n, cfg["ops"])
     sim = lrstab.Simulator(n, local)
-    sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"])
+    sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"], chi_total=cfg["chi"])
     sim.apply_clifford(low.gates)
     x0 = sim.sample_terms(C, seed=5)
     sim.chains_init(x0)
@@ -416,111 +730,30 @@ def metropolis_only(local=0, C=256, T=16):
         ms.append(a.elapsed_time(b))
     torch.cuda.synchronize()
     sim.close()
-    return {"workload": f"clifford_t_n40_chi{chi}_C{C}", "steps": T, "ms": ms}
+    return {"workload": f"{cfg['name']}_chi{chi}_C{C}", "steps": T, "ms": ms}
 
 
-def qaoa_apply_only(local=0, chi=1 << 16):
-    """apply_clifford alone on the n=50 QAOA circuit, chi = 2^16, two launches (the
-    second is the one to capture)."""
-    from paper_1808_00128_gb300 import lrstab, workloads
-    cfg = workloads.config_qaoa(chi=chi)
+def qaoa_apply_only(local=0, chi=1 << 16, lanes=(1, 2, 4)):
+    """apply_clifford alone on the n=50 QAOA circuit, chi = 2^16, once per lanes-per-term
+    value (one launch each, after one warm-up launch)."""
+    from paper_1808_00128_gb300 import lrstab
+    cfg = workload_config("qaoa")
     low = lrstab.lower_circuit(cfg["n"], cfg["ops"])
     sim = lrstab.Simulator(cfg["n"], local)
-    ms = []
-    for rep in range(2):
-        sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"])
+    sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"], chi_total=cfg["chi"])
+    sim.apply_clifford(low.gates)
+    ms = {}
+    for lv in lanes:
+        sim.set_tuning("apply_lanes", lv)
+        sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"], chi_total=cfg["chi"])
         a, b = _ev()
         a.record()
         sim.apply_clifford(low.gates)
         b.record()
         b.synchronize()
-        ms.append(a.elapsed_time(b))
+        ms[lv] = a.elapsed_time(b)
     sim.close()
-    return {"workload": f"qaoa_e3lin2_n50_chi{chi}", "apply_ms": ms}
-
-
-def qaoa_study(local=0, chi=1 << 20, B=4096, C=256, T=64, L=512, alu_peak=None, hbm_peak=6695.2):
-    """Config-4 shapes: n=50 Max-E3LIN2 QAOA (gamma 0.3, beta 0.2), chi = 2^20: gate
-    updates, amplitudes, Metropolis and the norm estimate with L = 512."""
-    import numpy as np
-    import torch
-    from paper_1808_00128_gb300 import lrstab, workloads
-    cfg = workloads.config_qaoa(chi=chi)
-    n = cfg["n"]
-    low = lrstab.lower_circuit(n, cfg["ops"])
-    sim = lrstab.Simulator(n, local)
-    sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"])
-    ops_term = clifford_ops_per_term(n, low)
-    dev = torch.device(f"cuda:{local}")
-    x = torch.from_numpy(workloads.random_bitstrings(n, B, workloads.SEED_BASE + 41).view(np.int64)).to(dev)
-    out = torch.empty((B, 2), dtype=torch.float64, device=dev)
-    res = {"workload": f"qaoa_e3lin2_n50_chi{chi}", "n": n, "chi": chi, "gates": len(low.gates),
-           "slots": len(low.slots)}
-    # apply_clifford (re-init each rep; timed alone)
-    ts = []
-    for rep in range(3):
-        sim.init_terms(low, chi, mode="sparsify", seed=cfg["seed"])
-        a, b = _ev()
-        a.record()
-        sim.apply_clifford(low.gates)
-        b.record()
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
-    t_apply = min(ts) * 1e-3
-    ach = chi * ops_term / t_apply
-    res["apply_clifford"] = {"ms": t_apply * 1e3, "term_gates_per_s": chi * len(low.gates) / t_apply,
-                             "achieved_Tops": ach / 1e12, "frac": ach / alu_peak if alu_peak else None}
-    # amplitude (launch shape autotuned for this batch)
-    from paper_1808_00128_gb300 import autotune
-    tuned = {k: v for k, (v, ms) in autotune.tune(sim, x=x).items()}
-    res["tuned"] = tuned
-    sim.amplitude(x, out=out)
-    ts = []
-    for rep in range(3):
-        a, b = _ev()
-        a.record()
-        sim.amplitude(x, out=out)
-        b.record()
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
-    t_amp = min(ts) * 1e-3
-    ach = chi * B * (8 * ((n + 3) // 4) + 16) / t_amp
-    res["amplitude"] = {"ms": t_amp * 1e3, "x_term_per_s": chi * B / t_amp, "achieved_Tops": ach / 1e12,
-                        "frac": ach / alu_peak if alu_peak else None, "batch": B}
-    # norm estimate, L = 512 equatorial states
-    eta = torch.empty(L, dtype=torch.float64, device=dev)
-    sim.norm_estimate(L, seed=3, eta=eta)
-    a, b = _ev()
-    a.record()
-    sim.norm_estimate(L, seed=4, eta=eta)
-    b.record()
-    b.synchronize()
-    t_norm = a.elapsed_time(b) * 1e-3
-    ex = sim.export_terms(0, min(chi, 4096))
-    vw = np.array([bin(int(v)).count("1") for v in ex["v"]])
-    ach = chi * L * float(np.mean(norm_ops_per_unit(n, vw, sim.get_tuning("norm_max_folds")))) / t_norm
-    res["norm_estimate"] = {"ms": t_norm * 1e3, "A_term_per_s": chi * L / t_norm, "achieved_Tops": ach / 1e12,
-                            "frac": ach / alu_peak if alu_peak else None, "L": L,
-                            "mean_eta": float(eta.mean().item())}
-    # Metropolis (flip chains), graph-replayed steps, launch shape autotuned for C chains
-    x0 = sim.sample_terms(C, seed=5)
-    sim.chains_init(x0)
-    res["tuned"].update({k: v for k, (v, ms) in autotune.tune(sim, chains=C).items()})
-    sim.chains_init(x0)
-    sim.metropolis(T, seed=6)
-    torch.cuda.synchronize()
-    a, b = _ev()
-    a.record()
-    sim.metropolis(T, seed=6, step0=T)
-    b.record()
-    b.synchronize()
-    t_mc = a.elapsed_time(b) * 1e-3
-    byts = T * (chi * C * (16 + 16 * 0.5) + chi * 16 * n)
-    res["metropolis"] = {"ms_per_step": t_mc * 1e3 / T, "chain_term_steps_per_s": chi * C * T / t_mc,
-                         "achieved_GBs": byts / t_mc / 1e9, "frac": byts / t_mc / 1e9 / hbm_peak,
-                         "chains": C}
-    sim.close()
-    return res
+    return {"workload": f"qaoa_e3lin2_n50_chi{chi}", "apply_ms_by_lanes": ms}
 
 
 def batch_study(local=0, k=8, seed=0):
@@ -724,28 +957,55 @@ def mlp_gemm_study(local=0, n=64, H=2048, batch=16384, reps=5, bf16_peak=None):
 # ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
+def side_step_study(name, local, alu_peak, hbm_peak, steps=5, warmup=3):
+    """The same step on another workload (n = 40 random Clifford+T at chi = 2^16):
+    phase times, rooflines on both counts, the stated error bound."""
+    import torch
+    r = StepRunner(name, local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=r.dev)
+    for w in range(warmup):
+        r.step(idx=w)
+    tuned = r.tune()
+    r.step(idx=warmup)
+    step_ms, phase_ms = r.timed(steps, warmup + 1, flush)
+    ms = statistics.mean(step_ms)
+    out = {"workload": r.cfg["name"], "n": r.n, "chi": r.chi, **r.shape, "ms_per_step": ms,
+           "value": r.units() / (ms * 1e-3), "unit": UNIT, "tuned": tuned,
+           "phases": r.rooflines(phase_ms, alu_peak, hbm_peak), "amplitude_error": r.error_statement()}
+    r.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    peaks = _peaks()
     if args.mlp_gemm_only:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         print(json.dumps(mlp_gemm_study(0, reps=2, bf16_peak=peaks.get("bf16_tflops"))))
         return
     if args.qaoa_apply_only:
         print(json.dumps(qaoa_apply_only(0)))
         return
     if args.metropolis_only:
-        print(json.dumps(metropolis_only(0)))
+        print(json.dumps(metropolis_only(0, workload=args.workload)))
         return
-    import numpy as np
     import torch
-    from paper_1808_00128_gb300 import lrstab, workloads
+    from paper_1808_00128_gb300 import lrstab, sharding
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    small = args.small
+    if small:
+        args.no_cpu_baseline = args.no_e2e = args.no_extra = args.no_sampler_study = True
+    # the oracle's host pool starts (spawn) before the first GPU call
+    timer = OracleTimer() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
     if world > 1:
@@ -753,188 +1013,84 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     lrstab.lib()
 
-    global B_X, L_A, C_CH, T_MC
-    cfg = workloads.config_mid()
-    n, chi, seed = cfg["n"], cfg["chi"], cfg["seed"] + 1000 * rank   # rank r: its own instance
-    chi_total = chi
-    if args.small:
-        chi, B_X, L_A, C_CH, T_MC = 1 << 15, 2048, 128, 128, 2
-        args.no_cpu_baseline = args.no_e2e = True
-    low = lrstab.lower_circuit(n, cfg["ops"])
-    x_host = torch.from_numpy(workloads.random_bitstrings(n, B_X, seed=workloads.SEED_BASE + 40)
-                              .view(np.int64)).pin_memory()
-    x_dev = x_host.to(dev)
-    amp = torch.empty((B_X, 2), dtype=torch.float64, device=dev)
-    eta = torch.empty(L_A, dtype=torch.float64, device=dev)
-    x0 = torch.empty(C_CH, dtype=torch.int64, device=dev)
-    xo = torch.empty(C_CH, dtype=torch.int64, device=dev)
-    po = torch.empty(C_CH, dtype=torch.float64, device=dev)
+    r = StepRunner(args.workload, local, rank, small=small)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    sim = lrstab.Simulator(n, local)
-    stream = torch.cuda.current_stream()
-    phases = ["init_terms", "apply_clifford", "amplitude", "norm_estimate", "chains_init",
-              "metropolis"]
-
-    def step(ev=None, step_idx=0):
-        def mark(i):
-            if ev is not None:
-                ev[i].record(stream)
-        mark(0)
-        sim.init_terms(low, chi, mode="sparsify", seed=seed, chi_total=chi_total)
-        mark(1)
-        sim.apply_clifford(low.gates)
-        mark(2)
-        sim.amplitude(x_dev, out=amp)
-        mark(3)
-        sim.norm_estimate(L_A, seed=1000 + step_idx, eta=eta)
-        mark(4)
-        sim.sample_terms(C_CH, seed=2000 + step_idx, x=x0)
-        sim.chains_init(x0)
-        mark(5)
-        sim.metropolis(T_MC, seed=3000 + step_idx, x_out=xo, p_out=po)
-        mark(6)
-
-    # init, apply, amplitude + reduce, norm prep + draw A + norm + reduce, chain starts,
-    # chains_init (amplitude with Q + reduce + set), Metropolis (set, first, T x (propose +
-    # accept), advance, out)
-    launches_per_step = 1 + 1 + 2 + 4 + 1 + 3 + (2 + 2 * T_MC + 2)
-
     for w in range(args.warmup):
-        step(step_idx=w)
+        r.step(idx=w)
     torch.cuda.synchronize()
-    from paper_1808_00128_gb300 import autotune
-    tuned = {k: v for k, (v, ms) in autotune.tune(sim, x=x_dev, L=L_A, chains=C_CH,
-                                                   cache_path=os.environ.get("LRS_TUNE_CACHE")).items()}
-    step(step_idx=args.warmup)
+    tuned = r.tune(cache_path=os.environ.get("LRS_TUNE_CACHE"))
+    r.step(idx=args.warmup)
     torch.cuda.synchronize()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            step(evs[k], step_idx=args.warmup + k)
-        torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    per_phase = {p: [] for p in phases}
-    step_ms = []
-    for k in range(args.steps):
-        e = evs[k]
-        for i, p in enumerate(phases):
-            per_phase[p].append(e[i].elapsed_time(e[i + 1]))
-        step_ms.append(e[0].elapsed_time(e[6]))
-    from paper_1808_00128_gb300 import sharding
+        step_ms, phase_ms = r.timed(args.steps, args.warmup + 1, flush, world)
     ms = sharding.max_over_ranks(statistics.mean(step_ms), device=dev)
-    units = units_per_step(chi)
+    units = r.units()
     value = world * units / (ms * 1e-3)
 
-    # ---- roofline of the dominant phase
-    import math
-    ex = sim.export_terms(0, min(chi, 4096))
-    vw = np.array([bin(int(v)).count("1") for v in ex["v"]])
-    xs_np = x_host.numpy().view(np.uint64)
-    xpop = float(np.mean([bin(int(x)).count("1") for x in xs_np]))
-    phase_ms = {p: statistics.mean(v) for p, v in per_phase.items()}
-    ops = {
-        "apply_clifford": chi * clifford_ops_per_term(n, low),
-        "amplitude": chi * B_X * (8 * ((n + 3) // 4) + 16),
-        "norm_estimate": chi * L_A * float(np.mean(norm_ops_per_unit(n, vw, sim.get_tuning("norm_max_folds")))),
-    }
-    norm_formula = chi * L_A * float(np.mean(8 * n * n + 4 * vw ** 2))
-    mc_bytes = T_MC * (chi * C_CH * (16 + 16 * 0.5) + chi * 16 * n)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    alu_measured = lrstab.alu_probe(local, 4000)
-    rows = {}
-    for p in ("apply_clifford", "amplitude", "norm_estimate"):
-        ach = ops[p] / (phase_ms[p] * 1e-3)
-        rows[p] = {"bound": "alu", "achieved": ach / 1e12, "peak": alu_measured / 1e12,
-                   "unit": "Tops/s", "frac": ach / alu_measured, "ms": phase_ms[p]}
-    # the same phase counted with 8 n^2 + 4 |v|^2 per (A, term) for every term, as if
-    # K = G^T (A+J) G were formed (the change-of-variables path skips that product)
-    rows["norm_estimate"]["frac_k_formula"] = norm_formula / (phase_ms["norm_estimate"] * 1e-3) / alu_measured
-    ach = mc_bytes / (phase_ms["metropolis"] * 1e-3) / 1e9
-    rows["metropolis"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                          "frac": ach / hbm, "ms": phase_ms["metropolis"]}
+    alu = lrstab.alu_probe(local, 4000)
+    rows = r.rooflines(phase_ms, alu, hbm)
     dom = max(("apply_clifford", "amplitude", "norm_estimate", "metropolis"), key=lambda p: phase_ms[p])
-    roof = dict(rows[dom])
+    roof = {k: v for k, v in rows[dom].items() if k not in ("ms", "rate", "rate_unit", "ms_per_metropolis_step")}
     roof["kernel"] = dom
-    # DRAM bytes per launch from ncu (profiles/): dram__bytes_read.sum + dram__bytes_write.sum
-    # of the kernel's capture on this workload (the timed step's launch; one pass); null
-    # for kernels changed since their capture.
-    traffic = {"norm_estimate": 27.16e6}   # k_norm DRAM bytes per launch (ncu), re-taken after each change of the kernel
-    roof["traffic"] = traffic.get(dom) if not args.small else None
-    roof.pop("ms", None)
-    roof["peak_source"] = ("measured LOP3 probe on this GPU" if roof["bound"] == "alu"
-                           else "MEASURED_PEAKS.json hbm_gbs")
+    unit_count = {"norm_estimate": r.chi * r.shape["L"], "amplitude": r.chi * r.shape["B"],
+                  "apply_clifford": r.chi, "metropolis": r.chi * r.shape["C"] * r.shape["T"]}[dom]
+    roof["traffic"], roof["traffic_source"] = (None, None) if small else traffic_for(dom, unit_count)
+    roof["peak_source"] = ("measured LOP3 probe on this GPU (of measured)" if roof["bound"] == "alu"
+                           else "MEASURED_PEAKS.json hbm_gbs (of measured)")
+    err = r.error_statement()
+    cert = None if small else lrstab.sparsification_certificate(r.sim, r.shape["L"], 3, seed=777)
 
-    # ---- e2e: host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        amp_h = torch.empty((B_X, 2), dtype=torch.float64).pin_memory()
-        eta_h = torch.empty(L_A, dtype=torch.float64).pin_memory()
-        xo_h = torch.empty(C_CH, dtype=torch.int64).pin_memory()
-        po_h = torch.empty(C_CH, dtype=torch.float64).pin_memory()
-        e2e_ms = []
-        for k in range(args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            x_dev.copy_(x_host, non_blocking=True)
-            step(step_idx=100 + k)
-            amp_h.copy_(amp, non_blocking=True)
-            eta_h.copy_(eta, non_blocking=True)
-            xo_h.copy_(xo, non_blocking=True)
-            po_h.copy_(po, non_blocking=True)
-            e1.record(stream)
-            e1.synchronize()
-            e2e_ms.append(e0.elapsed_time(e1))
-        gate_bytes = len(low.gates) * 4
-        h2d = x_host.numel() * 8 + gate_bytes
-        d2h = amp_h.numel() * 8 + eta_h.numel() * 8 + xo_h.numel() * 8 + po_h.numel() * 8
-        e2e = {"value": world * units / (statistics.mean(e2e_ms) * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e_ms, h2d, d2h = r.e2e(args.steps, 100, flush)
+        e_ms = sharding.max_over_ranks(e_ms, device=dev)
+        e2e = {"value": world * units / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    r.close()
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    cpu = parity = None
+    if timer is not None:
         t0 = time.perf_counter()
-        rates = oracle_sample_rates(cfg)
-        cpu = {"value": units / oracle_step_time(cfg, rates), "unit": UNIT, "cores": 1,
-               "kind": "oracle",
-               "sample": "24 terms of the n=40 chi=2^16 decomposition built by the oracle, 256 "
-                         "amplitude evals and 8 equatorial inner products per term; per-unit "
-                         "times scaled to one full step",
+        k, n_x, n_a = (16, 512, 4) if args.workload == "qaoa" else (24, 256, 8)
+        rates = timer.sample(args.workload, k=k, n_x=n_x, n_a=n_a, alpha0=0)
+        cpu = {"value": units / oracle_step_seconds(r.chi, r.shape, rates), "unit": UNIT,
+               "cores": timer.workers, "kind": "oracle",
+               "sample": f"{k} terms per core of the {r.cfg['name']} decomposition built by the oracle, "
+                         f"{n_x} amplitude evaluations and {n_a} equatorial inner products per term; per-unit "
+                         f"times scaled to one full step and divided by the parallelism achieved "
+                         f"({rates['parallel']:.1f} of {timer.workers} cores)",
                "seconds": round(time.perf_counter() - t0, 1)}
-    cert = None
-    if rank == 0 and not args.small:
-        cert = lrstab.sparsification_certificate(sim, low, L=L_A, K=3, seed=777)
-    sim.close()
-    ess = qaoa = batch = gemm = marg = gadget = prefix = None
-    if rank == 0 and not args.small and not args.no_sampler_study:
+        parity = [slice_parity(args.workload, local, timer=timer)]
+    ess = side = None
+    extra = {}
+    if rank == 0 and not args.no_sampler_study:
         ess = sampler_study(local)
-    if rank == 0 and not args.small and not args.no_extra:
-        qaoa = qaoa_study(local, alu_peak=alu_measured, hbm_peak=hbm)
-        batch = batch_study(local)
-        gemm = mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops"))
-        marg = marginal_study(local)
-        gadget = gadget_study(local)
-        prefix = prefix_study(local)
+    if rank == 0 and not args.no_extra:
+        other = "mid" if args.workload == "qaoa" else "qaoa"
+        side = side_step_study(other, local, alu, hbm)
+        if timer is not None:
+            parity.append(slice_parity(other, local, timer=timer))
+        extra = {"batch8": batch_study(local), "mlp_gemm": mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops")),
+                 "marginals": marginal_study(local), "gadget_vs_sum": gadget_study(local),
+                 "prefix_sharing": prefix_study(local)}
+    if timer is not None:
+        timer.close()
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u64+f32", "data": "synthetic",
-           "config": {"workload": cfg["name"], "n": n, "chi": chi, "batch": B_X, "L": L_A,
-                      "chains": C_CH, "metropolis_steps": T_MC, "l2": "flushed (256 MB write) "
-                      "before every timed step", "parallelism": f"replicas x{world}", "tuned": tuned},
-           "roofline": roof, "phases": rows, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "ess": ess,
-           "qaoa_n50": qaoa, "batch8": batch, "mlp_gemm": gemm, "marginals": marg,
-           "sparsification_certificate": cert, "gadget_vs_sum": gadget, "prefix_sharing": prefix}
+           "config": {"workload": r.cfg["name"] + (f"_chi{r.chi}" if small else ""), "n": r.n, "chi": r.chi,
+                      "batch": r.shape["B"], "L": r.shape["L"], "chains": r.shape["C"],
+                      "metropolis_steps": r.shape["T"], "gates": len(r.low.gates), "slots": len(r.low.slots),
+                      "l2": "flushed (256 MB write) before every timed step",
+                      "parallelism": f"replicas x{world}", "tuned": tuned},
+           "roofline": roof, "phases": rows, "amplitude_error": err, "parity_slices": parity,
+           "sparsification_certificate": cert,
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step(r.shape["T"]) * args.steps,
+           "clocks": clk.summary(), "ess": ess, "side_step": side, **extra}
     print(json.dumps(out))
 
 

@@ -148,8 +148,21 @@ lrs_status lrs_lower_gadget(int32_t n_qubits, const lrs_circuit_op* ops_host, in
                             lrs_slot* slots_host, int64_t slots_cap, int64_t* n_slots,
                             lrs_gate* k_gates_host, int64_t k_cap, int64_t* n_k_gates);
 
+/* Sizes of the decomposition a slot table defines (Sec. 2.3.2, Lemma
+ * (Sparsification)), host only: *l1_norm = ||c||_1 = prod_p sum_j |c_j^(p)| (the
+ * sparsification error is delta^2 = ||c||_1^2 / k for k sampled terms) and
+ * *exact_chi = prod_p (number of nonzero c_j^(p)), the number of terms of the
+ * exact enumeration, or -1 when it exceeds 2^62; *log2_exact_chi its base-2
+ * logarithm (any output may be NULL).
+ * Errors: LRS_ERR_ARG (n_slots < 0, NULL table, n_choices out of range).     */
+lrs_status lrs_decomposition_stats(const lrs_slot* slots_host, int64_t n_slots, double* l1_norm,
+                                   int64_t* exact_chi, double* log2_exact_chi);
+
 /* ---- context ------------------------------------------------------------------ */
-/* Create a context for n_qubits (1..64) on CUDA device `device`.
+/* Create a context for n_qubits (1..64) on CUDA device `device`.  There is no
+ * options argument: the launch shapes a context uses are set per context, at any
+ * time, with lrs_set_tuning (defaults suit a GB300), and everything else a call
+ * needs travels with the call.
  * Errors: LRS_ERR_ARG (n out of range), LRS_ERR_CUDA (bad device).           */
 lrs_status lrs_create(int32_t device, int32_t n_qubits, lrs_ctx** out);
 
@@ -224,10 +237,20 @@ lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_gate* const*
  * are exact Z8 phases times powers of sqrt2 times b_alpha; the chi-sum is a
  * per-thread compensated (Kahan) FP32 sum over a tile of terms, then an FP64
  * tree sum across tiles.
+ * err_est_dev (may be NULL; device, batch floats): a rigorous bound on
+ * |out_i - exact chi-sum of the stored coefficients|,
+ *   err_i = (8u + 8 t u^2)(1 + t u)(1 + 1e-4) M_i + n_tiles 2^-52 P_i,
+ * u = 2^-24, t the tile length, M_i = sum over the terms that contribute at x_i of
+ * |b_alpha <x_i|phi_alpha>|, P_i = sum of the tiles' |FP32 partial sum|: 4u per
+ * addend (FP32 coefficient and phase factors), 2 sqrt2 u for the Kahan sum of a
+ * complex tile, u for its final rounding, the FP64 tile sum.  It is a worst case,
+ * linear in M_i: where the terms cancel (sparsified states, M_i >> |out_i|) the
+ * observed error is far below it.  Asking for it costs one FP32 add per
+ * contributing (x, term) and an extra FP32 partial per (x, tile).
  * x_dev: batch uint64 basis strings.  batch = 0 is a no-op.
  * Errors: LRS_ERR_ARG (batch < 0, NULL pointers), LRS_ERR_STATE.            */
 lrs_status lrs_amplitude(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch, double* out_dev,
-                         void* stream);
+                         float* err_est_dev, void* stream);
 
 /* Same result as lrs_amplitude, but the call allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
@@ -303,6 +326,26 @@ lrs_status lrs_copy_terms(lrs_ctx* dst, const lrs_ctx* src, void* stream);
  * L K <= 2^22.  Writes *estimate_host; synchronises the stream.                  */
 lrs_status lrs_norm_median_of_means(lrs_ctx* ctx, int64_t L, int32_t K, uint64_t seed,
                                     double* estimate_host, void* stream);
+/* Sparsification certificate (Lemma (Sparsification tail bound), Sec. 5.2): for the
+ * sparsified state Omega held by ctx (chi_total sampled terms of the decomposition its
+ * slot tables define), ||psi - Omega||^2 <= <Omega|Omega> - 1 + delta^2 with high
+ * probability, delta^2 = ||c||_1^2 / chi_total.  <Omega|Omega> is estimated as
+ * lrs_norm_median_of_means(L, K, seed).  The bound is informative only when the
+ * estimate's own error is well below delta^2: `conclusive` is 1 when twice the
+ * standard error of the mean of the L K values eta_l is below delta^2.  Writes
+ * *out_host; synchronises the stream.  Errors: as lrs_norm_median_of_means.     */
+typedef struct {
+    double omega_norm2;   /* median of K means of L eta values: <Omega|Omega>      */
+    double stderr_mean;   /* standard error of the mean of the L K eta values       */
+    double delta2;        /* ||c||_1^2 / chi_total                                  */
+    double bound;         /* omega_norm2 - 1 + delta2                               */
+    double bound_upper;   /* omega_norm2 + 2 stderr_mean - 1 + delta2               */
+    int32_t conclusive;   /* 2 stderr_mean < delta2                                 */
+    int32_t reserved;
+} lrs_certificate;
+lrs_status lrs_sparsification_certificate(lrs_ctx* ctx, int64_t L, int32_t K, uint64_t seed,
+                                          lrs_certificate* out_host, void* stream);
+
 /* Chain-rule sample of the bits on qubits[0..w) by norm estimation: step i fixes
  * the bits drawn so far by the projectors (I + (-1)^x Z_q)/2 (Sec. 4.1, projective
  * gates), estimates both branches p_b = ||Pi_{x_<i, b} psi||^2 by
@@ -422,13 +465,20 @@ lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
  *                                 per-term value.
  *   LRS_TUNE_MC_STAGES            Metropolis: chains whose inputs a block keeps
  *                                 in flight in shared memory (1..4, 2; 12 KB each)
+ *   LRS_TUNE_APPLY_LANES          apply_clifford for n > 48 (64-bit rows): lanes
+ *                                 per term (1, 2 or 4; default 2).  The lanes of a
+ *                                 term share its tableau in shared memory and split
+ *                                 its rows, so more warps share an SM; results are
+ *                                 bit-identical for every value.  Narrower tableaux
+ *                                 take one lane per term.
  */
 enum {
     LRS_TUNE_AMP_BLOCKS_PER_SM = 0,
     LRS_TUNE_NORM_MAX_TILES = 1,
     LRS_TUNE_MC_CHAINS_PER_BLOCK = 2,
     LRS_TUNE_NORM_MAX_FOLDS = 3,
-    LRS_TUNE_MC_STAGES = 4
+    LRS_TUNE_MC_STAGES = 4,
+    LRS_TUNE_APPLY_LANES = 5
 };
 lrs_status lrs_set_tuning(lrs_ctx* ctx, int32_t param, int64_t value);
 lrs_status lrs_get_tuning(const lrs_ctx* ctx, int32_t param, int64_t* value);

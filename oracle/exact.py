@@ -184,6 +184,12 @@ class ExactDecomposition:
     def amplitude(self, terms, choices, x: int):
         """Exact <x|psi> for the given terms (CHForm) and their slot choices, as
         (Re, Im) Decimals (Eq. (amplitude1) per term)."""
+        return self.finish_parts([self.amplitude_parts(terms, choices, x)])
+
+    def amplitude_parts(self, terms, choices, x: int):
+        """The exact sum at x over the given terms as {magnitude key: (magnitude,
+        integer coordinates)}; parts of disjoint groups of terms add exactly
+        (finish_parts)."""
         groups = {}
         for t, ch in zip(terms, choices):
             if t.zero:
@@ -197,7 +203,19 @@ class ExactDecomposition:
             if key not in groups:
                 groups[key] = (mag, Z8Sum())
             groups[key][1].add(M + t.k + 2 * mu + 4 * sign, popcount(t.v) + t.h)
-        return self._finish(groups)
+        return {k: (mag, tuple(acc.c)) for k, (mag, acc) in groups.items()}
+
+    def finish_parts(self, parts_list):
+        """Merge parts (integer coordinates add exactly), then convert once."""
+        merged = {}
+        for parts in parts_list:
+            for key, (mag, c) in parts.items():
+                if key not in merged:
+                    merged[key] = (mag, Z8Sum())
+                acc = merged[key][1]
+                for i in range(4):
+                    acc.c[i] += c[i]
+        return self._finish(merged)
 
     def overlap_A(self, terms, choices, A):
         """Exact <phi_A|psi> = sum_alpha b_alpha omega_alpha conj(<phi'_alpha|phi_A>)

@@ -40,15 +40,19 @@ struct AmpEntry {
 // plain amplitude batch, six (80 registers, four strings) for the variant that also
 // writes the Pauli states.
 constexpr int amp_min_blocks(bool qout) { return qout ? 6 : 5; }
-template <int NCH, bool QOUT, bool PK>
+// ERR: also sum |b_alpha <x|phi_alpha>| over the terms that contribute at x (one FP32
+// add per contributing (x, term)), written to magp[i * n_tiles + tile]: the input of
+// the per-result error bound of k_amp_reduce.
+template <int NCH, bool QOUT, bool PK, bool ERR>
 __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
                                                       int64_t batch, int64_t tt,
                                                       float2* __restrict__ partial, int64_t n_tiles,
-                                                      void* __restrict__ Qout) {
+                                                      void* __restrict__ Qout, float* __restrict__ magp) {
     __shared__ AmpEntry tab[PK ? 1 : NCH][16];
     __shared__ uint64_t tabU[PK ? NCH : 1][16], tabW[PK ? NCH : 1][16];
     __shared__ uint64_t sF[64], sM[64];
     __shared__ float2 val8[8];              // b e^{i pi k/4} 2^{-(|v|+h)/2}, k = 0..7
+    __shared__ float val_abs;               // |b| 2^{-(|v|+h)/2} (ERR)
     __shared__ uint64_t sc[4];              // glo, ghi, v, s
     __shared__ uint32_t sc_live;
     // compact Pauli states of the last QG terms for each of the block's strings, private
@@ -69,8 +73,11 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
         xv[k] = i < batch ? (xs[i] & T.nmask) : 0ull;   // bits >= n are ignored
     }
     KahanC acc[AMP_XP];
+    float mag[ERR ? AMP_XP : 1];
 #pragma unroll
     for (int k = 0; k < AMP_XP; ++k) acc[k].init();
+#pragma unroll
+    for (int k = 0; k < (ERR ? AMP_XP : 1); ++k) mag[k] = 0.f;
 
     const int64_t a0 = tile * tt;
     const int64_t a1 = (a0 + tt < T.cap) ? a0 + tt : T.cap;
@@ -106,6 +113,7 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
             const int e0 = __popcll(pv) + (int)(om >> 8);
 #pragma unroll
             for (int k = 0; k < 8; ++k) val8[k] = z8_scale(b, k + (int)(om & 7u), e0);
+            if (ERR) val_abs = ldexpf(hypotf(b.x, b.y), -(e0 >> 1)) * ((e0 & 1) ? 0.70710678f : 1.f);
         }
         __syncthreads();
         if (a + 1 < a1) prefetch(a + 1);
@@ -178,6 +186,7 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
             if (live && ((u ^ s) & nv) == 0) {
                 const int sign = (int)par64(u & (w ^ sv));
                 acc[k].add(val8[(2 * mu + 4 * sign) & 7]);
+                if (ERR) mag[k] += val_abs;
             }
         }
         if (CQ && ((a - a0) & (QG - 1)) == QG - 1) {
@@ -201,35 +210,60 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
 #pragma unroll
     for (int k = 0; k < AMP_XP; ++k) {
         const int64_t i = xb + tid + k * AMP_XT;
-        if (i < batch) partial[i * n_tiles + tile] = acc[k].value();
+        if (i < batch) {
+            partial[i * n_tiles + tile] = acc[k].value();
+            if (ERR) magp[i * n_tiles + tile] = mag[ERR ? k : 0];
+        }
     }
 }
 
-// FP64 sum of the block partials of each x.
-__global__ void k_amp_reduce(const float2* __restrict__ partial, int64_t n_tiles, int64_t batch,
-                             double* __restrict__ out) {
+// FP64 sum of the block partials of each x, and (magp != NULL) the error bound of
+// that sum against the exact chi-sum:
+//   |a_gpu - a| <= (8u + 8 tt u^2)(1 + tt u)(1 + 1e-4) M + n_tiles 2^-52 P,
+// u = 2^-24, M = sum over contributing terms of |b_alpha <x|phi_alpha>| (FP32 sums of
+// the tiles), P = sum over tiles of |partial|.  Per addend: the FP32 coefficient and
+// the FP32 phase/sqrt2 factors of z8_scale give at most 4u |a_alpha|; the Kahan sum of
+// a tile of tt addends adds (2u + O(tt u^2)) per real component, 2 sqrt2 u |a_alpha|
+// for the complex pair; the final s - c rounding u; M itself is an FP32 sum of tt
+// positive values (relative tt u) of magnitudes computed to 1e-4.  The FP64 sum of
+// n_tiles partials adds at most n_tiles 2^-53 P per component.
+__global__ void k_amp_reduce(const float2* __restrict__ partial, const float* __restrict__ magp, int64_t n_tiles,
+                             int64_t batch, int64_t tt, double* __restrict__ out, float* __restrict__ err) {
     const int64_t xi = blockIdx.x;
     if (xi >= batch) return;
-    double re = 0.0, im = 0.0;
+    double re = 0.0, im = 0.0, m = 0.0, pa = 0.0;
     for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
         const float2 p = partial[xi * n_tiles + t];
         re += (double)p.x;
         im += (double)p.y;
+        if (magp) {
+            m += (double)magp[xi * n_tiles + t];
+            pa += hypot((double)p.x, (double)p.y);
+        }
     }
-    __shared__ double sre[256], sim[256];
+    __shared__ double sre[256], sim[256], sm[256], spa[256];
     sre[threadIdx.x] = re;
     sim[threadIdx.x] = im;
+    sm[threadIdx.x] = m;
+    spa[threadIdx.x] = pa;
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
         if ((int)threadIdx.x < off) {
             sre[threadIdx.x] += sre[threadIdx.x + off];
             sim[threadIdx.x] += sim[threadIdx.x + off];
+            sm[threadIdx.x] += sm[threadIdx.x + off];
+            spa[threadIdx.x] += spa[threadIdx.x + off];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         out[2 * xi] = sre[0];
         out[2 * xi + 1] = sim[0];
+        if (magp) {
+            const double u = 5.9604644775390625e-8, ttd = (double)tt;
+            const double c = (8.0 * u + 8.0 * ttd * u * u) * (1.0 + ttd * u) * (1.0 + 1e-4);
+            err[xi] = (float)((c * sm[0] + (double)n_tiles * 2.220446049250313e-16 * spa[0]) * (1.0 + 1e-6));
+        }
     }
 }
 
@@ -253,45 +287,54 @@ AmpPlan amp_plan(const lrs_ctx* ctx, int64_t batch, bool qout) {
 
 template <int NCH>
 lrs_status launch_amp_t(lrs_ctx* ctx, const uint64_t* x, int64_t batch, float2* partial,
-                        const AmpPlan& P, void* Qout, cudaStream_t st) {
+                        const AmpPlan& P, void* Qout, float* magp, cudaStream_t st) {
     dim3 grid((unsigned)P.n_tiles, (unsigned)P.xblocks);
     const bool pk = ctx->n <= 62;
+    const TermsView T = ctx->view();
     if (Qout)   // chains need n <= 62 (mu lives in bits 62-63 of Q), so the packed tables apply
-        k_amplitude<NCH, true, true><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles, Qout);
+        k_amplitude<NCH, true, true, false><<<grid, AMP_XT, 0, st>>>(T, x, batch, P.tt, partial, P.n_tiles, Qout,
+                                                                    nullptr);
+    else if (pk && magp)
+        k_amplitude<NCH, false, true, true><<<grid, AMP_XT, 0, st>>>(T, x, batch, P.tt, partial, P.n_tiles,
+                                                                    nullptr, magp);
     else if (pk)
-        k_amplitude<NCH, false, true><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles,
-                                                              nullptr);
+        k_amplitude<NCH, false, true, false><<<grid, AMP_XT, 0, st>>>(T, x, batch, P.tt, partial, P.n_tiles,
+                                                                     nullptr, nullptr);
+    else if (magp)
+        k_amplitude<NCH, false, false, true><<<grid, AMP_XT, 0, st>>>(T, x, batch, P.tt, partial, P.n_tiles,
+                                                                     nullptr, magp);
     else
-        k_amplitude<NCH, false, false><<<grid, AMP_XT, 0, st>>>(ctx->view(), x, batch, P.tt, partial, P.n_tiles,
-                                                               nullptr);
+        k_amplitude<NCH, false, false, false><<<grid, AMP_XT, 0, st>>>(T, x, batch, P.tt, partial, P.n_tiles,
+                                                                      nullptr, nullptr);
     LRS_LAUNCH_CHECK("amplitude kernel");
     return LRS_OK;
 }
 
 lrs_status launch_amp_kernels(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
-                              float2* partial, const AmpPlan& P, cudaStream_t st, void* Qout) {
+                              float2* partial, const AmpPlan& P, cudaStream_t st, void* Qout,
+                              float* magp = nullptr, float* err = nullptr) {
     if (P.xblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "amplitude batch too large");
     lrs_status rc;
     switch ((ctx->n + 3) / 4) {
-        case 1: rc = launch_amp_t<1>(ctx, x, batch, partial, P, Qout, st); break;
-        case 2: rc = launch_amp_t<2>(ctx, x, batch, partial, P, Qout, st); break;
-        case 3: rc = launch_amp_t<3>(ctx, x, batch, partial, P, Qout, st); break;
-        case 4: rc = launch_amp_t<4>(ctx, x, batch, partial, P, Qout, st); break;
-        case 5: rc = launch_amp_t<5>(ctx, x, batch, partial, P, Qout, st); break;
-        case 6: rc = launch_amp_t<6>(ctx, x, batch, partial, P, Qout, st); break;
-        case 7: rc = launch_amp_t<7>(ctx, x, batch, partial, P, Qout, st); break;
-        case 8: rc = launch_amp_t<8>(ctx, x, batch, partial, P, Qout, st); break;
-        case 9: rc = launch_amp_t<9>(ctx, x, batch, partial, P, Qout, st); break;
-        case 10: rc = launch_amp_t<10>(ctx, x, batch, partial, P, Qout, st); break;
-        case 11: rc = launch_amp_t<11>(ctx, x, batch, partial, P, Qout, st); break;
-        case 12: rc = launch_amp_t<12>(ctx, x, batch, partial, P, Qout, st); break;
-        case 13: rc = launch_amp_t<13>(ctx, x, batch, partial, P, Qout, st); break;
-        case 14: rc = launch_amp_t<14>(ctx, x, batch, partial, P, Qout, st); break;
-        case 15: rc = launch_amp_t<15>(ctx, x, batch, partial, P, Qout, st); break;
-        default: rc = launch_amp_t<16>(ctx, x, batch, partial, P, Qout, st); break;
+        case 1: rc = launch_amp_t<1>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 2: rc = launch_amp_t<2>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 3: rc = launch_amp_t<3>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 4: rc = launch_amp_t<4>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 5: rc = launch_amp_t<5>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 6: rc = launch_amp_t<6>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 7: rc = launch_amp_t<7>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 8: rc = launch_amp_t<8>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 9: rc = launch_amp_t<9>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 10: rc = launch_amp_t<10>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 11: rc = launch_amp_t<11>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 12: rc = launch_amp_t<12>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 13: rc = launch_amp_t<13>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 14: rc = launch_amp_t<14>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        case 15: rc = launch_amp_t<15>(ctx, x, batch, partial, P, Qout, magp, st); break;
+        default: rc = launch_amp_t<16>(ctx, x, batch, partial, P, Qout, magp, st); break;
     }
     if (rc != LRS_OK) return rc;
-    k_amp_reduce<<<(unsigned)batch, 256, 0, st>>>(partial, P.n_tiles, batch, out);
+    k_amp_reduce<<<(unsigned)batch, 256, 0, st>>>(partial, magp, P.n_tiles, batch, P.tt, out, err);
     LRS_LAUNCH_CHECK("amplitude reduce kernel");
     return LRS_OK;
 }
@@ -311,14 +354,16 @@ lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, vo
     return launch_amp_kernels(ctx, x, batch, *amp_out, (float2*)scr, P, st, Q);
 }
 
-lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
+lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out, float* err,
                             cudaStream_t st) {
     if (batch == 0) return LRS_OK;
     const AmpPlan P = amp_plan(ctx, batch, false);
+    const size_t part = ((size_t)batch * P.n_tiles * sizeof(float2) + 255) & ~(size_t)255;
     void* scr = nullptr;
-    lrs_status rc = lrs_scratch(ctx, (size_t)batch * P.n_tiles * sizeof(float2), &scr);
+    lrs_status rc = lrs_scratch(ctx, part + (err ? (size_t)batch * P.n_tiles * sizeof(float) : 0), &scr);
     if (rc != LRS_OK) return rc;
-    return launch_amp_kernels(ctx, x, batch, out, (float2*)scr, P, st, nullptr);
+    float* magp = err ? (float*)((char*)scr + part) : nullptr;
+    return launch_amp_kernels(ctx, x, batch, out, (float2*)scr, P, st, nullptr, magp, err);
 }
 
 // ---------------------------------------------------------------------------------

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
                                                           const int32_t* __restrict__ pend,
                                                           const int32_t* __restrict__ jprop,
                                                           float2* __restrict__ partial, int64_t n_tiles,
-                                                          int cg, int nst, int* err) {
+                                                          int cg, int nst, int* err, int groups_fast) {
     extern __shared__ __align__(128) unsigned char mc_dyn[];
     McStage* stage = reinterpret_cast<McStage*>(mc_dyn);
     __shared__ float2 red[MC_CG][MC_TPB / 32];
@@ -108,8 +108,10 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     __shared__ __align__(8) uint64_t full[MC_ST];
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
-    const int64_t tile = blockIdx.x;
-    const int64_t c0 = (int64_t)blockIdx.y * cg;
+    // groups_fast: blockIdx.x is the chain group, so the blocks that read the same
+    // term tile's rows F_j, M_j run together and share them through L2
+    const int64_t tile = groups_fast ? blockIdx.y : blockIdx.x;
+    const int64_t c0 = (int64_t)(groups_fast ? blockIdx.x : blockIdx.y) * cg;
     const int nc = (int)(C - c0 < cg ? C - c0 : cg);
     const int64_t a0 = tile * MC_TERMS;
     const int64_t pairs = C * T.cap;   // entries of the Pauli-state arrays
@@ -370,15 +372,19 @@ static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2*
     const int64_t C = ctx->n_chains;
     const int64_t n_tiles = ctx->cap / MC_TERMS;
     const int cg = (int)ctx->tune_mc_cg;
-    dim3 grid((unsigned)n_tiles, (unsigned)((C + cg - 1) / cg));
+    // chain groups fastest (the rows of a tile are read from DRAM once per step, not once
+    // per group); tiles along x when they exceed the grid's y limit
+    const int64_t groups = (C + cg - 1) / cg;
+    const int gf = n_tiles <= 65535 ? 1 : 0;
+    dim3 grid = gf ? dim3((unsigned)groups, (unsigned)n_tiles) : dim3((unsigned)n_tiles, (unsigned)groups);
     for (int64_t t = t0; t < t0 + count; ++t) {
         const int nst = (int)ctx->tune_mc_stages;
         if (q_compact(ctx->n))
             k_metro_propose<true><<<grid, MC_TPB, nst * sizeof(McStage), st>>>(
-                ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d);
+                ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d, gf);
         else
             k_metro_propose<false><<<grid, MC_TPB, nst * sizeof(McStage), st>>>(
-                ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d);
+                ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d, gf);
         LRS_LAUNCH_CHECK("metropolis propose kernel");
         k_metro_accept<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, ctx->mc_par, t, ctx->n, ctx->cx,
                                                      ctx->cp, ctx->pend, jprop,
@@ -489,7 +495,7 @@ lrs_status launch_metropolis_learned(lrs_ctx* ctx, lrs_mlp* mlp, int64_t steps, 
         const int64_t step = step0 + t;
         rc = lrs_mlp_sample(mlp, C, seed, step * C, ctx->ybuf, ctx->lqy, st);
         if (rc != LRS_OK) return rc;
-        rc = launch_amplitude(ctx, ctx->ybuf, C, ctx->ampy, st);
+        rc = launch_amplitude(ctx, ctx->ybuf, C, ctx->ampy, nullptr, st);
         if (rc != LRS_OK) return rc;
         k_mh_accept<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(ctx->ampy, ctx->ybuf, ctx->lqy, seed, step, C,
                                                                   ctx->cx, ctx->cp, ctx->lqx,

@@ -65,8 +65,8 @@ __global__ void k_init_terms(TermsView T, int32_t mode, uint64_t seed, double sc
     T.coef[a] = make_float2((float)bre, (float)bim);
 }
 
-// ---- apply_clifford: one thread per term, tableau rows in shared memory -----------
-// Shared layout [row][thread] makes every per-thread row index conflict-free.  For
+// ---- apply_clifford: TPT lanes per term, tableau rows in shared memory ------------
+// Shared layout [row][term] makes every per-lane row index conflict-free.  For
 // n <= 48 a row is kept as its low 32 bits plus its next HB bits (0, 8 or 16; bits at
 // or above n are zero in every row): a 40-qubit tableau takes 15n bytes per term
 // instead of 24n, so five 64-term blocks fit on an SM instead of three.  Wider
@@ -76,7 +76,14 @@ __global__ void k_init_terms(TermsView T, int32_t mode, uint64_t seed, double sc
 // The Hadamard row pass reads F and G through per-term pointers; the narrow high rows
 // of G and M are padded so that a warp reading row p of F for some terms and of G for
 // others hits other banks.
-constexpr int APPLY_TPB = 64;
+// A block holds APPLY_TERMS terms.  With TPT lanes per term (the wide layout), the
+// lanes of a term sit 32/TPT apart in one warp, keep identical scalars (gamma, v, s,
+// omega) and split the rows: lane `part` owns the rows p = part (mod TPT), loads,
+// stores and rewrites only those, and the Hadamard / projector row pass -- the bulk of
+// the work -- runs on each lane's own rows; the column-q parities of the row pass are
+// merged with shuffles.  A term's tableau stays in shared memory, so the split gives
+// TPT times the warps per SM (latency hiding) at the same shared-memory footprint.
+constexpr int APPLY_TERMS = 64;
 
 template <int HB> struct HiWord { typedef uint32_t T; };
 template <> struct HiWord<8> { typedef uint8_t T; };
@@ -87,12 +94,42 @@ template <> struct HiWord<16> { typedef uint16_t T; };
 // cover at most 16 banks when esz < 4; 4-byte entries are conflict-free anyway).
 __host__ __device__ __forceinline__ int rows_pad(int n, int esz) {
     if (esz >= 4) return 0;
-    const int offw = (n * APPLY_TPB * esz / 4) & 31;
+    const int offw = (n * APPLY_TERMS * esz / 4) & 31;
     return ((16 - offw) & 31) * 4 / esz;
 }
 
-template <int HB>
-struct SmemRows {
+// The lanes of one term: TPT lanes 32/TPT apart; `part` selects the owned rows.
+template <int TPT>
+struct TermLanes {
+    static constexpr int kStep = TPT;
+    int part_, col_;
+    unsigned mask_;
+    __device__ __forceinline__ TermLanes() {
+        const int lane = threadIdx.x & 31, span = 32 / TPT;
+        part_ = lane / span;
+        col_ = (int)(threadIdx.x >> 5) * span + lane % span;
+        unsigned m = 0;
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) m |= 1u << (lane % span + i * span);
+        mask_ = m;
+    }
+    __device__ __forceinline__ int part() const { return TPT == 1 ? 0 : part_; }
+    __device__ __forceinline__ int col() const { return col_; }
+    __device__ __forceinline__ bool own(int p) const { return TPT == 1 || (p & (TPT - 1)) == part_; }
+    __device__ __forceinline__ void sync() const {
+        if (TPT > 1) __syncwarp(mask_);
+    }
+    // OR over the term's lanes (their row bits are disjoint)
+    __device__ __forceinline__ uint64_t combine(uint64_t v) const {
+#pragma unroll
+        for (int off = 32 / TPT; off < 32; off <<= 1) v |= __shfl_xor_sync(mask_, v, off);
+        return v;
+    }
+};
+
+template <int HB, int TPT = 1>
+struct SmemRows : TermLanes<TPT> {
+    static_assert(TPT == 1, "narrow row layouts take one lane per term");
     typedef typename HiWord<HB>::T Hi;
     static constexpr int kRowUnroll = 2;   // rows per step of the Hadamard row pass
     struct Mat {
@@ -101,22 +138,22 @@ struct SmemRows {
     };
     Mat f, g, m;
     __device__ __forceinline__ SmemRows(uint64_t* smem, int n) {
-        const int rows = 3 * n * APPLY_TPB;
+        const int rows = 3 * n * APPLY_TERMS;
         const int hp = HB > 0 ? rows_pad(n, (int)sizeof(Hi)) : 0;
-        uint32_t* lo = reinterpret_cast<uint32_t*>(smem) + threadIdx.x;
-        Hi* hi = reinterpret_cast<Hi*>(reinterpret_cast<uint32_t*>(smem) + rows) + threadIdx.x;
+        uint32_t* lo = reinterpret_cast<uint32_t*>(smem) + this->col();
+        Hi* hi = reinterpret_cast<Hi*>(reinterpret_cast<uint32_t*>(smem) + rows) + this->col();
         f = Mat{lo, hi};
-        g = Mat{lo + n * APPLY_TPB, hi + n * APPLY_TPB + hp};
-        m = Mat{lo + 2 * n * APPLY_TPB, hi + 2 * n * APPLY_TPB + hp};
+        g = Mat{lo + n * APPLY_TERMS, hi + n * APPLY_TERMS + hp};
+        m = Mat{lo + 2 * n * APPLY_TERMS, hi + 2 * n * APPLY_TERMS + hp};
     }
     __device__ __forceinline__ uint64_t get(const Mat& x, int p) const {
-        uint64_t v = x.lo[p * APPLY_TPB];
-        if (HB > 0) v |= (uint64_t)x.hi[p * APPLY_TPB] << 32;
+        uint64_t v = x.lo[p * APPLY_TERMS];
+        if (HB > 0) v |= (uint64_t)x.hi[p * APPLY_TERMS] << 32;
         return v;
     }
     __device__ __forceinline__ void set(const Mat& x, int p, uint64_t v) {
-        x.lo[p * APPLY_TPB] = (uint32_t)v;
-        if (HB > 0) x.hi[p * APPLY_TPB] = (Hi)(v >> 32);
+        x.lo[p * APPLY_TERMS] = (uint32_t)v;
+        if (HB > 0) x.hi[p * APPLY_TERMS] = (Hi)(v >> 32);
     }
     __device__ __forceinline__ Mat matF() const { return f; }
     __device__ __forceinline__ Mat matG() const { return g; }
@@ -128,37 +165,39 @@ struct SmemRows {
     __device__ __forceinline__ void setG(int p, uint64_t x) { set(g, p, x); }
     __device__ __forceinline__ void setM(int p, uint64_t x) { set(m, p, x); }
     static size_t bytes(int n) {
-        const size_t rows = (size_t)3 * n * APPLY_TPB;
+        const size_t rows = (size_t)3 * n * APPLY_TERMS;
         size_t b = rows * 4;
         if (HB > 0) b += (rows + rows_pad(n, (int)sizeof(Hi))) * sizeof(Hi);
         return b;
     }
 };
 
-// Rows kept whole as one 64-bit word ([row][thread], one 64-bit shared access each),
+// Rows kept whole as one 64-bit word ([row][term], one 64-bit shared access each),
 // addressed by 32-bit shared-space addresses with explicit shared loads and stores
-// (4% faster at n = 50 than generic pointers).
-template <>
-struct SmemRows<64> {
+// (4% faster at n = 50 than generic pointers).  A warp's access to one row of 32 / TPT
+// terms for each of its TPT row sets is 256 bytes in two wavefronts, as for one row
+// of 32 terms.
+template <int TPT>
+struct SmemRows<64, TPT> : TermLanes<TPT> {
     static constexpr int kRowUnroll = 2;
     struct Mat {
         uint32_t a;
     };
     Mat f, g, m;
     __device__ __forceinline__ SmemRows(uint64_t* smem, int n) {
-        const uint32_t b = (uint32_t)__cvta_generic_to_shared(smem + threadIdx.x);
+        const uint32_t b = (uint32_t)__cvta_generic_to_shared(smem + this->col());
         f = Mat{b};
-        g = Mat{b + (uint32_t)(n * APPLY_TPB * 8)};
-        m = Mat{b + (uint32_t)(2 * n * APPLY_TPB * 8)};
+        g = Mat{b + (uint32_t)(n * APPLY_TERMS * 8)};
+        m = Mat{b + (uint32_t)(2 * n * APPLY_TERMS * 8)};
     }
     __device__ __forceinline__ uint64_t get(const Mat& x, int p) const {
         uint32_t lo, hi;
-        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(x.a + (uint32_t)(p * APPLY_TPB * 8))
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(x.a + (uint32_t)(p * APPLY_TERMS * 8))
                      : "memory");
         return ((uint64_t)hi << 32) | lo;
     }
     __device__ __forceinline__ void set(const Mat& x, int p, uint64_t v) {
-        asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(x.a + (uint32_t)(p * APPLY_TPB * 8)), "r"((uint32_t)v),
+        asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(x.a + (uint32_t)(p * APPLY_TERMS * 8)), "r"((uint32_t)v),
                      "r"((uint32_t)(v >> 32))
                      : "memory");
     }
@@ -171,20 +210,20 @@ struct SmemRows<64> {
     __device__ __forceinline__ void setF(int p, uint64_t x) { set(f, p, x); }
     __device__ __forceinline__ void setG(int p, uint64_t x) { set(g, p, x); }
     __device__ __forceinline__ void setM(int p, uint64_t x) { set(m, p, x); }
-    static size_t bytes(int n) { return (size_t)3 * n * APPLY_TPB * 8; }
+    static size_t bytes(int n) { return (size_t)3 * n * APPLY_TERMS * 8; }
 };
 
 // Row layout for n qubits.
 inline int apply_hb(int n) { return n <= 32 ? 0 : n <= 40 ? 8 : n <= 48 ? 16 : 64; }
 
-// One tile of APPLY_TPB terms through the whole gate list.
-template <int HB, class Gates>
+// One tile of APPLY_TERMS terms through the whole gate list.
+template <int HB, int TPT, class Gates>
 __device__ __forceinline__ void apply_tile(const TermsView T, const Gates gates, int64_t n_gates, int64_t tile,
                                            uint64_t* smem) {
     const int n = T.n;
-    const int64_t a = tile * APPLY_TPB + threadIdx.x;   // cap % APPLY_TPB == 0
-    SmemRows<HB> R(smem, n);
-    for (int p = 0; p < n; ++p) {
+    SmemRows<HB, TPT> R(smem, n);
+    const int64_t a = tile * APPLY_TERMS + R.col();   // cap % APPLY_TERMS == 0
+    for (int p = R.part(); p < n; p += TPT) {
         R.setF(p, T.F[(int64_t)p * T.cap + a]);
         R.setG(p, T.G[(int64_t)p * T.cap + a]);
         R.setM(p, T.M[(int64_t)p * T.cap + a]);
@@ -205,13 +244,16 @@ __device__ __forceinline__ void apply_tile(const TermsView T, const Gates gates,
             apply_gate(R, S, n, nmask, g);
         }
     }
-    for (int p = 0; p < n; ++p) {
+    R.sync();
+    for (int p = R.part(); p < n; p += TPT) {   // a lane's own rows were last written by it
         T.F[(int64_t)p * T.cap + a] = R.F(p);
         T.G[(int64_t)p * T.cap + a] = R.G(p);
         T.M[(int64_t)p * T.cap + a] = R.M(p);
     }
-    T.glo[a] = S.glo; T.ghi[a] = S.ghi; T.v[a] = S.v; T.s[a] = S.s;
-    T.omega[a] = omega_pack(S.k, S.zero, S.h);
+    if (R.part() == 0) {
+        T.glo[a] = S.glo; T.ghi[a] = S.ghi; T.v[a] = S.v; T.s[a] = S.s;
+        T.omega[a] = omega_pack(S.k, S.zero, S.h);
+    }
 }
 
 // The gate list of one launch is a kernel parameter (at most APPLY_PARAM_GATES gates;
@@ -230,11 +272,11 @@ struct GatesGlobal {
     __device__ __forceinline__ lrs_gate operator[](int64_t i) const { return p[i]; }
 };
 
-template <int HB>
-__global__ void __launch_bounds__(APPLY_TPB) k_apply_clifford(TermsView T, const __grid_constant__ GateList G,
-                                                              int n_gates) {
+template <int HB, int TPT>
+__global__ void __launch_bounds__(APPLY_TERMS * TPT) k_apply_clifford(TermsView T, const __grid_constant__ GateList G,
+                                                                      int n_gates) {
     extern __shared__ uint64_t smem[];
-    apply_tile<HB>(T, GatesParam{&G}, n_gates, blockIdx.x, smem);
+    apply_tile<HB, TPT>(T, GatesParam{&G}, n_gates, blockIdx.x, smem);
 }
 
 // Several circuits of uneven chi in one launch: block b runs global tile b; the
@@ -250,15 +292,16 @@ struct ApplyBatch {
     int64_t n_gates[LRS_APPLY_BATCH_MAX];
 };
 
-template <int HB>
-__global__ void __maxnreg__(168) k_apply_clifford_batch(const __grid_constant__ ApplyBatch B) {
+template <int HB, int TPT>
+__global__ void __maxnreg__(168)
+    k_apply_clifford_batch(const __grid_constant__ ApplyBatch B) {
     extern __shared__ uint64_t smem[];
     const int64_t tile = blockIdx.x;
     int c = 0;
 #pragma unroll 1
     for (int i = 1; i < B.count; ++i)
         if (B.first_tile[i] <= tile) c = i;
-    apply_tile<HB>(B.T[c], GatesGlobal{B.gates[c]}, B.n_gates[c], tile - B.first_tile[c], smem);
+    apply_tile<HB, TPT>(B.T[c], GatesGlobal{B.gates[c]}, B.n_gates[c], tile - B.first_tile[c], smem);
 }
 
 // ---- sample x from single terms (Sec. 4.1, "Simulating measurements") --------------
@@ -315,33 +358,39 @@ lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64
     return launch_apply_clifford_range(ctx, gates_host, n_gates, ctx->cap, st);
 }
 
-template <int HB>
+template <int HB, int TPT>
 static lrs_status launch_apply_hb(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, int64_t blocks,
                                   cudaStream_t st) {
-    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford<HB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SmemRows<HB>::bytes(64)));
+    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford<HB, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SmemRows<HB, TPT>::bytes(64)));
     static thread_local GateList G;
     for (int64_t i0 = 0; i0 < n_gates; i0 += APPLY_PARAM_GATES) {
         const int len = (int)std::min<int64_t>(APPLY_PARAM_GATES, n_gates - i0);
         memcpy(G.g, gates_host + i0, (size_t)len * sizeof(lrs_gate));
-        k_apply_clifford<HB><<<(unsigned)blocks, APPLY_TPB, SmemRows<HB>::bytes(ctx->n), st>>>(ctx->view(), G, len);
+        k_apply_clifford<HB, TPT><<<(unsigned)blocks, APPLY_TERMS * TPT, SmemRows<HB, TPT>::bytes(ctx->n), st>>>(
+            ctx->view(), G, len);
         LRS_LAUNCH_CHECK("apply_clifford kernel");
     }
     return LRS_OK;
 }
 
 // The gate list (host memory, read before return) on the terms of the first
-// ceil(n_terms / APPLY_TPB) tiles only.
+// ceil(n_terms / APPLY_TERMS) tiles only.
 lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, int64_t n_terms,
                                        cudaStream_t st) {
     if (n_terms > ctx->cap) n_terms = ctx->cap;
-    const int64_t blocks = (n_terms + APPLY_TPB - 1) / APPLY_TPB;
+    const int64_t blocks = (n_terms + APPLY_TERMS - 1) / APPLY_TERMS;
     if (blocks == 0 || n_gates == 0) return LRS_OK;
     switch (apply_hb(ctx->n)) {
-        case 0: return launch_apply_hb<0>(ctx, gates_host, n_gates, blocks, st);
-        case 8: return launch_apply_hb<8>(ctx, gates_host, n_gates, blocks, st);
-        case 16: return launch_apply_hb<16>(ctx, gates_host, n_gates, blocks, st);
-        default: return launch_apply_hb<64>(ctx, gates_host, n_gates, blocks, st);
+        case 0: return launch_apply_hb<0, 1>(ctx, gates_host, n_gates, blocks, st);
+        case 8: return launch_apply_hb<8, 1>(ctx, gates_host, n_gates, blocks, st);
+        case 16: return launch_apply_hb<16, 1>(ctx, gates_host, n_gates, blocks, st);
+        default:
+            switch (ctx->tune_apply_lanes) {
+                case 1: return launch_apply_hb<64, 1>(ctx, gates_host, n_gates, blocks, st);
+                case 4: return launch_apply_hb<64, 4>(ctx, gates_host, n_gates, blocks, st);
+                default: return launch_apply_hb<64, 2>(ctx, gates_host, n_gates, blocks, st);
+            }
     }
 }
 
@@ -356,12 +405,12 @@ lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint6
 }
 
 // The circuits of one batch share the layout of the widest one (a narrower tableau
-// keeps zero high bits).
-template <int HB>
+// keeps zero high bits) and the lane split of the first context.
+template <int HB, int TPT>
 static lrs_status launch_apply_batch_hb(const ApplyBatch& B, int64_t tiles, int nmax, cudaStream_t st) {
-    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford_batch<HB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SmemRows<HB>::bytes(64)));
-    k_apply_clifford_batch<HB><<<(unsigned)tiles, APPLY_TPB, SmemRows<HB>::bytes(nmax), st>>>(B);
+    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford_batch<HB, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SmemRows<HB, TPT>::bytes(64)));
+    k_apply_clifford_batch<HB, TPT><<<(unsigned)tiles, APPLY_TERMS * TPT, SmemRows<HB, TPT>::bytes(nmax), st>>>(B);
     LRS_LAUNCH_CHECK("batched apply_clifford kernel");
     return LRS_OK;
 }
@@ -382,16 +431,21 @@ lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cuda
             B.gates[i] = c->gates_dev;
             B.n_gates[i] = c->batch_n_gates;
             B.first_tile[i] = tiles;
-            tiles += c->cap / APPLY_TPB;
+            tiles += c->cap / APPLY_TERMS;
             if (c->n > nmax) nmax = c->n;
         }
         B.first_tile[B.count] = tiles;
         lrs_status rc;
         switch (apply_hb(nmax)) {
-            case 0: rc = launch_apply_batch_hb<0>(B, tiles, nmax, st); break;
-            case 8: rc = launch_apply_batch_hb<8>(B, tiles, nmax, st); break;
-            case 16: rc = launch_apply_batch_hb<16>(B, tiles, nmax, st); break;
-            default: rc = launch_apply_batch_hb<64>(B, tiles, nmax, st); break;
+            case 0: rc = launch_apply_batch_hb<0, 1>(B, tiles, nmax, st); break;
+            case 8: rc = launch_apply_batch_hb<8, 1>(B, tiles, nmax, st); break;
+            case 16: rc = launch_apply_batch_hb<16, 1>(B, tiles, nmax, st); break;
+            default:
+                switch (ctxs[base]->tune_apply_lanes) {
+                    case 1: rc = launch_apply_batch_hb<64, 1>(B, tiles, nmax, st); break;
+                    case 4: rc = launch_apply_batch_hb<64, 4>(B, tiles, nmax, st); break;
+                    default: rc = launch_apply_batch_hb<64, 2>(B, tiles, nmax, st); break;
+                }
         }
         if (rc != LRS_OK) return rc;
     }

@@ -159,8 +159,8 @@ __device__ __forceinline__ void prop_h_row(Rows& R, const Mat& X, const Mat& Y, 
     const uint32_t fs = ((k.qh ? fh : fl) >> k.qs) & k.a;
     Mnl ^= fl & k.aql;
     Mnh ^= fh & k.aqh;
-    add2 = 2u * add2 + f2;
-    sub1 = 2u * sub1 + fs;
+    add2 = (add2 << Rows::kStep) + f2;   // own rows are kStep apart
+    sub1 = (sub1 << Rows::kStep) + fs;
     if (FAN) {
         R.set(X, p, ((uint64_t)Xnh << 32) | Xnl);
         R.set(Y, p, ((uint64_t)Ynh << 32) | Ynl);
@@ -191,12 +191,18 @@ __device__ __forceinline__ void prop_h_rows(Rows& R, int n, const HRowMasks& k0,
     const auto Y = k.first ? R.matF() : R.matG();
     const auto Mm = R.matM();
     uint32_t ah = 0, sh = 0, al = 0, sl = 0;
+    // this lane's rows: p = part (mod kStep), walked downwards in each 32-row half; the
+    // bit of row p lands at p - (lowest own row of the half) and is shifted into place
+    constexpr int ST = Rows::kStep;
+    const int part = R.part();
+    const int top = n - 1 - ((n - 1 - part) & (ST - 1));
 #pragma unroll (Rows::kRowUnroll)
-    for (int p = n - 1; p >= 32; --p) prop_h_row<FAN>(R, X, Y, Mm, p, k, ah, sh);
+    for (int p = top; p >= 32; p -= ST) prop_h_row<FAN>(R, X, Y, Mm, p, k, ah, sh);
+    const int lt = (n < 32 ? n : 32) - 1;
 #pragma unroll (Rows::kRowUnroll)
-    for (int p = (n < 32 ? n : 32) - 1; p >= 0; --p) prop_h_row<FAN>(R, X, Y, Mm, p, k, al, sl);
-    add2 = ((uint64_t)ah << 32) | al;
-    sub1 = ((uint64_t)sh << 32) | sl;
+    for (int p = lt - ((lt - part) & (ST - 1)); p >= 0; p -= ST) prop_h_row<FAN>(R, X, Y, Mm, p, k, al, sl);
+    add2 = R.combine(((uint64_t)(ah << part) << 32) | (al << part));
+    sub1 = R.combine(((uint64_t)(sh << part) << 32) | (sl << part));
 }
 
 // Prop. (prop:H): U_H(|t> + i^delta |u>) = sqrt2 e^{i pi k1/4} W_C W_H |s'> for t != u.
@@ -242,6 +248,7 @@ __device__ __forceinline__ void prop_h(Rows& R, TermRegs& T, int n, uint64_t t, 
     k.mPl = first ? k.ml : 0u; k.mPh = first ? k.mh : 0u;
     k.mFl = first ? k.m1l : k.ml; k.mFh = first ? k.m1h : k.mh;
     uint64_t add2 = 0, sub1 = 0;
+    R.sync();   // every lane of the term has read the rows the row pass rewrites
     // The warp skips the fan-out when no active term has one (e.g. H on |0>), and the
     // row pass altogether when no term needs R[S_q] either.
     const unsigned am = __activemask();
@@ -302,10 +309,12 @@ __device__ __forceinline__ void gate_proj(Rows& R, TermRegs& T, int n, uint64_t 
 }
 
 // Left multiplications (Sec. 4.1 update rules).
+// With several lanes per term (Rows::kStep > 1) every lane keeps the same scalars and
+// only the owner of a row writes it; apply_gate starts each gate with R.sync().
 template <class Rows>
 __device__ __forceinline__ void gate_s(Rows& R, TermRegs& T, int q, uint32_t dg) {
     // S: dg = 3 (gamma_q -= 1); S^dagger: dg = 1; both M_q ^= G_q.
-    R.setM(q, R.M(q) ^ R.G(q));
+    if (R.own(q)) R.setM(q, R.M(q) ^ R.G(q));
     gamma_set(T, q, (gamma_get(T, q) + dg) & 3u);
 }
 template <class Rows>
@@ -317,21 +326,25 @@ template <class Rows>
 __device__ __forceinline__ void gate_cz(Rows& R, TermRegs& T, int q, int r) {
     (void)T;
     const uint64_t Gq = R.G(q), Gr = R.G(r);
-    R.setM(q, R.M(q) ^ Gr);
-    R.setM(r, R.M(r) ^ Gq);
+    if (R.own(q)) R.setM(q, R.M(q) ^ Gr);
+    if (R.own(r)) R.setM(r, R.M(r) ^ Gq);
 }
 template <class Rows>
 __device__ __forceinline__ void gate_cx(Rows& R, TermRegs& T, int q, int r) {
     const uint64_t Mq = R.M(q), Fr = R.F(r);
     const uint32_t g = (gamma_get(T, q) + gamma_get(T, r) + 2u * par64(Mq & Fr)) & 3u;
     gamma_set(T, q, g);
-    R.setG(r, R.G(r) ^ R.G(q));
-    R.setF(q, R.F(q) ^ Fr);
-    R.setM(q, Mq ^ R.M(r));
+    R.sync();   // every lane has read the pre-gate M_q before its owner rewrites it
+    if (R.own(r)) R.setG(r, R.G(r) ^ R.G(q));
+    if (R.own(q)) {
+        R.setF(q, R.F(q) ^ Fr);
+        R.setM(q, Mq ^ R.M(r));
+    }
 }
 
 template <class Rows>
 __device__ __forceinline__ void apply_gate(Rows& R, TermRegs& T, int n, uint64_t nmask, lrs_gate g) {
+    R.sync();   // rows written by the term's other lanes in the previous gate are visible
     switch (g.op) {
         case LRS_OP_H: gate_h(R, T, n, nmask, g.q); break;
         case LRS_OP_S: gate_s(R, T, g.q, 3u); break;

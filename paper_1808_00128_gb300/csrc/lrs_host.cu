@@ -238,6 +238,34 @@ extern "C" lrs_status lrs_lower_circuit(int32_t n, const lrs_circuit_op* ops, in
     return emit(L, gates, gates_cap, n_gates, slots, slots_cap, n_slots, k_gates, k_cap, n_k_gates);
 }
 
+extern "C" lrs_status lrs_decomposition_stats(const lrs_slot* slots, int64_t n_slots, double* l1_norm,
+                                              int64_t* exact_chi, double* log2_exact_chi) {
+    if (n_slots < 0 || (n_slots > 0 && !slots)) return lrs_fail(LRS_ERR_ARG, "bad slot table");
+    double l1 = 1.0, lg = 0.0;
+    bool fits = true;
+    int64_t chi = 1;
+    for (int64_t p = 0; p < n_slots; ++p) {
+        const lrs_slot& sl = slots[p];
+        if (sl.n_choices < 1 || sl.n_choices > LRS_MAX_CHOICES)
+            return lrs_fail(LRS_ERR_ARG, "slot %lld: n_choices %d", (long long)p, sl.n_choices);
+        double norm = 0.0;
+        int64_t nz = 0;
+        for (int j = 0; j < sl.n_choices; ++j) {
+            norm += hypot(sl.c_re[j], sl.c_im[j]);
+            nz += (sl.c_re[j] != 0.0 || sl.c_im[j] != 0.0) ? 1 : 0;
+        }
+        l1 *= norm;
+        lg += log2((double)(nz > 0 ? nz : 1));
+        if (nz == 0) chi = 0;
+        else if (fits && chi > ((int64_t)1 << 62) / nz) fits = false;
+        else if (fits) chi *= nz;
+    }
+    if (l1_norm) *l1_norm = l1;
+    if (exact_chi) *exact_chi = fits ? chi : -1;
+    if (log2_exact_chi) *log2_exact_chi = lg;
+    return LRS_OK;
+}
+
 // ---------------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------------
@@ -552,13 +580,13 @@ extern "C" lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_g
 }
 
 extern "C" lrs_status lrs_amplitude(lrs_ctx* c, const uint64_t* x, int64_t batch, double* out,
-                                    void* stream) {
+                                    float* err_est, void* stream) {
     if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
     if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
     if (batch < 0) return lrs_fail(LRS_ERR_ARG, "batch < 0");
     if (batch > 0 && (!x || !out)) return lrs_fail(LRS_ERR_ARG, "NULL buffer");
     LRS_CUDA(cudaSetDevice(c->device));
-    return launch_amplitude(c, x, batch, out, as_stream(stream));
+    return launch_amplitude(c, x, batch, out, err_est, as_stream(stream));
 }
 
 extern "C" lrs_status lrs_norm_estimate(lrs_ctx* c, int64_t L, uint64_t seed, double* eta,
@@ -665,6 +693,38 @@ extern "C" lrs_status lrs_norm_median_of_means(lrs_ctx* c, int64_t L, int32_t K,
     if (L < 1 || K < 1 || L * (int64_t)K > (1ll << 22)) return lrs_fail(LRS_ERR_ARG, "need L, K >= 1 and L K <= 2^22");
     LRS_CUDA(cudaSetDevice(c->device));
     return norm_mom(c, L, K, seed, estimate_host, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_sparsification_certificate(lrs_ctx* c, int64_t L, int32_t K, uint64_t seed,
+                                                      lrs_certificate* out, void* stream) {
+    if (!c || !out) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (L < 1 || K < 1 || L * (int64_t)K > (1ll << 22)) return lrs_fail(LRS_ERR_ARG, "need L, K >= 1 and L K <= 2^22");
+    LRS_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    double mom = 0.0;
+    lrs_status rc = norm_mom(c, L, K, seed, &mom, st);   // leaves the L K values in eta_buf
+    if (rc != LRS_OK) return rc;
+    const int64_t LK = L * K;
+    std::vector<double> h((size_t)LK);
+    LRS_CUDA(cudaMemcpy(h.data(), c->eta_buf, (size_t)LK * sizeof(double), cudaMemcpyDeviceToHost));
+    double mean = 0.0;
+    for (double x : h) mean += x;
+    mean /= (double)LK;
+    double var = 0.0;
+    for (double x : h) var += (x - mean) * (x - mean);
+    const double se = LK > 1 ? sqrt(var / (double)(LK - 1) / (double)LK) : INFINITY;
+    double l1 = 1.0;
+    rc = lrs_decomposition_stats(c->slots_host.data(), (int64_t)c->slots_host.size(), &l1, nullptr, nullptr);
+    if (rc != LRS_OK) return rc;
+    memset(out, 0, sizeof(*out));
+    out->omega_norm2 = mom;
+    out->stderr_mean = se;
+    out->delta2 = l1 * l1 / (double)c->chi_total;
+    out->bound = mom - 1.0 + out->delta2;
+    out->bound_upper = mom + 2.0 * se - 1.0 + out->delta2;
+    out->conclusive = (2.0 * se < out->delta2) ? 1 : 0;
+    return LRS_OK;
 }
 
 extern "C" lrs_status lrs_marginal_sample(lrs_ctx* c, lrs_ctx* work0, lrs_ctx* work1, const int32_t* qubits,
@@ -840,6 +900,10 @@ extern "C" lrs_status lrs_set_tuning(lrs_ctx* c, int32_t param, int64_t value) {
             if (value < -1 || value > 12) return lrs_fail(LRS_ERR_ARG, "norm max folds in -1..12");
             c->tune_norm_folds = value;
             return LRS_OK;
+        case LRS_TUNE_APPLY_LANES:
+            if (value != 1 && value != 2 && value != 4) return lrs_fail(LRS_ERR_ARG, "apply lanes per term: 1, 2 or 4");
+            c->tune_apply_lanes = value;
+            return LRS_OK;
         default:
             return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
     }
@@ -853,6 +917,7 @@ extern "C" lrs_status lrs_get_tuning(const lrs_ctx* c, int32_t param, int64_t* v
         case LRS_TUNE_MC_CHAINS_PER_BLOCK: *value = c->tune_mc_cg; return LRS_OK;
         case LRS_TUNE_MC_STAGES: *value = c->tune_mc_stages; return LRS_OK;
         case LRS_TUNE_NORM_MAX_FOLDS: *value = c->tune_norm_folds; return LRS_OK;
+        case LRS_TUNE_APPLY_LANES: *value = c->tune_apply_lanes; return LRS_OK;
         default: return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
     }
 }

@@ -97,6 +97,7 @@ struct lrs_ctx {
     int64_t tune_mc_cg = 64;        // Metropolis: chains per block (1..64)
     int64_t tune_mc_stages = 2;     // Metropolis: chains in flight per block (1..4)
     int64_t tune_norm_folds = 12;   // norm: terms with n - |v| <= this sum over y = G x (-1..12)
+    int64_t tune_apply_lanes = 2;   // apply_clifford, 64-bit rows (n > 48): lanes per term (1, 2, 4)
     // equatorial samples of median-of-means estimates
     double* eta_buf = nullptr;
     size_t eta_bytes = 0;
@@ -163,7 +164,8 @@ lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64
 lrs_status launch_apply_clifford_range(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, int64_t n_terms,
                                        cudaStream_t st);
 lrs_status launch_expand_terms(lrs_ctx* ctx, int64_t R, int64_t Rn, cudaStream_t st);
-lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out,
+// err (may be NULL): per-result bound on |out - exact chi-sum| (see k_amp_reduce).
+lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, double* out, float* err,
                             cudaStream_t st);
 lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, void* Q, double** amp_out,
                               cudaStream_t st);

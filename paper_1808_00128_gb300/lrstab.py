@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "liblrstab.so")
 OP = dict(H=0, S=1, SDG=2, Z=3, CX=4, CZ=5, P0=6, P1=7, SLOT=8)
 CKIND = dict(H=0, S=1, SDG=2, Z=3, CX=4, CZ=5, T=6, RZ=7, CCZ=8)
 CCZ_MODE = dict(proj=0, sum8=1)
-TUNE = dict(amp_blocks_per_sm=0, norm_max_tiles=1, mc_chains_per_block=2, norm_max_folds=3, mc_stages=4)
+TUNE = dict(amp_blocks_per_sm=0, norm_max_tiles=1, mc_chains_per_block=2, norm_max_folds=3, mc_stages=4,
+            apply_lanes=5)
 MODE = dict(exact=0, sparsify=1)
 STATUS = {0: "LRS_OK", -1: "LRS_ERR_ARG", -2: "LRS_ERR_OOM", -3: "LRS_ERR_CUDA",
           -4: "LRS_ERR_TIMEOUT", -5: "LRS_ERR_STATE", -6: "LRS_ERR_UNSUPPORTED"}
@@ -40,7 +41,7 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned",
             "lrs_apply_clifford_batch", "lrs_set_tuning", "lrs_get_tuning", "lrs_copy_terms",
             "lrs_norm_median_of_means", "lrs_marginal_sample", "lrs_lower_gadget",
-            "lrs_apply_circuit_shared"]
+            "lrs_apply_circuit_shared", "lrs_decomposition_stats", "lrs_sparsification_certificate"]
 
 
 class LrsError(RuntimeError):
@@ -69,7 +70,7 @@ def lib():
         "lrs_destroy": [vp],
         "lrs_init_terms": [vp, vp, i64, vp, i64, i64, i64, i64, i32, u64, vp],
         "lrs_apply_clifford": [vp, vp, i64, vp],
-        "lrs_amplitude": [vp, vp, i64, vp, vp],
+        "lrs_amplitude": [vp, vp, i64, vp, vp, vp],
         "lrs_norm_estimate": [vp, i64, u64, vp, vp, vp],
         "lrs_sample_terms": [vp, i64, u64, vp, vp, vp],
         "lrs_chains_init": [vp, i64, vp, vp],
@@ -98,6 +99,8 @@ def lib():
         "lrs_norm_median_of_means": [vp, i64, i32, u64, vp, vp],
         "lrs_marginal_sample": [vp, vp, vp, vp, i32, i64, i32, u64, vp, vp, vp],
         "lrs_get_tuning": [vp, i32, vp],
+        "lrs_decomposition_stats": [vp, i64, vp, vp, vp],
+        "lrs_sparsification_certificate": [vp, i64, i32, u64, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -145,6 +148,10 @@ def circuit_ops(ops) -> np.ndarray:
     return arr
 
 
+CERT_DT = np.dtype([("omega_norm2", "<f8"), ("stderr_mean", "<f8"), ("delta2", "<f8"), ("bound", "<f8"),
+                    ("bound_upper", "<f8"), ("conclusive", "<i4"), ("reserved", "<i4")])
+
+
 class Lowered:
     """Lowered circuit: gates (with SLOT entries), slot tables and K_j gate lists, on
     n_total qubits (the circuit's own n, or n + tau for the gadget form)."""
@@ -153,39 +160,31 @@ class Lowered:
         self.gates, self.slots, self.kgates = gates, slots, kgates
         self.n_total = n_total
 
+    def _stats(self):
+        l1, chi, lg = C.c_double(0.0), C.c_int64(0), C.c_double(0.0)
+        slots = np.ascontiguousarray(self.slots)
+        _check(lib().lrs_decomposition_stats(_ptr(slots), len(slots), C.byref(l1), C.byref(chi), C.byref(lg)))
+        return l1.value, chi.value, lg.value
+
     @property
     def exact_chi(self) -> int:
-        out = 1
-        for s in self.slots:
-            nz = int(np.count_nonzero((s["c_re"][: s["n_choices"]] != 0) |
-                                      (s["c_im"][: s["n_choices"]] != 0)))
-            out *= nz
-        return out
-
+        """Terms of the exact enumeration (lrs_decomposition_stats; -1 above 2^62)."""
+        return self._stats()[1]
 
     @property
     def l1_norm(self) -> float:
-        """||c||_1 of the whole decomposition: the product over slots of sum_j |c_j|
-        (Sec. 5.2; the sparsification error is delta^2 = ||c||_1^2 / chi)."""
-        out = 1.0
-        for s in self.slots:
-            k = s["n_choices"]
-            out *= float(np.sum(np.hypot(s["c_re"][:k], s["c_im"][:k])))
-        return out
+        """||c||_1 of the whole decomposition (lrs_decomposition_stats)."""
+        return self._stats()[0]
 
 
-def sparsification_certificate(sim: "Simulator", lowered: Lowered, L: int, K: int, seed: int) -> dict:
-    """Lemma (Sparsification tail bound): for Omega the sparsified state on sim's chi
-    terms, ||psi - Omega||^2 <= <Omega|Omega> - 1 + delta^2 with high probability,
-    delta^2 = ||c||_1^2 / chi; <Omega|Omega> is estimated by the median of K means of L
-    equatorial samples."""
-    eta = sim.norm_estimate(L * K, seed).cpu().numpy()
-    means = eta.reshape(K, L).mean(axis=1)
-    omega2 = float(np.median(means))            # as lrs_norm_median_of_means
-    stderr = float(eta.std(ddof=1) / np.sqrt(eta.size)) if eta.size > 1 else float("nan")
-    delta2 = lowered.l1_norm ** 2 / sim.chi_total
-    return {"omega_norm2": omega2, "stderr": stderr, "delta2": delta2, "bound": omega2 - 1.0 + delta2,
-            "bound_plus_2_stderr": omega2 + 2 * stderr - 1.0 + delta2, "L": L, "K": K}
+def sparsification_certificate(sim: "Simulator", L: int, K: int, seed: int, stream=None) -> dict:
+    """lrs_sparsification_certificate: Lemma (Sparsification tail bound) for the
+    sparsified state held by `sim`."""
+    out = np.zeros(1, CERT_DT)
+    _check(lib().lrs_sparsification_certificate(sim._h, L, K, seed & (2 ** 64 - 1), _ptr(out), _stream(stream)))
+    r = {k: float(out[0][k]) for k in ("omega_norm2", "stderr_mean", "delta2", "bound", "bound_upper")}
+    r.update(conclusive=bool(out[0]["conclusive"]), L=L, K=K)
+    return r
 
 
 def lower_circuit(n: int, ops, ccz_mode: str = "proj", method: str = "sum") -> Lowered:
@@ -282,12 +281,13 @@ class Simulator:
         sharing the work of common choice prefixes."""
         _check(lib().lrs_apply_circuit_shared(self._h, _ptr(gates), len(gates), _stream(stream)))
 
-    def amplitude(self, x, out=None, stream=None):
-        """x: int64/uint64 CUDA tensor [B] -> float64 CUDA tensor [B, 2] (Re, Im)."""
+    def amplitude(self, x, out=None, err=None, stream=None):
+        """x: int64/uint64 CUDA tensor [B] -> float64 CUDA tensor [B, 2] (Re, Im).
+        err: optional float32 CUDA tensor [B] receiving the per-result error bound."""
         import torch
         if out is None:
             out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
-        _check(lib().lrs_amplitude(self._h, _ptr(x), x.numel(), _ptr(out), _stream(stream)))
+        _check(lib().lrs_amplitude(self._h, _ptr(x), x.numel(), _ptr(out), _ptr(err), _stream(stream)))
         return out
 
     def amplitude_noalloc(self, x, out, stream=None):

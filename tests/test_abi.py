@@ -104,3 +104,18 @@ def test_lowered_l1_norm_matches_oracle_tables():
         low = lrstab.lower_circuit(cfg["n"], cfg["ops"])
         _, slots = decomp.lower(cfg["ops"])
         assert low.l1_norm == pytest.approx(decomp.l1_norm(slots), rel=1e-12)
+
+
+def test_decomposition_stats_match_oracle_tables(lib):
+    """lrs_decomposition_stats: ||c||_1 and the exact term count of the lowered slot
+    tables equal the oracle's, with -1 once the count exceeds 2^62."""
+    import math
+    for cfg in (workloads.config_tiny(), workloads.config_mid(), workloads.config_qaoa(),
+                workloads.config_hidden_shift()):
+        low = lrstab.lower_circuit(cfg["n"], cfg["ops"])
+        _, slots = decomp.lower(cfg["ops"])
+        l1, chi, lg = low._stats()
+        assert l1 == pytest.approx(decomp.l1_norm(slots), rel=1e-12)
+        want = decomp.exact_chi(slots)
+        assert chi == (want if want <= 2 ** 62 else -1)
+        assert lg == pytest.approx(math.log2(want), rel=1e-12)

@@ -47,9 +47,45 @@ def test_norm_op_model_by_route():
     assert m[2] > 12
 
 
-def test_units_per_step():
-    chi = 1 << 16
-    assert bench.units_per_step(chi) == chi * (bench.B_X + bench.C_CH * (bench.T_MC + 1))
+def test_units_and_launches_per_step():
+    chi = 1 << 20
+    s = bench.SHAPES["qaoa"]
+    assert bench.units_per_step(chi, s["B"], s["C"], s["T"]) == chi * (4096 + 256 * 65)
+    # init, apply, amplitude (2), norm (4), chain starts, chains_init (3), Metropolis:
+    # set + first + 4 graphs of 16 steps (33 launches each) + out
+    assert bench.launches_per_step(64) == 1 + 1 + 2 + 4 + 1 + 3 + 2 + 4 * 33 + 1
+    assert bench.launches_per_step(18) == 1 + 1 + 2 + 4 + 1 + 3 + 2 + 33 + 4 + 1
+
+
+def test_formula_and_kernel_counts():
+    """The hot-path table's formulas count every H at 30 n + 40, every (x, term) at
+    10 |x| + 30 and every (A, term) at 8 n^2 + 4 |v|^2; the kernel counts are lower."""
+    n = 4
+    low = lrstab.lower_circuit(n, [("H", 0), ("H", 1), ("CX", 0, 1)])
+    assert bench.clifford_ops_per_term(n, low, formula=True) == 2 * (30 * n + 40) + 12
+    assert bench.clifford_ops_per_term(n, low) == 2 * 40 + 12
+    assert bench.amplitude_ops_per_unit(50, 25.0, formula=True) == 280.0
+    assert bench.amplitude_ops_per_unit(50, 25.0) == 8 * 13 + 16
+    assert bench.metropolis_bytes(2, 3, 5, 10) == 5 * (2 * 3 * 24 + 2 * 160)
+
+
+def test_traffic_is_dropped_when_the_kernel_changes(monkeypatch):
+    sha = bench.source_sha16("bench.py")
+    monkeypatch.setitem(bench.TRAFFIC, "norm_estimate",
+                        {"bytes_per_unit": 2.0, "source": "bench.py", "sha16": sha, "profile": "p.md"})
+    assert bench.traffic_for("norm_estimate", 10) == (20.0, "p.md")
+    monkeypatch.setitem(bench.TRAFFIC, "norm_estimate",
+                        {"bytes_per_unit": 2.0, "source": "bench.py", "sha16": "0" * 16, "profile": "p.md"})
+    t, src = bench.traffic_for("norm_estimate", 10)
+    assert t is None and "changed" in src
+    assert bench.traffic_for("amplitude", 10) == (None, None)
+
+
+def test_oracle_step_time_model():
+    rates = {"t_build": 1e-3, "t_amp": 1e-6, "t_inner": 1e-4, "parallel": 4.0}
+    s = dict(B=10, L=3, C=2, T=4)
+    want = 8 * (1e-3 + (10 + 2 * 5) * 1e-6 + 3 * 1e-4) / 4.0
+    assert abs(bench.oracle_step_seconds(8, s, rates) - want) < 1e-15
 
 
 def test_tau_int_white_noise_and_ar1():

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import dense
+from oracle import dense, exact
 from oracle import estimators as E
 from paper_1808_00128_gb300 import lrstab, workloads
 from tests._gpu import amp_tol, oracle_terms, require_cuda
@@ -126,4 +126,86 @@ def test_hidden_shift_full_size_outputs_shift():
     got = _amps(sim, xs)
     assert abs(got[0] - 1.0) <= 1e-5
     assert np.all(np.abs(got[1:]) <= 1e-5 * 2 ** (-n / 2))
+    sim.close()
+
+
+def _amps_err(sim, xs):
+    x = torch.tensor(np.asarray(xs, dtype=np.uint64).view(np.int64), device="cuda:0")
+    err = torch.empty(len(xs), dtype=torch.float32, device="cuda:0")
+    out = sim.amplitude(x, err=err).cpu().numpy()
+    return out[:, 0] + 1j * out[:, 1], err.cpu().numpy().astype(np.float64)
+
+
+def _check_vs_oracles(got, err, terms, coefs, chs, ex, xs, n, norm):
+    """FP64 oracle within the 1e-5 tolerance; exact Z[zeta8] sum within the kernel's
+    stated per-result bound.  Returns the measured errors against the exact sums."""
+    want = np.array([E.amplitude(terms, coefs, x) for x in xs])
+    exc = np.array([exact.to_complex(ex.amplitude(terms, chs, x)) for x in xs])
+    assert np.all(np.abs(got - want) <= amp_tol(want, n, norm))
+    d = np.abs(got - exc)
+    assert np.all(d <= err), f"bound violated: max d/err = {np.max(d / np.maximum(err, 1e-300)):.3g}"
+    # the FP64 oracle is itself within 1e-12 of the exact sum
+    assert np.all(np.abs(want - exc) <= 1e-12 * np.maximum(np.abs(exc), norm * 2.0 ** (-n / 2)))
+    return d
+
+
+@pytest.mark.parametrize("n", [50, 56, 63, 64])
+def test_wide_registers_vs_oracle_and_exact(n):
+    """n = 50..64: Four-Russians tables of 13..16 chunks, packed (n <= 62) and the
+    unpacked form n > 62, against the FP64 oracle and the exact chi-sums; 300 ragged
+    terms of a sparsified Clifford+T circuit, strings drawn from the terms plus random
+    ones."""
+    require_cuda()
+    ops = workloads.random_clifford_t(n, 160, 8, seed=500 + n)
+    chi, seed = 300, 17
+    sim = _sim(n, ops, chi, "sparsify", seed=seed)
+    terms, coefs, chs = oracle_terms(n, ops, chi, "sparsify", seed=seed, parallel=True)
+    ex = exact.ExactDecomposition(n, ops, chi, "sparsify")
+    xs = [terms[i].sample(0x9E3779B9 * (i + 3)) for i in range(0, chi, 3)]
+    xs += [int(x) for x in workloads.random_bitstrings(n, 28, seed=n)]
+    got, err = _amps_err(sim, xs)
+    norm = abs(coefs[0]) * np.sqrt(chi)          # incoherent scale of the terms
+    _check_vs_oracles(got, err, terms, coefs, chs, ex, xs, n, norm)
+    assert np.count_nonzero(np.abs(got) > 0) >= len(xs) // 2
+    sim.close()
+
+
+def test_qaoa_n50_slice_vs_oracle_and_exact():
+    """The QAOA Max-E3LIN2 workload at n = 50 (gamma 0.3, beta 0.2, 116 rotation
+    slots; chi = 2^20 sparsified terms): a 256-term slice of that decomposition, strings
+    sampled from the slice's terms plus random ones, against the FP64 oracle and the
+    exact chi-sums, with the per-result bound checked."""
+    require_cuda()
+    cfg = workloads.config_qaoa()
+    n, ops, chi_total, seed = cfg["n"], cfg["ops"], cfg["chi"], cfg["seed"]
+    alpha0, chi = 777_777, 256
+    sim = _sim(n, ops, chi, "sparsify", seed=seed, alpha0=alpha0, chi_total=chi_total)
+    terms, coefs, chs = oracle_terms(n, ops, chi_total, "sparsify", seed=seed,
+                                     alphas=range(alpha0, alpha0 + chi), parallel=True)
+    ex = exact.ExactDecomposition(n, ops, chi_total, "sparsify")
+    xs = [terms[i].sample(0x5DEECE66D * (i + 1)) for i in range(0, chi, 2)]
+    xs += [int(x) for x in workloads.random_bitstrings(n, 64, seed=4)]
+    got, err = _amps_err(sim, xs)
+    norm = abs(coefs[0]) * np.sqrt(chi)
+    d = _check_vs_oracles(got, err, terms, coefs, chs, ex, xs, n, norm)
+    scale = np.maximum(np.abs(got), norm * 2.0 ** (-n / 2))
+    assert np.max(d / scale) < 1e-6
+    assert np.count_nonzero(np.abs(got) > 0) >= 100
+    sim.close()
+
+
+def test_error_bound_full_size_mid():
+    """At the full n = 40, 2^16-term size the stated bound is finite, positive where
+    terms contribute, and small against the 1e-5 tolerance (||psi|| ~ 1)."""
+    require_cuda()
+    cfg = workloads.config_mid()
+    n, ops, chi, seed = cfg["n"], cfg["ops"], cfg["chi"], cfg["seed"]
+    sim = _sim(n, ops, chi, "sparsify", seed=seed)
+    xs = sim.sample_terms(1024, seed=31).cpu().numpy().view(np.uint64)
+    got, err = _amps_err(sim, xs)
+    assert np.all(np.isfinite(err)) and np.all(err > 0)
+    assert np.max(err) < 1e-5 * 2.0 ** (-n / 2)
+    # the bound and the plain call agree on the values
+    plain = _amps(sim, xs)
+    assert np.array_equal(plain, got)
     sim.close()

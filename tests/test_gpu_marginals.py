@@ -5,6 +5,7 @@ follows the GPU), and the full-size hidden shift, whose output is its shift."""
 import numpy as np
 import pytest
 
+from oracle import decomp
 from oracle import estimators as E
 from oracle import marginals as MG
 from oracle import rng
@@ -93,4 +94,31 @@ def test_hidden_shift_marginals_give_the_shift():
         right, wrong = (p1, p0) if b else (p0, p1)
         assert right == pytest.approx(1.0, abs=1e-4)
         assert abs(wrong) <= 1e-6
+    sim.close()
+
+
+def test_sparsification_certificate_vs_oracle():
+    """lrs_sparsification_certificate (Lemma (Sparsification tail bound)): the median of
+    means, the standard error of the L K equatorial samples and delta^2 = ||c||_1^2 /
+    chi against the oracle's values on the same equatorial states."""
+    require_cuda()
+    n = 10
+    ops = workloads.random_clifford_t(n, 150, 8, seed=71)
+    chi, seed = 96, 5
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, 0)
+    sim.init_terms(low, chi, mode="sparsify", seed=seed)
+    sim.apply_clifford(low.gates)
+    L, K, aseed = 40, 3, 1234
+    cert = lrstab.sparsification_certificate(sim, L, K, aseed)
+    terms, coefs, _ = oracle_terms(n, ops, chi, "sparsify", seed=seed)
+    etas = np.array([E.eta(terms, coefs, E.draw_A(n, aseed, l)) for l in range(L * K)])
+    mom = MG.median_of_means(etas, L, K)
+    se = etas.std(ddof=1) / np.sqrt(etas.size)
+    delta2 = decomp.l1_norm(decomp.lower(ops)[1]) ** 2 / chi
+    assert cert["omega_norm2"] == pytest.approx(mom, rel=1e-5)
+    assert cert["stderr_mean"] == pytest.approx(se, rel=1e-4)
+    assert cert["delta2"] == pytest.approx(delta2, rel=1e-12)
+    assert cert["bound"] == pytest.approx(mom - 1 + delta2, rel=1e-4, abs=1e-6)
+    assert cert["conclusive"] == (2 * se < delta2)
     sim.close()

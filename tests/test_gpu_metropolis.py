@@ -171,3 +171,52 @@ def test_hidden_shift_chains_stay_at_the_shift():
     assert np.all(xo == np.uint64(s))
     assert np.all(np.abs(po - 1.0) <= 1e-5)
     sim.close()
+
+
+def test_chain_replay_qaoa_n50_slice():
+    """Chains on 16-byte Pauli states at the QAOA workload's width (n = 50, gamma 0.3,
+    beta 0.2): a 256-term slice of its 2^20-term sparsified decomposition, 24 chains x
+    20 steps replayed decision by decision by the oracle."""
+    require_cuda()
+    cfg = workloads.config_qaoa()
+    n, ops, chi_total, seed = cfg["n"], cfg["ops"], cfg["chi"], cfg["seed"]
+    alpha0, chi, C, T, mseed = 4096, 256, 24, 20, 4321
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, 0)
+    sim.init_terms(low, chi, mode="sparsify", seed=seed, alpha0=alpha0, chi_total=chi_total)
+    sim.apply_clifford(low.gates)
+    x0 = sim.sample_terms(C, seed=9)
+    sim.chains_init(x0)
+    trace = torch.empty((T, C), dtype=torch.int64, device="cuda:0")
+    pout = torch.empty(C, dtype=torch.float64, device="cuda:0")
+    sim.metropolis(T, seed=mseed, trace=trace, p_out=pout)
+    trace = trace.cpu().numpy().view(np.uint64)
+    pout = pout.cpu().numpy()
+    x0 = x0.cpu().numpy().view(np.uint64)
+    terms, coefs, _ = oracle_terms(n, ops, chi_total, "sparsify", seed=seed,
+                                   alphas=range(alpha0, alpha0 + chi), parallel=True)
+    close, moves = 0, 0
+    for c in range(C):
+        x = int(x0[c])
+        px = E.probability(terms, coefs, x)
+        for t in range(T):
+            j, r = E.metropolis_draws(n, mseed, c, t)
+            y = x ^ (1 << j)
+            py = E.probability(terms, coefs, y)
+            acc = int(trace[t, c]) == y
+            assert acc or int(trace[t, c]) == x
+            if px <= 0 or py >= px:
+                want = True
+            else:
+                want = r < py / px
+                if abs(py / px - r) <= 1e-4 * (py / px):
+                    close += 1
+                    want = acc
+            assert acc == want, (c, t)
+            if want:
+                x, px = y, py
+                moves += 1
+        assert abs(pout[c] - px) <= 1e-5 * max(px, 1e-300) + 1e-300
+    assert close < C * T // 50
+    assert moves > 0
+    sim.close()

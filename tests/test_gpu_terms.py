@@ -220,3 +220,51 @@ def test_sample_terms_matches_oracle_sampler():
         assert int(x[i]) == terms[a].sample(flips)
         assert abs(terms[a].amplitude(int(x[i]))) > 0
     sim.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("n", [49, 50, 57, 63, 64])
+def test_lane_split_bit_exact(n, lanes):
+    """The 64-bit-row kernel with 1, 2 or 4 lanes per term (each lane owns the rows
+    p = part mod lanes): exact decompositions with T and projector-form CCZ, every
+    term bit-exact against the oracle."""
+    require_cuda()
+    rng = random.Random(2000 + n)
+    ops = _random_circuit(n, 5 * n, 3, 2, rng)
+    chi = 2 ** 5
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, 0)
+    sim.set_tuning("apply_lanes", lanes)
+    sim.init_terms(low, chi, mode="exact")
+    sim.apply_clifford(low.gates)
+    ex = sim.export_terms()
+    terms, _, _ = oracle_terms(n, ops, chi, "exact", parallel=True)
+    for a in range(chi):
+        compare_term(ex, a, terms[a], f"n={n} lanes={lanes} term {a}")
+    sim.close()
+
+
+def test_lane_split_qaoa_n50_identical_terms():
+    """The n = 50 QAOA circuit (gamma 0.3, beta 0.2) on 2^14 sparsified terms: 1, 2 and 4
+    lanes per term give the same tableaux, phases and omega for every term, and a
+    64-term sample equals the oracle bit for bit."""
+    require_cuda()
+    cfg = workloads.config_qaoa()
+    n, ops, seed = cfg["n"], cfg["ops"], cfg["seed"]
+    chi = 1 << 14
+    low = lrstab.lower_circuit(n, ops)
+    out = {}
+    for lanes in (1, 2, 4):
+        sim = lrstab.Simulator(n, 0)
+        sim.set_tuning("apply_lanes", lanes)
+        sim.init_terms(low, chi, mode="sparsify", seed=seed, chi_total=cfg["chi"])
+        sim.apply_clifford(low.gates)
+        out[lanes] = sim.export_terms()
+        sim.close()
+    for k in out[1]:
+        assert np.array_equal(out[1][k], out[2][k]), k
+        assert np.array_equal(out[1][k], out[4][k]), k
+    alphas = list(range(0, chi, chi // 64))
+    terms, _, _ = oracle_terms(n, ops, cfg["chi"], "sparsify", seed=seed, alphas=alphas, parallel=True)
+    for i, a in enumerate(alphas):
+        compare_term(out[2], a, terms[i], f"term {a}")
