@@ -594,111 +594,219 @@ def tau_int(series):
     return max(tau, 1.0)
 
 
-def sampler_study(local=0, n=20, chi=1 << 14, C=1024, T_plain=2000, T_learned=200, hidden=512,
-                  train_steps=1000, seed=0):
-    """Plain single-flip Metropolis vs Metropolis-Hastings with the learned MADE
-    proposal, on a QAOA Max-E3LIN2 circuit small enough (n=20) for the exact
-    distribution P of the sparsified state to be computed by the amplitude
-    kernel over all 2^n strings.  Returns ESS/s of both samplers and their
-    total-variation distance to P on the Hamming-weight and cost histograms."""
+def _cost_table(inst, n):
+    """Per-triple (mask, sign) of the E3LIN2 objective C(z) = 1/2 sum d z_u z_v z_w."""
+    return [((1 << u) | (1 << v) | (1 << w), d) for (u, v, w), d in inst]
+
+
+def _parity64(v):
+    """Parity of each uint64 (XOR folding)."""
+    import numpy as np
+    v = v.copy()
+    for sh in (32, 16, 8, 4, 2, 1):
+        v ^= v >> np.uint64(sh)
+    return (v & np.uint64(1)).astype(np.int64)
+
+
+def _observables(xs, n, table):
+    """Cost 2 C(z) (integer), Hamming weight and bits of uint64 strings."""
+    import numpy as np
+    xs = np.asarray(xs, dtype=np.uint64).reshape(-1)
+    bits = ((xs[:, None] >> np.arange(n, dtype=np.uint64)[None, :]) & np.uint64(1)).astype(np.int8)
+    cost2 = np.zeros(xs.size, np.int64)
+    for mask, d in table:
+        # z_u z_v z_w = (-1)^{x_u + x_v + x_w}
+        cost2 += d * (1 - 2 * _parity64(xs & np.uint64(mask)))
+    return cost2, bits.sum(axis=1), bits
+
+
+def _tv_hist(a, b_probs, offset, size):
+    import numpy as np
+    h = np.bincount(a + offset, minlength=size)[:size] / max(a.size, 1)
+    return 0.5 * float(np.abs(h - b_probs).sum())
+
+
+def _run_traced(fn, C, steps, chunk, dev):
+    """Run `steps` steps of a sampler in chunks with traces; returns (trace [steps, C]
+    on the host, per-chunk cumulative GPU seconds)."""
+    import numpy as np
+    import torch
+    trace = np.empty((steps, C), np.uint64)
+    buf = torch.empty((chunk, C), dtype=torch.int64, device=dev)
+    t, times, done = 0.0, [], 0
+    while done < steps:
+        k = min(chunk, steps - done)
+        a, b = _ev()
+        a.record()
+        fn(k, done, buf[:k])
+        b.record()
+        b.synchronize()
+        t += a.elapsed_time(b) * 1e-3
+        trace[done:done + k] = buf[:k].cpu().numpy().view(np.uint64)
+        done += k
+        times.append((done, t))
+    return trace, times
+
+
+def sampler_study(local=0, n=20, chi=1 << 14, C=1024, hidden=512, train_samples=100_000, epochs=20,
+                  plain_steps=1500, learned_steps=150, burn=100, chunk=50, tv_targets=(0.05, 0.02),
+                  ref_steps=0, seed=0, qaoa_instance=False):
+    """Plain single-flip Metropolis (Sec. 4.2) against Metropolis-Hastings with the
+    learned MADE proposal, on a QAOA Max-E3LIN2 state (gamma 0.3, beta 0.2), at equal
+    accuracy and with every cost charged.
+
+    Reference distribution: for n <= 24 the exact P of the sparsified state over all 2^n
+    strings (amplitude kernel); otherwise `ref_steps` further steps of plain chains.
+    Accuracy: total-variation distance of the pooled samples' cost histogram C(z) to
+    the reference, and the largest error of a single-bit marginal.  For each target the
+    GPU seconds each sampler needs to get there; ESS/s from the integrated
+    autocorrelation of C(z); the learned sampler is charged, besides its own steps, the
+    plain steps that produced its training samples and the training itself.
+    n = 50 with qaoa_instance=True takes the 50-variable instance of the QAOA workload."""
     import numpy as np
     import torch
     from paper_1808_00128_gb300 import lrstab, workloads
     dev = torch.device(f"cuda:{local}")
-    ops, inst = workloads.qaoa_e3lin2_circuit(n, 4, 0.3, 0.2, workloads.SEED_BASE + 20 + seed)
+    if qaoa_instance:
+        cfg = workload_config("qaoa")
+        ops, inst, dseed, chi_total = cfg["ops"], cfg["instance"], cfg["seed"], cfg["chi"]
+        n = cfg["n"]
+    else:
+        ops, inst = workloads.qaoa_e3lin2_circuit(n, 4, 0.3, 0.2, workloads.SEED_BASE + 20 + seed)
+        dseed, chi_total = workloads.SEED_BASE + 21 + seed, chi
+    table = _cost_table(inst, n)
     low = lrstab.lower_circuit(n, ops)
     sim = lrstab.Simulator(n, local)
-    sim.init_terms(low, chi, mode="sparsify", seed=workloads.SEED_BASE + 21 + seed)
+    sim.init_terms(low, chi, mode="sparsify", seed=dseed, chi_total=chi_total)
     sim.apply_clifford(low.gates)
-    allx = torch.arange(1 << n, dtype=torch.int64, device=dev)
-    amp = sim.amplitude(allx).cpu().numpy()
-    P = amp[:, 0] ** 2 + amp[:, 1] ** 2
-    P /= P.sum()
-    xs = np.arange(1 << n)
-    bits = ((xs[:, None] >> np.arange(n)[None, :]) & 1)
-    hw = bits.sum(axis=1)
-    z = 1 - 2 * bits
-    cost = np.zeros(1 << n)
-    for (u, v, w), d in inst:
-        cost += 0.5 * d * z[:, u] * z[:, v] * z[:, w]
-    cbins = np.round(2 * cost).astype(int)
-    cbins -= cbins.min()
-
-    def tv(samples):
-        s = np.asarray(samples, np.int64).reshape(-1)
-        t1 = 0.5 * np.abs(np.bincount(hw[s], minlength=n + 1) / s.size
-                          - np.bincount(hw, weights=P, minlength=n + 1)).sum()
-        nb = cbins.max() + 1
-        t2 = 0.5 * np.abs(np.bincount(cbins[s], minlength=nb) / s.size
-                          - np.bincount(cbins, weights=P, minlength=nb)).sum()
-        return float(t1), float(t2)
-
+    off = 2 * len(table) + 1
+    size = 2 * off + 1
     x0 = sim.sample_terms(C, seed=7)
-    sim.chains_init(x0)
-    sim.metropolis(200, seed=11)                      # burn-in
-    trace = torch.empty((T_plain, C), dtype=torch.int64, device=dev)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    sim.metropolis(T_plain, seed=11, step0=200, trace=trace)
-    e1.record()
-    e1.synchronize()
-    t_plain = e0.elapsed_time(e1) * 1e-3
-    tr = trace.cpu().numpy()
-    tau_p = tau_int(cost[tr])
-    ess_plain = C * T_plain / tau_p / t_plain
-    tv_plain = tv(tr)
 
-    # training data: every 10th state of the plain chains (chain samples of the method)
-    data = torch.from_numpy(tr[::10].reshape(-1).copy()).to(dev)
+    def plain(k, done, buf, step0):
+        sim.metropolis(k, seed=11, step0=step0 + done, trace=buf)
+
+    # burn-in of the plain chains
+    sim.chains_init(x0)
+    sim.metropolis(burn, seed=11)
+    # reference
+    if n <= 24:
+        allx = torch.arange(1 << n, dtype=torch.int64, device=dev)
+        amp = sim.amplitude(allx).cpu().numpy()
+        P = amp[:, 0] ** 2 + amp[:, 1] ** 2
+        P /= P.sum()
+        c_all, _, b_all = _observables(np.arange(1 << n, dtype=np.uint64), n, table)
+        ref_cost = np.bincount(c_all + off, weights=P, minlength=size)
+        ref_bits = (b_all * P[:, None]).sum(axis=0)
+        ref_kind = "exact P of the sparsified state (all 2^n strings)"
+        del amp, allx
+    else:
+        rtrace, _ = _run_traced(lambda k, d, b: plain(k, d, b, 10 ** 6), C, ref_steps, chunk, dev)
+        rc, _, rb = _observables(rtrace[::2], n, table)
+        ref_cost = np.bincount(rc + off, minlength=size) / rc.size
+        ref_bits = rb.mean(axis=0)
+        ref_kind = f"{ref_steps} steps of {C} plain chains (every 2nd step, {rc.size} samples)"
+        sim.chains_init(x0)
+        sim.metropolis(burn, seed=11)
+
+    def accuracy(trace, times):
+        """Per target: first (steps, GPU seconds) at which the pooled samples reach it."""
+        cost, _, bits = _observables(trace, n, table)
+        cost = cost.reshape(trace.shape)
+        bits = bits.reshape(trace.shape + (n,))
+        out = {}
+        for tgt in tv_targets:
+            hit = None
+            for steps, t in times:
+                tv = _tv_hist(cost[:steps].reshape(-1), ref_cost, off, size)
+                mb = float(np.abs(bits[:steps].reshape(-1, n).mean(axis=0) - ref_bits).max())
+                if tv <= tgt and mb <= tgt:
+                    hit = {"steps": steps, "gpu_s": t, "tv_cost": tv, "max_bit_err": mb}
+                    break
+            out[str(tgt)] = hit
+        tv_end = _tv_hist(cost.reshape(-1), ref_cost, off, size)
+        mb_end = float(np.abs(bits.reshape(-1, n).mean(axis=0) - ref_bits).max())
+        return out, tv_end, mb_end, cost
+
+    # plain chains
+    ptrace, ptimes = _run_traced(lambda k, d, b: plain(k, d, b, burn), C, plain_steps, chunk, dev)
+    t_plain = ptimes[-1][1]
+    p_hits, p_tv, p_mb, p_cost = accuracy(ptrace, ptimes)
+    tau_p = tau_int(p_cost)
+    ess_plain = C * plain_steps / tau_p / t_plain
+
+    # training data: plain-chain states, thinned to about one per autocorrelation time
+    thin = max(1, int(round(tau_p)))
+    need_steps = int(np.ceil(train_samples / C)) * thin
+    a, b = _ev()
+    a.record()
+    dtrace = torch.empty((need_steps, C), dtype=torch.int64, device=dev)
+    sim.metropolis(need_steps, seed=17, step0=10 ** 7, trace=dtrace)
+    data = dtrace[::thin].reshape(-1)[:train_samples].contiguous()
+    b.record()
+    b.synchronize()
+    t_data = a.elapsed_time(b) * 1e-3
+    del dtrace
     net = lrstab.MLP(n, hidden, local)
     rng = np.random.default_rng(5)
     lim1, lim2 = 1 / np.sqrt(n), 1 / np.sqrt(hidden)
     net.set_params(dict(W1=rng.uniform(-lim1, lim1, (hidden, n)), b1=rng.uniform(-lim1, lim1, hidden),
-                        W2=rng.uniform(-lim2, lim2, (hidden, hidden)),
-                        b2=rng.uniform(-lim2, lim2, hidden), W3=rng.uniform(-lim2, lim2, (n, hidden)),
-                        b3=rng.uniform(-lim2, lim2, n)))
+                        W2=rng.uniform(-lim2, lim2, (hidden, hidden)), b2=rng.uniform(-lim2, lim2, hidden),
+                        W3=rng.uniform(-lim2, lim2, (n, hidden)), b3=rng.uniform(-lim2, lim2, n)))
     bs = 1024
     net.backward(data[:bs].contiguous())   # first launches (module loading) outside the timed region
     torch.cuda.synchronize()
-    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2.record()
-    perm = torch.randperm(data.numel(), device=dev, generator=torch.Generator(device=dev).manual_seed(3))
-    for it in range(train_steps):
-        lo = (it * bs) % (data.numel() - bs)
-        net.train_step(data[perm[lo:lo + bs]].contiguous(), lr=1e-3)
-    e3.record()
-    e3.synchronize()
-    t_train = e2.elapsed_time(e3) * 1e-3
-    loss = float(net.backward(data[: 8192].contiguous()).item())
-    entropy = float(-(P[P > 0] * np.log(P[P > 0])).sum())
+    train_steps = max(1, epochs * data.numel() // bs)
+    gen = torch.Generator(device=dev).manual_seed(3)
+    a, b = _ev()
+    a.record()
+    for ep in range(epochs):
+        perm = torch.randperm(data.numel(), device=dev, generator=gen)
+        for it in range(data.numel() // bs):
+            net.train_step(data[perm[it * bs:(it + 1) * bs]].contiguous(), lr=1e-3)
+    b.record()
+    b.synchronize()
+    t_train = a.elapsed_time(b) * 1e-3
+    nll = float(net.backward(data[:8192].contiguous()).item())
 
+    # learned proposal
     sim.chains_init(x0)
     lrstab.metropolis_learned(sim, net, 20, seed=13)   # burn-in
-    ltrace = torch.empty((T_learned, C), dtype=torch.int64, device=dev)
     acc = torch.zeros(C, dtype=torch.int64, device=dev)
-    torch.cuda.synchronize()
-    e0.record()
-    lrstab.metropolis_learned(sim, net, T_learned, seed=13, step0=20, trace=ltrace, accepts=acc)
-    e1.record()
-    e1.synchronize()
-    t_learned = e0.elapsed_time(e1) * 1e-3
-    lt = ltrace.cpu().numpy()
-    tau_l = tau_int(cost[lt])
-    ess_learned = C * T_learned / tau_l / t_learned
-    tv_learned = tv(lt)
+    ltrace, ltimes = _run_traced(
+        lambda k, d, buf: lrstab.metropolis_learned(sim, net, k, seed=13, step0=20 + d, trace=buf, accepts=acc),
+        C, learned_steps, chunk, dev)
+    t_learned = ltimes[-1][1]
+    l_hits, l_tv, l_mb, l_cost = accuracy(ltrace, ltimes)
+    tau_l = tau_int(l_cost)
+    ess_learned = C * learned_steps / tau_l / t_learned
+    overhead = t_data + t_train
+    ess_learned_all = C * learned_steps / tau_l / (t_learned + overhead)
+    # effective samples above which the learned sampler, overhead included, is faster
+    gain = 1.0 / ess_plain - 1.0 / ess_learned
+    breakeven = overhead / gain if gain > 0 else None
+    matched = {}
+    for tgt in tv_targets:
+        ph, lh = p_hits[str(tgt)], l_hits[str(tgt)]
+        matched[str(tgt)] = {
+            "plain_gpu_s": ph["gpu_s"] if ph else None,
+            "learned_gpu_s": lh["gpu_s"] if lh else None,
+            "learned_gpu_s_with_overhead": (lh["gpu_s"] + overhead) if lh else None,
+            "plain_steps": ph["steps"] if ph else None, "learned_steps": lh["steps"] if lh else None}
     sim.close()
     net.close()
-    return {"workload": f"qaoa_e3lin2_n{n}_chi{chi}", "chains": C,
-            "observable": "E3LIN2 cost C(z)",
-            "plain": {"steps": T_plain, "seconds": t_plain, "tau_int": tau_p, "ess_per_s": ess_plain,
-                      "tv_hamming": tv_plain[0], "tv_cost": tv_plain[1]},
-            "learned": {"steps": T_learned, "seconds": t_learned, "tau_int": tau_l,
-                        "ess_per_s": ess_learned, "tv_hamming": tv_learned[0], "tv_cost": tv_learned[1],
-                        "acceptance": float(acc.sum().item()) / (C * T_learned),
-                        "train_seconds": t_train, "train_samples": int(data.numel()),
-                        "nll": loss, "entropy_of_P": entropy, "hidden": hidden},
-            "ess_ratio_learned_over_plain": ess_learned / ess_plain}
+    return {"workload": f"qaoa_e3lin2_n{n}_chi{chi}", "chains": C, "hidden": hidden,
+            "observable": "E3LIN2 cost C(z); single-bit marginals", "reference": ref_kind,
+            "plain": {"steps": plain_steps, "gpu_s": t_plain, "tau_int": tau_p, "ess_per_s": ess_plain,
+                      "tv_cost_end": p_tv, "max_bit_err_end": p_mb},
+            "learned": {"steps": learned_steps, "gpu_s": t_learned, "tau_int": tau_l, "ess_per_s": ess_learned,
+                        "ess_per_s_with_overhead": ess_learned_all, "tv_cost_end": l_tv, "max_bit_err_end": l_mb,
+                        "acceptance": float(acc.sum().item()) / (C * learned_steps),
+                        "train_samples": int(data.numel()), "train_steps": int(train_steps), "epochs": epochs,
+                        "data_gpu_s": t_data, "train_gpu_s": t_train, "nll": nll},
+            "ess_ratio_learned_over_plain": ess_learned / ess_plain,
+            "ess_ratio_with_overhead": ess_learned_all / ess_plain,
+            "breakeven_effective_samples": breakeven, "matched_tv": matched}
 
 
 def _ev():
@@ -1066,7 +1174,9 @@ def main():
     ess = side = None
     extra = {}
     if rank == 0 and not args.no_sampler_study:
-        ess = sampler_study(local)
+        ess = {"n20_exact_reference": sampler_study(local),
+               "n50_qaoa_instance": sampler_study(local, chi=1 << 18, qaoa_instance=True, plain_steps=600,
+                                                  learned_steps=100, ref_steps=1200, burn=100)}
     if rank == 0 and not args.no_extra:
         other = "mid" if args.workload == "qaoa" else "qaoa"
         side = side_step_study(other, local, alu, hbm)

@@ -314,6 +314,30 @@ lrs_status lrs_metropolis_step(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64
                                uint64_t* x_out_dev, double* p_out_dev, uint64_t* trace_dev,
                                void* stream);
 
+/* Term-sharded Metropolis.  Every estimator of Sec. 4 is a sum over terms, so a
+ * decomposition can be split into contiguous term ranges (lrs_init_terms' alpha0 /
+ * chi_total), one per context (one per GPU of a job).  The chain step then has one
+ * exchange: each shard forms its partial amplitudes of the proposals, the caller sums
+ * them over the shards (an all-reduce of 2 C doubles), and every shard takes the same
+ * FP64 decision from the same draws.
+ *   lrs_chains_set_amplitude  after lrs_chains_init on every shard with the same
+ *                             strings: P(x_c) = |amp_dev[c]|^2 from the summed
+ *                             amplitudes (amp_dev: 2 C doubles, Re/Im; device)
+ *   lrs_metropolis_propose    step `step` (global index) of lrs_metropolis_step's draws:
+ *                             applies the previous step's accepted flips to the Pauli
+ *                             states, draws j, writes the shard's sum over its terms of
+ *                             b <y_c|phi> into amp_dev (2 C doubles, not squared)
+ *   lrs_metropolis_accept     the FP64 accept rule of lrs_metropolis_step on the summed
+ *                             amp_dev of the same step; trace_dev (may be NULL) gets x
+ *                             after the step
+ * Steps alternate propose, accept; lrs_metropolis_step may follow on the same chains.
+ * Errors: LRS_ERR_STATE (no chains, or an accept without the propose of its step),
+ * LRS_ERR_ARG, LRS_ERR_TIMEOUT (as lrs_metropolis_step).                        */
+lrs_status lrs_chains_set_amplitude(lrs_ctx* ctx, const double* amp_dev, void* stream);
+lrs_status lrs_metropolis_propose(lrs_ctx* ctx, uint64_t seed, int64_t step, double* amp_dev, void* stream);
+lrs_status lrs_metropolis_accept(lrs_ctx* ctx, const double* amp_dev, uint64_t seed, int64_t step,
+                                 uint64_t* trace_dev, void* stream);
+
 /* ---- median of means and marginal sampling (end of Sec. 4.3) ------------------ */
 /* Copy the terms of src (tableaux, gamma, v, s, omega, coefficients, slot choices
  * and slot tables) into dst, which must have the same qubit count and device;
@@ -427,6 +451,25 @@ lrs_status lrs_metropolis_learned(lrs_ctx* ctx, lrs_mlp* mlp, int64_t steps, uin
                                   int64_t step0, uint64_t* x_out_dev, double* p_out_dev,
                                   uint64_t* trace_dev, int64_t* accepts_dev, void* stream);
 
+/* ---- failure-path test support (no counterpart in the paper) ------------------- */
+/* Every device-side wait of the library is bounded (1 s); a kernel whose wait runs out
+ * records it in a flag, waits (bounded) for the copies it has in flight, frees what it
+ * holds and returns, and the next synchronising call reports LRS_ERR_TIMEOUT.  These
+ * calls let a test make one such wait run out without faulting anything: each sets a
+ * one-shot request that the next launch of the kernel concerned takes in one block,
+ * whose first shared-memory stage then expects 16 bytes more than its copies deliver.
+ *   lrs_debug_inject_wait_timeout      the next Metropolis propose kernel of ctx: that
+ *                                      launch ends about 2 s later with one block's
+ *                                      partial sums unwritten; the next
+ *                                      lrs_metropolis_step returns LRS_ERR_TIMEOUT
+ *                                      (re-initialise the chains after it)
+ *   lrs_mlp_debug_inject_wait_timeout  the next tcgen05 GEMM of mlp: one output tile is
+ *                                      not written; lrs_mlp_get_params or
+ *                                      lrs_mlp_set_gemm then returns LRS_ERR_TIMEOUT
+ * A later call of the same kind runs normally.                                       */
+lrs_status lrs_debug_inject_wait_timeout(lrs_ctx* ctx);
+lrs_status lrs_mlp_debug_inject_wait_timeout(lrs_mlp* mlp);
+
 /* ---- export (checkpoint / bit-exact parity) ----------------------------------- */
 /* Copy local terms [first, first + count) (global index alpha0 + first ..) to host arrays (each may be NULL):
  *   F, G, M: count * n uint64, term-major (row p of term i at [i*n + p]);
@@ -466,11 +509,12 @@ lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
  *   LRS_TUNE_MC_STAGES            Metropolis: chains whose inputs a block keeps
  *                                 in flight in shared memory (1..4, 2; 12 KB each)
  *   LRS_TUNE_APPLY_LANES          apply_clifford for n > 48 (64-bit rows): lanes
- *                                 per term (1, 2 or 4; default 2).  The lanes of a
+ *                                 per term (1, 2 or 4; default 1).  The lanes of a
  *                                 term share its tableau in shared memory and split
- *                                 its rows, so more warps share an SM; results are
- *                                 bit-identical for every value.  Narrower tableaux
- *                                 take one lane per term.
+ *                                 its rows, so more warps share an SM, at the cost of
+ *                                 repeating the per-gate scalar work in every lane;
+ *                                 results are bit-identical for every value.
+ *                                 Narrower tableaux take one lane per term.
  */
 enum {
     LRS_TUNE_AMP_BLOCKS_PER_SM = 0,

@@ -123,13 +123,21 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     if (tid == 0) abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
+    // err[1] is a one-shot test request (lrs_debug_inject_wait_timeout): block (0, 0)
+    // takes it and makes its first stage expect 16 bytes that no copy delivers, so the
+    // stage's bounded wait runs out
+    uint32_t extra = 0;
+    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && *(volatile int*)&err[1] != 0) {
+        *(volatile int*)&err[1] = 0;
+        extra = 16;
+    }
     auto issue = [&](int ci, int si) {   // thread 0: chain ci into stage si
         McStage& S = stage[si];
         const uint32_t bar = mc_smem(&full[si]);
         const int pj = spj[ci], j = sj[ci];
         const int64_t c = c0 + ci;
         const uint32_t qb = CQ ? MC_TERMS * 12 : MC_TERMS * 16;
-        mc_bar_expect(bar, (uint32_t)(qb + 2 * sizeof(S.fj) + (pj >= 0 ? 2 * sizeof(S.fp) : 0)));
+        mc_bar_expect(bar, (uint32_t)(qb + 2 * sizeof(S.fj) + (pj >= 0 ? 2 * sizeof(S.fp) : 0)) + (ci == 0 ? extra : 0u));
         if (CQ) {
             mc_bulk_load(mc_smem(S.q), reinterpret_cast<const uint64_t*>(Q) + c * T.cap + a0, MC_TERMS * 8, bar);
             mc_bulk_load(mc_smem(S.q + MC_TERMS * 8),
@@ -344,6 +352,65 @@ __global__ void k_mh_accept(const double* __restrict__ ampy, const uint64_t* __r
     if (trace) trace[c] = cx[c];
 }
 
+// Term-sharded steps: the FP64 sum over tiles of each chain's partial <y|psi_shard>
+// (not squared: the shards' sums add before P(y) is formed).
+__global__ void k_metro_partial_out(const float2* __restrict__ partial, int64_t n_tiles, double* __restrict__ amp) {
+    const int64_t c = blockIdx.x;
+    double re = 0.0, im = 0.0;
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const float2 p = partial[c * n_tiles + t];
+        re += (double)p.x;
+        im += (double)p.y;
+    }
+    __shared__ double sre[256], sim[256];
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            sre[threadIdx.x] += sre[threadIdx.x + off];
+            sim[threadIdx.x] += sim[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        amp[2 * c] = sre[0];
+        amp[2 * c + 1] = sim[0];
+    }
+}
+
+// The FP64 accept test of step `step` (Sec. 4.2) on the summed amplitudes of the
+// proposals: the same rule and draws as k_metro_accept.
+__global__ void k_metro_accept_amp(const double* __restrict__ amp, int64_t C, uint64_t seed, int64_t step,
+                                   const int32_t* __restrict__ jprop, uint64_t* cx, double* cp, int32_t* pend,
+                                   uint64_t* trace) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const double py = amp[2 * c] * amp[2 * c] + amp[2 * c + 1] * amp[2 * c + 1];
+    const double px = cp[c];
+    const int j = jprop[c];
+    bool acc;
+    if (py >= px) {
+        acc = true;
+    } else {
+        const double r = sm64_unit(sm64_at(sm64_key(seed, (uint64_t)c), (uint64_t)(2 * step + 1)));
+        acc = r < py / px;
+    }
+    if (acc) {
+        cx[c] ^= 1ull << j;
+        cp[c] = py;
+        pend[c] = j;
+    } else {
+        pend[c] = -1;
+    }
+    if (trace) trace[c] = cx[c];
+}
+
+__global__ void k_chains_set_prob(const double* __restrict__ amp, int64_t C, double* cp) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C) cp[c] = amp[2 * c] * amp[2 * c] + amp[2 * c + 1] * amp[2 * c + 1];
+}
+
 __global__ void k_metro_out(int64_t C, const uint64_t* cx, const double* cp, uint64_t* x_out,
                             double* p_out) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -431,6 +498,17 @@ static lrs_status mc_graph(lrs_ctx* ctx, float2* partial, int32_t* jprop, cudaGr
     return LRS_OK;
 }
 
+// The mapped host words of the propose kernels: [0] a stage wait gave up, [1] a
+// one-shot test request (lrs_debug_inject_wait_timeout).
+lrs_status mc_flags(lrs_ctx* ctx) {
+    if (ctx->mc_err_h) return LRS_OK;
+    LRS_CUDA(cudaHostAlloc((void**)&ctx->mc_err_h, 2 * sizeof(int), cudaHostAllocMapped));
+    ctx->mc_err_h[0] = 0;
+    ctx->mc_err_h[1] = 0;
+    LRS_CUDA(cudaHostGetDevicePointer((void**)&ctx->mc_err_d, ctx->mc_err_h, 0));
+    return LRS_OK;
+}
+
 lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t step0,
                              uint64_t* x_out, double* p_out, uint64_t* trace, cudaStream_t st) {
     const int64_t C = ctx->n_chains;
@@ -440,11 +518,8 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
     lrs_status rc = lrs_scratch(ctx, part_bytes + (size_t)C * sizeof(int32_t) + 256, &scr);
     if (rc != LRS_OK) return rc;
     if (!ctx->mc_par) LRS_CUDA(cudaMalloc(&ctx->mc_par, sizeof(McParams)));
-    if (!ctx->mc_err_h) {
-        LRS_CUDA(cudaHostAlloc((void**)&ctx->mc_err_h, sizeof(int), cudaHostAllocMapped));
-        *ctx->mc_err_h = 0;
-        LRS_CUDA(cudaHostGetDevicePointer((void**)&ctx->mc_err_d, ctx->mc_err_h, 0));
-    }
+    lrs_status rf = mc_flags(ctx);
+    if (rf != LRS_OK) return rf;
     if (*(volatile int*)ctx->mc_err_h) {   // set by an earlier propose launch that gave up waiting
         *(volatile int*)ctx->mc_err_h = 0;
         return lrs_fail(LRS_ERR_TIMEOUT, "a Metropolis propose kernel gave up waiting for its copies");
@@ -471,6 +546,64 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
     if (rc != LRS_OK) return rc;
     k_metro_out<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->cx, ctx->cp, x_out, p_out);
     LRS_LAUNCH_CHECK("metropolis out kernel");
+    return LRS_OK;
+}
+
+// One term-sharded proposal: every chain's partial amplitude of its proposal y over
+// this context's terms (the pending flip of the previous step is applied to Q first).
+lrs_status launch_metropolis_propose(lrs_ctx* ctx, uint64_t seed, int64_t step, double* amp, cudaStream_t st) {
+    const int64_t C = ctx->n_chains;
+    const int64_t n_tiles = ctx->cap / MC_TERMS;
+    void* scr = nullptr;
+    lrs_status rc = lrs_scratch(ctx, (size_t)C * n_tiles * sizeof(float2), &scr);
+    if (rc != LRS_OK) return rc;
+    if (!ctx->mc_par) LRS_CUDA(cudaMalloc(&ctx->mc_par, sizeof(McParams)));
+    size_t have = ctx->jbuf_bytes;
+    if ((rc = lrs_ensure((void**)&ctx->jbuf, &have, (size_t)C * sizeof(int32_t))) != LRS_OK) return rc;
+    ctx->jbuf_bytes = have;
+    if ((rc = mc_flags(ctx)) != LRS_OK) return rc;
+    if (*(volatile int*)ctx->mc_err_h) {
+        *(volatile int*)ctx->mc_err_h = 0;
+        return lrs_fail(LRS_ERR_TIMEOUT, "a Metropolis propose kernel gave up waiting for its copies");
+    }
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(MC_ST * sizeof(McStage))));
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(MC_ST * sizeof(McStage))));
+    k_mc_set<<<1, 1, 0, st>>>(ctx->mc_par, seed, step);
+    k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->mc_par, ctx->n, ctx->jbuf);
+    LRS_LAUNCH_CHECK("metropolis first kernel");
+    const int cg = (int)ctx->tune_mc_cg;
+    const int64_t groups = (C + cg - 1) / cg;
+    const int gf = n_tiles <= 65535 ? 1 : 0;
+    dim3 grid = gf ? dim3((unsigned)groups, (unsigned)n_tiles) : dim3((unsigned)n_tiles, (unsigned)groups);
+    const int nst = (int)ctx->tune_mc_stages;
+    float2* partial = (float2*)scr;
+    if (q_compact(ctx->n))
+        k_metro_propose<true><<<grid, MC_TPB, nst * sizeof(McStage), st>>>(
+            ctx->view(), C, ctx->Q, ctx->pend, ctx->jbuf, partial, n_tiles, cg, nst, ctx->mc_err_d, gf);
+    else
+        k_metro_propose<false><<<grid, MC_TPB, nst * sizeof(McStage), st>>>(
+            ctx->view(), C, ctx->Q, ctx->pend, ctx->jbuf, partial, n_tiles, cg, nst, ctx->mc_err_d, gf);
+    LRS_LAUNCH_CHECK("metropolis propose kernel");
+    k_metro_partial_out<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, amp);
+    LRS_LAUNCH_CHECK("metropolis partial amplitude kernel");
+    return LRS_OK;
+}
+
+lrs_status launch_metropolis_accept(lrs_ctx* ctx, const double* amp, uint64_t seed, int64_t step, uint64_t* trace,
+                                    cudaStream_t st) {
+    const int64_t C = ctx->n_chains;
+    k_metro_accept_amp<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(amp, C, seed, step, ctx->jbuf, ctx->cx, ctx->cp,
+                                                                     ctx->pend, trace);
+    LRS_LAUNCH_CHECK("metropolis accept kernel");
+    return LRS_OK;
+}
+
+lrs_status launch_chains_set_prob(lrs_ctx* ctx, const double* amp, cudaStream_t st) {
+    const int64_t C = ctx->n_chains;
+    k_chains_set_prob<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(amp, C, ctx->cp);
+    LRS_LAUNCH_CHECK("chain probability kernel");
     return LRS_OK;
 }
 

@@ -25,7 +25,7 @@ struct lrs_mlp {
     // FP32 master parameters and AdamW moments (device)
     float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *W3 = nullptr, *b3 = nullptr;
     int gemm = 0;                         // LRS_MLP_GEMM_TCGEN05 or LRS_MLP_GEMM_MMA_SYNC
-    int* err = nullptr;                   // device flag: a tensor-core completion wait gave up
+    int* err = nullptr;                   // device [2]: a tensor-core wait gave up; test request
     float *mW = nullptr, *vW = nullptr;   // moments for all parameters, packed
     float *grad = nullptr;                // gradients, packed like the parameters
     float *mask = nullptr;                // MADE masks, packed like the weights (1 for biases)
@@ -277,7 +277,10 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
 
     int issued = 0;
     if (warp == 0 && lane == 0) {
-        // TMA producer
+        // TMA producer.  err[1] is a one-shot test request (lrs_mlp_debug_inject_wait_timeout):
+        // block (0, 0) takes it and makes its first stage expect 16 bytes that no copy
+        // delivers, so the MMA issuer's bounded wait on that stage runs out.
+        const uint32_t extra = (blockIdx.x == 0 && blockIdx.y == 0 && atomicExch(&err[1], 0) != 0) ? 16u : 0u;
         for (int kt = 0; kt < nk; ++kt) {
             const int s = kt % ST;
             if (kt >= ST && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((kt / ST) - 1) & 1u)) {
@@ -287,7 +290,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
             if (*(volatile int*)&abort_flag) break;
             const uint32_t fb = smem_u32(&full[s]);
             const uint32_t sa = sbase + (uint32_t)(s * S::STAGE), sb = sa + (uint32_t)S::A_BYTES;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(S::STAGE)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb),
+                         "r"((uint32_t)S::STAGE + (kt == 0 ? extra : 0u))
                          : "memory");
             if constexpr (!MN) {
                 tma_load_2d(sa, &tmA, kt * TC_BK, m0, fb);
@@ -341,8 +345,9 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
         if (tid == 0) {
             atomicExch(err, 1);
             // let the producer's copies that no MMA waited for land before the CTA exits
-            for (int kt = consumed; kt < issued; ++kt)
-                if (!mbar_wait(smem_u32(&full[kt % ST]), (uint32_t)(kt / ST) & 1u)) break;
+            // (each stage's wait is bounded; a stage whose wait runs out does not stop the
+            // drain of the later ones)
+            for (int kt = consumed; kt < issued; ++kt) mbar_wait(smem_u32(&full[kt % ST]), (uint32_t)(kt / ST) & 1u);
         }
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -427,7 +432,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tcp(const __grid_constant__ CUt
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
+        // TMA producer (block 0 takes a pending one-shot test request, as in k_gemm_tc)
+        const uint32_t extra = (blockIdx.x == 0 && atomicExch(&err[1], 0) != 0) ? 16u : 0u;
         int g = 0;
         for (int u = blockIdx.x; u < units; u += gridDim.x) {
             const int t = u % tiles, k0 = (u / tiles) * nk;
@@ -446,7 +452,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tcp(const __grid_constant__ CUt
                 }
                 const uint32_t fb = smem_u32(&full[s]);
                 const uint32_t sa = sbase + (uint32_t)(s * S::STAGE), sb = sa + (uint32_t)S::A_BYTES;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(S::STAGE)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb),
+                             "r"((uint32_t)S::STAGE + (g == 0 ? extra : 0u))
                              : "memory");
                 if constexpr (!MN) {
                     tma_load_2d(sa, &tmA, kt * TC_BK, m0, fb);
@@ -555,8 +562,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tcp(const __grid_constant__ CUt
     if (tid == 0 && (*(volatile int*)&abort_flag || !mma_done)) {
         atomicExch(err, 1);
         // let the producer's copies that no MMA waited for land before the CTA exits
-        for (int g = s_consumed; g < s_issued; ++g)
-            if (!mbar_wait(smem_u32(&full[g % ST]), (uint32_t)(g / ST) & 1u)) break;
+        for (int g = s_consumed; g < s_issued; ++g) mbar_wait(smem_u32(&full[g % ST]), (uint32_t)(g / ST) & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -1158,8 +1164,8 @@ extern "C" lrs_status lrs_mlp_create(int32_t device, int32_t n, int32_t hidden, 
     if (e == cudaSuccess) e = cudaMalloc(&m->W3b, (size_t)64 * H * 2);
     if (e == cudaSuccess) e = cudaMalloc(&m->W2t, (size_t)H * H * 2);
     if (e == cudaSuccess) e = cudaMalloc(&m->W3t, (size_t)H * 64 * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&m->err, 2 * sizeof(int));   // flag, one-shot test request
+    if (e == cudaSuccess) e = cudaMemset(m->err, 0, 2 * sizeof(int));
     if (e != cudaSuccess) {
         delete m;
         return lrs_cuda_check(e, "mlp storage");
@@ -1229,6 +1235,14 @@ static lrs_status mlp_check_err(lrs_mlp* m) {
         LRS_CUDA(cudaMemset(m->err, 0, sizeof(int)));
         return lrs_fail(LRS_ERR_TIMEOUT, "a tcgen05 GEMM gave up waiting for its MMAs; results are invalid");
     }
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_mlp_debug_inject_wait_timeout(lrs_mlp* m) {
+    if (!m) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    LRS_CUDA(cudaSetDevice(m->device));
+    const int one = 1;
+    LRS_CUDA(cudaMemcpy(m->err + 1, &one, sizeof(int), cudaMemcpyHostToDevice));
     return LRS_OK;
 }
 

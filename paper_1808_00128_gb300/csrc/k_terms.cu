@@ -84,6 +84,11 @@ __global__ void k_init_terms(TermsView T, int32_t mode, uint64_t seed, double sc
 // merged with shuffles.  A term's tableau stays in shared memory, so the split gives
 // TPT times the warps per SM (latency hiding) at the same shared-memory footprint.
 constexpr int APPLY_TERMS = 64;
+// Launch-internal gate codes (never in the public gate lists): a slot whose choice 0 is
+// the identity and whose choice 1 is one S (S^dagger) on q -- every T and RZ slot of the
+// lowering -- so that a term needs its choice byte only, not the slot table and K-gate
+// list behind it (two dependent global loads fewer per slot).
+constexpr uint8_t APPLY_OP_SLOT_S = 16, APPLY_OP_SLOT_SDG = 17;
 
 template <int HB> struct HiWord { typedef uint32_t T; };
 template <> struct HiWord<8> { typedef uint8_t T; };
@@ -179,7 +184,7 @@ struct SmemRows : TermLanes<TPT> {
 // of 32 terms.
 template <int TPT>
 struct SmemRows<64, TPT> : TermLanes<TPT> {
-    static constexpr int kRowUnroll = 2;
+    static constexpr int kRowUnroll = 4;   // registers are free here (shared memory caps the blocks per SM)
     struct Mat {
         uint32_t a;
     };
@@ -240,6 +245,10 @@ __device__ __forceinline__ void apply_tile(const TermsView T, const Gates gates,
             const int j = T.choice[(int64_t)g.r * T.cap + a];
             const int off = sl.k_off[j], len = sl.k_len[j];
             for (int e = 0; e < len; ++e) apply_gate(R, S, n, nmask, T.kgates[off + e]);
+        } else if (g.op == APPLY_OP_SLOT_S || g.op == APPLY_OP_SLOT_SDG) {
+            // two-choice slot K_0 = I, K_1 = S (or S^dagger) on q: one choice load
+            R.sync();
+            if (T.choice[(int64_t)g.r * T.cap + a] != 0) gate_s(R, S, g.q, g.op == APPLY_OP_SLOT_S ? 3u : 1u);
         } else {
             apply_gate(R, S, n, nmask, g);
         }
@@ -358,6 +367,26 @@ lrs_status launch_apply_clifford(lrs_ctx* ctx, const lrs_gate* gates_host, int64
     return launch_apply_clifford_range(ctx, gates_host, n_gates, ctx->cap, st);
 }
 
+// The launch-internal code of gate g (APPLY_OP_SLOT_S / _SDG for a slot of the form
+// {I, S_q} or {I, S^dagger_q} with both coefficients nonzero; g itself otherwise).
+static lrs_gate specialise_gate(const lrs_ctx* ctx, lrs_gate g) {
+    if (g.op != LRS_OP_SLOT || (size_t)g.r >= ctx->slots_host.size()) return g;
+    const lrs_slot& sl = ctx->slots_host[g.r];
+    if (sl.n_choices != 2 || sl.k_len[0] != 0 || sl.k_len[1] != 1) return g;
+    if ((sl.c_re[0] == 0.0 && sl.c_im[0] == 0.0) || (sl.c_re[1] == 0.0 && sl.c_im[1] == 0.0)) return g;
+    const lrs_gate k = ctx->kgates_host[(size_t)sl.k_off[1]];
+    if (k.op != LRS_OP_S && k.op != LRS_OP_SDG) return g;
+    lrs_gate o;
+    o.op = k.op == LRS_OP_S ? APPLY_OP_SLOT_S : APPLY_OP_SLOT_SDG;
+    o.q = k.q;
+    o.r = g.r;
+    return o;
+}
+
+void specialise_gates(const lrs_ctx* ctx, const lrs_gate* in, int64_t n, lrs_gate* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = specialise_gate(ctx, in[i]);
+}
+
 template <int HB, int TPT>
 static lrs_status launch_apply_hb(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, int64_t blocks,
                                   cudaStream_t st) {
@@ -366,7 +395,7 @@ static lrs_status launch_apply_hb(lrs_ctx* ctx, const lrs_gate* gates_host, int6
     static thread_local GateList G;
     for (int64_t i0 = 0; i0 < n_gates; i0 += APPLY_PARAM_GATES) {
         const int len = (int)std::min<int64_t>(APPLY_PARAM_GATES, n_gates - i0);
-        memcpy(G.g, gates_host + i0, (size_t)len * sizeof(lrs_gate));
+        specialise_gates(ctx, gates_host + i0, len, G.g);
         k_apply_clifford<HB, TPT><<<(unsigned)blocks, APPLY_TERMS * TPT, SmemRows<HB, TPT>::bytes(ctx->n), st>>>(
             ctx->view(), G, len);
         LRS_LAUNCH_CHECK("apply_clifford kernel");

@@ -316,6 +316,7 @@ extern "C" lrs_status lrs_destroy(lrs_ctx* c) {
     cudaFree(c->mc_par);
     cudaFree(c->batch_buf);
     cudaFree(c->eta_buf);
+    cudaFree(c->jbuf);
     if (c->mc_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->mc_exec);
     if (c->cap_stream) cudaStreamDestroy((cudaStream_t)c->cap_stream);
     if (c->mc_err_h) cudaFreeHost(c->mc_err_h);
@@ -569,9 +570,13 @@ extern "C" lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_g
         lrs_status rc = lrs_ensure((void**)&c->gates_dev, &have, (size_t)std::max<int64_t>(1, n_gates[i]) * sizeof(lrs_gate));
         if (rc != LRS_OK) return rc;
         c->gates_cap = (int64_t)(have / sizeof(lrs_gate));
-        if (n_gates[i] > 0)
-            LRS_CUDA(cudaMemcpyAsync(c->gates_dev, gates[i], (size_t)n_gates[i] * sizeof(lrs_gate),
+        if (n_gates[i] > 0) {
+            std::vector<lrs_gate> sg((size_t)n_gates[i]);
+            specialise_gates(c, gates[i], n_gates[i], sg.data());
+            LRS_CUDA(cudaMemcpyAsync(c->gates_dev, sg.data(), (size_t)n_gates[i] * sizeof(lrs_gate),
                                      cudaMemcpyHostToDevice, st));
+            LRS_CUDA(cudaStreamSynchronize(st));   // the staging vector is freed on return
+        }
         c->batch_n_gates = n_gates[i];
         c->n_chains = 0;
         c->fresh = false;
@@ -801,6 +806,7 @@ extern "C" lrs_status lrs_chains_init(lrs_ctx* c, int64_t n_chains, const uint64
     }
     c->n_chains = n_chains;
     c->q_stale = false;
+    c->split_step = -1;
     return launch_chains_init(c, x, as_stream(stream));
 }
 
@@ -817,6 +823,35 @@ extern "C" lrs_status lrs_metropolis_step(lrs_ctx* c, int64_t steps, uint64_t se
     return launch_metropolis(c, steps, seed, step0, x_out, p_out, trace, as_stream(stream));
 }
 
+extern "C" lrs_status lrs_chains_set_amplitude(lrs_ctx* c, const double* amp, void* stream) {
+    if (!c || !amp) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (c->n_chains < 1) return lrs_fail(LRS_ERR_STATE, "chains not initialised");
+    LRS_CUDA(cudaSetDevice(c->device));
+    return launch_chains_set_prob(c, amp, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_metropolis_propose(lrs_ctx* c, uint64_t seed, int64_t step, double* amp, void* stream) {
+    if (!c || !amp) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (c->n_chains < 1) return lrs_fail(LRS_ERR_STATE, "chains not initialised");
+    if (step < 0) return lrs_fail(LRS_ERR_ARG, "step < 0");
+    if (c->q_stale) return lrs_fail(LRS_ERR_STATE, "chains moved by learned proposals: re-initialise them");
+    LRS_CUDA(cudaSetDevice(c->device));
+    lrs_status rc = launch_metropolis_propose(c, seed, step, amp, as_stream(stream));
+    if (rc == LRS_OK) c->split_step = step;
+    return rc;
+}
+
+extern "C" lrs_status lrs_metropolis_accept(lrs_ctx* c, const double* amp, uint64_t seed, int64_t step,
+                                            uint64_t* trace, void* stream) {
+    if (!c || !amp) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (c->n_chains < 1) return lrs_fail(LRS_ERR_STATE, "chains not initialised");
+    if (c->split_step != step) return lrs_fail(LRS_ERR_STATE, "no lrs_metropolis_propose of step %lld", (long long)step);
+    LRS_CUDA(cudaSetDevice(c->device));
+    lrs_status rc = launch_metropolis_accept(c, amp, seed, step, trace, as_stream(stream));
+    c->split_step = -1;
+    return rc;
+}
+
 extern "C" lrs_status lrs_metropolis_learned(lrs_ctx* c, lrs_mlp* mlp, int64_t steps, uint64_t seed,
                                              int64_t step0, uint64_t* x_out, double* p_out,
                                              uint64_t* trace, int64_t* accepts, void* stream) {
@@ -829,6 +864,15 @@ extern "C" lrs_status lrs_metropolis_learned(lrs_ctx* c, lrs_mlp* mlp, int64_t s
     LRS_CUDA(cudaSetDevice(c->device));
     return launch_metropolis_learned(c, mlp, steps, seed, step0, x_out, p_out, trace, accepts,
                                      as_stream(stream));
+}
+
+extern "C" lrs_status lrs_debug_inject_wait_timeout(lrs_ctx* c) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    LRS_CUDA(cudaSetDevice(c->device));
+    lrs_status rc = mc_flags(c);
+    if (rc != LRS_OK) return rc;
+    *(volatile int*)&c->mc_err_h[1] = 1;
+    return LRS_OK;
 }
 
 extern "C" lrs_status lrs_export_terms(lrs_ctx* c, int64_t first, int64_t count, uint64_t* F,

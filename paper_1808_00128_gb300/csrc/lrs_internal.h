@@ -97,7 +97,7 @@ struct lrs_ctx {
     int64_t tune_mc_cg = 64;        // Metropolis: chains per block (1..64)
     int64_t tune_mc_stages = 2;     // Metropolis: chains in flight per block (1..4)
     int64_t tune_norm_folds = 12;   // norm: terms with n - |v| <= this sum over y = G x (-1..12)
-    int64_t tune_apply_lanes = 2;   // apply_clifford, 64-bit rows (n > 48): lanes per term (1, 2, 4)
+    int64_t tune_apply_lanes = 1;   // apply_clifford, 64-bit rows (n > 48): lanes per term (1, 2, 4)
     // equatorial samples of median-of-means estimates
     double* eta_buf = nullptr;
     size_t eta_bytes = 0;
@@ -115,7 +115,7 @@ struct lrs_ctx {
     int64_t chains_cap = 0;
     bool q_stale = false;           // x moved by learned proposals: Q must be rebuilt
     McParams* mc_par = nullptr;     // device parameters of the flip-chain kernels
-    int* mc_err_h = nullptr;        // mapped host flag: a propose kernel gave up waiting
+    int* mc_err_h = nullptr;        // mapped host [2]: a propose kernel gave up waiting; test request
     int* mc_err_d = nullptr;        // its device address
     void* mc_exec = nullptr;        // cudaGraphExec_t of LRS_MC_GRAPH_STEPS steps
     const void* mc_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -126,6 +126,10 @@ struct lrs_ctx {
     float* lqx = nullptr;           // [chain] log q(x)
     double* ampy = nullptr;         // [chain][2] <y|psi>
     int64_t mh_cap = 0;
+    // proposals of a term-sharded step (lrs_metropolis_propose -> lrs_metropolis_accept)
+    int32_t* jbuf = nullptr;
+    size_t jbuf_bytes = 0;
+    int64_t split_step = -1;        // step of the proposal awaiting its accept
 
     TermsView view() const {
         TermsView t;
@@ -180,5 +184,12 @@ lrs_status launch_metropolis_learned(lrs_ctx* ctx, lrs_mlp* mlp, int64_t steps, 
                                      int64_t step0, uint64_t* x_out, double* p_out, uint64_t* trace,
                                      int64_t* accepts, cudaStream_t st);
 lrs_status launch_chains_refresh(lrs_ctx* ctx, cudaStream_t st);
+lrs_status mc_flags(lrs_ctx* ctx);
+lrs_status launch_metropolis_propose(lrs_ctx* ctx, uint64_t seed, int64_t step, double* amp, cudaStream_t st);
+lrs_status launch_metropolis_accept(lrs_ctx* ctx, const double* amp, uint64_t seed, int64_t step, uint64_t* trace,
+                                    cudaStream_t st);
+lrs_status launch_chains_set_prob(lrs_ctx* ctx, const double* amp, cudaStream_t st);
+// Gate list with the launch-internal slot codes of the apply kernels (k_terms.cu).
+void specialise_gates(const lrs_ctx* ctx, const lrs_gate* in, int64_t n, lrs_gate* out);
 lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cudaStream_t st,
                                        void** dev_buf, size_t* dev_buf_bytes);

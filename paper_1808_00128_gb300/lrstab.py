@@ -41,7 +41,9 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_mlp_backward", "lrs_mlp_train_step", "lrs_mlp_sample", "lrs_metropolis_learned",
             "lrs_apply_clifford_batch", "lrs_set_tuning", "lrs_get_tuning", "lrs_copy_terms",
             "lrs_norm_median_of_means", "lrs_marginal_sample", "lrs_lower_gadget",
-            "lrs_apply_circuit_shared", "lrs_decomposition_stats", "lrs_sparsification_certificate"]
+            "lrs_apply_circuit_shared", "lrs_decomposition_stats", "lrs_sparsification_certificate",
+            "lrs_debug_inject_wait_timeout", "lrs_mlp_debug_inject_wait_timeout", "lrs_chains_set_amplitude",
+            "lrs_metropolis_propose", "lrs_metropolis_accept"]
 
 
 class LrsError(RuntimeError):
@@ -101,6 +103,11 @@ def lib():
         "lrs_get_tuning": [vp, i32, vp],
         "lrs_decomposition_stats": [vp, i64, vp, vp, vp],
         "lrs_sparsification_certificate": [vp, i64, i32, u64, vp, vp],
+        "lrs_debug_inject_wait_timeout": [vp],
+        "lrs_mlp_debug_inject_wait_timeout": [vp],
+        "lrs_chains_set_amplitude": [vp, vp, vp],
+        "lrs_metropolis_propose": [vp, u64, i64, vp, vp],
+        "lrs_metropolis_accept": [vp, vp, u64, i64, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -347,11 +354,30 @@ class Simulator:
 
     def chains_init(self, x, stream=None):
         _check(lib().lrs_chains_init(self._h, x.numel(), _ptr(x), _stream(stream)))
+        self._chains = x.numel()
 
     def metropolis(self, steps: int, seed: int, step0: int = 0, x_out=None, p_out=None, trace=None,
                    stream=None):
         _check(lib().lrs_metropolis_step(self._h, steps, seed & (2 ** 64 - 1), step0, _ptr(x_out),
                                          _ptr(p_out), _ptr(trace), _stream(stream)))
+
+    def chains_set_amplitude(self, amp, stream=None):
+        """lrs_chains_set_amplitude: P(x_c) from summed amplitudes (float64 [C, 2])."""
+        _check(lib().lrs_chains_set_amplitude(self._h, _ptr(amp), _stream(stream)))
+
+    def metropolis_propose(self, seed: int, step: int, amp=None, stream=None):
+        """lrs_metropolis_propose: this shard's partial amplitudes of the proposals of
+        step `step` (float64 CUDA tensor [C, 2])."""
+        import torch
+        if amp is None:
+            amp = torch.empty((self._chains, 2), dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(lib().lrs_metropolis_propose(self._h, seed & (2 ** 64 - 1), step, _ptr(amp), _stream(stream)))
+        return amp
+
+    def metropolis_accept(self, amp, seed: int, step: int, trace=None, stream=None):
+        """lrs_metropolis_accept on the summed amplitudes of step `step`."""
+        _check(lib().lrs_metropolis_accept(self._h, _ptr(amp), seed & (2 ** 64 - 1), step, _ptr(trace),
+                                           _stream(stream)))
 
     def set_tuning(self, name: str, value: int):
         _check(lib().lrs_set_tuning(self._h, TUNE[name], int(value)))
@@ -360,6 +386,10 @@ class Simulator:
         v = C.c_int64(0)
         _check(lib().lrs_get_tuning(self._h, TUNE[name], C.byref(v)))
         return v.value
+
+    def debug_inject_wait_timeout(self):
+        """lrs_debug_inject_wait_timeout (failure-path tests)."""
+        _check(lib().lrs_debug_inject_wait_timeout(self._h))
 
     def export_terms(self, first: int = 0, count: int | None = None) -> dict:
         count = self.chi - first if count is None else count
@@ -423,6 +453,10 @@ class MLP:
             out[k] = flat[o:o + sz].reshape(shapes[k])
             o += sz
         return out
+
+    def debug_inject_wait_timeout(self):
+        """lrs_mlp_debug_inject_wait_timeout (failure-path tests)."""
+        _check(lib().lrs_mlp_debug_inject_wait_timeout(self._h))
 
     def set_params(self, params: dict):
         flat = np.ascontiguousarray(self.pack(params))

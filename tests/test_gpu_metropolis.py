@@ -220,3 +220,42 @@ def test_chain_replay_qaoa_n50_slice():
     assert close < C * T // 50
     assert moves > 0
     sim.close()
+
+
+def test_term_sharded_chains_equal_full_context():
+    """Two contexts holding the two halves of the n = 40, 2^16-term decomposition run
+    the chains through lrs_metropolis_propose / sum / lrs_metropolis_accept; the chains
+    equal those of one context holding all terms (same draws, same decisions), and the
+    final P(x) agree to FP32 summation accuracy."""
+    require_cuda()
+    from paper_1808_00128_gb300 import sharding
+    cfg = workloads.config_mid()
+    n, ops, chi, seed = cfg["n"], cfg["ops"], cfg["chi"], cfg["seed"]
+    low = lrstab.lower_circuit(n, ops)
+    full = lrstab.Simulator(n, 0)
+    full.init_terms(low, chi, mode="sparsify", seed=seed)
+    full.apply_clifford(low.gates)
+    shards = []
+    for r in range(2):
+        a0, c = sharding.shard_range(chi, r, 2)
+        s = lrstab.Simulator(n, 0)
+        s.init_terms(low, c, mode="sparsify", seed=seed, alpha0=a0, chi_total=chi)
+        s.apply_clifford(low.gates)
+        shards.append(s)
+    C, T, mseed = 48, 24, 777
+    x0 = full.sample_terms(C, seed=5)
+    full.chains_init(x0)
+    tr_full = torch.empty((T, C), dtype=torch.int64, device="cuda:0")
+    pf = torch.empty(C, dtype=torch.float64, device="cuda:0")
+    full.metropolis(T, seed=mseed, trace=tr_full, p_out=pf)
+    sharding.chains_init_sharded(shards, x0)
+    tr = torch.empty((T, C), dtype=torch.int64, device="cuda:0")
+    sharding.metropolis_sharded(shards, T, mseed, trace=tr)
+    assert torch.equal(tr, tr_full)
+    ps = torch.empty(C, dtype=torch.float64, device="cuda:0")
+    shards[0].metropolis(0, seed=mseed, step0=T, p_out=ps)
+    np.testing.assert_allclose(ps.cpu().numpy(), pf.cpu().numpy(), rtol=1e-5)
+    with pytest.raises(lrstab.LrsError):
+        shards[0].metropolis_accept(torch.zeros((C, 2), dtype=torch.float64, device="cuda:0"), mseed, T + 5)
+    for s in shards + [full]:
+        s.close()
