@@ -170,7 +170,13 @@ def launches_per_step(T):
 # DRAM bytes per launch of the dominant kernel (ncu: dram__bytes_read.sum +
 # dram__bytes_write.sum), per unit of work, with the hash of the kernel source the
 # capture ran; `traffic` is reported only while that source is unchanged.
-TRAFFIC = {}
+TRAFFIC = {
+    # k_norm<13, 7> on the profiling case (n = 50 QAOA, chi = 2^16, L = 64): 34,197,248 B
+    # read + 26,880 B written per launch for 2^16 x 64 (A, term) units
+    "norm_estimate": {"bytes_per_unit": (34197248 + 26880) / (65536 * 64),
+                      "source": "paper_1808_00128_gb300/csrc/k_norm.cu", "sha16": "c4208c59490e2d05",
+                      "profile": "profiles/k_norm_n50_chi65536_L64.md"},
+}
 
 
 def source_sha16(path):
@@ -649,7 +655,7 @@ def _run_traced(fn, C, steps, chunk, dev):
 
 
 def sampler_study(local=0, n=20, chi=1 << 14, C=1024, hidden=512, train_samples=100_000, epochs=20,
-                  plain_steps=1500, learned_steps=150, burn=100, chunk=50, tv_targets=(0.05, 0.02),
+                  plain_steps=1500, learned_steps=150, burn=100, chunk=10, tv_targets=(0.05, 0.02, 0.01),
                   ref_steps=0, seed=0, qaoa_instance=False):
     """Plain single-flip Metropolis (Sec. 4.2) against Metropolis-Hastings with the
     learned MADE proposal, on a QAOA Max-E3LIN2 state (gamma 0.3, beta 0.2), at equal
@@ -735,8 +741,8 @@ def sampler_study(local=0, n=20, chi=1 << 14, C=1024, hidden=512, train_samples=
     tau_p = tau_int(p_cost)
     ess_plain = C * plain_steps / tau_p / t_plain
 
-    # training data: plain-chain states, thinned to about one per autocorrelation time
-    thin = max(1, int(round(tau_p)))
+    # training data: plain-chain states, one every third of an autocorrelation time
+    thin = max(1, int(round(tau_p / 3)))
     need_steps = int(np.ceil(train_samples / C)) * thin
     a, b = _ev()
     a.record()
