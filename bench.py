@@ -321,6 +321,37 @@ def _noop(_):
     return 0
 
 
+class COracleTimer:
+    """The C restatement of the oracle (oracle/c/chform_oracle.c) on all host threads:
+    wall times of building k terms alone, with their amplitudes at n_x strings, and with
+    their equatorial inner products with n_a states give per-unit times of the whole
+    machine."""
+
+    def __init__(self, name):
+        from oracle import fast
+        cfg = workload_config(name)
+        self.cfg = cfg
+        self.prep = fast.Prepared(cfg["n"], cfg["ops"], cfg["chi"], cfg["mode"], cfg["seed"])
+        self.threads = max(1, os.cpu_count() or 1)
+
+    def sample(self, k, n_x, n_a, alpha0=0):
+        from oracle import estimators as E
+        from paper_1808_00128_gb300 import workloads
+        n = self.cfg["n"]
+        xs = [int(x) for x in workloads.random_bitstrings(n, n_x, seed=workloads.SEED_BASE + 50 + alpha0)]
+        As = [E.draw_A(n, 7 + alpha0, l) for l in range(n_a)]
+        t0 = time.perf_counter()
+        self.prep.sums([], [], alpha0=alpha0, count=k, threads=self.threads)
+        t1 = time.perf_counter()
+        self.prep.sums(xs, [], alpha0=alpha0, count=k, threads=self.threads)
+        t2 = time.perf_counter()
+        self.prep.sums([], As, alpha0=alpha0, count=k, threads=self.threads)
+        t3 = time.perf_counter()
+        tb = (t1 - t0) / k
+        return {"t_build": tb, "t_amp": max(t2 - t1 - (t1 - t0), 0.0) / (k * n_x),
+                "t_inner": max(t3 - t2 - (t1 - t0), 0.0) / (k * n_a), "parallel": 1.0, "wall": t3 - t0}
+
+
 def oracle_step_seconds(chi, shape, rates):
     serial = chi * (rates["t_build"] + (shape["B"] + shape["C"] * (shape["T"] + 1)) * rates["t_amp"]
                     + shape["L"] * rates["t_inner"])
@@ -336,29 +367,29 @@ def run_reference(args):
     cfg, shape = workload_config(name), SHAPES[name]
     chi = cfg["chi"]
     units = units_per_step(chi, shape["B"], shape["C"], shape["T"])
-    timer = OracleTimer()
-    per = dict(k=2, n_x=256, n_a=2)
+    timer = COracleTimer(name)
+    per = dict(k=4096, n_x=128, n_a=4)
     for w in range(args.warmup):
-        timer.sample(name, alpha0=1000 * w, **per)
+        timer.sample(alpha0=10000 * w, **per)
     times, vals = [], []
     for k in range(args.steps):
         t0 = time.perf_counter()
-        r = timer.sample(name, alpha0=100000 + 1000 * k, **per)
+        r = timer.sample(alpha0=100000 + 10000 * k, **per)
         times.append(time.perf_counter() - t0)
         vals.append(units / oracle_step_seconds(chi, shape, r))
-    timer.close()
     value = statistics.median(vals)
-    sample = (f"per step: {per['k']} term per core ({timer.workers} cores) of the {cfg['name']} decomposition "
-              f"built by the oracle, {per['n_x']} amplitude evaluations and {per['n_a']} equatorial inner "
-              "product per term; per-unit times scaled to one full step (chi (B + C (T+1)) amplitude "
-              "evaluations, chi L inner products) and divided by the parallelism achieved")
+    sample = (f"per step: {per['k']} terms of the {cfg['name']} decomposition built by the C restatement "
+              f"of the oracle on {timer.threads} host threads, with {per['n_x']} amplitude evaluations and "
+              f"{per['n_a']} equatorial inner products per term (exact integer sums); wall times per unit "
+              "scaled to one full step (chi terms, chi (B + C (T+1)) amplitude evaluations, chi L inner "
+              "products)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": cfg["name"], "n": cfg["n"], "chi": chi, "batch": shape["B"],
                       "L": shape["L"], "chains": shape["C"], "metropolis_steps": shape["T"]},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": timer.workers, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": timer.threads, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -1164,18 +1195,29 @@ def main():
                "d2h_bytes_per_step": d2h}
     r.close()
 
-    cpu = parity = None
+    cpu = cpu_py = parity = None
     if timer is not None:
+        t0 = time.perf_counter()
+        ct = COracleTimer(args.workload)
+        k, n_x, n_a = 8192, 256, 8
+        rates = ct.sample(k=k, n_x=n_x, n_a=n_a, alpha0=0)
+        cpu = {"value": units / oracle_step_seconds(r.chi, r.shape, rates), "unit": UNIT,
+               "cores": ct.threads, "kind": "oracle",
+               "sample": f"{k} terms of the {r.cfg['name']} decomposition built by the C restatement of the "
+                         f"oracle on {ct.threads} host threads, with {n_x} amplitude evaluations and {n_a} "
+                         "equatorial inner products per term (exact integer sums); wall times per unit "
+                         "scaled to one full step",
+               "seconds": round(time.perf_counter() - t0, 1)}
         t0 = time.perf_counter()
         k, n_x, n_a = (16, 512, 4) if args.workload == "qaoa" else (24, 256, 8)
         rates = timer.sample(args.workload, k=k, n_x=n_x, n_a=n_a, alpha0=0)
-        cpu = {"value": units / oracle_step_seconds(r.chi, r.shape, rates), "unit": UNIT,
-               "cores": timer.workers, "kind": "oracle",
-               "sample": f"{k} terms per core of the {r.cfg['name']} decomposition built by the oracle, "
-                         f"{n_x} amplitude evaluations and {n_a} equatorial inner products per term; per-unit "
-                         f"times scaled to one full step and divided by the parallelism achieved "
-                         f"({rates['parallel']:.1f} of {timer.workers} cores)",
-               "seconds": round(time.perf_counter() - t0, 1)}
+        cpu_py = {"value": units / oracle_step_seconds(r.chi, r.shape, rates), "unit": UNIT,
+                  "cores": timer.workers, "kind": "oracle (Python)",
+                  "sample": f"{k} terms per core built by the Python oracle, {n_x} amplitude evaluations and "
+                            f"{n_a} equatorial inner products per term; per-unit times scaled to one full step "
+                            f"and divided by the parallelism achieved ({rates['parallel']:.1f} of "
+                            f"{timer.workers} cores)",
+                  "seconds": round(time.perf_counter() - t0, 1)}
         parity = [slice_parity(args.workload, local, timer=timer)]
     ess = side = None
     extra = {}
@@ -1205,7 +1247,7 @@ def main():
                       "parallelism": f"replicas x{world}", "tuned": tuned},
            "roofline": roof, "phases": rows, "amplitude_error": err, "parity_slices": parity,
            "sparsification_certificate": cert,
-           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step(r.shape["T"]) * args.steps,
+           "cpu_baseline": cpu, "cpu_baseline_python": cpu_py, "e2e": e2e, "gpu_launches": launches_per_step(r.shape["T"]) * args.steps,
            "clocks": clk.summary(), "ess": ess, "side_step": side, **extra}
     print(json.dumps(out))
 

@@ -145,3 +145,26 @@ def test_fold_paths_agree_at_scale():
     for f in FOLDS[1:]:
         assert np.all(np.abs(e[f] - ref) <= 1e-5 * np.maximum(np.abs(ref), 4096 / cfg["chi"])), f
     sim.close()
+
+
+def test_qaoa_n50_slice_eta_vs_oracle_and_exact():
+    """The n = 50 QAOA workload (gamma 0.3, beta 0.2; 2^20 sparsified terms): eta_l of a
+    128-term slice on 16 equatorial states, against the FP64 oracle (both exact routes
+    of the kernel) and the oracle's exact Z[zeta8] overlap sums."""
+    require_cuda()
+    from oracle import exact
+    cfg = workloads.config_qaoa()
+    n, ops, chi_total, seed = cfg["n"], cfg["ops"], cfg["chi"], cfg["seed"]
+    alpha0, chi, L, aseed = 2 ** 19 + 1234, 128, 16, 99
+    sim = _sim(n, ops, chi, "sparsify", seed=seed, alpha0=alpha0, chi_total=chi_total)
+    terms, coefs, chs = oracle_terms(n, ops, chi_total, "sparsify", seed=seed,
+                                     alphas=range(alpha0, alpha0 + chi), parallel=True)
+    ov = oracle_overlaps(terms, coefs, n, aseed, L, parallel=True)
+    norm2 = float(np.mean((2.0 ** n) * np.abs(ov) ** 2))
+    _check(_etas(sim, L, aseed), ov, n, norm2)
+    ex = exact.ExactDecomposition(n, ops, chi_total, "sparsify")
+    got = sim.norm_estimate(L, seed=aseed).cpu().numpy()
+    for l in range(4):
+        want = float(ex.eta(terms, chs, E.draw_A(n, aseed, l)))
+        assert abs(got[l] - want) <= 1e-5 * max(want, norm2)
+    sim.close()
