@@ -830,9 +830,18 @@ def sampler_study(local=0, n=20, chi=1 << 14, C=1024, hidden=512, train_samples=
             "learned_gpu_s": lh["gpu_s"] if lh else None,
             "learned_gpu_s_with_overhead": (lh["gpu_s"] + overhead) if lh else None,
             "plain_steps": ph["steps"] if ph else None, "learned_steps": lh["steps"] if lh else None}
+    # the paper's QAOA run length (Sec. 2.4.1: 10^4 burn-in and 4 x 10^4 sample steps per
+    # chain) on these chains: the plain chains' GPU time, and the learned sampler's time,
+    # overheads included, for the same number of effective samples
+    n_eff = C * 4 * 10 ** 4 / tau_p
+    t_plain_run = 5 * 10 ** 4 * t_plain / plain_steps
+    t_learned_run = overhead + (20 + n_eff * tau_l / C) * t_learned / learned_steps
     sim.close()
     net.close()
     return {"workload": f"qaoa_e3lin2_n{n}_chi{chi}", "chains": C, "hidden": hidden,
+            "paper_run_length": {"effective_samples": n_eff, "plain_gpu_s": t_plain_run,
+                                 "learned_gpu_s_with_overhead": t_learned_run,
+                                 "speedup": t_plain_run / t_learned_run},
             "observable": "E3LIN2 cost C(z); single-bit marginals", "reference": ref_kind,
             "plain": {"steps": plain_steps, "gpu_s": t_plain, "tau_int": tau_p, "ess_per_s": ess_plain,
                       "tv_cost_end": p_tv, "max_bit_err_end": p_mb},
