@@ -286,6 +286,17 @@ lrs_status lrs_amplitude_noalloc(lrs_ctx* ctx, const uint64_t* x_dev, int64_t ba
 lrs_status lrs_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta_dev,
                              double* mean_host, void* stream);
 
+/* Term-sharded norm estimation (Sec. 4.3: <phi_A|psi> is a sum over terms).
+ *   lrs_norm_overlaps           ov_dev[2l], ov_dev[2l+1] = Re, Im of
+ *                               2^{n/2} <phi_{A_l}|psi_ctx> over ctx's terms, the same
+ *                               A_l and sums as lrs_norm_estimate (ov_dev: 2 L doubles)
+ *   lrs_norm_eta_from_overlaps  eta_dev[l] = |ov_dev[l]|^2 for overlaps summed over the
+ *                               shards (2^n |<phi_{A_l}|psi>|^2, as lrs_norm_estimate)
+ * Both are stream-ordered.  Errors: LRS_ERR_ARG (L < 1, NULL), LRS_ERR_STATE.    */
+lrs_status lrs_norm_overlaps(lrs_ctx* ctx, int64_t L, uint64_t seed, double* ov_dev, void* stream);
+lrs_status lrs_norm_eta_from_overlaps(lrs_ctx* ctx, int64_t L, const double* ov_dev, double* eta_dev,
+                                      void* stream);
+
 /* Draw count basis strings from the terms (Sec. 4.1, "Simulating
  * measurements"): term alpha = floor(rand64(seed, i, 0) * chi / 2^64)
  * (uniform), w = s ^ (rand64(seed, i, 1) & v), x = w G^T.  Writes x_dev[i]

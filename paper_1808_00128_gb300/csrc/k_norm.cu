@@ -526,8 +526,11 @@ __global__ void __launch_bounds__(NRM_TPB, norm_min_blocks(NCH)) k_norm(TermsVie
     if (l < L) partial[l * n_tiles + tile] = acc.value();
 }
 
+// ov (may be NULL) receives the FP64 sums themselves, 2^{n/2} <phi_{A_l}|psi> (the
+// per-term values carry the 2^{n/2}), for term-sharded estimates; eta (may be NULL)
+// their squared magnitude.
 __global__ void k_norm_reduce(const float2* __restrict__ partial, int64_t n_tiles, int64_t L,
-                              double* __restrict__ eta) {
+                              double* __restrict__ eta, double* __restrict__ ov) {
     const int64_t l = blockIdx.x;
     if (l >= L) return;
     double re = 0.0, im = 0.0;
@@ -547,7 +550,18 @@ __global__ void k_norm_reduce(const float2* __restrict__ partial, int64_t n_tile
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) eta[l] = sre[0] * sre[0] + sim[0] * sim[0];
+    if (threadIdx.x == 0) {
+        if (eta) eta[l] = sre[0] * sre[0] + sim[0] * sim[0];
+        if (ov) {
+            ov[2 * l] = sre[0];
+            ov[2 * l + 1] = sim[0];
+        }
+    }
+}
+
+__global__ void k_norm_eta(const double* __restrict__ ov, int64_t L, double* __restrict__ eta) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < L) eta[l] = ov[2 * l] * ov[2 * l] + ov[2 * l + 1] * ov[2 * l + 1];
 }
 
 }  // namespace
@@ -567,7 +581,13 @@ static lrs_status launch_norm_t(lrs_ctx* ctx, const NormPrep& P, int64_t L, int6
     return LRS_OK;
 }
 
-lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta,
+lrs_status launch_norm_eta(const double* ov, int64_t L, double* eta, cudaStream_t st) {
+    k_norm_eta<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(ov, L, eta);
+    LRS_LAUNCH_CHECK("norm eta kernel");
+    return LRS_OK;
+}
+
+lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta, double* ov,
                                 cudaStream_t st) {
     // tile of terms per block: keep the partial buffer at <= 2048 tiles per A
     int64_t tt = 32;
@@ -616,7 +636,7 @@ lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* 
         default: rc = launch_norm_t<16>(ctx, P, L, tt, partial, n_tiles, st); break;
     }
     if (rc != LRS_OK) return rc;
-    k_norm_reduce<<<(unsigned)L, 256, 0, st>>>(partial, n_tiles, L, eta);
+    k_norm_reduce<<<(unsigned)L, 256, 0, st>>>(partial, n_tiles, L, eta, ov);
     LRS_LAUNCH_CHECK("norm reduce kernel");
     return LRS_OK;
 }

@@ -602,7 +602,7 @@ extern "C" lrs_status lrs_norm_estimate(lrs_ctx* c, int64_t L, uint64_t seed, do
     if (!eta) return lrs_fail(LRS_ERR_ARG, "eta is NULL");
     LRS_CUDA(cudaSetDevice(c->device));
     cudaStream_t st = as_stream(stream);
-    lrs_status rc = launch_norm_estimate(c, L, seed, eta, st);
+    lrs_status rc = launch_norm_estimate(c, L, seed, eta, nullptr, st);
     if (rc != LRS_OK) return rc;
     if (mean_host) {
         std::vector<double> h((size_t)L);
@@ -613,6 +613,23 @@ extern "C" lrs_status lrs_norm_estimate(lrs_ctx* c, int64_t L, uint64_t seed, do
         *mean_host = m / (double)L;
     }
     return LRS_OK;
+}
+
+extern "C" lrs_status lrs_norm_overlaps(lrs_ctx* c, int64_t L, uint64_t seed, double* ov, void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "no terms");
+    if (L < 1) return lrs_fail(LRS_ERR_ARG, "L must be >= 1");
+    if (!ov) return lrs_fail(LRS_ERR_ARG, "ov is NULL");
+    LRS_CUDA(cudaSetDevice(c->device));
+    return launch_norm_estimate(c, L, seed, nullptr, ov, as_stream(stream));
+}
+
+extern "C" lrs_status lrs_norm_eta_from_overlaps(lrs_ctx* c, int64_t L, const double* ov, double* eta,
+                                                 void* stream) {
+    if (!c || !ov || !eta) return lrs_fail(LRS_ERR_ARG, "NULL argument");
+    if (L < 1) return lrs_fail(LRS_ERR_ARG, "L must be >= 1");
+    LRS_CUDA(cudaSetDevice(c->device));
+    return launch_norm_eta(ov, L, eta, as_stream(stream));
 }
 
 extern "C" lrs_status lrs_copy_terms(lrs_ctx* dst, const lrs_ctx* src, void* stream) {
@@ -682,7 +699,7 @@ static lrs_status norm_mom(lrs_ctx* c, int64_t L, int32_t K, uint64_t seed, doub
     lrs_status rc = lrs_ensure((void**)&c->eta_buf, &have, (size_t)LK * sizeof(double));
     if (rc != LRS_OK) return rc;
     c->eta_bytes = have;
-    rc = launch_norm_estimate(c, LK, seed, c->eta_buf, st);
+    rc = launch_norm_estimate(c, LK, seed, c->eta_buf, nullptr, st);
     if (rc != LRS_OK) return rc;
     std::vector<double> h((size_t)LK);
     LRS_CUDA(cudaMemcpyAsync(h.data(), c->eta_buf, (size_t)LK * sizeof(double), cudaMemcpyDeviceToHost, st));

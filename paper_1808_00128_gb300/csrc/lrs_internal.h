@@ -173,8 +173,10 @@ lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, doub
                             cudaStream_t st);
 lrs_status launch_amplitude_q(lrs_ctx* ctx, const uint64_t* x, int64_t batch, void* Q, double** amp_out,
                               cudaStream_t st);
-lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta,
+// eta and ov may each be NULL (ov: 2^{n/2} <phi_{A_l}|psi> as Re, Im pairs)
+lrs_status launch_norm_estimate(lrs_ctx* ctx, int64_t L, uint64_t seed, double* eta, double* ov,
                                 cudaStream_t st);
+lrs_status launch_norm_eta(const double* ov, int64_t L, double* eta, cudaStream_t st);
 lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint64_t* x,
                                int64_t* alpha, cudaStream_t st);
 lrs_status launch_chains_init(lrs_ctx* ctx, const uint64_t* x, cudaStream_t st);

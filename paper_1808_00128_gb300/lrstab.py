@@ -43,7 +43,8 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_norm_median_of_means", "lrs_marginal_sample", "lrs_lower_gadget",
             "lrs_apply_circuit_shared", "lrs_decomposition_stats", "lrs_sparsification_certificate",
             "lrs_debug_inject_wait_timeout", "lrs_mlp_debug_inject_wait_timeout", "lrs_chains_set_amplitude",
-            "lrs_metropolis_propose", "lrs_metropolis_accept"]
+            "lrs_metropolis_propose", "lrs_metropolis_accept", "lrs_norm_overlaps",
+            "lrs_norm_eta_from_overlaps"]
 
 
 class LrsError(RuntimeError):
@@ -108,6 +109,8 @@ def lib():
         "lrs_chains_set_amplitude": [vp, vp, vp],
         "lrs_metropolis_propose": [vp, u64, i64, vp, vp],
         "lrs_metropolis_accept": [vp, vp, u64, i64, vp, vp],
+        "lrs_norm_overlaps": [vp, i64, u64, vp, vp],
+        "lrs_norm_eta_from_overlaps": [vp, i64, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -311,6 +314,24 @@ class Simulator:
         _check(lib().lrs_norm_estimate(self._h, L, seed & (2 ** 64 - 1), _ptr(eta),
                                        C.byref(mean) if want_mean else None, _stream(stream)))
         return (eta, mean.value) if want_mean else eta
+
+    def norm_overlaps(self, L: int, seed: int, ov=None, stream=None):
+        """lrs_norm_overlaps: 2^{n/2} <phi_{A_l}|psi> over this context's terms (float64
+        CUDA tensor [L, 2])."""
+        import torch
+        if ov is None:
+            ov = torch.empty((L, 2), dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(lib().lrs_norm_overlaps(self._h, L, seed & (2 ** 64 - 1), _ptr(ov), _stream(stream)))
+        return ov
+
+    def norm_eta_from_overlaps(self, ov, eta=None, stream=None):
+        """lrs_norm_eta_from_overlaps: eta_l = |ov_l|^2 of summed overlaps."""
+        import torch
+        L = ov.shape[0]
+        if eta is None:
+            eta = torch.empty(L, dtype=torch.float64, device=ov.device)
+        _check(lib().lrs_norm_eta_from_overlaps(self._h, L, _ptr(ov), _ptr(eta), _stream(stream)))
+        return eta
 
     def norm_median_of_means(self, L: int, K: int, seed: int, stream=None) -> float:
         est = C.c_double(0.0)

@@ -68,3 +68,16 @@ def metropolis_sharded(shards, steps, seed, step0=0, trace=None, allreduce=None)
         amp = _sum_parts([s.metropolis_propose(seed, step) for s in shards], allreduce)
         for i, s in enumerate(shards):
             s.metropolis_accept(amp, seed, step, trace=trace[t] if (trace is not None and i == 0) else None)
+
+
+def amplitude_sharded(shards, x, allreduce=None):
+    """<x|psi> over a term-sharded decomposition: the shards' amplitudes added (and
+    all-reduced over ranks)."""
+    return _sum_parts([s.amplitude(x) for s in shards], allreduce)
+
+
+def norm_estimate_sharded(shards, L, seed, allreduce=None):
+    """eta_l = 2^n |<phi_{A_l}|psi>|^2 over a term-sharded decomposition: the shards'
+    overlaps summed (and all-reduced over ranks) before the library squares them."""
+    ov = _sum_parts([s.norm_overlaps(L, seed) for s in shards], allreduce)
+    return shards[0].norm_eta_from_overlaps(ov)
