@@ -950,6 +950,26 @@ def batch_study(local=0, k=8, seed=0):
             ts.append(a.elapsed_time(b))
         res[mode] = {"ms": min(ts), "term_gates_per_s": work / (min(ts) * 1e-3)}
     res["speedup"] = res["per_circuit"]["ms"] / res["batched"]["ms"]
+    # amplitudes (B = 4096 uniform strings per circuit): one launch per circuit against
+    # one batched launch and one batched reduction
+    xs = [torch.from_numpy(workloads.random_bitstrings(50, 4096, seed=workloads.SEED_BASE + 70 + i).view(np.int64))
+          .cuda(local) for i in range(k)]
+    outs = [torch.empty((4096, 2), dtype=torch.float64, device=xs[0].device) for _ in range(k)]
+    amp = {}
+    for mode in ("per_circuit", "batched", "per_circuit", "batched"):
+        torch.cuda.synchronize()
+        a, b = _ev()
+        a.record()
+        if mode == "batched":
+            lrstab.amplitude_batch(sims, xs, outs)
+        else:
+            for s, x, o in zip(sims, xs, outs):
+                s.amplitude(x, out=o)
+        b.record()
+        b.synchronize()
+        amp[mode] = min(amp.get(mode, 1e30), a.elapsed_time(b))
+    res["amplitude"] = {"per_circuit_ms": amp["per_circuit"], "batched_ms": amp["batched"],
+                        "speedup": amp["per_circuit"] / amp["batched"]}
     for s in sims:
         s.close()
     return res
@@ -1030,6 +1050,41 @@ def prefix_study(local=0, sizes=(16, 20)):
         sim.close()
         out.append(res)
     return out
+
+
+def hidden_shift_sum8_study(local=0, chi=1 << 24, L=256, K=3):
+    """The 40-qubit hidden shift with its 16 CCZ in the 8-term form (prefactor 1/6,
+    xi = 16/9) sparsified to chi = 2^24 terms (17 GB of tableau): term set-up and gate
+    updates, <s|psi> and the amplitudes at the neighbours of s, the norm estimate and
+    the sparsification certificate."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    n = 40
+    ops, s = workloads.hidden_shift_circuit(n, 16, workloads.SEED_BASE + 3)
+    low = lrstab.lower_circuit(n, ops, "sum8")
+    sim = lrstab.Simulator(n, local)
+    a, b = _ev()
+    a.record()
+    sim.init_terms(low, chi, mode="sparsify", seed=77)
+    sim.apply_clifford(low.gates)
+    b.record()
+    b.synchronize()
+    t_build = a.elapsed_time(b)
+    xs = [s] + [s ^ (1 << j) for j in range(n)]
+    x = torch.tensor(np.asarray(xs, dtype=np.uint64).view(np.int64), device=f"cuda:{local}")
+    a.record()
+    amp = sim.amplitude(x).cpu().numpy()
+    b.record()
+    b.synchronize()
+    eta = sim.norm_estimate(L, seed=5).cpu().numpy()
+    cert = lrstab.sparsification_certificate(sim, L, K, seed=6)
+    sim.close()
+    mags = np.hypot(amp[:, 0], amp[:, 1])
+    return {"workload": f"hidden_shift_n40_ccz16_sum8_chi{chi}", "chi": chi, "gates": len(low.gates),
+            "init_and_apply_ms": t_build, "amplitude_ms": a.elapsed_time(b),
+            "abs_amp_at_shift": float(mags[0]), "max_abs_amp_at_neighbours": float(mags[1:].max()),
+            "mean_eta": float(eta.mean()), "sparsification_certificate": cert}
 
 
 def marginal_study(local=0, w=8, L=256, K=3):
@@ -1241,7 +1296,7 @@ def main():
             parity.append(slice_parity(other, local, timer=timer))
         extra = {"batch8": batch_study(local), "mlp_gemm": mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops")),
                  "marginals": marginal_study(local), "gadget_vs_sum": gadget_study(local),
-                 "prefix_sharing": prefix_study(local)}
+                 "prefix_sharing": prefix_study(local), "hidden_shift_sum8": hidden_shift_sum8_study(local)}
     if timer is not None:
         timer.close()
     if rank != 0:

@@ -252,6 +252,17 @@ lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_gate* const*
 lrs_status lrs_amplitude(lrs_ctx* ctx, const uint64_t* x_dev, int64_t batch, double* out_dev,
                          float* err_est_dev, void* stream);
 
+/* lrs_amplitude for several circuits (contexts with the same qubit count on one
+ * device, e.g. decompositions of uneven chi) in two launches: one amplitude launch
+ * covering every circuit's term tiles (at most 12 circuits per launch; more take
+ * further launches) and one FP64 reduction for all their strings.  Circuit i gets
+ * batch[i] strings x_dev[i] and writes out_dev[i] (2 batch[i] doubles), with the tile
+ * plan of its own lrs_amplitude call, so its values equal that call's bit for bit.
+ * Errors: LRS_ERR_ARG (NULL or repeated contexts, different devices or widths),
+ * LRS_ERR_STATE (a context without terms).                                       */
+lrs_status lrs_amplitude_batch(lrs_ctx* const* ctxs, const uint64_t* const* x_dev, const int64_t* batch,
+                               double* const* out_dev, int32_t count, void* stream);
+
 /* Same result as lrs_amplitude, but the call allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc when they need amplitudes (for example a serving

@@ -11,6 +11,8 @@
 // One thread owns XP strings x and walks the block's tile of terms, so its
 // chi-sum is a private FP32 Kahan sum (no cross-thread reduction); the tile
 // partials are summed in FP64 by k_amp_reduce.
+#include <string.h>
+
 #include <atomic>
 
 #include "lrs_device.cuh"
@@ -43,11 +45,13 @@ constexpr int amp_min_blocks(bool qout) { return qout ? 6 : 5; }
 // ERR: also sum |b_alpha <x|phi_alpha>| over the terms that contribute at x (one FP32
 // add per contributing (x, term)), written to magp[i * n_tiles + tile]: the input of
 // the per-result error bound of k_amp_reduce.
+// One block of the amplitude launch: term tile `tile`, strings xblk * AMP_XB ... (shared
+// by the single-circuit kernel and the batched kernel of several circuits).
 template <int NCH, bool QOUT, bool PK, bool ERR>
-__global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
-                                                      int64_t batch, int64_t tt,
-                                                      float2* __restrict__ partial, int64_t n_tiles,
-                                                      void* __restrict__ Qout, float* __restrict__ magp) {
+__device__ __forceinline__ void amp_block(const TermsView& T, const uint64_t* __restrict__ xs, int64_t batch,
+                                          int64_t tt, float2* __restrict__ partial, int64_t n_tiles,
+                                          void* __restrict__ Qout, float* __restrict__ magp, int64_t tile,
+                                          int64_t xblk) {
     __shared__ AmpEntry tab[PK ? 1 : NCH][16];
     __shared__ uint64_t tabU[PK ? NCH : 1][16], tabW[PK ? NCH : 1][16];
     __shared__ uint64_t sF[64], sM[64];
@@ -64,8 +68,7 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
     __shared__ uint32_t qb4[CQ ? QG : 1][CQ ? AMP_XB : 1];
     const int n = T.n;
     const int tid = threadIdx.x;
-    const int64_t tile = blockIdx.x;
-    const int64_t xb = (int64_t)blockIdx.y * AMP_XB;
+    const int64_t xb = xblk * AMP_XB;
     uint64_t xv[AMP_XP];
 #pragma unroll
     for (int k = 0; k < AMP_XP; ++k) {
@@ -217,6 +220,41 @@ __global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(Term
     }
 }
 
+template <int NCH, bool QOUT, bool PK, bool ERR>
+__global__ void __launch_bounds__(AMP_XT, amp_min_blocks(QOUT)) k_amplitude(TermsView T, const uint64_t* __restrict__ xs,
+                                                      int64_t batch, int64_t tt,
+                                                      float2* __restrict__ partial, int64_t n_tiles,
+                                                      void* __restrict__ Qout, float* __restrict__ magp) {
+    amp_block<NCH, QOUT, PK, ERR>(T, xs, batch, tt, partial, n_tiles, Qout, magp, blockIdx.x, blockIdx.y);
+}
+
+// Several circuits of the same width in one launch: block b runs block b - first[c]
+// of circuit c's own launch shape (term tile fastest), so every circuit gets exactly the
+// partial sums of its single-circuit launch; the table is a kernel parameter, so the
+// circuit lookup and every value read from it are warp-uniform.
+#define LRS_AMP_BATCH_MAX 12
+struct AmpBatch {
+    int count;
+    int64_t first[LRS_AMP_BATCH_MAX + 1];
+    TermsView T[LRS_AMP_BATCH_MAX];
+    const uint64_t* xs[LRS_AMP_BATCH_MAX];
+    int64_t batch[LRS_AMP_BATCH_MAX], tt[LRS_AMP_BATCH_MAX], n_tiles[LRS_AMP_BATCH_MAX];
+    float2* partial[LRS_AMP_BATCH_MAX];
+    double* out[LRS_AMP_BATCH_MAX];
+};
+
+template <int NCH, bool PK>
+__global__ void __launch_bounds__(AMP_XT, amp_min_blocks(false)) k_amplitude_batch(const __grid_constant__ AmpBatch B) {
+    const int64_t b = blockIdx.x;
+    int c = 0;
+#pragma unroll 1
+    for (int i = 1; i < B.count; ++i)
+        if (B.first[i] <= b) c = i;
+    const int64_t local = b - B.first[c];
+    amp_block<NCH, false, PK, false>(B.T[c], B.xs[c], B.batch[c], B.tt[c], B.partial[c], B.n_tiles[c], nullptr,
+                                     nullptr, local % B.n_tiles[c], local / B.n_tiles[c]);
+}
+
 // FP64 sum of the block partials of each x, and (magp != NULL) the error bound of
 // that sum against the exact chi-sum:
 //   |a_gpu - a| <= (8u + 8 tt u^2)(1 + tt u)(1 + 1e-4) M + n_tiles 2^-52 P,
@@ -264,6 +302,41 @@ __global__ void k_amp_reduce(const float2* __restrict__ partial, const float* __
             const double c = (8.0 * u + 8.0 * ttd * u * u) * (1.0 + ttd * u) * (1.0 + 1e-4);
             err[xi] = (float)((c * sm[0] + (double)n_tiles * 2.220446049250313e-16 * spa[0]) * (1.0 + 1e-6));
         }
+    }
+}
+
+// The FP64 tile sums of several circuits in one launch: block b is string b - xfirst[c]
+// of circuit c (same summation order as k_amp_reduce).
+__global__ void k_amp_reduce_batch(const __grid_constant__ AmpBatch B, int64_t total) {
+    const int64_t b = blockIdx.x;
+    if (b >= total) return;
+    int c = 0;
+#pragma unroll 1
+    for (int i = 1; i < B.count; ++i)
+        if (B.first[i] <= b) c = i;
+    const int64_t xi = b - B.first[c];
+    const float2* partial = B.partial[c];
+    const int64_t n_tiles = B.n_tiles[c];
+    double re = 0.0, im = 0.0;
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const float2 p = partial[xi * n_tiles + t];
+        re += (double)p.x;
+        im += (double)p.y;
+    }
+    __shared__ double sre[256], sim[256];
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            sre[threadIdx.x] += sre[threadIdx.x + off];
+            sim[threadIdx.x] += sim[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        B.out[c][2 * xi] = sre[0];
+        B.out[c][2 * xi + 1] = sim[0];
     }
 }
 
@@ -364,6 +437,84 @@ lrs_status launch_amplitude(lrs_ctx* ctx, const uint64_t* x, int64_t batch, doub
     if (rc != LRS_OK) return rc;
     float* magp = err ? (float*)((char*)scr + part) : nullptr;
     return launch_amp_kernels(ctx, x, batch, out, (float2*)scr, P, st, nullptr, magp, err);
+}
+
+template <int NCH>
+static lrs_status launch_amp_batch_t(const AmpBatch& B, int64_t blocks, bool pk, cudaStream_t st) {
+    if (pk)
+        k_amplitude_batch<NCH, true><<<(unsigned)blocks, AMP_XT, 0, st>>>(B);
+    else
+        k_amplitude_batch<NCH, false><<<(unsigned)blocks, AMP_XT, 0, st>>>(B);
+    LRS_LAUNCH_CHECK("batched amplitude kernel");
+    return LRS_OK;
+}
+
+// Amplitudes of several circuits of the same width (count <= LRS_AMP_BATCH_MAX per
+// launch pair): one amplitude launch and one reduction launch for all of them, each
+// circuit with the tile plan and partial buffer of its own single launch.
+lrs_status launch_amplitude_batch(lrs_ctx* const* ctxs, const uint64_t* const* xs, const int64_t* batch,
+                                  double* const* out, int32_t count, cudaStream_t st) {
+    const int n = ctxs[0]->n;
+    for (int32_t base = 0; base < count; base += LRS_AMP_BATCH_MAX) {
+        AmpBatch B;
+        memset(&B, 0, sizeof(B));
+        int64_t xfirst[LRS_AMP_BATCH_MAX + 1];
+        int k = 0;
+        int64_t blocks = 0, strings = 0;
+        const int32_t end = (count - base < LRS_AMP_BATCH_MAX) ? count : base + LRS_AMP_BATCH_MAX;
+        for (int32_t i = base; i < end; ++i) {
+            if (batch[i] == 0) continue;
+            lrs_ctx* c = ctxs[i];
+            const AmpPlan P = amp_plan(c, batch[i], false);
+            if (P.xblocks > 65535) return lrs_fail(LRS_ERR_UNSUPPORTED, "amplitude batch too large");
+            void* scr = nullptr;
+            lrs_status rc = lrs_scratch(c, (size_t)batch[i] * P.n_tiles * sizeof(float2), &scr);
+            if (rc != LRS_OK) return rc;
+            B.first[k] = blocks;
+            B.T[k] = c->view();
+            B.xs[k] = xs[i];
+            B.batch[k] = batch[i];
+            B.tt[k] = P.tt;
+            B.n_tiles[k] = P.n_tiles;
+            B.partial[k] = (float2*)scr;
+            B.out[k] = out[i];
+            xfirst[k] = strings;
+            blocks += P.n_tiles * P.xblocks;
+            strings += batch[i];
+            ++k;
+        }
+        if (k == 0) continue;
+        if (blocks > 0x7FFFFFFF) return lrs_fail(LRS_ERR_UNSUPPORTED, "batched amplitude grid too large");
+        B.count = k;
+        B.first[k] = blocks;
+        xfirst[k] = strings;
+        AmpBatch R = B;   // the reduction indexes strings instead of blocks
+        for (int j = 0; j <= k; ++j) R.first[j] = xfirst[j];
+        lrs_status rc;
+        const bool pk = n <= 62;
+        switch ((n + 3) / 4) {
+            case 1: rc = launch_amp_batch_t<1>(B, blocks, pk, st); break;
+            case 2: rc = launch_amp_batch_t<2>(B, blocks, pk, st); break;
+            case 3: rc = launch_amp_batch_t<3>(B, blocks, pk, st); break;
+            case 4: rc = launch_amp_batch_t<4>(B, blocks, pk, st); break;
+            case 5: rc = launch_amp_batch_t<5>(B, blocks, pk, st); break;
+            case 6: rc = launch_amp_batch_t<6>(B, blocks, pk, st); break;
+            case 7: rc = launch_amp_batch_t<7>(B, blocks, pk, st); break;
+            case 8: rc = launch_amp_batch_t<8>(B, blocks, pk, st); break;
+            case 9: rc = launch_amp_batch_t<9>(B, blocks, pk, st); break;
+            case 10: rc = launch_amp_batch_t<10>(B, blocks, pk, st); break;
+            case 11: rc = launch_amp_batch_t<11>(B, blocks, pk, st); break;
+            case 12: rc = launch_amp_batch_t<12>(B, blocks, pk, st); break;
+            case 13: rc = launch_amp_batch_t<13>(B, blocks, pk, st); break;
+            case 14: rc = launch_amp_batch_t<14>(B, blocks, pk, st); break;
+            case 15: rc = launch_amp_batch_t<15>(B, blocks, pk, st); break;
+            default: rc = launch_amp_batch_t<16>(B, blocks, pk, st); break;
+        }
+        if (rc != LRS_OK) return rc;
+        k_amp_reduce_batch<<<(unsigned)strings, 256, 0, st>>>(R, strings);
+        LRS_LAUNCH_CHECK("batched amplitude reduce kernel");
+    }
+    return LRS_OK;
 }
 
 // ---------------------------------------------------------------------------------

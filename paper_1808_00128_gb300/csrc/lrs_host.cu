@@ -594,6 +594,25 @@ extern "C" lrs_status lrs_amplitude(lrs_ctx* c, const uint64_t* x, int64_t batch
     return launch_amplitude(c, x, batch, out, err_est, as_stream(stream));
 }
 
+extern "C" lrs_status lrs_amplitude_batch(lrs_ctx* const* ctxs, const uint64_t* const* x, const int64_t* batch,
+                                          double* const* out, int32_t count, void* stream) {
+    if (!ctxs || !x || !batch || !out || count < 1) return lrs_fail(LRS_ERR_ARG, "bad batch arguments");
+    const lrs_ctx* c0 = ctxs[0];
+    if (!c0) return lrs_fail(LRS_ERR_ARG, "ctx 0 is NULL");
+    for (int32_t i = 0; i < count; ++i) {
+        const lrs_ctx* c = ctxs[i];
+        if (!c) return lrs_fail(LRS_ERR_ARG, "ctx %d is NULL", i);
+        if (c->device != c0->device || c->n != c0->n)
+            return lrs_fail(LRS_ERR_ARG, "contexts differ in device or qubit count");
+        if (!c->have_terms) return lrs_fail(LRS_ERR_STATE, "ctx %d has no terms", i);
+        for (int32_t j = 0; j < i; ++j)
+            if (ctxs[j] == c) return lrs_fail(LRS_ERR_ARG, "ctx %d repeated", i);
+        if (batch[i] < 0 || (batch[i] > 0 && (!x[i] || !out[i]))) return lrs_fail(LRS_ERR_ARG, "bad buffers %d", i);
+    }
+    LRS_CUDA(cudaSetDevice(c0->device));
+    return launch_amplitude_batch(ctxs, x, batch, out, count, as_stream(stream));
+}
+
 extern "C" lrs_status lrs_norm_estimate(lrs_ctx* c, int64_t L, uint64_t seed, double* eta,
                                         double* mean_host, void* stream) {
     if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");

@@ -191,6 +191,8 @@ lrs_status launch_metropolis_propose(lrs_ctx* ctx, uint64_t seed, int64_t step, 
 lrs_status launch_metropolis_accept(lrs_ctx* ctx, const double* amp, uint64_t seed, int64_t step, uint64_t* trace,
                                     cudaStream_t st);
 lrs_status launch_chains_set_prob(lrs_ctx* ctx, const double* amp, cudaStream_t st);
+lrs_status launch_amplitude_batch(lrs_ctx* const* ctxs, const uint64_t* const* xs, const int64_t* batch,
+                                  double* const* out, int32_t count, cudaStream_t st);
 // Gate list with the launch-internal slot codes of the apply kernels (k_terms.cu).
 void specialise_gates(const lrs_ctx* ctx, const lrs_gate* in, int64_t n, lrs_gate* out);
 lrs_status launch_apply_clifford_batch(lrs_ctx* const* ctxs, int32_t count, cudaStream_t st,

@@ -44,7 +44,7 @@ EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", 
             "lrs_apply_circuit_shared", "lrs_decomposition_stats", "lrs_sparsification_certificate",
             "lrs_debug_inject_wait_timeout", "lrs_mlp_debug_inject_wait_timeout", "lrs_chains_set_amplitude",
             "lrs_metropolis_propose", "lrs_metropolis_accept", "lrs_norm_overlaps",
-            "lrs_norm_eta_from_overlaps"]
+            "lrs_norm_eta_from_overlaps", "lrs_amplitude_batch"]
 
 
 class LrsError(RuntimeError):
@@ -111,6 +111,7 @@ def lib():
         "lrs_metropolis_accept": [vp, vp, u64, i64, vp, vp],
         "lrs_norm_overlaps": [vp, i64, u64, vp, vp],
         "lrs_norm_eta_from_overlaps": [vp, i64, vp, vp, vp],
+        "lrs_amplitude_batch": [vp, vp, vp, vp, i32, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -522,6 +523,21 @@ def metropolis_learned(sim: "Simulator", mlp: MLP, steps: int, seed: int, step0:
     _check(lib().lrs_metropolis_learned(sim._h, mlp._h, steps, seed & (2 ** 64 - 1), step0,
                                         _ptr(x_out), _ptr(p_out), _ptr(trace), _ptr(accepts),
                                         _stream(stream)))
+
+
+def amplitude_batch(sims, xs, outs=None, stream=None):
+    """lrs_amplitude_batch: <x|psi> of several circuits (same width, one device) in one
+    amplitude launch and one reduction; returns float64 CUDA tensors [B_i, 2]."""
+    import torch
+    k = len(sims)
+    if outs is None:
+        outs = [torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device) for x in xs]
+    handles = (C.c_void_p * k)(*[s._h.value for s in sims])
+    xp = (C.c_void_p * k)(*[x.data_ptr() for x in xs])
+    bs = (C.c_int64 * k)(*[x.numel() for x in xs])
+    op = (C.c_void_p * k)(*[o.data_ptr() for o in outs])
+    _check(lib().lrs_amplitude_batch(handles, xp, bs, op, k, _stream(stream)))
+    return outs
 
 
 def apply_clifford_batch(sims, gate_lists, stream=None):

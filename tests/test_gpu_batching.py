@@ -81,3 +81,36 @@ def test_tuning_knobs_keep_results():
         assert v in autotune.CANDIDATES[k] and ms > 0
         assert sim.get_tuning(k) == v
     sim.close()
+
+
+def test_batched_amplitudes_equal_single_calls_and_oracle():
+    """Four circuits of uneven chi (ragged term counts, one empty batch) in one batched
+    amplitude launch and one reduction: each equals its own lrs_amplitude call bit for
+    bit, and the smallest equals the oracle within the amplitude tolerance."""
+    require_cuda()
+    from oracle import estimators as E
+    from tests._gpu import oracle_terms
+    n = 14
+    sims, xs, specs = [], [], []
+    for i, (chi, B) in enumerate([(300, 37), (4096, 2048), (1000, 0), (256 * 7 + 5, 777)]):
+        ops, _ = workloads.qaoa_e3lin2_circuit(n, 4, 0.3, 0.2, seed=200 + i)
+        low = lrstab.lower_circuit(n, ops)
+        s = lrstab.Simulator(n, 0)
+        s.init_terms(low, chi, mode="sparsify", seed=9 + i)
+        s.apply_clifford(low.gates)
+        sims.append(s)
+        specs.append((ops, chi, 9 + i))
+        xs.append(torch.from_numpy(workloads.random_bitstrings(n, B, seed=50 + i).view(np.int64)).cuda())
+    outs = lrstab.amplitude_batch(sims, xs)
+    for s, x, o in zip(sims, xs, outs):
+        assert torch.equal(o, s.amplitude(x))
+    ops, chi, seed = specs[0]
+    terms, coefs, _ = oracle_terms(n, ops, chi, "sparsify", seed=seed, parallel=True)
+    got = outs[0].cpu().numpy()
+    got = got[:, 0] + 1j * got[:, 1]
+    want = np.array([E.amplitude(terms, coefs, int(x)) for x in xs[0].cpu().numpy().view(np.uint64)])
+    assert np.all(np.abs(got - want) <= amp_tol(want, n, abs(coefs[0]) * np.sqrt(chi)))
+    with pytest.raises(lrstab.LrsError):
+        lrstab.amplitude_batch([sims[0], sims[0]], [xs[0], xs[0]])
+    for s in sims:
+        s.close()

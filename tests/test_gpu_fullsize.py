@@ -97,3 +97,33 @@ def test_full_size_launch_vs_exact_oracle(case):
             assert acc == want_acc, (t, c)
         cur = tr[t]
     assert close <= 2
+
+
+def test_hidden_shift_eight_term_ccz_chi_2_24_vs_exact_oracle():
+    """The 40-qubit hidden shift with its 16 CCZ in the 8-term form (Eq.
+    (CCZ_decomposition), prefactor 1/6, xi = 16/9) sparsified to chi = 2^24 terms (17 GB
+    of tableau): <s|psi>, the amplitudes at the 40 neighbours of s and at random strings
+    against the exact sums over all 2^24 terms; <s|psi> is 1 up to the sparsification
+    error (delta^2 = ||c||_1^2 / chi = 5.9e-4)."""
+    require_cuda()
+    n, chi, dseed = 40, 1 << 24, 77
+    ops, s = workloads.hidden_shift_circuit(n, 16, workloads.SEED_BASE + 3)
+    low = lrstab.lower_circuit(n, ops, "sum8")
+    sim = lrstab.Simulator(n, 0)
+    sim.init_terms(low, chi, mode="sparsify", seed=dseed)
+    sim.apply_clifford(low.gates)
+    xs = [s] + [s ^ (1 << j) for j in range(n)] + [int(x) for x in workloads.random_bitstrings(n, 15, seed=9)]
+    x = torch.tensor(np.asarray(xs, dtype=np.uint64).view(np.int64), device="cuda:0")
+    err = torch.empty(len(xs), dtype=torch.float32, device="cuda:0")
+    a = sim.amplitude(x, err=err).cpu().numpy()
+    err = err.cpu().numpy().astype(np.float64)
+    sim.close()
+    got = a[:, 0] + 1j * a[:, 1]
+    prep = fast.Prepared(n, ops, chi, "sparsify", dseed, ccz_mode="sum8")
+    want = np.array([fast.to_complex(z) for z in prep.sums(xs)[0]])
+    scale = np.maximum(np.abs(want), 2.0 ** (-n / 2))
+    d = np.abs(got - want)
+    assert np.all(d <= 1e-5 * scale), float((d / scale).max())
+    assert np.all(d <= err)
+    delta = np.sqrt(low.l1_norm ** 2 / chi)
+    assert abs(abs(want[0]) - 1.0) <= 5 * delta
