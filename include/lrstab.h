@@ -537,6 +537,11 @@ lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
  *                                 repeating the per-gate scalar work in every lane;
  *                                 results are bit-identical for every value.
  *                                 Narrower tableaux take one lane per term.
+ *   LRS_TUNE_NORM_FUSE_FOLDS      norm estimate: a term that takes the y = G x
+ *                                 route with n - |v| <= this value (0..8, 8) folds
+ *                                 its constraints into the rows of A+J while the
+ *                                 rows are formed (one pass), above it one pass
+ *                                 per constraint.  Same exact per-term value.
  */
 enum {
     LRS_TUNE_AMP_BLOCKS_PER_SM = 0,
@@ -544,7 +549,8 @@ enum {
     LRS_TUNE_MC_CHAINS_PER_BLOCK = 2,
     LRS_TUNE_NORM_MAX_FOLDS = 3,
     LRS_TUNE_MC_STAGES = 4,
-    LRS_TUNE_APPLY_LANES = 5
+    LRS_TUNE_APPLY_LANES = 5,
+    LRS_TUNE_NORM_FUSE_FOLDS = 6
 };
 lrs_status lrs_set_tuning(lrs_ctx* ctx, int32_t param, int64_t value);
 lrs_status lrs_get_tuning(const lrs_ctx* ctx, int32_t param, int64_t* value);

@@ -30,6 +30,7 @@ namespace {
 constexpr int NRM_TPB = 64;   // A's per block
 constexpr int NRM_MFOLD = 12; // most constraints a change-of-variables term may carry
 constexpr int NRM_PIVOTS = 4; // elimination pairs applied per pass over the rows
+constexpr int NRM_MFUSE = 8;  // most constraints folded in the single row pass
 
 struct NormTerm {
     uint64_t glo, ghi, v, s, z0;
@@ -361,7 +362,7 @@ constexpr int norm_min_blocks(int nch) { return nch <= 10 ? 10 : nch <= 14 ? 6 :
 template <int NCH, int NB>
 __global__ void __launch_bounds__(NRM_TPB, norm_min_blocks(NCH)) k_norm(TermsView T, NormPrep P, int64_t L, int64_t tt,
                                                   float2* __restrict__ partial, int64_t n_tiles,
-                                                  int max_folds) {
+                                                  int max_folds, int fuse_folds) {
     extern __shared__ uint64_t smem[];
     __shared__ uint64_t tG[64], tJ[64];
     __shared__ NormTerm tS;
@@ -431,7 +432,77 @@ __global__ void __launch_bounds__(NRM_TPB, norm_min_blocks(NCH)) k_norm(TermsVie
         const uint64_t z0 = tz0;
         uint64_t act, odd, Lb;
         uint32_t sKs;
-        if (fold) {
+        if (fold && mf <= fuse_folds) {   // fuse_folds <= NRM_MFUSE
+            // The folds of the sequential form below, reordered: the pivot rows p_i are
+            // folded first (row p_i only takes h_j from an earlier fold j with p_i in
+            // q_j, since no h holds a pivot, and for the same reason the odd and linear
+            // bits at p_i are those of D), then one pass builds every row of D, applies
+            // every fold's update (x ^= hq_i if c in h_i, h_i if c in q_i) and the lift,
+            // and stores the row once.  The updates are XORs fixed by the q_i, so their
+            // order does not matter.
+            uint64_t Q[NRM_MFUSE], HQ[NRM_MFUSE], Hv[NRM_MFUSE];
+            uint64_t actf = nmask, oddf = dlo, dLb = 0;
+            const uint64_t lb0 = dhi ^ tU ^ (dlo & z0);
+#pragma unroll
+            for (int i = 0; i < NRM_MFUSE; ++i) {
+                Q[i] = 0;
+                HQ[i] = 0;
+                Hv[i] = 0;
+                if (i < mf) {
+                    const int p = tPiv[i];
+                    const uint64_t h = tH[i];
+                    const uint64_t Dp = NRM_AROW(p) ^ tJ[p];
+                    uint64_t r = Dp;
+#pragma unroll
+                    for (int j = 0; j < i; ++j) r ^= Hv[j] & (0ull - getb(Q[j], p));
+                    const uint64_t q = r & actf & ~bit64(p);
+                    const uint64_t op = getb(dlo, p);
+                    const uint64_t lp = getb(lb0, p) ^ (uint64_t)par64(Dp & z0);
+                    dLb ^= h & ((0ull - lp) ^ (oddf & (0ull - op)) ^ q);
+                    oddf ^= h & (0ull - op);
+                    Q[i] = q;
+                    HQ[i] = q ^ (h & (0ull - op));
+                    Hv[i] = h;
+                    actf &= ~bit64(p);
+                }
+            }
+            const uint64_t oddm = oddf & actf;
+            uint64_t dz0 = 0;
+            uint32_t pcnt = 0;
+#pragma unroll
+            for (int hw = 0; hw < 2; ++hw) {
+                const int c0 = 32 * hw, c1 = n < c0 + 32 ? n : c0 + 32;
+                uint32_t hh[NRM_MFUSE], qh[NRM_MFUSE];
+#pragma unroll
+                for (int i = 0; i < NRM_MFUSE; ++i) {
+                    hh[i] = (uint32_t)(Hv[i] >> c0);
+                    qh[i] = (uint32_t)(Q[i] >> c0);
+                }
+                const uint32_t oh = (uint32_t)(oddm >> c0), zh = (uint32_t)(z0 >> c0);
+                for (int c = c0; c < c1; ++c) {
+                    const uint32_t lb = 1u << (c - c0);
+                    const uint64_t Doff = NRM_AROW(c) ^ tJ[c];
+                    uint64_t x = Doff;
+                    if (zh & lb) {
+                        dz0 ^= Doff;
+                        pcnt += (uint32_t)__popcll(Doff & z0);
+                    }
+#pragma unroll
+                    for (int i = 0; i < NRM_MFUSE; ++i) {
+                        if (i >= mf) break;
+                        if (hh[i] & lb) x ^= HQ[i];
+                        if (qh[i] & lb) x ^= Hv[i];
+                    }
+                    if (oh & lb) x ^= oddm;
+                    sW[c * NRM_TPB] = x;
+                }
+            }
+            dz0 ^= dlo & z0;
+            sKs = ((uint32_t)__popcll(z0 & dlo) + 2u * (uint32_t)__popcll(z0 & dhi) + pcnt) & 3u;
+            odd = oddm;
+            Lb = (dhi ^ tU ^ dz0 ^ dLb) & actf;
+            act = actf;
+        } else if (fold) {
             // rows of D off the diagonal, D z0 (mod 2), and sum_{c in z0} |D_c & z0| =
             // twice the number of pairs of z0 joined in D
             uint64_t dz0 = 0, zs = z0;
@@ -576,7 +647,9 @@ static lrs_status launch_norm_t(lrs_ctx* ctx, const NormPrep& P, int64_t L, int6
     const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
     dim3 grid((unsigned)n_tiles, (unsigned)lblocks);
     k_norm<NCH, NB><<<grid, NRM_TPB, smem, st>>>(ctx->view(), P, L, tt, partial, n_tiles,
-                                                  (int)ctx->tune_norm_folds);
+                                                  (int)ctx->tune_norm_folds,
+                                                  (int)(ctx->tune_norm_fuse < NRM_MFUSE ? ctx->tune_norm_fuse
+                                                                                        : NRM_MFUSE));
     LRS_LAUNCH_CHECK("norm kernel");
     return LRS_OK;
 }

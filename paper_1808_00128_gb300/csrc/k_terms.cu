@@ -136,7 +136,7 @@ template <int HB, int TPT = 1>
 struct SmemRows : TermLanes<TPT> {
     static_assert(TPT == 1, "narrow row layouts take one lane per term");
     typedef typename HiWord<HB>::T Hi;
-    static constexpr int kRowUnroll = 2;   // rows per step of the Hadamard row pass
+    static constexpr int kRowUnroll = 4;   // rows per load group of the Hadamard row pass
     struct Mat {
         uint32_t* lo;
         Hi* hi;
@@ -184,7 +184,7 @@ struct SmemRows : TermLanes<TPT> {
 // of 32 terms.
 template <int TPT>
 struct SmemRows<64, TPT> : TermLanes<TPT> {
-    static constexpr int kRowUnroll = 4;   // registers are free here (shared memory caps the blocks per SM)
+    static constexpr int kRowUnroll = 4;   // rows per load group (2, 3, 6 and 8 measured slower)
     struct Mat {
         uint32_t a;
     };

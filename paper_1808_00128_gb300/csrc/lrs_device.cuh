@@ -132,8 +132,8 @@ struct HRowMasks {
 
 template <bool FAN, class Rows, class Mat>
 __device__ __forceinline__ void prop_h_row(Rows& R, const Mat& X, const Mat& Y, const Mat& Mm, int p,
-                                           const HRowMasks& k, uint32_t& add2, uint32_t& sub1) {
-    const uint64_t Xp = R.get(X, p), Yp = R.get(Y, p), Mp = R.get(Mm, p);
+                                           const HRowMasks& k, uint64_t Xp, uint64_t Yp, uint64_t Mp,
+                                           uint32_t& add2, uint32_t& sub1) {
     const uint32_t Xl = (uint32_t)Xp, Xh = (uint32_t)(Xp >> 32);
     const uint32_t Yl = (uint32_t)Yp, Yh = (uint32_t)(Yp >> 32);
     const uint32_t Ml = (uint32_t)Mp, Mh = (uint32_t)(Mp >> 32);
@@ -168,6 +168,35 @@ __device__ __forceinline__ void prop_h_row(Rows& R, const Mat& X, const Mat& Y, 
     R.set(Mm, p, ((uint64_t)Mnh << 32) | Mnl);
 }
 
+// Rows p, p - ST, .., p - (U - 1) ST (all >= lo): the 3U row loads are issued before
+// the first row is rewritten, so the loads of a group overlap one another and the
+// rewrites of its rows are independent chains.  (The row accessors order every shared
+// access after the previous store, so a load placed after a store waits for it.)
+template <int U, bool FAN, class Rows, class Mat>
+__device__ __forceinline__ void prop_h_group(Rows& R, const Mat& X, const Mat& Y, const Mat& Mm, int p,
+                                             const HRowMasks& k, uint32_t& add2, uint32_t& sub1) {
+    constexpr int ST = Rows::kStep;
+    uint64_t xs[U], ys[U], ms[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        xs[u] = R.get(X, p - u * ST);
+        ys[u] = R.get(Y, p - u * ST);
+        ms[u] = R.get(Mm, p - u * ST);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) prop_h_row<FAN>(R, X, Y, Mm, p - u * ST, k, xs[u], ys[u], ms[u], add2, sub1);
+}
+
+// This lane's rows from p down to lo (p = lo mod ST), top row first, in groups of
+// Rows::kRowUnroll.
+template <bool FAN, class Rows, class Mat>
+__device__ __forceinline__ void prop_h_span(Rows& R, const Mat& X, const Mat& Y, const Mat& Mm, int p, int lo,
+                                            const HRowMasks& k, uint32_t& add2, uint32_t& sub1) {
+    constexpr int ST = Rows::kStep, U = Rows::kRowUnroll;
+    for (; p - (U - 1) * ST >= lo; p -= U * ST) prop_h_group<U, FAN>(R, X, Y, Mm, p, k, add2, sub1);
+    for (; p >= lo; p -= ST) prop_h_group<1, FAN>(R, X, Y, Mm, p, k, add2, sub1);
+}
+
 // QLO: q < 32 for every term of the warp (the usual case: q is the lowest bit of a
 // mask), so column q lies in the low halves and the high halves only take part in the
 // parities and the fan-out copies.
@@ -196,11 +225,9 @@ __device__ __forceinline__ void prop_h_rows(Rows& R, int n, const HRowMasks& k0,
     constexpr int ST = Rows::kStep;
     const int part = R.part();
     const int top = n - 1 - ((n - 1 - part) & (ST - 1));
-#pragma unroll (Rows::kRowUnroll)
-    for (int p = top; p >= 32; p -= ST) prop_h_row<FAN>(R, X, Y, Mm, p, k, ah, sh);
+    prop_h_span<FAN>(R, X, Y, Mm, top, 32, k, ah, sh);
     const int lt = (n < 32 ? n : 32) - 1;
-#pragma unroll (Rows::kRowUnroll)
-    for (int p = lt - ((lt - part) & (ST - 1)); p >= 0; p -= ST) prop_h_row<FAN>(R, X, Y, Mm, p, k, al, sl);
+    prop_h_span<FAN>(R, X, Y, Mm, lt - ((lt - part) & (ST - 1)), 0, k, al, sl);
     add2 = R.combine(((uint64_t)(ah << part) << 32) | (al << part));
     sub1 = R.combine(((uint64_t)(sh << part) << 32) | (sl << part));
 }
@@ -322,23 +349,27 @@ __device__ __forceinline__ void gate_z(Rows& R, TermRegs& T, int q) {
     (void)R;
     T.ghi ^= bit64(q);
 }
+// Every row a gate reads is loaded before its first store (q != r, so no load reads a
+// row the gate writes): the row accessors keep shared accesses in program order, and a
+// load placed after a store would wait for the stored value's whole dependency chain.
 template <class Rows>
 __device__ __forceinline__ void gate_cz(Rows& R, TermRegs& T, int q, int r) {
     (void)T;
-    const uint64_t Gq = R.G(q), Gr = R.G(r);
-    if (R.own(q)) R.setM(q, R.M(q) ^ Gr);
-    if (R.own(r)) R.setM(r, R.M(r) ^ Gq);
+    const uint64_t Gq = R.G(q), Gr = R.G(r), Mq = R.M(q), Mr = R.M(r);
+    R.sync();   // every lane has read M_q, M_r before their owners rewrite them
+    if (R.own(q)) R.setM(q, Mq ^ Gr);
+    if (R.own(r)) R.setM(r, Mr ^ Gq);
 }
 template <class Rows>
 __device__ __forceinline__ void gate_cx(Rows& R, TermRegs& T, int q, int r) {
-    const uint64_t Mq = R.M(q), Fr = R.F(r);
+    const uint64_t Mq = R.M(q), Fr = R.F(r), Gr = R.G(r), Gq = R.G(q), Fq = R.F(q), Mr = R.M(r);
     const uint32_t g = (gamma_get(T, q) + gamma_get(T, r) + 2u * par64(Mq & Fr)) & 3u;
     gamma_set(T, q, g);
-    R.sync();   // every lane has read the pre-gate M_q before its owner rewrites it
-    if (R.own(r)) R.setG(r, R.G(r) ^ R.G(q));
+    R.sync();   // every lane has read the pre-gate rows before their owners rewrite them
+    if (R.own(r)) R.setG(r, Gr ^ Gq);
     if (R.own(q)) {
-        R.setF(q, R.F(q) ^ Fr);
-        R.setM(q, Mq ^ R.M(r));
+        R.setF(q, Fq ^ Fr);
+        R.setM(q, Mq ^ Mr);
     }
 }
 

@@ -984,6 +984,10 @@ extern "C" lrs_status lrs_set_tuning(lrs_ctx* c, int32_t param, int64_t value) {
             if (value != 1 && value != 2 && value != 4) return lrs_fail(LRS_ERR_ARG, "apply lanes per term: 1, 2 or 4");
             c->tune_apply_lanes = value;
             return LRS_OK;
+        case LRS_TUNE_NORM_FUSE_FOLDS:
+            if (value < 0 || value > 8) return lrs_fail(LRS_ERR_ARG, "norm fused folds in 0..8");
+            c->tune_norm_fuse = value;
+            return LRS_OK;
         default:
             return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
     }
@@ -998,6 +1002,7 @@ extern "C" lrs_status lrs_get_tuning(const lrs_ctx* c, int32_t param, int64_t* v
         case LRS_TUNE_MC_STAGES: *value = c->tune_mc_stages; return LRS_OK;
         case LRS_TUNE_NORM_MAX_FOLDS: *value = c->tune_norm_folds; return LRS_OK;
         case LRS_TUNE_APPLY_LANES: *value = c->tune_apply_lanes; return LRS_OK;
+        case LRS_TUNE_NORM_FUSE_FOLDS: *value = c->tune_norm_fuse; return LRS_OK;
         default: return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
     }
 }

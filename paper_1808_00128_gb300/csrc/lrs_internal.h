@@ -97,6 +97,7 @@ struct lrs_ctx {
     int64_t tune_mc_cg = 64;        // Metropolis: chains per block (1..64)
     int64_t tune_mc_stages = 2;     // Metropolis: chains in flight per block (1..4)
     int64_t tune_norm_folds = 12;   // norm: terms with n - |v| <= this sum over y = G x (-1..12)
+    int64_t tune_norm_fuse = 8;     // norm: of those, n - |v| <= this fold while forming the rows (0..8)
     int64_t tune_apply_lanes = 1;   // apply_clifford, 64-bit rows (n > 48): lanes per term (1, 2, 4)
     // equatorial samples of median-of-means estimates
     double* eta_buf = nullptr;

@@ -22,16 +22,20 @@ def _sim(n, ops, chi, mode, seed=0, ccz_mode="proj", alpha0=0, chi_total=None):
 
 
 # per-term paths of the kernel: -1 forms K = G^T (A+J) G for every term; 0 sums over
-# y = G x for terms with v = all qubits; 12 for terms with up to 12 qubits outside v
-FOLDS = (-1, 0, 12)
+# y = G x for terms with v = all qubits; 12 for terms with up to 12 qubits outside v,
+# their constraints folded while the rows are formed (up to 8) or one pass each
+# ("seq": every constraint in its own pass)
+FOLDS = (-1, 0, 12, "seq")
 
 
 def _etas(sim, L, seed):
     out = {}
     for f in FOLDS:
-        sim.set_tuning("norm_max_folds", f)
+        sim.set_tuning("norm_max_folds", 12 if f == "seq" else f)
+        sim.set_tuning("norm_fuse_folds", 0 if f == "seq" else 8)
         out[f] = sim.norm_estimate(L, seed=seed).cpu().numpy()
     sim.set_tuning("norm_max_folds", 12)
+    sim.set_tuning("norm_fuse_folds", 8)
     return out
 
 
