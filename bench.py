@@ -147,24 +147,32 @@ def norm_ops_per_unit(n, vw, max_folds):
     return np.where(m <= max_folds, 8 * n + 5 * m * n + 4 * vw ** 2, 8 * n * n + 4 * vw ** 2)
 
 
-def metropolis_bytes(chi, C, T, n, accept=0.5):
+def metropolis_bytes(chi, C, T, n, accept=0.5, lookahead=1):
     """Algorithmic HBM bytes of T steps of C chains: the 16-byte state of every (chain,
     term) read, written back for accepted moves, and the rows F_j, M_j of every term
-    (16 n bytes per term per step)."""
-    return T * (chi * C * (16 + 16 * accept) + chi * 16 * n)
+    (16 n bytes per term per step).  With two steps per pass the state is read once per
+    pass and written back when either of its two moves was accepted."""
+    one = chi * C * (16 + 16 * accept) + chi * 16 * n
+    if lookahead == 1:
+        return T * one
+    two = chi * C * (16 + 16 * (1 - (1 - accept) ** 2)) + 2 * chi * 16 * n
+    return (T // 2) * two + (T % 2) * one
 
 
 def units_per_step(chi, B, C, T):
     return chi * (B + C * (T + 1))
 
 
-def launches_per_step(T):
+def launches_per_step(T, lookahead=1):
     """Library kernels one step launches: init, apply, amplitude + reduce, norm (prep,
     equatorial draws, norm, reduce), chain starts, chains_init (amplitude with Pauli
     states, reduce, chain scalars), Metropolis (set, first, graphs of 16 steps with
-    2 launches per step and an advance node, the remaining steps, out)."""
+    2 launches per pass of `lookahead` steps and an advance node, the remaining steps,
+    out)."""
     g, r = divmod(T, 16)
-    return 1 + 1 + 2 + 4 + 1 + 3 + (2 + g * (2 * 16 + 1) + 2 * r + 1)
+    per_graph = 2 * (16 // lookahead) + 1
+    rest = 2 * (r // lookahead + r % lookahead)
+    return 1 + 1 + 2 + 4 + 1 + 3 + (2 + g * per_graph + rest + 1)
 
 
 # DRAM bytes per launch of the dominant kernel (ncu: dram__bytes_read.sum +
@@ -432,6 +440,11 @@ class StepRunner:
         s = self.shape
         return units_per_step(self.chi, s["B"], s["C"], s["T"])
 
+    @property
+    def lookahead(self):
+        """Metropolis steps per pass over the Pauli states (the context's knob)."""
+        return self.sim.get_tuning("mc_lookahead")
+
     def step(self, ev=None, idx=0):
         st = self.stream
 
@@ -532,9 +545,13 @@ class StepRunner:
                        "frac": k_ops / t / alu_peak, "frac_formula": f_ops / t / alu_peak, "ms": phase_ms[p],
                        "rate": units[p][1] / t, "rate_unit": units[p][0] + "/s"}
         t = phase_ms["metropolis"] * 1e-3
-        byts = metropolis_bytes(chi, s["C"], s["T"], n)
+        # the kernel's own bytes (two steps per pass read the states once) and the
+        # hot-path table's one-step-per-pass bytes
+        byts = metropolis_bytes(chi, s["C"], s["T"], n, lookahead=self.lookahead)
+        byts1 = metropolis_bytes(chi, s["C"], s["T"], n)
         rows["metropolis"] = {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                              "frac": byts / t / 1e9 / hbm_peak, "frac_formula": byts / t / 1e9 / hbm_peak,
+                              "frac": byts / t / 1e9 / hbm_peak, "frac_formula": byts1 / t / 1e9 / hbm_peak,
+                              "steps_per_pass": self.lookahead,
                               "ms": phase_ms["metropolis"], "ms_per_metropolis_step": phase_ms["metropolis"] / s["T"],
                               "rate": units["metropolis"][1] / t, "rate_unit": units["metropolis"][0] + "/s"}
         return rows
@@ -1310,7 +1327,7 @@ def main():
                       "parallelism": f"replicas x{world}", "tuned": tuned},
            "roofline": roof, "phases": rows, "amplitude_error": err, "parity_slices": parity,
            "sparsification_certificate": cert,
-           "cpu_baseline": cpu, "cpu_baseline_python": cpu_py, "e2e": e2e, "gpu_launches": launches_per_step(r.shape["T"]) * args.steps,
+           "cpu_baseline": cpu, "cpu_baseline_python": cpu_py, "e2e": e2e, "gpu_launches": launches_per_step(r.shape["T"], r.lookahead) * args.steps,
            "clocks": clk.summary(), "ess": ess, "side_step": side, **extra}
     print(json.dumps(out))
 

@@ -542,6 +542,14 @@ lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
  *                                 its constraints into the rows of A+J while the
  *                                 rows are formed (one pass), above it one pass
  *                                 per constraint.  Same exact per-term value.
+ *   LRS_TUNE_MC_LOOKAHEAD         Metropolis flip chains: steps per pass over the
+ *                                 chains' Pauli states (1 or 2, default 2).  With 2
+ *                                 one pass forms <y|psi> for step t's proposal and
+ *                                 for both strings step t + 1 may propose (after an
+ *                                 accepted or a rejected move; proposals do not
+ *                                 depend on the chain), then both decisions are taken
+ *                                 in order: the same chains, bit for bit, as one step
+ *                                 per pass, with half the Pauli-state reads.
  */
 enum {
     LRS_TUNE_AMP_BLOCKS_PER_SM = 0,
@@ -550,7 +558,8 @@ enum {
     LRS_TUNE_NORM_MAX_FOLDS = 3,
     LRS_TUNE_MC_STAGES = 4,
     LRS_TUNE_APPLY_LANES = 5,
-    LRS_TUNE_NORM_FUSE_FOLDS = 6
+    LRS_TUNE_NORM_FUSE_FOLDS = 6,
+    LRS_TUNE_MC_LOOKAHEAD = 7
 };
 lrs_status lrs_set_tuning(lrs_ctx* ctx, int32_t param, int64_t value);
 lrs_status lrs_get_tuning(const lrs_ctx* ctx, int32_t param, int64_t* value);

@@ -18,6 +18,7 @@ CANDIDATES = {
     "mc_chains_per_block": [32, 64],
     "norm_max_folds": [-1, 4, 8, 12],
     "mc_stages": [1, 2, 3, 4],
+    "mc_lookahead": [1, 2],
 }
 
 
@@ -88,6 +89,7 @@ def tune(sim, x=None, L: int | None = None, chains: int | None = None, cache_pat
     if chains:
         jobs.append(("mc_chains_per_block", chains, lambda: sim.metropolis(16, seed=1)))
         jobs.append(("mc_stages", chains, lambda: sim.metropolis(16, seed=1)))
+        jobs.append(("mc_lookahead", chains, lambda: sim.metropolis(16, seed=1)))
     for knob, batch, fn in jobs:
         key = f"{knob}|n={sim.n}|chi={sim.chi}|batch={batch}"
         if key in cache:

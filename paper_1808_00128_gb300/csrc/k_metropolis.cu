@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     extern __shared__ __align__(128) unsigned char mc_dyn[];
     McStage* stage = reinterpret_cast<McStage*>(mc_dyn);
     __shared__ float2 red[MC_CG][MC_TPB / 32];
-    __shared__ int32_t spj[MC_CG], sj[MC_CG];
+    __shared__ int32_t spj[MC_CG], spq[MC_CG], sj[MC_CG];
     __shared__ __align__(8) uint64_t full[MC_ST];
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     const int64_t pairs = C * T.cap;   // entries of the Pauli-state arrays
     if (tid < nc) {
         spj[tid] = pend[c0 + tid];
+        spq[tid] = pend[C + c0 + tid];
         sj[tid] = jprop[c0 + tid];
     }
     if (tid < MC_ST) mc_bar_init(mc_smem(&full[tid]));
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
         __syncthreads();
         if (abort_flag) break;   // uniform: read after the barrier
         const int64_t c = c0 + ci;
-        const int pj = spj[ci], j = sj[ci];
+        const int pj = spj[ci], pq = spq[ci], j = sj[ci];
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < MC_TPT; ++k) {
@@ -199,8 +200,14 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
                 mu = (mu + (uint32_t)(getb(glo[k], pj) | (getb(ghi[k], pj) << 1)) + 2u * par64(w & Fp)) & 3u;
                 u ^= Fp;
                 w ^= S.mp[tl[k]];
-                q_store<CQ>(Q, pairs, c * T.cap + a0 + tl[k], u, w, mu);
             }
+            if (pq >= 0) {   // the second flip of a two-step pass (rows from global memory)
+                const uint64_t Fq = T.F[(int64_t)pq * T.cap + a0 + tl[k]];
+                mu = (mu + (uint32_t)(getb(glo[k], pq) | (getb(ghi[k], pq) << 1)) + 2u * par64(w & Fq)) & 3u;
+                u ^= Fq;
+                w ^= T.M[(int64_t)pq * T.cap + a0 + tl[k]];
+            }
+            if (pj >= 0 || pq >= 0) q_store<CQ>(Q, pairs, c * T.cap + a0 + tl[k], u, w, mu);
             const uint64_t Fj = S.fj[tl[k]];
             const uint32_t muy =
                 (mu + (uint32_t)(getb(glo[k], j) | (getb(ghi[k], j) << 1)) + 2u * par64(w & Fj)) & 3u;
@@ -245,6 +252,198 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
     }
 }
 
+// Two steps per pass over the Pauli states.  The proposals j1 = j_t and j2 = j_{t+1}
+// are drawn from the counter RNG and do not depend on the chain, so one pass can form
+// <y|psi> for every string step t + 1 may propose: y1 = x ^ e_j1 (step t), y1 ^ e_j2
+// (step t + 1 after an accepted move) and x ^ e_j2 (after a rejected one), with
+// Q_y1 = Q_x P_j1, Q_y1 P_j2 and Q_x P_j2.  The accept kernel then takes both
+// decisions in order.  Each term's contribution to each sum is the one a single step
+// would add for the same string, in the same order, so the chains are bit-identical to
+// single steps; the pass reads Q once per two steps (HBM-bound at one step per pass).
+// Pending flips: both accepted flips of the previous pass, committed in order.
+struct McStage2 {
+    __align__(16) unsigned char q[MC_TERMS * 16];
+    uint64_t f1[MC_TERMS], m1[MC_TERMS], f2[MC_TERMS], m2[MC_TERMS];   // rows F, M of j1, j2
+    uint64_t fp[MC_TERMS], mp[MC_TERMS], fq[MC_TERMS], mq[MC_TERMS];   // rows of the pending flips
+};
+
+// b i^m <0|X(u) Z(w) U_H|s> contribution of one term to a sum over terms (Eq. (amplitude1)).
+__device__ __forceinline__ void mc_add(float2& acc, float2 base, uint64_t s, uint64_t nv, uint64_t sv,
+                                       uint32_t mu, uint64_t u, uint64_t w) {
+    if (((u ^ s) & nv) == 0) {
+        const uint32_t sign = par64(u & w) ^ par64(u & sv);
+        const float2 t = times_i_pow(base, mu + 2u * sign);
+        acc.x += t.x;
+        acc.y += t.y;
+    }
+}
+
+template <bool CQ>
+__global__ void __launch_bounds__(MC_TPB) k_metro_propose2(TermsView T, int64_t C, void* __restrict__ Q,
+                                                           const int32_t* __restrict__ pend,
+                                                           const int32_t* __restrict__ jprop,
+                                                           float2* __restrict__ partial, int64_t n_tiles,
+                                                           int cg, int nst, int* err, int groups_fast) {
+    extern __shared__ __align__(128) unsigned char mc_dyn[];
+    McStage2* stage = reinterpret_cast<McStage2*>(mc_dyn);
+    __shared__ float2 red[3 * MC_CG][MC_TPB / 32];
+    __shared__ int32_t sp1[MC_CG], sp2[MC_CG], sj1[MC_CG], sj2[MC_CG];
+    __shared__ __align__(8) uint64_t full[MC_ST];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x;
+    const int64_t tile = groups_fast ? blockIdx.y : blockIdx.x;
+    const int64_t c0 = (int64_t)(groups_fast ? blockIdx.x : blockIdx.y) * cg;
+    const int nc = (int)(C - c0 < cg ? C - c0 : cg);
+    const int64_t a0 = tile * MC_TERMS;
+    const int64_t pairs = C * T.cap;
+    if (tid < nc) {
+        sp1[tid] = pend[c0 + tid];
+        sp2[tid] = pend[C + c0 + tid];
+        sj1[tid] = jprop[c0 + tid];
+        sj2[tid] = jprop[C + c0 + tid];
+    }
+    if (tid < MC_ST) mc_bar_init(mc_smem(&full[tid]));
+    if (tid == 0) abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    // one-shot test request, as in k_metro_propose
+    uint32_t extra = 0;
+    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && *(volatile int*)&err[1] != 0) {
+        *(volatile int*)&err[1] = 0;
+        extra = 16;
+    }
+    auto issue = [&](int ci, int si) {   // thread 0: chain ci into stage si
+        McStage2& S = stage[si];
+        const uint32_t bar = mc_smem(&full[si]);
+        const int p1 = sp1[ci], p2 = sp2[ci], j1 = sj1[ci], j2 = sj2[ci];
+        const int64_t c = c0 + ci;
+        const uint32_t qb = CQ ? MC_TERMS * 12 : MC_TERMS * 16;
+        const uint32_t rb = (uint32_t)sizeof(S.f1);
+        mc_bar_expect(bar, qb + 4 * rb + (p1 >= 0 ? 2 * rb : 0u) + (p2 >= 0 ? 2 * rb : 0u) + (ci == 0 ? extra : 0u));
+        if (CQ) {
+            mc_bulk_load(mc_smem(S.q), reinterpret_cast<const uint64_t*>(Q) + c * T.cap + a0, MC_TERMS * 8, bar);
+            mc_bulk_load(mc_smem(S.q + MC_TERMS * 8),
+                         reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint64_t*>(Q) + pairs) + c * T.cap + a0,
+                         MC_TERMS * 4, bar);
+        } else {
+            mc_bulk_load(mc_smem(S.q), reinterpret_cast<const ulonglong2*>(Q) + c * T.cap + a0, MC_TERMS * 16, bar);
+        }
+        mc_bulk_load(mc_smem(S.f1), T.F + (int64_t)j1 * T.cap + a0, rb, bar);
+        mc_bulk_load(mc_smem(S.m1), T.M + (int64_t)j1 * T.cap + a0, rb, bar);
+        mc_bulk_load(mc_smem(S.f2), T.F + (int64_t)j2 * T.cap + a0, rb, bar);
+        mc_bulk_load(mc_smem(S.m2), T.M + (int64_t)j2 * T.cap + a0, rb, bar);
+        if (p1 >= 0) {
+            mc_bulk_load(mc_smem(S.fp), T.F + (int64_t)p1 * T.cap + a0, rb, bar);
+            mc_bulk_load(mc_smem(S.mp), T.M + (int64_t)p1 * T.cap + a0, rb, bar);
+        }
+        if (p2 >= 0) {
+            mc_bulk_load(mc_smem(S.fq), T.F + (int64_t)p2 * T.cap + a0, rb, bar);
+            mc_bulk_load(mc_smem(S.mq), T.M + (int64_t)p2 * T.cap + a0, rb, bar);
+        }
+    };
+    if (tid == 0)
+        for (int ci = 0; ci < nc && ci < nst; ++ci) issue(ci, ci);
+
+    int tl[MC_TPT];
+    uint64_t glo[MC_TPT], ghi[MC_TPT], s[MC_TPT], nv[MC_TPT], sv[MC_TPT];
+    float2 base[MC_TPT];
+    bool live[MC_TPT];
+#pragma unroll
+    for (int k = 0; k < MC_TPT; ++k) {
+        tl[k] = tid + k * MC_TPB;
+        const int64_t a = a0 + tl[k];
+        glo[k] = T.glo[a];
+        ghi[k] = T.ghi[a];
+        const uint64_t v = T.v[a];
+        s[k] = T.s[a];
+        nv[k] = ~v & T.nmask;
+        sv[k] = s[k] & v;
+        const uint32_t om = T.omega[a];
+        live[k] = ((om >> 3) & 1u) == 0u;
+        base[k] = z8_scale(T.coef[a], (int)(om & 7u), __popcll(v) + (int)(om >> 8));
+    }
+    int ci = 0, si = 0;
+    uint32_t ph = 0;
+    for (; ci < nc; ++ci) {
+        const McStage2& S = stage[si];
+        if (!mc_bar_wait(mc_smem(&full[si]), ph)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;   // uniform: read after the barrier
+        const int64_t c = c0 + ci;
+        const int p1 = sp1[ci], p2 = sp2[ci], j1 = sj1[ci], j2 = sj2[ci];
+        float2 acc1 = make_float2(0.f, 0.f), acc2a = acc1, acc2r = acc1;
+#pragma unroll
+        for (int k = 0; k < MC_TPT; ++k) {
+            uint64_t u, w;
+            uint32_t mu;
+            if (CQ)
+                q_unpack<true>(reinterpret_cast<const uint64_t*>(S.q)[tl[k]],
+                               reinterpret_cast<const uint32_t*>(S.q + MC_TERMS * 8)[tl[k]], u, w, mu);
+            else
+                q_unpack<false>(reinterpret_cast<const ulonglong2*>(S.q)[tl[k]].x,
+                                reinterpret_cast<const ulonglong2*>(S.q)[tl[k]].y, u, w, mu);
+            if (p1 >= 0) {   // commit the flips accepted in the previous pass, in order
+                const uint64_t Fp = S.fp[tl[k]];
+                mu = (mu + (uint32_t)(getb(glo[k], p1) | (getb(ghi[k], p1) << 1)) + 2u * par64(w & Fp)) & 3u;
+                u ^= Fp;
+                w ^= S.mp[tl[k]];
+            }
+            if (p2 >= 0) {
+                const uint64_t Fq = S.fq[tl[k]];
+                mu = (mu + (uint32_t)(getb(glo[k], p2) | (getb(ghi[k], p2) << 1)) + 2u * par64(w & Fq)) & 3u;
+                u ^= Fq;
+                w ^= S.mq[tl[k]];
+            }
+            if (p1 >= 0 || p2 >= 0) q_store<CQ>(Q, pairs, c * T.cap + a0 + tl[k], u, w, mu);
+            if (!live[k]) continue;
+            const uint64_t F1 = S.f1[tl[k]], M1 = S.m1[tl[k]], F2 = S.f2[tl[k]], M2 = S.m2[tl[k]];
+            const uint32_t g1 = (uint32_t)(getb(glo[k], j1) | (getb(ghi[k], j1) << 1));
+            const uint32_t g2 = (uint32_t)(getb(glo[k], j2) | (getb(ghi[k], j2) << 1));
+            // y1 = x ^ e_j1
+            const uint32_t mu1 = (mu + g1 + 2u * par64(w & F1)) & 3u;
+            const uint64_t u1 = u ^ F1, w1 = w ^ M1;
+            mc_add(acc1, base[k], s[k], nv[k], sv[k], mu1, u1, w1);
+            // y1 ^ e_j2 (step t accepted)
+            mc_add(acc2a, base[k], s[k], nv[k], sv[k], (mu1 + g2 + 2u * par64(w1 & F2)) & 3u, u1 ^ F2, w1 ^ M2);
+            // x ^ e_j2 (step t rejected)
+            mc_add(acc2r, base[k], s[k], nv[k], sv[k], (mu + g2 + 2u * par64(w & F2)) & 3u, u ^ F2, w ^ M2);
+        }
+        block_sum(acc1, red, 3 * ci);
+        block_sum(acc2a, red, 3 * ci + 1);
+        block_sum(acc2r, red, 3 * ci + 2);
+        __syncthreads();   // every thread is done with this stage
+        if (tid == 0 && ci + nst < nc) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(ci + nst, si);
+        }
+        if (++si == nst) {
+            si = 0;
+            ph ^= 1u;
+        }
+    }
+    if (ci < nc) {
+        // gave up: wait (bounded) for the copies still in flight, report, and leave the
+        // partial sums unwritten
+        if (tid == 0) {
+            for (int cj = ci; cj < nc && cj < ci + nst; ++cj) {
+                mc_bar_wait(mc_smem(&full[si]), ph);
+                if (++si == nst) {
+                    si = 0;
+                    ph ^= 1u;
+                }
+            }
+            atomicExch(err, 1);
+        }
+        return;
+    }
+    for (int e = tid; e < 3 * nc; e += MC_TPB) {   // sum r of chain cc: [r][chain][tile]
+        const int cc = e / 3, r = e - 3 * cc;
+        float2 acc = red[e][0];
+        for (int w2 = 1; w2 < MC_TPB / 32; ++w2) { acc.x += red[e][w2].x; acc.y += red[e][w2].y; }
+        partial[((int64_t)r * C + c0 + cc) * n_tiles + tile] = acc;
+    }
+}
+
 __device__ __forceinline__ double chain_reduce(const float2* __restrict__ partial, int64_t c,
                                                int64_t n_tiles) {
     double re = 0.0, im = 0.0;
@@ -280,6 +479,7 @@ __global__ void k_chains_set(const double* __restrict__ amp, int64_t C, const ui
     cx[c] = xs[c] & nmask;
     cp[c] = re * re + im * im;
     pend[c] = -1;
+    pend[C + c] = -1;
 }
 
 // Per-call parameters live in device memory so that a captured graph of steps
@@ -290,9 +490,11 @@ __global__ void k_mc_set(McParams* P, uint64_t seed, int64_t step0) {
 }
 __global__ void k_mc_advance(McParams* P, int64_t by) { P->step0 += by; }
 
-__global__ void k_metro_first(int64_t C, const McParams* __restrict__ P, int n, int32_t* jprop) {
+__global__ void k_metro_first(int64_t C, const McParams* __restrict__ P, int n, int32_t* jprop, int32_t* jprop2) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < C) jprop[c] = draw_j(P->seed, c, P->step0, n);
+    if (c >= C) return;
+    jprop[c] = draw_j(P->seed, c, P->step0, n);
+    if (jprop2) jprop2[c] = draw_j(P->seed, c, P->step0 + 1, n);
 }
 
 // FP64 accept test (Sec. 4.2) and the proposal index of the next step.
@@ -320,8 +522,55 @@ __global__ void k_metro_accept(const float2* __restrict__ partial, int64_t n_til
         } else {
             pend[c] = -1;
         }
+        pend[C + c] = -1;
         if (trace) trace[c] = cx[c];
         jprop[c] = draw_j(seed, c, step + 1, n);
+    }
+}
+
+// The two decisions of a two-step pass (steps t and t + 1), each the FP64 test of
+// k_metro_accept with the same draws: step t + 1 compares the sum of the string it
+// proposes from the state step t left.  Sums in partial: [0] y1, [1] y1 ^ e_j2,
+// [2] x ^ e_j2; proposals j1 = jprop[c], j2 = jprop[C + c].
+__global__ void k_metro_accept2(const float2* __restrict__ partial, int64_t n_tiles,
+                                const McParams* __restrict__ P, int64_t t, int n, uint64_t* cx, double* cp,
+                                int32_t* pend, int32_t* jprop, uint64_t* trace, int64_t C) {
+    const int64_t c = blockIdx.x;
+    const double p1 = chain_reduce(partial, c, n_tiles);
+    __syncthreads();   // every thread has read the first result before the shared sums are reused
+    const double p2a = chain_reduce(partial + C * n_tiles, c, n_tiles);
+    __syncthreads();
+    const double p2r = chain_reduce(partial + 2 * C * n_tiles, c, n_tiles);
+    if (threadIdx.x == 0) {
+        const uint64_t seed = P->seed;
+        const uint64_t key = sm64_key(seed, (uint64_t)c);
+        const int64_t step = P->step0 + t;
+        const int j1 = jprop[c], j2 = jprop[C + c];
+        uint64_t x = cx[c];
+        double px = cp[c];
+        bool a1;
+        if (p1 >= px) a1 = true;
+        else a1 = sm64_unit(sm64_at(key, (uint64_t)(2 * step + 1))) < p1 / px;
+        if (a1) {
+            x ^= 1ull << j1;
+            px = p1;
+        }
+        if (trace) trace[c] = x;
+        const double py = a1 ? p2a : p2r;
+        bool a2;
+        if (py >= px) a2 = true;
+        else a2 = sm64_unit(sm64_at(key, (uint64_t)(2 * (step + 1) + 1))) < py / px;
+        if (a2) {
+            x ^= 1ull << j2;
+            px = py;
+        }
+        if (trace) trace[C + c] = x;
+        cx[c] = x;
+        cp[c] = px;
+        pend[c] = a1 ? j1 : -1;
+        pend[C + c] = a2 ? j2 : -1;
+        jprop[c] = draw_j(seed, c, step + 2, n);
+        jprop[C + c] = draw_j(seed, c, step + 3, n);
     }
 }
 
@@ -403,6 +652,7 @@ __global__ void k_metro_accept_amp(const double* __restrict__ amp, int64_t C, ui
     } else {
         pend[c] = -1;
     }
+    pend[C + c] = -1;
     if (trace) trace[c] = cx[c];
 }
 
@@ -444,8 +694,24 @@ static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2*
     const int64_t groups = (C + cg - 1) / cg;
     const int gf = n_tiles <= 65535 ? 1 : 0;
     dim3 grid = gf ? dim3((unsigned)groups, (unsigned)n_tiles) : dim3((unsigned)n_tiles, (unsigned)groups);
-    for (int64_t t = t0; t < t0 + count; ++t) {
-        const int nst = (int)ctx->tune_mc_stages;
+    const int nst = (int)ctx->tune_mc_stages;
+    int64_t t = t0;
+    if (ctx->tune_mc_lookahead == 2) {
+        for (; t + 1 < t0 + count; t += 2) {
+            if (q_compact(ctx->n))
+                k_metro_propose2<true><<<grid, MC_TPB, nst * sizeof(McStage2), st>>>(
+                    ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d, gf);
+            else
+                k_metro_propose2<false><<<grid, MC_TPB, nst * sizeof(McStage2), st>>>(
+                    ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d, gf);
+            LRS_LAUNCH_CHECK("metropolis two-step propose kernel");
+            k_metro_accept2<<<(unsigned)C, 256, 0, st>>>(partial, n_tiles, ctx->mc_par, t, ctx->n, ctx->cx,
+                                                          ctx->cp, ctx->pend, jprop,
+                                                          trace ? trace + t * C : nullptr, C);
+            LRS_LAUNCH_CHECK("metropolis two-step accept kernel");
+        }
+    }
+    for (; t < t0 + count; ++t) {
         if (q_compact(ctx->n))
             k_metro_propose<true><<<grid, MC_TPB, nst * sizeof(McStage), st>>>(
                 ctx->view(), C, ctx->Q, ctx->pend, jprop, partial, n_tiles, cg, nst, ctx->mc_err_d, gf);
@@ -465,7 +731,8 @@ static lrs_status enqueue_steps(lrs_ctx* ctx, int64_t t0, int64_t count, float2*
 // rebuilt whenever the buffers it was captured with change.
 static lrs_status mc_graph(lrs_ctx* ctx, float2* partial, int32_t* jprop, cudaGraphExec_t* out) {
     const void* key[6] = {partial, jprop, ctx->Q, ctx->F,
-                          (void*)(intptr_t)((ctx->n_chains * 128 + ctx->tune_mc_cg) * 8 + ctx->tune_mc_stages),
+                          (void*)(intptr_t)(((ctx->n_chains * 128 + ctx->tune_mc_cg) * 8 + ctx->tune_mc_stages) * 4 +
+                                            ctx->tune_mc_lookahead),
                           (void*)(intptr_t)ctx->cap};
     if (ctx->mc_exec && memcmp(key, ctx->mc_key, sizeof(key)) == 0) {
         *out = (cudaGraphExec_t)ctx->mc_exec;
@@ -514,8 +781,9 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
     const int64_t C = ctx->n_chains;
     const int64_t n_tiles = ctx->cap / MC_TERMS;
     void* scr = nullptr;
-    const size_t part_bytes = (size_t)C * n_tiles * sizeof(float2);
-    lrs_status rc = lrs_scratch(ctx, part_bytes + (size_t)C * sizeof(int32_t) + 256, &scr);
+    // partial sums: three per chain and tile for two-step passes; proposals j_t, j_{t+1}
+    const size_t part_bytes = 3 * (size_t)C * n_tiles * sizeof(float2);
+    lrs_status rc = lrs_scratch(ctx, part_bytes + 2 * (size_t)C * sizeof(int32_t) + 256, &scr);
     if (rc != LRS_OK) return rc;
     if (!ctx->mc_par) LRS_CUDA(cudaMalloc(&ctx->mc_par, sizeof(McParams)));
     lrs_status rf = mc_flags(ctx);
@@ -528,10 +796,14 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
                                   (int)(MC_ST * sizeof(McStage))));
     LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(MC_ST * sizeof(McStage))));
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(MC_ST * sizeof(McStage2))));
+    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(MC_ST * sizeof(McStage2))));
     float2* partial = (float2*)scr;
     int32_t* jprop = (int32_t*)((char*)scr + ((part_bytes + 255) & ~(size_t)255));
     k_mc_set<<<1, 1, 0, st>>>(ctx->mc_par, seed, step0);
-    k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->mc_par, ctx->n, jprop);
+    k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->mc_par, ctx->n, jprop, jprop + C);
     LRS_LAUNCH_CHECK("metropolis first kernel");
     int64_t done = 0;
     if (!trace && steps >= LRS_MC_GRAPH_STEPS) {
@@ -571,7 +843,7 @@ lrs_status launch_metropolis_propose(lrs_ctx* ctx, uint64_t seed, int64_t step, 
     LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(MC_ST * sizeof(McStage))));
     k_mc_set<<<1, 1, 0, st>>>(ctx->mc_par, seed, step);
-    k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->mc_par, ctx->n, ctx->jbuf);
+    k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->mc_par, ctx->n, ctx->jbuf, nullptr);
     LRS_LAUNCH_CHECK("metropolis first kernel");
     const int cg = (int)ctx->tune_mc_cg;
     const int64_t groups = (C + cg - 1) / cg;

@@ -837,7 +837,7 @@ extern "C" lrs_status lrs_chains_init(lrs_ctx* c, int64_t n_chains, const uint64
         c->chains_cap = 0;
         LRS_CUDA(cudaMalloc(&c->cx, (size_t)n_chains * sizeof(uint64_t)));
         LRS_CUDA(cudaMalloc(&c->cp, (size_t)n_chains * sizeof(double)));
-        LRS_CUDA(cudaMalloc(&c->pend, (size_t)n_chains * sizeof(int32_t)));
+        LRS_CUDA(cudaMalloc(&c->pend, 2 * (size_t)n_chains * sizeof(int32_t)));
         c->chains_cap = n_chains;
     }
     c->n_chains = n_chains;
@@ -988,6 +988,10 @@ extern "C" lrs_status lrs_set_tuning(lrs_ctx* c, int32_t param, int64_t value) {
             if (value < 0 || value > 8) return lrs_fail(LRS_ERR_ARG, "norm fused folds in 0..8");
             c->tune_norm_fuse = value;
             return LRS_OK;
+        case LRS_TUNE_MC_LOOKAHEAD:
+            if (value != 1 && value != 2) return lrs_fail(LRS_ERR_ARG, "Metropolis steps per pass: 1 or 2");
+            c->tune_mc_lookahead = value;
+            return LRS_OK;
         default:
             return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
     }
@@ -1003,6 +1007,7 @@ extern "C" lrs_status lrs_get_tuning(const lrs_ctx* c, int32_t param, int64_t* v
         case LRS_TUNE_NORM_MAX_FOLDS: *value = c->tune_norm_folds; return LRS_OK;
         case LRS_TUNE_APPLY_LANES: *value = c->tune_apply_lanes; return LRS_OK;
         case LRS_TUNE_NORM_FUSE_FOLDS: *value = c->tune_norm_fuse; return LRS_OK;
+        case LRS_TUNE_MC_LOOKAHEAD: *value = c->tune_mc_lookahead; return LRS_OK;
         default: return lrs_fail(LRS_ERR_ARG, "unknown tuning parameter %d", param);
     }
 }

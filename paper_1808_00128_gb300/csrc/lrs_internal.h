@@ -96,6 +96,7 @@ struct lrs_ctx {
     int64_t tune_norm_tiles = 2048; // norm: maximum term tiles per A-block column
     int64_t tune_mc_cg = 64;        // Metropolis: chains per block (1..64)
     int64_t tune_mc_stages = 2;     // Metropolis: chains in flight per block (1..4)
+    int64_t tune_mc_lookahead = 2;  // Metropolis: steps per pass over the Pauli states (1, 2)
     int64_t tune_norm_folds = 12;   // norm: terms with n - |v| <= this sum over y = G x (-1..12)
     int64_t tune_norm_fuse = 8;     // norm: of those, n - |v| <= this fold while forming the rows (0..8)
     int64_t tune_apply_lanes = 1;   // apply_clifford, 64-bit rows (n > 48): lanes per term (1, 2, 4)
@@ -112,7 +113,7 @@ struct lrs_ctx {
     size_t Q_bytes = 0;
     uint64_t* cx = nullptr;         // [chain] current x
     double* cp = nullptr;           // [chain] P(x) (unnormalised)
-    int32_t* pend = nullptr;        // [chain] pending accepted flip (-1 none)
+    int32_t* pend = nullptr;        // [2][chain] pending accepted flips, committed in order (-1 none)
     int64_t chains_cap = 0;
     bool q_stale = false;           // x moved by learned proposals: Q must be rebuilt
     McParams* mc_par = nullptr;     // device parameters of the flip-chain kernels

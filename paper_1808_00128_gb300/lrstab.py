@@ -23,7 +23,7 @@ OP = dict(H=0, S=1, SDG=2, Z=3, CX=4, CZ=5, P0=6, P1=7, SLOT=8)
 CKIND = dict(H=0, S=1, SDG=2, Z=3, CX=4, CZ=5, T=6, RZ=7, CCZ=8)
 CCZ_MODE = dict(proj=0, sum8=1)
 TUNE = dict(amp_blocks_per_sm=0, norm_max_tiles=1, mc_chains_per_block=2, norm_max_folds=3, mc_stages=4,
-            apply_lanes=5, norm_fuse_folds=6)
+            apply_lanes=5, norm_fuse_folds=6, mc_lookahead=7)
 MODE = dict(exact=0, sparsify=1)
 STATUS = {0: "LRS_OK", -1: "LRS_ERR_ARG", -2: "LRS_ERR_OOM", -3: "LRS_ERR_CUDA",
           -4: "LRS_ERR_TIMEOUT", -5: "LRS_ERR_STATE", -6: "LRS_ERR_UNSUPPORTED"}

@@ -11,7 +11,7 @@ class FakeSim:
     n, chi, device = 40, 1 << 16, 0
 
     def __init__(self, **tuning):
-        self.tuning = dict(mc_chains_per_block=64, mc_stages=2)
+        self.tuning = dict(mc_chains_per_block=64, mc_stages=2, mc_lookahead=2)
         self.tuning.update(tuning)
 
     def set_tuning(self, name, value):

@@ -55,6 +55,10 @@ def test_units_and_launches_per_step():
     # set + first + 4 graphs of 16 steps (33 launches each) + out
     assert bench.launches_per_step(64) == 1 + 1 + 2 + 4 + 1 + 3 + 2 + 4 * 33 + 1
     assert bench.launches_per_step(18) == 1 + 1 + 2 + 4 + 1 + 3 + 2 + 33 + 4 + 1
+    # two steps per pass: 8 passes (16 launches) + advance per graph; 3 leftover steps
+    # take one pass and one single step
+    assert bench.launches_per_step(64, 2) == 1 + 1 + 2 + 4 + 1 + 3 + 2 + 4 * 17 + 1
+    assert bench.launches_per_step(19, 2) == 1 + 1 + 2 + 4 + 1 + 3 + 2 + 17 + 4 + 1
 
 
 def test_formula_and_kernel_counts():
@@ -67,6 +71,9 @@ def test_formula_and_kernel_counts():
     assert bench.amplitude_ops_per_unit(50, 25.0, formula=True) == 280.0
     assert bench.amplitude_ops_per_unit(50, 25.0) == 8 * 13 + 16
     assert bench.metropolis_bytes(2, 3, 5, 10) == 5 * (2 * 3 * 24 + 2 * 160)
+    # two steps per pass: states read once per pass, written back with probability
+    # 1 - (1 - 1/2)^2, rows of both proposals; the fifth step is a single step
+    assert bench.metropolis_bytes(2, 3, 5, 10, lookahead=2) == 2 * (2 * 3 * 28 + 2 * 2 * 160) + (2 * 3 * 24 + 2 * 160)
 
 
 def test_traffic_is_dropped_when_the_kernel_changes(monkeypatch):

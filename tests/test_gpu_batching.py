@@ -76,7 +76,7 @@ def test_tuning_knobs_keep_results():
     sim.set_tuning("mc_stages", 2)
     chosen = autotune.tune(sim, x=x, L=64, chains=100)
     assert set(chosen) == {"amp_blocks_per_sm", "norm_max_tiles", "norm_max_folds", "mc_chains_per_block",
-                           "mc_stages"}
+                           "mc_stages", "mc_lookahead"}
     for k, (v, ms) in chosen.items():
         assert v in autotune.CANDIDATES[k] and ms > 0
         assert sim.get_tuning(k) == v

@@ -88,6 +88,16 @@ def test_metropolis_continuation_and_errors():
     sim.metropolis(10, seed=5, step0=0)
     sim.metropolis(10, seed=5, step0=10, x_out=xb)
     assert torch.equal(xa, xb)
+    # odd splits: a two-step pass's second pending flip carries into a single step and
+    # into the next call
+    for look in (1, 2):
+        sim.set_tuning("mc_lookahead", look)
+        sim.chains_init(x0)
+        sim.metropolis(7, seed=5, step0=0)
+        sim.metropolis(13, seed=5, step0=7, x_out=xb)
+        assert torch.equal(xa, xb), look
+    with pytest.raises(lrstab.LrsError):
+        sim.set_tuning("mc_lookahead", 3)
     with pytest.raises(lrstab.LrsError):
         sim.metropolis(-1, seed=0)
     sim.close()
@@ -259,3 +269,36 @@ def test_term_sharded_chains_equal_full_context():
         shards[0].metropolis_accept(torch.zeros((C, 2), dtype=torch.float64, device="cuda:0"), mseed, T + 5)
     for s in shards + [full]:
         s.close()
+
+
+@pytest.mark.parametrize("case", ["n40_12_byte_states", "qaoa_n50_16_byte_states"])
+def test_two_step_passes_equal_single_steps(case):
+    """Two steps per pass over the Pauli states (the default) against one step per
+    pass: the same chains bit for bit -- every trace row, final string and P(x) --
+    with ragged chain groups (70 chains), an odd step count with a trace (no graph) and
+    one with graph replays and a leftover single step."""
+    require_cuda()
+    cfg = workloads.config_mid() if case.startswith("n40") else workloads.config_qaoa()
+    n, ops = cfg["n"], cfg["ops"]
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, 0)
+    sim.init_terms(low, 8192, mode="sparsify", seed=cfg["seed"], chi_total=cfg["chi"])
+    sim.apply_clifford(low.gates)
+    C = 70
+    x0 = sim.sample_terms(C, seed=4)
+    res = {}
+    for look in (1, 2):
+        sim.set_tuning("mc_lookahead", look)
+        sim.chains_init(x0)
+        tr = torch.empty((37, C), dtype=torch.int64, device="cuda:0")
+        po = torch.empty(C, dtype=torch.float64, device="cuda:0")
+        sim.metropolis(37, seed=77, trace=tr, p_out=po)
+        xo = torch.empty(C, dtype=torch.int64, device="cuda:0")
+        po2 = torch.empty(C, dtype=torch.float64, device="cuda:0")
+        sim.metropolis(35, seed=78, step0=37, x_out=xo, p_out=po2)
+        res[look] = (tr.cpu(), po.cpu(), xo.cpu(), po2.cpu())
+    for a, b in zip(res[1], res[2]):
+        assert torch.equal(a, b)
+    moved = (res[2][0][-1] != x0.cpu()).sum().item()
+    assert moved > C // 4          # the chains do move
+    sim.close()
