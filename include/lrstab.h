@@ -529,7 +529,9 @@ lrs_status lrs_alu_probe(int32_t device, int64_t iters, double* ops_per_s);
  *                                 K for every term.  Both give the same exact
  *                                 per-term value.
  *   LRS_TUNE_MC_STAGES            Metropolis: chains whose inputs a block keeps
- *                                 in flight in shared memory (1..4, 2; 12 KB each)
+ *                                 in flight in shared memory (1..4, 1; 12 KB each
+ *                                 for one step per pass, 20 KB for two: one stage
+ *                                 leaves room for the most blocks per SM)
  *   LRS_TUNE_APPLY_LANES          apply_clifford for n > 48 (64-bit rows): lanes
  *                                 per term (1, 2 or 4; default 1).  The lanes of a
  *                                 term share its tableau in shared memory and split

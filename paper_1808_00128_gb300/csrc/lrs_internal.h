@@ -95,7 +95,7 @@ struct lrs_ctx {
     int64_t tune_amp_bps = 8;       // amplitude: target blocks per SM
     int64_t tune_norm_tiles = 2048; // norm: maximum term tiles per A-block column
     int64_t tune_mc_cg = 64;        // Metropolis: chains per block (1..64)
-    int64_t tune_mc_stages = 2;     // Metropolis: chains in flight per block (1..4)
+    int64_t tune_mc_stages = 1;     // Metropolis: chains in flight per block (1..4)
     int64_t tune_mc_lookahead = 2;  // Metropolis: steps per pass over the Pauli states (1, 2)
     int64_t tune_norm_folds = 12;   // norm: terms with n - |v| <= this sum over y = G x (-1..12)
     int64_t tune_norm_fuse = 8;     // norm: of those, n - |v| <= this fold while forming the rows (0..8)
