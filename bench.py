@@ -442,8 +442,11 @@ class StepRunner:
 
     @property
     def lookahead(self):
-        """Metropolis steps per pass over the Pauli states (the context's knob)."""
-        return self.sim.get_tuning("mc_lookahead")
+        """Metropolis steps per pass over the Pauli states (the context's knob, read
+        while the context is open and kept)."""
+        if getattr(self, "_look", None) is None:
+            self._look = self.sim.get_tuning("mc_lookahead")
+        return self._look
 
     def step(self, ev=None, idx=0):
         st = self.stream
@@ -572,6 +575,7 @@ class StepRunner:
                 "norm_estimate": norm ** 2, "relative_to": "max(|a|, ||psi|| 2^{-n/2})"}
 
     def close(self):
+        _ = self.lookahead          # kept for the launch count after the context is gone
         self.sim.close()
 
 
@@ -814,9 +818,10 @@ def sampler_study(local=0, n=20, chi=1 << 14, C=1024, hidden=512, train_samples=
     a, b = _ev()
     a.record()
     for ep in range(epochs):
-        perm = torch.randperm(data.numel(), device=dev, generator=gen)
+        # one gather per epoch; the batches are then contiguous slices (no launch each)
+        shuf = data[torch.randperm(data.numel(), device=dev, generator=gen)]
         for it in range(data.numel() // bs):
-            net.train_step(data[perm[it * bs:(it + 1) * bs]].contiguous(), lr=1e-3)
+            net.train_step(shuf[it * bs:(it + 1) * bs], lr=1e-3)
     b.record()
     b.synchronize()
     t_train = a.elapsed_time(b) * 1e-3
