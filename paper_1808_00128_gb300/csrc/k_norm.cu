@@ -479,9 +479,14 @@ __global__ void __launch_bounds__(NRM_TPB, norm_min_blocks(NCH)) k_norm(TermsVie
                     qh[i] = (uint32_t)(Q[i] >> c0);
                 }
                 const uint32_t oh = (uint32_t)(oddm >> c0), zh = (uint32_t)(z0 >> c0);
+                // the next row of A is loaded one row ahead, so its L1 latency overlaps
+                // this row's folds
+                uint64_t anext = c0 < c1 ? NRM_AROW(c0) : 0ull;
                 for (int c = c0; c < c1; ++c) {
                     const uint32_t lb = 1u << (c - c0);
-                    const uint64_t Doff = NRM_AROW(c) ^ tJ[c];
+                    const uint64_t arow = anext;
+                    if (c + 1 < c1) anext = NRM_AROW(c + 1);
+                    const uint64_t Doff = arow ^ tJ[c];
                     uint64_t x = Doff;
                     if (zh & lb) {
                         dz0 ^= Doff;
