@@ -356,8 +356,10 @@ __global__ void __launch_bounds__(NRM_TPB) k_norm_prep(TermsView T, int max_fold
 
 // Blocks per SM the register budget is sized for: at n <= 40 96 registers (shared
 // memory then fits nine blocks; the few spilled values cost less than the extra
-// warps gain), fewer blocks for wider tableaux, whose elimination keeps more rows live.
-constexpr int norm_min_blocks(int nch) { return nch <= 10 ? 10 : nch <= 14 ? 6 : 5; }
+// warps gain); at 41 <= n <= 56 seven blocks, the most shared memory fits (128
+// registers: measured 2% faster at n = 50 than six blocks at 168, spills included);
+// five for wider tableaux.
+constexpr int norm_min_blocks(int nch) { return nch <= 10 ? 10 : nch <= 14 ? 7 : 5; }
 
 template <int NCH, int NB>
 __global__ void __launch_bounds__(NRM_TPB, norm_min_blocks(NCH)) k_norm(TermsView T, NormPrep P, int64_t L, int64_t tt,
