@@ -59,6 +59,8 @@ def parse(argv=None):
     ap.add_argument("--mlp-gemm-only", action="store_true",
                     help="run only the MADE network tensor-core study (n=64, H=2048, 16384 rows) and "
                          "print its JSON (for ncu captures of the GEMM kernels; not a bench line)")
+    ap.add_argument("--hidden-shift-chains", action="store_true",
+                    help="only the hidden shift's chain study (time for term-sampled chains to reach s)")
     ap.add_argument("--qaoa-apply-only", action="store_true",
                     help="run only apply_clifford on the n=50 QAOA circuit at chi = 2^16, twice, and "
                          "print its times (for ncu captures; not a bench line)")
@@ -813,6 +815,7 @@ def sampler_study(local=0, n=20, chi=1 << 14, C=1024, hidden=512, train_samples=
                         W3=rng.uniform(-lim2, lim2, (n, hidden)), b3=rng.uniform(-lim2, lim2, n)))
     bs = 1024
     net.backward(data[:bs].contiguous())   # first launches (module loading) outside the timed region
+    _ = data[torch.randperm(data.numel(), device=dev)]   # and the first shuffle (kernel loading)
     torch.cuda.synchronize()
     train_steps = max(1, epochs * data.numel() // bs)
     gen = torch.Generator(device=dev).manual_seed(3)
@@ -1109,6 +1112,108 @@ def hidden_shift_sum8_study(local=0, chi=1 << 24, L=256, K=3):
             "mean_eta": float(eta.mean()), "sparsification_certificate": cert}
 
 
+def hidden_shift_chain_study(local=0, plain_steps=2048, learned_steps=32, chunk=64, hidden=512,
+                             train_samples=100_000, epochs=5, exact_samples=4, L=256, K=3):
+    """The hidden shift's chains (n = 40, 16 CCZ, exact 2^16-term decomposition of |s>,
+    1024 chains): every chain starts at a string sampled from one term (the chain start
+    of Sec. 4.2, a term drawn by |b|^2, then x from that CH-form), and each sampler is
+    timed until its chains reach the shift s.  P(x) = |<x|psi>|^2 is 1 at s and 0
+    elsewhere, so from x != s a single flip sees no gradient (every neighbour has
+    P = 0 up to FP32 rounding) and the chain walks blindly on 2^40 strings.  The learned
+    proposal is trained (a) on 10^5 states of those flip chains (the protocol of the
+    sampler comparison) and (b) on `exact_samples` exact samples of the chain-rule
+    marginal sampler (end of Sec. 4.3), replicated to 10^5 rows; its MH steps then
+    propose from the network.  Reported: chains at s after each sampler, the first step
+    at which they got there, GPU seconds, and for (b) the marginal sampler's seconds."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    cfg = workloads.config_hidden_shift()
+    n, chi, s, C = cfg["n"], cfg["chi"], np.uint64(cfg["shift"]), cfg["chains"]
+    dev = torch.device(f"cuda:{local}")
+    low = lrstab.lower_circuit(n, cfg["ops"])
+    sim = lrstab.Simulator(n, local)
+    sim.init_terms(low, chi, mode="exact")
+    sim.apply_clifford(low.gates)
+    x0 = sim.sample_terms(C, seed=31)
+    start_at_s = int((x0.cpu().numpy().view(np.uint64) == s).sum())
+
+    def hits(trace):
+        at = trace == s
+        found = at.any(axis=0)
+        first = np.where(found, at.argmax(axis=0) + 1, -1)
+        return int(found.sum()), (int(np.median(first[found])) if found.any() else None)
+
+    # single flips
+    sim.chains_init(x0)
+    ptrace, ptimes = _run_traced(lambda k, d, b: sim.metropolis(k, seed=41, step0=d, trace=b), C, plain_steps,
+                                 chunk, dev)
+    p_found, p_med = hits(ptrace)
+    plain = {"steps": plain_steps, "gpu_s": ptimes[-1][1], "chains_at_s": p_found, "median_first_step": p_med,
+             "distinct_strings_visited": int(np.unique(ptrace).size)}
+
+    def train(data):
+        net = lrstab.MLP(n, hidden, local)
+        rng = np.random.default_rng(5)
+        lim1, lim2 = 1 / np.sqrt(n), 1 / np.sqrt(hidden)
+        net.set_params(dict(W1=rng.uniform(-lim1, lim1, (hidden, n)), b1=rng.uniform(-lim1, lim1, hidden),
+                            W2=rng.uniform(-lim2, lim2, (hidden, hidden)), b2=rng.uniform(-lim2, lim2, hidden),
+                            W3=rng.uniform(-lim2, lim2, (n, hidden)), b3=rng.uniform(-lim2, lim2, n)))
+        bs = 1024
+        net.backward(data[:bs].contiguous())   # first launches and first shuffle outside the timing
+        _ = data[torch.randperm(data.numel(), device=dev)]
+        torch.cuda.synchronize()
+        gen = torch.Generator(device=dev).manual_seed(3)
+        a, b = _ev()
+        a.record()
+        for ep in range(epochs):
+            shuf = data[torch.randperm(data.numel(), device=dev, generator=gen)]
+            for it in range(data.numel() // bs):
+                net.train_step(shuf[it * bs:(it + 1) * bs], lr=1e-3)
+        b.record()
+        b.synchronize()
+        return net, a.elapsed_time(b) * 1e-3
+
+    def learned(net):
+        sim.chains_init(x0)
+        ltrace, ltimes = _run_traced(lambda k, d, b: lrstab.metropolis_learned(sim, net, k, seed=43, step0=d,
+                                                                                  trace=b),
+                                     C, learned_steps, min(chunk, learned_steps), dev)
+        found, med = hits(ltrace)
+        return {"steps": learned_steps, "gpu_s": ltimes[-1][1], "chains_at_s": found, "median_first_step": med}
+
+    # (a) the flip chains' own states, thinned to 10^5
+    flat = ptrace[plain_steps // 2:].reshape(-1)
+    pick = np.random.default_rng(7).choice(flat.size, size=train_samples, replace=False)
+    data_a = torch.from_numpy(flat[pick].view(np.int64)).to(dev)
+    net_a, t_a = train(data_a)
+    res_a = learned(net_a)
+    res_a.update({"training": "10^5 states of the flip chains", "train_gpu_s": t_a})
+    net_a.close()
+    # (b) exact samples of the chain-rule marginal sampler
+    work = (lrstab.Simulator(n, local), lrstab.Simulator(n, local))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    samples = []
+    for i in range(exact_samples):
+        bits, _ = sim.marginal_sample(list(range(n)), L, K, seed=100 + i, work=work)
+        samples.append(sum(int(b_) << q for q, b_ in enumerate(bits)))
+    torch.cuda.synchronize()
+    t_marg = time.perf_counter() - t0
+    for w_ in work:
+        w_.close()
+    data_b = torch.tensor(samples, dtype=torch.int64, device=dev).repeat(train_samples // exact_samples + 1)
+    data_b = data_b[:train_samples].contiguous()
+    net_b, t_b = train(data_b)
+    res_b = learned(net_b)
+    res_b.update({"training": f"{exact_samples} chain-rule samples, replicated", "train_gpu_s": t_b,
+                  "sampler_s": t_marg, "samples_are_the_shift": all(np.uint64(v) == s for v in samples)})
+    net_b.close()
+    sim.close()
+    return {"workload": f"{cfg['name']}_chi{chi}", "chains": C, "chains_started_at_s": start_at_s,
+            "flip": plain, "learned_on_flip_chains": res_a, "learned_on_exact_samples": res_b}
+
+
 def marginal_study(local=0, w=8, L=256, K=3):
     """Chain-rule sampling of w bits by norm estimation (end of Sec. 4.3) on the n=40
     hidden shift (exact 2^16-term decomposition of |s>): every bit must come out as
@@ -1220,6 +1325,9 @@ def main():
     if args.mlp_gemm_only:
         print(json.dumps(mlp_gemm_study(0, reps=2, bf16_peak=peaks.get("bf16_tflops"))))
         return
+    if args.hidden_shift_chains:
+        print(json.dumps(hidden_shift_chain_study(0)))
+        return
     if args.qaoa_apply_only:
         print(json.dumps(qaoa_apply_only(0)))
         return
@@ -1318,7 +1426,8 @@ def main():
             parity.append(slice_parity(other, local, timer=timer))
         extra = {"batch8": batch_study(local), "mlp_gemm": mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops")),
                  "marginals": marginal_study(local), "gadget_vs_sum": gadget_study(local),
-                 "prefix_sharing": prefix_study(local), "hidden_shift_sum8": hidden_shift_sum8_study(local)}
+                 "prefix_sharing": prefix_study(local), "hidden_shift_sum8": hidden_shift_sum8_study(local),
+                 "hidden_shift_chains": hidden_shift_chain_study(local)}
     if timer is not None:
         timer.close()
     if rank != 0:

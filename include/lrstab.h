@@ -429,9 +429,12 @@ lrs_status lrs_mlp_info(const lrs_mlp* mlp, int32_t* n, int32_t* hidden, int64_t
  *                          128 x 64 tiles from shared memory, the accumulator
  *                          lives in tensor memory, completion arrives on an
  *                          mbarrier whose wait is bounded (a wait that gives
- *                          up sets a flag that the next synchronising call,
- *                          lrs_mlp_get_params or lrs_mlp_set_gemm, reports as
- *                          LRS_ERR_TIMEOUT)
+ *                          up sets a flag that lrs_mlp_get_params and
+ *                          lrs_mlp_set_gemm report as LRS_ERR_TIMEOUT, and so
+ *                          does the first forward, backward, train or sample
+ *                          call that starts after the call that set it has
+ *                          completed: each copies the flag to the host,
+ *                          asynchronously, when it has enqueued its work)
  *   LRS_MLP_GEMM_MMA_SYNC  warp-level mma.sync m16n8k16 on 64 x 64 tiles
  * Both accumulate exact BF16 products in FP32; results differ only in the
  * order of the FP32 additions.  Synchronises the device.                       */

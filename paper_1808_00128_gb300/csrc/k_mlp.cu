@@ -26,6 +26,7 @@ struct lrs_mlp {
     float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *W3 = nullptr, *b3 = nullptr;
     int gemm = 0;                         // LRS_MLP_GEMM_TCGEN05 or LRS_MLP_GEMM_MMA_SYNC
     int* err = nullptr;                   // device [2]: a tensor-core wait gave up; test request
+    int* err_h = nullptr;                 // pinned host copy of err[0], refreshed after every call
     float *mW = nullptr, *vW = nullptr;   // moments for all parameters, packed
     float *grad = nullptr;                // gradients, packed like the parameters
     float *mask = nullptr;                // MADE masks, packed like the weights (1 for biases)
@@ -1166,6 +1167,8 @@ extern "C" lrs_status lrs_mlp_create(int32_t device, int32_t n, int32_t hidden, 
     if (e == cudaSuccess) e = cudaMalloc(&m->W3t, (size_t)H * 64 * 2);
     if (e == cudaSuccess) e = cudaMalloc(&m->err, 2 * sizeof(int));   // flag, one-shot test request
     if (e == cudaSuccess) e = cudaMemset(m->err, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&m->err_h, sizeof(int), cudaHostAllocDefault);
+    if (e == cudaSuccess) *m->err_h = 0;
     if (e != cudaSuccess) {
         delete m;
         return lrs_cuda_check(e, "mlp storage");
@@ -1207,6 +1210,7 @@ extern "C" lrs_status lrs_mlp_destroy(lrs_mlp* m) {
     cudaFree(m->mW); cudaFree(m->vW); cudaFree(m->grad); cudaFree(m->mask);
     cudaFree(m->W1b); cudaFree(m->W2b); cudaFree(m->W3b); cudaFree(m->W2t); cudaFree(m->W3t);
     cudaFree(m->err);
+    cudaFreeHost(m->err_h);
     cudaFree(m->ws);
     delete m;
     return LRS_OK;
@@ -1231,11 +1235,24 @@ extern "C" lrs_status lrs_mlp_set_params(lrs_mlp* m, const float* params_host) {
 static lrs_status mlp_check_err(lrs_mlp* m) {
     int flag = 0;
     LRS_CUDA(cudaMemcpy(&flag, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+    *(volatile int*)m->err_h = 0;
     if (flag) {
         LRS_CUDA(cudaMemset(m->err, 0, sizeof(int)));
         return lrs_fail(LRS_ERR_TIMEOUT, "a tcgen05 GEMM gave up waiting for its MMAs; results are invalid");
     }
     return LRS_OK;
+}
+
+// Every enqueuing call ends by copying the device flag into the pinned host word
+// (4 bytes, asynchronous) and starts by reading that word: a wait that gave up in an
+// earlier call is reported by a later one without synchronising in the common case.
+static void mlp_post_err(lrs_mlp* m, cudaStream_t st) {
+    cudaMemcpyAsync(m->err_h, m->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+static lrs_status mlp_poll_err(lrs_mlp* m) {
+    if (*(volatile int*)m->err_h == 0) return LRS_OK;
+    LRS_CUDA(cudaDeviceSynchronize());   // no copy of the flag is left in flight
+    return mlp_check_err(m);
 }
 
 extern "C" lrs_status lrs_mlp_debug_inject_wait_timeout(lrs_mlp* m) {
@@ -1290,9 +1307,10 @@ extern "C" lrs_status lrs_mlp_forward(lrs_mlp* m, const uint64_t* x, int64_t bat
     if (batch > (1 << 24)) return lrs_fail(LRS_ERR_ARG, "batch too large");
     LRS_CUDA(cudaSetDevice(m->device));
     cudaStream_t st = (cudaStream_t)stream;
-    MlpWS w;
-    lrs_status rc = mlp_ws(m, pad64(batch), w);
+    lrs_status rc = mlp_poll_err(m);
     if (rc != LRS_OK) return rc;
+    MlpWS w;
+    if ((rc = mlp_ws(m, pad64(batch), w)) != LRS_OK) return rc;
     if ((rc = mlp_forward(m, x, (int)batch, w, st)) != LRS_OK) return rc;
     if (logits)
         LRS_CUDA(cudaMemcpy2DAsync(logits, (size_t)m->n * 4, w.logits, (size_t)m->NP * 4, (size_t)m->n * 4,
@@ -1301,6 +1319,7 @@ extern "C" lrs_status lrs_mlp_forward(lrs_mlp* m, const uint64_t* x, int64_t bat
         k_logq<<<(unsigned)((batch + 127) / 128), 128, 0, st>>>(w.logits, x, (int)batch, m->n, m->NP, logq);
         LRS_LAUNCH_CHECK("logq");
     }
+    mlp_post_err(m, st);
     return LRS_OK;
 }
 
@@ -1309,10 +1328,13 @@ extern "C" lrs_status lrs_mlp_backward(lrs_mlp* m, const uint64_t* x, int64_t ba
     if (!m || batch < 1 || !x) return lrs_fail(LRS_ERR_ARG, "bad arguments");
     if (batch > (1 << 24)) return lrs_fail(LRS_ERR_ARG, "batch too large");
     LRS_CUDA(cudaSetDevice(m->device));
-    MlpWS w;
-    lrs_status rc = mlp_ws(m, pad64(batch), w);
+    lrs_status rc = mlp_poll_err(m);
     if (rc != LRS_OK) return rc;
-    return mlp_backward(m, x, (int)batch, w, loss, (cudaStream_t)stream);
+    MlpWS w;
+    if ((rc = mlp_ws(m, pad64(batch), w)) != LRS_OK) return rc;
+    if ((rc = mlp_backward(m, x, (int)batch, w, loss, (cudaStream_t)stream)) != LRS_OK) return rc;
+    mlp_post_err(m, (cudaStream_t)stream);
+    return LRS_OK;
 }
 
 extern "C" lrs_status lrs_mlp_train_step(lrs_mlp* m, const uint64_t* x, int64_t batch, float lr,
@@ -1341,6 +1363,7 @@ extern "C" lrs_status lrs_mlp_sample(lrs_mlp* m, int64_t count, uint64_t seed, i
     MlpWS w;
     lrs_status rc = mlp_ws(m, Mp, w);
     if (rc != LRS_OK) return rc;
+    if ((rc = mlp_poll_err(m)) != LRS_OK) return rc;
     const int64_t tot = (int64_t)Mp * H;
     k_sample_init<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m->b1, Mp, H, M, w.Z1, w.H1, y, logq);
     LRS_LAUNCH_CHECK("sample init");
@@ -1350,5 +1373,6 @@ extern "C" lrs_status lrs_mlp_sample(lrs_mlp* m, int64_t count, uint64_t seed, i
                                                                      i, seed, sample0, w.Z1, w.H1, y, logq);
         LRS_LAUNCH_CHECK("sample bit");
     }
+    mlp_post_err(m, st);
     return LRS_OK;
 }

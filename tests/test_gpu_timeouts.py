@@ -70,4 +70,15 @@ def test_tcgen05_gemm_wait_runs_out_then_recovers():
     got = net.forward(x)[0].cpu().numpy()
     net.get_params()
     assert np.array_equal(got, want)
+    # without a synchronising call: the flag reaches the host with the call's own
+    # asynchronous copy, and the next enqueuing call reports it
+    net.debug_inject_wait_timeout()
+    net.forward(x)
+    torch.cuda.synchronize()
+    with pytest.raises(lrstab.LrsError) as e:
+        net.forward(x)
+    assert e.value.status == TIMEOUT
+    got = net.forward(x)[0].cpu().numpy()
+    net.get_params()
+    assert np.array_equal(got, want)
     net.close()
