@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,6 +38,7 @@ SHAPES = {
     "qaoa": dict(B=4096, L=512, C=256, T=64),
     "mid": dict(B=4096, L=256, C=256, T=16),
     "qaoa_small": dict(B=2048, L=64, C=64, T=2, chi=1 << 16),   # profiling case
+    "qaoa_pi4": dict(B=4096, L=512, C=256, T=64),   # the paper's beta = pi/4 line (Clifford mixer)
 }
 
 
@@ -294,6 +296,10 @@ def workload_config(name):
     from paper_1808_00128_gb300 import workloads
     if name == "qaoa":
         return workloads.config_qaoa()
+    if name == "qaoa_pi4":
+        cfg = workloads.config_qaoa(beta=math.pi / 4)
+        cfg["name"] = "qaoa_e3lin2_n50_beta_pi4"
+        return cfg
     return workloads.config_mid()
 
 
@@ -1298,10 +1304,12 @@ def _peaks():
     return json.load(open(p)) if os.path.exists(p) else {}
 
 
-def side_step_study(name, local, alu_peak, hbm_peak, steps=5, warmup=3):
-    """The same step on another workload (n = 40 random Clifford+T at chi = 2^16):
-    phase times, rooflines on both counts, the stated error bound."""
+def side_step_study(name, local, alu_peak, hbm_peak, steps=5, warmup=3, certificate=False):
+    """The same step on another workload (n = 40 random Clifford+T at chi = 2^16, or
+    the paper's beta = pi/4 QAOA line): phase times, rooflines on both counts, the
+    stated error bound, and optionally the sparsification certificate."""
     import torch
+    from paper_1808_00128_gb300 import lrstab
     r = StepRunner(name, local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=r.dev)
     for w in range(warmup):
@@ -1313,6 +1321,9 @@ def side_step_study(name, local, alu_peak, hbm_peak, steps=5, warmup=3):
     out = {"workload": r.cfg["name"], "n": r.n, "chi": r.chi, **r.shape, "ms_per_step": ms,
            "value": r.units() / (ms * 1e-3), "unit": UNIT, "tuned": tuned,
            "phases": r.rooflines(phase_ms, alu_peak, hbm_peak), "amplitude_error": r.error_statement()}
+    if certificate:
+        out["sparsification_certificate"] = lrstab.sparsification_certificate(r.sim, r.shape["L"], 3, seed=777)
+        out["l1_norm"] = r.low.l1_norm
     r.close()
     return out
 
@@ -1428,6 +1439,8 @@ def main():
                  "marginals": marginal_study(local), "gadget_vs_sum": gadget_study(local),
                  "prefix_sharing": prefix_study(local), "hidden_shift_sum8": hidden_shift_sum8_study(local),
                  "hidden_shift_chains": hidden_shift_chain_study(local)}
+        if args.workload == "qaoa":
+            extra["qaoa_beta_pi4"] = side_step_study("qaoa_pi4", local, alu, hbm, certificate=True)
     if timer is not None:
         timer.close()
     if rank != 0:

@@ -1,5 +1,7 @@
 """Amplitude parity: CUDA <x|psi> against the FP64 oracle (and the dense state
 vector where n is small).  Tolerance: |a_gpu - a| <= 1e-5 max(|a|, ||psi|| 2^{-n/2})."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -170,13 +172,15 @@ def test_wide_registers_vs_oracle_and_exact(n):
     sim.close()
 
 
-def test_qaoa_n50_slice_vs_oracle_and_exact():
+@pytest.mark.parametrize("beta", [0.2, math.pi / 4], ids=["beta_0.2", "beta_pi_4"])
+def test_qaoa_n50_slice_vs_oracle_and_exact(beta):
     """The QAOA Max-E3LIN2 workload at n = 50 (gamma 0.3, beta 0.2, 116 rotation
-    slots; chi = 2^20 sparsified terms): a 256-term slice of that decomposition, strings
-    sampled from the slice's terms plus random ones, against the FP64 oracle and the
-    exact chi-sums, with the per-result bound checked."""
+    slots; chi = 2^20 sparsified terms) and the paper's line beta = pi/4 (its 50 mixer
+    slots are Clifford, one choice each): a 256-term slice of that decomposition,
+    strings sampled from the slice's terms plus random ones, against the FP64 oracle
+    and the exact chi-sums, with the per-result bound checked."""
     require_cuda()
-    cfg = workloads.config_qaoa()
+    cfg = workloads.config_qaoa(beta=beta)
     n, ops, chi_total, seed = cfg["n"], cfg["ops"], cfg["chi"], cfg["seed"]
     alpha0, chi = 777_777, 256
     sim = _sim(n, ops, chi, "sparsify", seed=seed, alpha0=alpha0, chi_total=chi_total)
