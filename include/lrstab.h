@@ -159,12 +159,25 @@ lrs_status lrs_decomposition_stats(const lrs_slot* slots_host, int64_t n_slots, 
                                    int64_t* exact_chi, double* log2_exact_chi);
 
 /* ---- context ------------------------------------------------------------------ */
-/* Create a context for n_qubits (1..64) on CUDA device `device`.  There is no
- * options argument: the launch shapes a context uses are set per context, at any
- * time, with lrs_set_tuning (defaults suit a GB300), and everything else a call
- * needs travels with the call.
- * Errors: LRS_ERR_ARG (n out of range), LRS_ERR_CUDA (bad device).           */
-lrs_status lrs_create(int32_t device, int32_t n_qubits, lrs_ctx** out);
+/* Options of a new context (no counterpart in the paper).  `size` must be
+ * sizeof(lrs_options) as the caller compiled it (later versions may append fields);
+ * bit i of `tuning_mask` gives launch knob i (an LRS_TUNE_* value) the initial value
+ * tuning[i], exactly as lrs_set_tuning would; other knobs keep their defaults.
+ * Everything else a call needs travels with the call.                          */
+#define LRS_OPTIONS_TUNING 16
+typedef struct {
+    int32_t size;
+    uint32_t tuning_mask;
+    int64_t tuning[LRS_OPTIONS_TUNING];
+} lrs_options;
+
+/* Create a context for n_qubits (1..64) on CUDA device `device`; opts may be NULL
+ * (every knob at its default, which suits a GB300).  *out is owned by the caller
+ * and released with lrs_destroy.
+ * Errors: LRS_ERR_ARG (n out of range, opts->size smaller than the fields read, a
+ * tuning value lrs_set_tuning rejects; no context is created), LRS_ERR_CUDA (bad
+ * device).                                                                   */
+lrs_status lrs_create(int32_t device, int32_t n_qubits, const lrs_options* opts, lrs_ctx** out);
 
 /* Free all device storage of the context.  Synchronises the device.  NULL ok. */
 lrs_status lrs_destroy(lrs_ctx* ctx);

@@ -286,11 +286,13 @@ static void free_chains(lrs_ctx* c) {
     c->ybuf = nullptr; c->lqy = nullptr; c->lqx = nullptr; c->ampy = nullptr; c->mh_cap = 0;
 }
 
-extern "C" lrs_status lrs_create(int32_t device, int32_t n_qubits, lrs_ctx** out) {
+extern "C" lrs_status lrs_create(int32_t device, int32_t n_qubits, const lrs_options* opts, lrs_ctx** out) {
     if (!out) return lrs_fail(LRS_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n_qubits < 1 || n_qubits > 64)
         return lrs_fail(LRS_ERR_ARG, "n_qubits must be in 1..64 (got %d)", n_qubits);
+    if (opts && opts->size < (int32_t)sizeof(lrs_options))
+        return lrs_fail(LRS_ERR_ARG, "lrs_options.size %d is smaller than %d", opts->size, (int)sizeof(lrs_options));
     int count = 0;
     LRS_CUDA(cudaGetDeviceCount(&count));
     if (device < 0 || device >= count) return lrs_fail(LRS_ERR_ARG, "bad device %d", device);
@@ -302,6 +304,16 @@ extern "C" lrs_status lrs_create(int32_t device, int32_t n_qubits, lrs_ctx** out
     c->sm_count = sms;
     c->n = n_qubits;
     c->nmask = n_qubits == 64 ? ~0ull : ((1ull << n_qubits) - 1);
+    if (opts) {
+        for (int i = 0; i < LRS_OPTIONS_TUNING; ++i) {
+            if (!((opts->tuning_mask >> i) & 1u)) continue;
+            const lrs_status rc = lrs_set_tuning(c, i, opts->tuning[i]);
+            if (rc != LRS_OK) {
+                delete c;
+                return rc;
+            }
+        }
+    }
     *out = c;
     return LRS_OK;
 }

@@ -69,7 +69,7 @@ def lib():
     L.lrs_last_error.restype = C.c_char_p
     sigs = {
         "lrs_lower_circuit": [i32, vp, i64, i32, vp, i64, vp, vp, i64, vp, vp, i64, vp],
-        "lrs_create": [i32, i32, vp],
+        "lrs_create": [i32, i32, vp, vp],
         "lrs_destroy": [vp],
         "lrs_init_terms": [vp, vp, i64, vp, i64, i64, i64, i64, i32, u64, vp],
         "lrs_apply_clifford": [vp, vp, i64, vp],
@@ -242,14 +242,31 @@ def alu_probe(device: int = 0, iters: int = 20000) -> float:
 
 
 # ---- simulator context ------------------------------------------------------------------
-class Simulator:
-    """One lrs_ctx: chi CH-form terms of an n-qubit circuit on one GPU."""
+class LrsOptions(C.Structure):
+    _fields_ = [("size", C.c_int32), ("tuning_mask", C.c_uint32), ("tuning", C.c_int64 * 16)]
 
-    def __init__(self, n: int, device: int = 0):
+
+def options(tuning: dict | None = None) -> LrsOptions:
+    """lrs_options with the given initial launch knobs ({name: value}, names of TUNE)."""
+    o = LrsOptions()
+    o.size = C.sizeof(LrsOptions)
+    for name, value in (tuning or {}).items():
+        i = TUNE[name]
+        o.tuning_mask |= 1 << i
+        o.tuning[i] = int(value)
+    return o
+
+
+class Simulator:
+    """One lrs_ctx: chi CH-form terms of an n-qubit circuit on one GPU.  `tuning`:
+    initial launch knobs ({name: value}), passed to lrs_create as lrs_options."""
+
+    def __init__(self, n: int, device: int = 0, tuning: dict | None = None):
         self.n = n
         self.device = device
         h = C.c_void_p()
-        _check(lib().lrs_create(device, n, C.byref(h)))
+        opts = options(tuning) if tuning else None
+        _check(lib().lrs_create(device, n, C.byref(opts) if opts is not None else None, C.byref(h)))
         self._h = h
         self.chi = 0
         self.n_slots = 0

@@ -114,3 +114,22 @@ def test_batched_amplitudes_equal_single_calls_and_oracle():
         lrstab.amplitude_batch([sims[0], sims[0]], [xs[0], xs[0]])
     for s in sims:
         s.close()
+
+
+def test_create_with_options():
+    """lrs_options: initial knobs as lrs_set_tuning would set them, defaults for the
+    rest; a value lrs_set_tuning rejects or a short struct fails the create."""
+    require_cuda()
+    sim = lrstab.Simulator(50, 0, tuning={"apply_lanes": 2, "mc_lookahead": 1, "norm_max_folds": -1})
+    assert sim.get_tuning("apply_lanes") == 2
+    assert sim.get_tuning("mc_lookahead") == 1
+    assert sim.get_tuning("norm_max_folds") == -1
+    assert sim.get_tuning("mc_stages") == 1            # default
+    sim.close()
+    with pytest.raises(lrstab.LrsError):
+        lrstab.Simulator(50, 0, tuning={"apply_lanes": 3})
+    o = lrstab.options({"mc_stages": 2})
+    o.size = 8
+    h = lrstab.C.c_void_p()
+    rc = lrstab.lib().lrs_create(0, 50, lrstab.C.byref(o), lrstab.C.byref(h))
+    assert rc == -1 and not h.value
