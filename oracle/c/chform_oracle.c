@@ -15,7 +15,7 @@
  * is the lowest index, the single-qubit rewrite is found by brute force with a = 0
  * tried first.
  *
- * Exact sums (reading of SURVEY §8(c) 11): a term contributes
+ * Exact sums (the exact Z[zeta8] accumulation of the Python oracle): a term contributes
  * sgn * zeta^K * 2^{-e/2} times a factor common to all terms (zeta = e^{i pi/4}); the
  * sum is kept as four 128-bit integer coordinates over 1, zeta, zeta^2, zeta^3 at the
  * scale 2^-EX_S (zeta^4 = -1; an odd e uses 2^{-1/2} = 2^{-1}(zeta + zeta^7)).
