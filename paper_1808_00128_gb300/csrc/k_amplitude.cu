@@ -52,13 +52,17 @@ __device__ __forceinline__ void amp_block(const TermsView& T, const uint64_t* __
                                           int64_t tt, float2* __restrict__ partial, int64_t n_tiles,
                                           void* __restrict__ Qout, float* __restrict__ magp, int64_t tile,
                                           int64_t xblk) {
-    __shared__ AmpEntry tab[PK ? 1 : NCH][16];
-    __shared__ uint64_t tabU[PK ? NCH : 1][16], tabW[PK ? NCH : 1][16];
-    __shared__ uint64_t sF[64], sM[64];
-    __shared__ float2 val8[8];              // b e^{i pi k/4} 2^{-(|v|+h)/2}, k = 0..7
-    __shared__ float val_abs;               // |b| 2^{-(|v|+h)/2} (ERR)
-    __shared__ uint64_t sc[4];              // glo, ghi, v, s
-    __shared__ uint32_t sc_live;
+    // One barrier per term: while the block evaluates term a from table slot a, it
+    // builds the table of term a + 1 (from the rows stored in the previous interval)
+    // and stores the rows of term a + 2; tables and rows are double-buffered, the
+    // per-term scalars (read while the scalars of a + 2 are written) triple-buffered.
+    __shared__ AmpEntry tab[2][PK ? 1 : NCH][16];
+    __shared__ uint64_t tabU[2][PK ? NCH : 1][16], tabW[2][PK ? NCH : 1][16];
+    __shared__ uint64_t sF[2][64], sM[2][64];
+    __shared__ float2 val8[3][8];           // b e^{i pi k/4} 2^{-(|v|+h)/2}, k = 0..7
+    __shared__ float val_abs[3];            // |b| 2^{-(|v|+h)/2} (ERR)
+    __shared__ uint64_t sc[3][4];           // glo, ghi, v, s
+    __shared__ uint32_t sc_live[3];
     // compact Pauli states of the last QG terms for each of the block's strings, private
     // to the thread that owns the string: written out as 16-byte vectors every QG terms
     constexpr int AMP_XP = amp_xp(QOUT), AMP_XB = amp_xb(QOUT);
@@ -103,23 +107,23 @@ __device__ __forceinline__ void amp_block(const TermsView& T, const uint64_t* __
             pv = T.v[a];
         }
     };
-    if (a0 < a1) prefetch(a0);
-    for (int64_t a = a0; a < a1; ++a) {
-        __syncthreads();                    // previous term's table no longer in use
-        if (tid < n) { sF[tid] = pf; sM[tid] = pm; }
-        if (tid == 64) { sc[0] = pf; sc[1] = pm; }
-        if (tid == 65) { sc[2] = pf; sc[3] = pm; }
+    // thread-owned stores of the prefetched term into row slot rs and scalar slot ss
+    auto store = [&](int rs, int ss) {
+        if (tid < n) { sF[rs][tid] = pf; sM[rs][tid] = pm; }
+        if (tid == 64) { sc[ss][0] = pf; sc[ss][1] = pm; }
+        if (tid == 65) { sc[ss][2] = pf; sc[ss][3] = pm; }
         if (tid == 66) {
             const uint32_t om = (uint32_t)pf;
             const float2 b = make_float2(__uint_as_float((uint32_t)pm), __uint_as_float((uint32_t)(pm >> 32)));
-            sc_live = ((om >> 3) & 1u) ? 0u : 1u;
+            sc_live[ss] = ((om >> 3) & 1u) ? 0u : 1u;
             const int e0 = __popcll(pv) + (int)(om >> 8);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) val8[k] = z8_scale(b, k + (int)(om & 7u), e0);
-            if (ERR) val_abs = ldexpf(hypotf(b.x, b.y), -(e0 >> 1)) * ((e0 & 1) ? 0.70710678f : 1.f);
+            for (int k = 0; k < 8; ++k) val8[ss][k] = z8_scale(b, k + (int)(om & 7u), e0);
+            if (ERR) val_abs[ss] = ldexpf(hypotf(b.x, b.y), -(e0 >> 1)) * ((e0 & 1) ? 0.70710678f : 1.f);
         }
-        __syncthreads();
-        if (a + 1 < a1) prefetch(a + 1);
+    };
+    // the Four-Russians table of the term whose rows are in slot ts, into table slot ts
+    auto build = [&](int ts) {
         for (int e = tid; e < NCH * 16; e += AMP_XT) {
             const int c = e >> 4, q = e & 15;
             uint64_t u = 0, w = 0, z = 0;
@@ -127,88 +131,102 @@ __device__ __forceinline__ void amp_block(const TermsView& T, const uint64_t* __
             for (int b = 0; b < 4; ++b) {
                 const int r = 4 * c + b;
                 if (((q >> b) & 1) && r < n) {
-                    const uint64_t Fr = sF[r];
+                    const uint64_t Fr = sF[ts][r];
                     z ^= w & Fr;
                     u ^= Fr;
-                    w ^= sM[r];
+                    w ^= sM[ts][r];
                 }
             }
             if (PK) {
-                tabU[c][q] = u | ((uint64_t)par64(z) << 63);
-                tabW[c][q] = w;
+                tabU[ts][c][q] = u | ((uint64_t)par64(z) << 63);
+                tabW[ts][c][q] = w;
             } else {
-                tab[c][q].u = u;
-                tab[c][q].w = w;
-                tab[c][q].z = z;
+                tab[ts][c][q].u = u;
+                tab[ts][c][q].w = w;
+                tab[ts][c][q].z = z;
             }
         }
-        __syncthreads();
-        const bool live = sc_live != 0u;
-        if (!QOUT && !live) continue;       // zero term (uniform)
-        const uint64_t glo = sc[0], ghi = sc[1], v = sc[2], s = sc[3];
-        const uint64_t nv = ~v & T.nmask, sv = s & v;
-#pragma unroll
-        for (int k = 0; k < AMP_XP; ++k) {
-            const uint64_t x = xv[k];
-            uint64_t u = 0, w = 0;
-            uint32_t zpar;
-            if (PK) {
-                // only the parity of sum_c popc(w_c & u_q) enters, and that is the
-                // parity of the XOR of the terms: one popcount per string
-                uint64_t zx = 0;
-#pragma unroll
-                for (int c = 0; c < NCH; ++c) {
-                    const int q = (int)((x >> (4 * c)) & 15u);
-                    const uint64_t Eu = tabU[c][q], Ew = tabW[c][q];
-                    zx ^= w & Eu;   // w has no bit 63
-                    u ^= Eu;
-                    w ^= Ew;
-                }
-                zpar = ((uint32_t)__popcll(zx) + (uint32_t)(u >> 63)) & 1u;
-                u &= ~(1ull << 63);
-            } else {
-                uint64_t z = 0;
-#pragma unroll
-                for (int c = 0; c < NCH; ++c) {
-                    const AmpEntry& E = tab[c][(int)((x >> (4 * c)) & 15u)];
-                    z ^= (w & E.u) ^ E.z;
-                    u ^= E.u;
-                    w ^= E.w;
-                }
-                zpar = par64(z);
-            }
-            const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)zpar;
-            if (CQ) {
-                const int g = (int)((a - a0) & (QG - 1));
-                qb8[g][tid + k * AMP_XT] = u | (w << 40);
-                qb4[g][tid + k * AMP_XT] = (uint32_t)(w >> 24) | ((uint32_t)(mu & 3) << 16);
-            } else if (QOUT) {
-                const int64_t i = xb + tid + k * AMP_XT;
-                if (i < batch) q_store<false>(Qout, batch * T.cap, i * T.cap + a, u, w, (uint32_t)mu);
-            }
-            if (live && ((u ^ s) & nv) == 0) {
-                const int sign = (int)par64(u & (w ^ sv));
-                acc[k].add(val8[(2 * mu + 4 * sign) & 7]);
-                if (ERR) mag[k] += val_abs;
-            }
-        }
-        if (CQ && ((a - a0) & (QG - 1)) == QG - 1) {
-            // terms a-3 .. a of each of the thread's strings: 32 bytes of u | w << 40 and
-            // 16 bytes of (w >> 24) | mu << 16, contiguous and 16-byte aligned (a0 and
-            // the tile length are multiples of QG, cap of 256)
-            uint64_t* q8 = reinterpret_cast<uint64_t*>(Qout);
-            uint32_t* q4 = reinterpret_cast<uint32_t*>(q8 + batch * T.cap);
-#pragma unroll
+    };
+    if (a0 < a1) { prefetch(a0); store(0, 0); }
+    if (a0 + 1 < a1) { prefetch(a0 + 1); store(1, 1); }
+    if (a0 + 2 < a1) prefetch(a0 + 2);
+    __syncthreads();
+    if (a0 < a1) build(0);
+    __syncthreads();
+    for (int64_t a = a0; a < a1; ++a) {
+        const int kt = (int)(a - a0);
+        const int tb = kt & 1, ss = kt % 3;
+        if (a + 1 < a1) build(tb ^ 1);
+        if (a + 2 < a1) store(tb, (kt + 2) % 3);
+        if (a + 3 < a1) prefetch(a + 3);
+        const bool live = sc_live[ss] != 0u;
+        if (QOUT || live) {
+            const uint64_t glo = sc[ss][0], ghi = sc[ss][1], v = sc[ss][2], s = sc[ss][3];
+            const uint64_t nv = ~v & T.nmask, sv = s & v;
+    #pragma unroll
             for (int k = 0; k < AMP_XP; ++k) {
-                const int sl = tid + k * AMP_XT;
-                const int64_t i = xb + sl;
-                if (i >= batch) continue;
-                const int64_t e = i * T.cap + a - (QG - 1);
-                reinterpret_cast<ulonglong2*>(q8 + e)[0] = make_ulonglong2(qb8[0][sl], qb8[1][sl]);
-                reinterpret_cast<ulonglong2*>(q8 + e)[1] = make_ulonglong2(qb8[2][sl], qb8[3][sl]);
-                *reinterpret_cast<uint4*>(q4 + e) = make_uint4(qb4[0][sl], qb4[1][sl], qb4[2][sl], qb4[3][sl]);
+                const uint64_t x = xv[k];
+                uint64_t u = 0, w = 0;
+                uint32_t zpar;
+                if (PK) {
+                    // only the parity of sum_c popc(w_c & u_q) enters, and that is the
+                    // parity of the XOR of the terms: one popcount per string
+                    uint64_t zx = 0;
+    #pragma unroll
+                    for (int c = 0; c < NCH; ++c) {
+                        const int q = (int)((x >> (4 * c)) & 15u);
+                        const uint64_t Eu = tabU[tb][c][q], Ew = tabW[tb][c][q];
+                        zx ^= w & Eu;   // w has no bit 63
+                        u ^= Eu;
+                        w ^= Ew;
+                    }
+                    zpar = ((uint32_t)__popcll(zx) + (uint32_t)(u >> 63)) & 1u;
+                    u &= ~(1ull << 63);
+                } else {
+                    uint64_t z = 0;
+    #pragma unroll
+                    for (int c = 0; c < NCH; ++c) {
+                        const AmpEntry& E = tab[tb][c][(int)((x >> (4 * c)) & 15u)];
+                        z ^= (w & E.u) ^ E.z;
+                        u ^= E.u;
+                        w ^= E.w;
+                    }
+                    zpar = par64(z);
+                }
+                const int mu = __popcll(x & glo) + 2 * __popcll(x & ghi) + 2 * (int)zpar;
+                if (CQ) {
+                    const int g = (int)((a - a0) & (QG - 1));
+                    qb8[g][tid + k * AMP_XT] = u | (w << 40);
+                    qb4[g][tid + k * AMP_XT] = (uint32_t)(w >> 24) | ((uint32_t)(mu & 3) << 16);
+                } else if (QOUT) {
+                    const int64_t i = xb + tid + k * AMP_XT;
+                    if (i < batch) q_store<false>(Qout, batch * T.cap, i * T.cap + a, u, w, (uint32_t)mu);
+                }
+                if (live && ((u ^ s) & nv) == 0) {
+                    const int sign = (int)par64(u & (w ^ sv));
+                    acc[k].add(val8[ss][(2 * mu + 4 * sign) & 7]);
+                    if (ERR) mag[k] += val_abs[ss];
+                }
             }
-        }
+            if (CQ && ((a - a0) & (QG - 1)) == QG - 1) {
+                // terms a-3 .. a of each of the thread's strings: 32 bytes of u | w << 40 and
+                // 16 bytes of (w >> 24) | mu << 16, contiguous and 16-byte aligned (a0 and
+                // the tile length are multiples of QG, cap of 256)
+                uint64_t* q8 = reinterpret_cast<uint64_t*>(Qout);
+                uint32_t* q4 = reinterpret_cast<uint32_t*>(q8 + batch * T.cap);
+    #pragma unroll
+                for (int k = 0; k < AMP_XP; ++k) {
+                    const int sl = tid + k * AMP_XT;
+                    const int64_t i = xb + sl;
+                    if (i >= batch) continue;
+                    const int64_t e = i * T.cap + a - (QG - 1);
+                    reinterpret_cast<ulonglong2*>(q8 + e)[0] = make_ulonglong2(qb8[0][sl], qb8[1][sl]);
+                    reinterpret_cast<ulonglong2*>(q8 + e)[1] = make_ulonglong2(qb8[2][sl], qb8[3][sl]);
+                    *reinterpret_cast<uint4*>(q4 + e) = make_uint4(qb4[0][sl], qb4[1][sl], qb4[2][sl], qb4[3][sl]);
+                }
+            }
+        }   // live (every term for the Pauli-state output)
+        __syncthreads();   // slot tb ^ 1 and the next rows and scalars are complete
     }
 #pragma unroll
     for (int k = 0; k < AMP_XP; ++k) {
