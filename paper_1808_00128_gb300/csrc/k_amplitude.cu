@@ -70,6 +70,11 @@ __device__ __forceinline__ void amp_block(const TermsView& T, const uint64_t* __
     constexpr int QG = 4;
     __shared__ uint64_t qb8[CQ ? QG : 1][CQ ? AMP_XB : 1];
     __shared__ uint32_t qb4[CQ ? QG : 1][CQ ? AMP_XB : 1];
+    // the 16-byte states (n > 40) of the last QW terms, written out as one full 32-byte
+    // sector per string every QW terms (a store per term would write half sectors)
+    constexpr bool WQ = QOUT && !CQ;
+    constexpr int QW = 2;
+    __shared__ uint64_t qwu[WQ ? QW : 1][WQ ? AMP_XB : 1], qww[WQ ? QW : 1][WQ ? AMP_XB : 1];
     const int n = T.n;
     const int tid = threadIdx.x;
     const int64_t xb = xblk * AMP_XB;
@@ -198,9 +203,10 @@ __device__ __forceinline__ void amp_block(const TermsView& T, const uint64_t* __
                     const int g = (int)((a - a0) & (QG - 1));
                     qb8[g][tid + k * AMP_XT] = u | (w << 40);
                     qb4[g][tid + k * AMP_XT] = (uint32_t)(w >> 24) | ((uint32_t)(mu & 3) << 16);
-                } else if (QOUT) {
-                    const int64_t i = xb + tid + k * AMP_XT;
-                    if (i < batch) q_store<false>(Qout, batch * T.cap, i * T.cap + a, u, w, (uint32_t)mu);
+                } else if (WQ) {
+                    const int g = (int)((a - a0) & (QW - 1));
+                    qwu[g][tid + k * AMP_XT] = u | ((uint64_t)(mu & 3) << 62);   // the q_store layout
+                    qww[g][tid + k * AMP_XT] = w;
                 }
                 if (live && ((u ^ s) & nv) == 0) {
                     const int sign = (int)par64(u & (w ^ sv));
@@ -223,6 +229,20 @@ __device__ __forceinline__ void amp_block(const TermsView& T, const uint64_t* __
                     reinterpret_cast<ulonglong2*>(q8 + e)[0] = make_ulonglong2(qb8[0][sl], qb8[1][sl]);
                     reinterpret_cast<ulonglong2*>(q8 + e)[1] = make_ulonglong2(qb8[2][sl], qb8[3][sl]);
                     *reinterpret_cast<uint4*>(q4 + e) = make_uint4(qb4[0][sl], qb4[1][sl], qb4[2][sl], qb4[3][sl]);
+                }
+            }
+            if (WQ && ((a - a0) & (QW - 1)) == QW - 1) {
+                // terms a-1, a of each of the thread's strings: one 32-byte sector (a0
+                // and the tile length are even, cap a multiple of 256)
+                ulonglong2* q16 = reinterpret_cast<ulonglong2*>(Qout);
+#pragma unroll
+                for (int k = 0; k < AMP_XP; ++k) {
+                    const int sl = tid + k * AMP_XT;
+                    const int64_t i = xb + sl;
+                    if (i >= batch) continue;
+                    const int64_t e = i * T.cap + a - (QW - 1);
+                    q16[e] = make_ulonglong2(qwu[0][sl], qww[0][sl]);
+                    q16[e + 1] = make_ulonglong2(qwu[1][sl], qww[1][sl]);
                 }
             }
         }   // live (every term for the Pauli-state output)
