@@ -1354,6 +1354,10 @@ def main():
     small = args.small
     if small:
         args.no_cpu_baseline = args.no_e2e = args.no_extra = args.no_sampler_study = True
+    if world > 1:
+        # the side studies are single-GPU measurements: a scaling run holds all its GPUs
+        # only for the step itself
+        args.no_extra = args.no_sampler_study = True
     # the oracle's host pool starts (spawn) before the first GPU call
     timer = OracleTimer() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     torch.cuda.set_device(local)
