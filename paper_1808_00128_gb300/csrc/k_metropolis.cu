@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(MC_TPB) k_metro_propose(TermsView T, int64_t C
 // Q_y1 = Q_x P_j1, Q_y1 P_j2 and Q_x P_j2.  The accept kernel then takes both
 // decisions in order.  Each term's contribution to each sum is the one a single step
 // would add for the same string, in the same order, so the chains are bit-identical to
-// single steps; the pass reads Q once per two steps (HBM-bound at one step per pass).
+// single steps; the pass reads Q once per two steps instead of once per step.
 // Pending flips: both accepted flips of the previous pass, committed in order.
 struct McStage2 {
     __align__(16) unsigned char q[MC_TERMS * 16];
