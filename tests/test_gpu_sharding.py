@@ -72,3 +72,36 @@ def test_chain_checkpoint_and_resume():
     assert np.array_equal(ckpt, tr[T1 - 1].cpu().numpy())
     assert torch.equal(tr2, tr[T1:])
     b.close()
+
+
+def test_single_steps_continue_a_two_step_pass():
+    """A two-step pass leaves up to two flips to commit; the one-step calls of the
+    sharded protocol (propose, accept) that follow commit both, in order: one pass plus
+    one propose/accept step equals three steps in one call (n = 50, 16-byte states)."""
+    require_cuda()
+    cfg = workloads.config_qaoa()
+    n, ops, seed = cfg["n"], cfg["ops"], cfg["seed"]
+    low = lrstab.lower_circuit(n, ops)
+    sim = lrstab.Simulator(n, 0)
+    sim.init_terms(low, 4096, mode="sparsify", seed=seed, chi_total=cfg["chi"])
+    sim.apply_clifford(low.gates)
+    assert sim.get_tuning("mc_lookahead") == 2
+    C, mseed = 96, 17
+    x0 = sim.sample_terms(C, seed=8)
+    xa = torch.empty(C, dtype=torch.int64, device="cuda:0")
+    tr = torch.empty((4, C), dtype=torch.int64, device="cuda:0")
+    sim.chains_init(x0)
+    sim.metropolis(4, seed=mseed, trace=tr, x_out=xa)
+    # the same chains: one two-step pass, then steps 2 and 3 through propose / accept
+    sim.chains_init(x0)
+    sim.metropolis(2, seed=mseed)
+    for step in (2, 3):
+        amp = sim.metropolis_propose(mseed, step)
+        row = torch.empty(C, dtype=torch.int64, device="cuda:0")
+        sim.metropolis_accept(amp, mseed, step, trace=row)
+        assert torch.equal(row, tr[step])
+    xb = torch.empty(C, dtype=torch.int64, device="cuda:0")
+    sim.metropolis(0, seed=mseed, step0=4, x_out=xb)
+    assert torch.equal(xa, xb)
+    assert int((tr[1] != x0).sum()) > 0           # moves were accepted in the pass
+    sim.close()
