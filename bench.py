@@ -61,6 +61,8 @@ def parse(argv=None):
     ap.add_argument("--mlp-gemm-only", action="store_true",
                     help="run only the MADE network tensor-core study (n=64, H=2048, 16384 rows) and "
                          "print its JSON (for ncu captures of the GEMM kernels; not a bench line)")
+    ap.add_argument("--hs-marginals", action="store_true",
+                    help="only the single-qubit marginals of the 40-qubit hidden shift (2/4/6 CCZ)")
     ap.add_argument("--hidden-shift-chains", action="store_true",
                     help="only the hidden shift's chain study (time for term-sampled chains to reach s)")
     ap.add_argument("--qaoa-apply-only", action="store_true",
@@ -1220,6 +1222,50 @@ def hidden_shift_chain_study(local=0, plain_steps=2048, learned_steps=32, chunk=
             "flip": plain, "learned_on_flip_chains": res_a, "learned_on_exact_samples": res_b}
 
 
+def hs_marginals_table_study(local=0, L=256, K=3, seed=0):
+    """The paper's single-qubit marginal workload (end of Sec. 4.3, its table of norm
+    estimation times): the 40-qubit hidden shift with 2, 4 and 6 CCZ, each CCZ in the
+    8-term form (xi = 16/9) and the decomposition sparsified to chi = 39, 149 and 497
+    terms (the state counts that table lists; delta = ||c||_1 / sqrt(chi) = 0.28, 0.26,
+    0.25); for every one of the 40 qubits P(x_i = 1) from two median-of-means norm
+    estimates of the projected decomposition (L K equatorial states each).  Reported:
+    GPU wall seconds for all 40 marginals, the largest |P(x_i = 1) - s_i| (the
+    infinity-norm error of the paper's figure), and the paper's single-threaded CPU
+    time for the same shapes (context: other hardware)."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    n = 40
+    paper_s = {2: 0.30, 4: 1.02, 6: 3.82}
+    out = []
+    for n_ccz, chi in ((2, 39), (4, 149), (6, 497)):
+        ops, s = workloads.hidden_shift_circuit(n, n_ccz, workloads.SEED_BASE + 3)
+        low = lrstab.lower_circuit(n, ops, "sum8")
+        sim = lrstab.Simulator(n, local)
+        sim.init_terms(low, chi, mode="sparsify", seed=90 + n_ccz)
+        sim.apply_clifford(low.gates)
+        work = (lrstab.Simulator(n, local), lrstab.Simulator(n, local))
+        sim.marginal_sample([0], L, K, seed=seed, work=work)          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p1 = []
+        for q in range(n):
+            _, probs = sim.marginal_sample([q], L, K, seed=seed + 1 + q, work=work)
+            p0_, p1_ = probs[0]
+            p1.append(p1_ / (p0_ + p1_) if p0_ + p1_ > 0 else 0.5)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        bits = np.array([(s >> q) & 1 for q in range(n)], np.float64)
+        err = float(np.max(np.abs(np.array(p1) - bits)))
+        delta = low.l1_norm / math.sqrt(chi)
+        for w_ in (sim,) + work:
+            w_.close()
+        out.append({"ccz": n_ccz, "chi": chi, "delta": delta, "L": L, "K": K, "seconds_40_marginals": dt,
+                    "ms_per_marginal": 1e3 * dt / n, "max_marginal_error": err,
+                    "paper_cpu_seconds_per_norm_estimation": paper_s[n_ccz]})
+    return {"workload": "hidden_shift_n40_single_qubit_marginals", "rows": out}
+
+
 def marginal_study(local=0, w=8, L=256, K=3):
     """Chain-rule sampling of w bits by norm estimation (end of Sec. 4.3) on the n=40
     hidden shift (exact 2^16-term decomposition of |s>): every bit must come out as
@@ -1336,6 +1382,9 @@ def main():
     if args.mlp_gemm_only:
         print(json.dumps(mlp_gemm_study(0, reps=2, bf16_peak=peaks.get("bf16_tflops"))))
         return
+    if args.hs_marginals:
+        print(json.dumps(hs_marginals_table_study(0)))
+        return
     if args.hidden_shift_chains:
         print(json.dumps(hidden_shift_chain_study(0)))
         return
@@ -1442,7 +1491,8 @@ def main():
         extra = {"batch8": batch_study(local), "mlp_gemm": mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops")),
                  "marginals": marginal_study(local), "gadget_vs_sum": gadget_study(local),
                  "prefix_sharing": prefix_study(local), "hidden_shift_sum8": hidden_shift_sum8_study(local),
-                 "hidden_shift_chains": hidden_shift_chain_study(local)}
+                 "hidden_shift_chains": hidden_shift_chain_study(local),
+                 "hs_marginals_table": hs_marginals_table_study(local)}
         if args.workload == "qaoa":
             extra["qaoa_beta_pi4"] = side_step_study("qaoa_pi4", local, alu, hbm, certificate=True)
     if timer is not None:
