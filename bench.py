@@ -65,6 +65,8 @@ def parse(argv=None):
                     help="only the single-qubit marginals of the 40-qubit hidden shift (2/4/6 CCZ)")
     ap.add_argument("--hidden-shift-chains", action="store_true",
                     help="only the hidden shift's chain study (time for term-sampled chains to reach s)")
+    ap.add_argument("--hs-sum8-chains", action="store_true",
+                    help="only the chains on the 2^24-term hidden shift (1024 chains, 206 GB of Pauli states)")
     ap.add_argument("--qaoa-apply-only", action="store_true",
                     help="run only apply_clifford on the n=50 QAOA circuit at chi = 2^16, twice, and "
                          "print its times (for ncu captures; not a bench line)")
@@ -1120,6 +1122,123 @@ def hidden_shift_sum8_study(local=0, chi=1 << 24, L=256, K=3):
             "mean_eta": float(eta.mean()), "sparsification_certificate": cert}
 
 
+def hidden_shift_sum8_chain_study(local=0, chi=1 << 24, flip_steps=32, learned_steps=8, chunk=16, hidden=512,
+                                  train_samples=100_000, epochs=5, exact_samples=4, L=256, K=3):
+    """Chains on the 2^24-term hidden shift (16 CCZ in the 8-term form, prefactor 1/6,
+    sparsified; n = 40): 1024 single-flip chains hold 206 GB of Pauli states next to
+    the 17 GB tableau.  (a) every chain started at s: how many steps stay at s (P(s)
+    is near 1 and every neighbour's amplitude near 0, so a move away is almost never
+    accepted); (b) chains started by the term sampler of Sec. 4.2 (a term drawn by
+    |b|^2, x from its CH form): chains at s and the first step there, for single flips
+    and for Metropolis-Hastings with the learned proposal.  The network is trained on
+    `exact_samples` chain-rule samples (end of Sec. 4.3) of the same circuit's exact
+    2^16-term decomposition, replicated to 10^5 rows: any proposal leaves the chains'
+    target P(x) of the 2^24-term state unchanged, and chain-rule sampling on 2^24 terms
+    would take about 256 times as long.  The incremental P(x) of every flip chain is
+    compared at the end with |<x|psi>|^2 from the amplitude kernel."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    cfg = workloads.config_hidden_shift()
+    n, s, C = cfg["n"], np.uint64(cfg["shift"]), cfg["chains"]
+    dev = torch.device(f"cuda:{local}")
+    low = lrstab.lower_circuit(n, cfg["ops"], "sum8")
+    sim = lrstab.Simulator(n, local)
+    sim.init_terms(low, chi, mode="sparsify", seed=77)
+    sim.apply_clifford(low.gates)
+    x_s = torch.full((C,), int(s), dtype=torch.int64, device=dev)
+    x0 = sim.sample_terms(C, seed=31)
+    start_at_s = int((x0.cpu().numpy().view(np.uint64) == s).sum())
+
+    def timed(fn):
+        a, b = _ev()
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) * 1e-3
+
+    def hits(trace):
+        at = trace == s
+        found = at.any(axis=0)
+        first = np.where(found, at.argmax(axis=0) + 1, -1)
+        return int(found.sum()), (int(np.median(first[found])) if found.any() else None)
+
+    def p_check(po, xo):
+        amp = sim.amplitude(xo)
+        pa = (amp[:, 0] ** 2 + amp[:, 1] ** 2).cpu().numpy()
+        pc = po.cpu().numpy()
+        return float(np.max(np.abs(pc - pa) / np.maximum(pa, 1e-30)))
+
+    out = {"workload": f"hidden_shift_n40_ccz16_sum8_chi{chi}", "chi": chi, "chains": C,
+           "pauli_state_gb": C * chi * 12 / 1e9, "chains_started_at_s": start_at_s}
+    xo = torch.empty(C, dtype=torch.int64, device=dev)
+    po = torch.empty(C, dtype=torch.float64, device=dev)
+    # (a) chains at s
+    t_init = timed(lambda: sim.chains_init(x_s))
+    trace_s, times_s = _run_traced(lambda k, d, b: sim.metropolis(k, seed=41, step0=d, trace=b), C, flip_steps,
+                                   chunk, dev)
+    sim.metropolis(0, seed=41, step0=flip_steps, x_out=xo, p_out=po)
+    out["from_s"] = {"steps": flip_steps, "chains_init_s": t_init, "gpu_s": times_s[-1][1],
+                     "chain_steps_at_s": int((trace_s == s).sum()), "chain_steps": int(trace_s.size),
+                     "max_rel_err_p_vs_amplitude": p_check(po, xo)}
+    # (b) chains from the term sampler, single flips
+    t_init = timed(lambda: sim.chains_init(x0))
+    ptrace, ptimes = _run_traced(lambda k, d, b: sim.metropolis(k, seed=42, step0=d, trace=b), C, flip_steps,
+                                 chunk, dev)
+    sim.metropolis(0, seed=42, step0=flip_steps, x_out=xo, p_out=po)
+    p_found, p_med = hits(ptrace)
+    out["flip"] = {"steps": flip_steps, "chains_init_s": t_init, "gpu_s": ptimes[-1][1], "chains_at_s": p_found,
+                   "median_first_step": p_med, "max_rel_err_p_vs_amplitude": p_check(po, xo)}
+    # (b) learned proposal trained on exact samples of the 2^16-term decomposition
+    ex = lrstab.Simulator(n, local)
+    ex.init_terms(lrstab.lower_circuit(n, cfg["ops"]), cfg["chi"], mode="exact")
+    ex.apply_clifford(lrstab.lower_circuit(n, cfg["ops"]).gates)
+    work = (lrstab.Simulator(n, local), lrstab.Simulator(n, local))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    samples = []
+    for i in range(exact_samples):
+        bits, _ = ex.marginal_sample(list(range(n)), L, K, seed=100 + i, work=work)
+        samples.append(sum(int(b_) << q for q, b_ in enumerate(bits)))
+    torch.cuda.synchronize()
+    t_marg = time.perf_counter() - t0
+    for w_ in work + (ex,):
+        w_.close()
+    data = torch.tensor(samples, dtype=torch.int64, device=dev).repeat(train_samples // exact_samples + 1)
+    data = data[:train_samples].contiguous()
+    net = lrstab.MLP(n, hidden, local)
+    rng = np.random.default_rng(5)
+    lim1, lim2 = 1 / np.sqrt(n), 1 / np.sqrt(hidden)
+    net.set_params(dict(W1=rng.uniform(-lim1, lim1, (hidden, n)), b1=rng.uniform(-lim1, lim1, hidden),
+                        W2=rng.uniform(-lim2, lim2, (hidden, hidden)), b2=rng.uniform(-lim2, lim2, hidden),
+                        W3=rng.uniform(-lim2, lim2, (n, hidden)), b3=rng.uniform(-lim2, lim2, n)))
+    bs = 1024
+    net.backward(data[:bs].contiguous())   # first launches and first shuffle outside the timing
+    _ = data[torch.randperm(data.numel(), device=dev)]
+    torch.cuda.synchronize()
+    gen = torch.Generator(device=dev).manual_seed(3)
+
+    def train():
+        for ep in range(epochs):
+            shuf = data[torch.randperm(data.numel(), device=dev, generator=gen)]
+            for it in range(data.numel() // bs):
+                net.train_step(shuf[it * bs:(it + 1) * bs], lr=1e-3)
+    t_train = timed(train)
+    t_init = timed(lambda: sim.chains_init(x0))
+    ltrace, ltimes = _run_traced(lambda k, d, b: lrstab.metropolis_learned(sim, net, k, seed=43, step0=d, trace=b),
+                                 C, learned_steps, min(chunk, learned_steps), dev)
+    net.close()
+    sim.close()
+    l_found, l_med = hits(ltrace)
+    out["learned_on_exact_samples"] = {
+        "steps": learned_steps, "chains_init_s": t_init, "gpu_s": ltimes[-1][1], "chains_at_s": l_found,
+        "median_first_step": l_med, "chain_steps_at_s": int((ltrace == s).sum()),
+        "training": f"{exact_samples} chain-rule samples of the exact 2^16-term decomposition, replicated",
+        "train_gpu_s": t_train, "sampler_s": t_marg, "samples_are_the_shift": all(np.uint64(v) == s for v in samples)}
+    return out
+
+
 def hidden_shift_chain_study(local=0, plain_steps=2048, learned_steps=32, chunk=64, hidden=512,
                              train_samples=100_000, epochs=5, exact_samples=4, L=256, K=3):
     """The hidden shift's chains (n = 40, 16 CCZ, exact 2^16-term decomposition of |s>,
@@ -1387,6 +1506,9 @@ def main():
         return
     if args.hidden_shift_chains:
         print(json.dumps(hidden_shift_chain_study(0)))
+        return
+    if args.hs_sum8_chains:
+        print(json.dumps(hidden_shift_sum8_chain_study(0)))
         return
     if args.qaoa_apply_only:
         print(json.dumps(qaoa_apply_only(0)))
