@@ -103,16 +103,18 @@ def test_metropolis_continuation_and_errors():
     sim.close()
 
 
-def test_full_size_chains_match_amplitudes():
-    """n=40 benchmark decomposition at full size (2^16 terms), 64 chains x 32 steps
-    (two graph replays): every decision replayed with P = |<x|psi>|^2 from the
-    amplitude kernel (oracle-checked on slices), and the incremental P(x) of every
-    chain equal to the amplitude kernel's at the end."""
+@pytest.mark.parametrize("chi,C", [(1 << 16, 64), (1 << 24, 8)], ids=["chi65536", "chi16777216_tiles_on_x"])
+def test_full_size_chains_match_amplitudes(chi, C):
+    """n=40 benchmark circuit at full size (2^16 terms, 64 chains) and sparsified to
+    2^24 terms (8 chains: 65536 term tiles, more than the grid's y limit, so the tiles
+    run along x), 32 steps (two graph replays): every decision replayed with
+    P = |<x|psi>|^2 from the amplitude kernel (oracle-checked on slices), and the
+    incremental P(x) of every chain equal to the amplitude kernel's at the end."""
     require_cuda()
     cfg = workloads.config_mid()
-    n, ops, chi, seed = cfg["n"], cfg["ops"], cfg["chi"], cfg["seed"]
+    n, ops, seed = cfg["n"], cfg["ops"], cfg["seed"]
     sim = _sim(n, ops, chi, "sparsify", seed)
-    C, T, mseed = 64, 32, 99
+    T, mseed = 32, 99
     x0 = sim.sample_terms(C, seed=12)
     sim.chains_init(x0)
     xo = torch.empty(C, dtype=torch.int64, device="cuda:0")
