@@ -65,6 +65,8 @@ def parse(argv=None):
                     help="only the single-qubit marginals of the 40-qubit hidden shift (2/4/6 CCZ)")
     ap.add_argument("--hidden-shift-chains", action="store_true",
                     help="only the hidden shift's chain study (time for term-sampled chains to reach s)")
+    ap.add_argument("--config5-graph", action="store_true",
+                    help="only config 5's eight-circuit step, uncaptured and as one CUDA graph")
     ap.add_argument("--hs-sum8-chains", action="store_true",
                     help="only the chains on the 2^24-term hidden shift (1024 chains, 206 GB of Pauli states)")
     ap.add_argument("--qaoa-apply-only", action="store_true",
@@ -947,7 +949,7 @@ def qaoa_apply_only(local=0, chi=1 << 16, lanes=(1, 2, 4)):
 
 def batch_study(local=0, k=8, seed=0):
     """8 QAOA n=50 circuits (seeds +i) with chi_i = 2^e_i, e_i uniform in 14..20:
-    term-gate throughput of one batched persistent launch vs one launch per circuit."""
+    term-gate throughput of one batched launch vs one launch per circuit."""
     import numpy as np
     import torch
     from paper_1808_00128_gb300 import lrstab, workloads
@@ -1085,6 +1087,86 @@ def prefix_study(local=0, sizes=(16, 20)):
         sim.close()
         out.append(res)
     return out
+
+
+def config5_graph_study(local=0, k=8, B=4096, L=64, C=256, T=16, seed=0):
+    """Config 5's eight n = 50 QAOA circuits (seeds +i, chi_i = 2^e_i with e_i uniform
+    in 14..20) through the whole path as one step: terms re-initialised (new
+    sparsification), gate updates in one batched launch, B amplitudes per circuit in
+    one batched launch, an L-state norm estimate, C chain starts and T Metropolis
+    steps per circuit.  The step runs as uncaptured calls and as one CUDA graph
+    captured from the same calls; reported: both step times, and whether every output
+    of the replay (amplitudes, eta, chain starts, final strings and P(x)) equals the
+    uncaptured step's bit for bit."""
+    import numpy as np
+    import torch
+    from paper_1808_00128_gb300 import lrstab, workloads
+    dev = torch.device(f"cuda:{local}")
+    rng = np.random.default_rng(workloads.SEED_BASE + 5 + seed)
+    exps = [int(e) for e in rng.integers(14, 21, size=k)]
+    sims, lows = [], []
+    for i, e in enumerate(exps):
+        ops, _ = workloads.qaoa_e3lin2_circuit(50, 4, 0.3, 0.2, workloads.SEED_BASE + 4 + i)
+        low = lrstab.lower_circuit(50, ops)
+        s = lrstab.Simulator(50, local)
+        s.init_terms(low, 1 << e, mode="sparsify", seed=workloads.SEED_BASE + 14 + i)
+        sims.append(s)
+        lows.append(low)
+    gates = [l.gates for l in lows]
+    xs = [torch.from_numpy(workloads.random_bitstrings(50, B, seed=workloads.SEED_BASE + 70 + i).view(np.int64))
+          .to(dev) for i in range(k)]
+    amps = [torch.empty((B, 2), dtype=torch.float64, device=dev) for _ in sims]
+    etas = [torch.empty(L, dtype=torch.float64, device=dev) for _ in sims]
+    x0s = [torch.empty(C, dtype=torch.int64, device=dev) for _ in sims]
+    xos = [torch.empty(C, dtype=torch.int64, device=dev) for _ in sims]
+    pos = [torch.empty(C, dtype=torch.float64, device=dev) for _ in sims]
+    outs = amps + etas + x0s + xos + pos
+
+    def step():
+        for i, s in enumerate(sims):
+            s.reinit_terms(seed=workloads.SEED_BASE + 14 + i)
+        lrstab.apply_clifford_batch(sims, gates)
+        lrstab.amplitude_batch(sims, xs, amps)
+        for i, s in enumerate(sims):
+            s.norm_estimate(L, seed=200 + i, eta=etas[i])
+            s.sample_terms(C, seed=300 + i, x=x0s[i])
+            s.chains_init(x0s[i])
+            s.metropolis(T, seed=400 + i, x_out=xos[i], p_out=pos[i])
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a, b = _ev()
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()                                   # sizes every buffer, sets kernel attributes
+    torch.cuda.current_stream().wait_stream(side)
+    eager_ms = timed(step)
+    ref = [o.clone() for o in outs]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for o in outs:
+        o.zero_()
+    graph_ms = timed(g.replay)
+    same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    g.reset()
+    for s in sims:
+        s.close()
+    chis = [1 << e for e in exps]
+    return {"chi": chis, "B": B, "L": L, "chains": C, "metropolis_steps": T,
+            "step_ms_uncaptured": eager_ms, "step_ms_one_graph": graph_ms, "speedup": eager_ms / graph_ms,
+            "replay_equals_uncaptured": same,
+            "term_amplitude_evals_per_s_graph": sum(chis) * (B + C * (T + 1)) / (graph_ms * 1e-3)}
 
 
 def hidden_shift_sum8_study(local=0, chi=1 << 24, L=256, K=3):
@@ -1510,6 +1592,9 @@ def main():
     if args.hs_sum8_chains:
         print(json.dumps(hidden_shift_sum8_chain_study(0)))
         return
+    if args.config5_graph:
+        print(json.dumps(config5_graph_study(0)))
+        return
     if args.qaoa_apply_only:
         print(json.dumps(qaoa_apply_only(0)))
         return
@@ -1610,7 +1695,12 @@ def main():
         side = side_step_study(other, local, alu, hbm)
         if timer is not None:
             parity.append(slice_parity(other, local, timer=timer))
-        extra = {"batch8": batch_study(local), "mlp_gemm": mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops")),
+        try:
+            c5 = config5_graph_study(local)
+        except Exception as e:   # reported in the line; the step's numbers above stand
+            c5 = {"error": str(e)[:300]}
+        extra = {"batch8": batch_study(local), "config5_graph": c5,
+                 "mlp_gemm": mlp_gemm_study(local, bf16_peak=peaks.get("bf16_tflops")),
                  "marginals": marginal_study(local), "gadget_vs_sum": gadget_study(local),
                  "prefix_sharing": prefix_study(local), "hidden_shift_sum8": hidden_shift_sum8_study(local),
                  "hidden_shift_chains": hidden_shift_chain_study(local),

@@ -39,6 +39,17 @@
  *     calls are stream-ordered and asynchronous; they return after enqueuing
  *     unless stated otherwise.  A context must not be used from two host
  *     threads at once.
+ *   - Graph capture: lrs_reinit_terms, lrs_apply_clifford (a gate list of at
+ *     most 7680 gates), lrs_apply_clifford_batch (the gate lists of its previous
+ *     call), lrs_amplitude, lrs_amplitude_batch, lrs_norm_estimate (mean_host
+ *     NULL), lrs_sample_terms, lrs_chains_init and lrs_metropolis_step enqueue
+ *     only kernel launches and device copies once a first, uncaptured call of the
+ *     same sizes has sized the context's buffers and set its kernels' attributes,
+ *     so a stream that runs them can be captured into one CUDA graph (Metropolis
+ *     steps are then captured as plain launches).  The graph keeps the device
+ *     addresses of the context's buffers: replay it only while no later call on
+ *     those contexts has needed larger buffers (more strings, chains, L or terms),
+ *     and before lrs_destroy.  Scalars (seeds, step0) are fixed at capture.
  *   - Random numbers are drawn on the device from SplitMix64 in counter mode
  *     (Steele, Lea and Flood 2014):
  *        mix(z) = z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27;
@@ -207,6 +218,15 @@ lrs_status lrs_init_terms(lrs_ctx* ctx, const lrs_slot* slots_host, int64_t n_sl
                           const lrs_gate* k_gates_host, int64_t n_k_gates,
                           int64_t chi_total, int64_t alpha0, int64_t chi, int32_t mode,
                           uint64_t seed, void* stream);
+
+/* Re-initialise the terms of the last lrs_init_terms (or lrs_copy_terms) call from
+ * the slot tables already on the device: the same term range, mode and b_alpha
+ * scale, the choices of SPARSIFY drawn again with `seed` (Lemma (Sparsification)),
+ * every CH-form reset to |0^n>.  One kernel launch, no copy and no host wait, so
+ * it can be captured into a CUDA graph (see "Graph capture" above).  Chains are
+ * dropped (lrs_chains_init again).
+ * Errors: LRS_ERR_STATE (no earlier lrs_init_terms), LRS_ERR_CUDA.            */
+lrs_status lrs_reinit_terms(lrs_ctx* ctx, uint64_t seed, void* stream);
 
 /* Apply the lowered gate list to every term (left multiplications for
  * S, S^dagger, Z, CX, CZ; Eqs. (H1)-(H7) with Prop. (prop:H) for H; the

@@ -792,21 +792,26 @@ lrs_status launch_metropolis(lrs_ctx* ctx, int64_t steps, uint64_t seed, int64_t
         *(volatile int*)ctx->mc_err_h = 0;
         return lrs_fail(LRS_ERR_TIMEOUT, "a Metropolis propose kernel gave up waiting for its copies");
     }
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(MC_ST * sizeof(McStage))));
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(MC_ST * sizeof(McStage))));
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(MC_ST * sizeof(McStage2))));
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(MC_ST * sizeof(McStage2))));
+    // inside a graph capture: the attributes were set by an earlier uncaptured call, and
+    // the steps are captured as plain launches (no nested graph)
+    const bool capturing = lrs_capturing(st);
+    if (!capturing) {
+        LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(MC_ST * sizeof(McStage))));
+        LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(MC_ST * sizeof(McStage))));
+        LRS_CUDA(cudaFuncSetAttribute(k_metro_propose2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(MC_ST * sizeof(McStage2))));
+        LRS_CUDA(cudaFuncSetAttribute(k_metro_propose2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(MC_ST * sizeof(McStage2))));
+    }
     float2* partial = (float2*)scr;
     int32_t* jprop = (int32_t*)((char*)scr + ((part_bytes + 255) & ~(size_t)255));
     k_mc_set<<<1, 1, 0, st>>>(ctx->mc_par, seed, step0);
     k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->mc_par, ctx->n, jprop, jprop + C);
     LRS_LAUNCH_CHECK("metropolis first kernel");
     int64_t done = 0;
-    if (!trace && steps >= LRS_MC_GRAPH_STEPS) {
+    if (!trace && !capturing && steps >= LRS_MC_GRAPH_STEPS) {
         // replay a captured graph of LRS_MC_GRAPH_STEPS steps (one launch instead of 2 per step)
         cudaGraphExec_t ex = nullptr;
         rc = mc_graph(ctx, partial, jprop, &ex);
@@ -838,10 +843,12 @@ lrs_status launch_metropolis_propose(lrs_ctx* ctx, uint64_t seed, int64_t step, 
         *(volatile int*)ctx->mc_err_h = 0;
         return lrs_fail(LRS_ERR_TIMEOUT, "a Metropolis propose kernel gave up waiting for its copies");
     }
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(MC_ST * sizeof(McStage))));
-    LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(MC_ST * sizeof(McStage))));
+    if (!lrs_capturing(st)) {
+        LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(MC_ST * sizeof(McStage))));
+        LRS_CUDA(cudaFuncSetAttribute(k_metro_propose<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(MC_ST * sizeof(McStage))));
+    }
     k_mc_set<<<1, 1, 0, st>>>(ctx->mc_par, seed, step);
     k_metro_first<<<(unsigned)((C + 127) / 128), 128, 0, st>>>(C, ctx->mc_par, ctx->n, ctx->jbuf, nullptr);
     LRS_LAUNCH_CHECK("metropolis first kernel");

@@ -649,8 +649,8 @@ static lrs_status launch_norm_t(lrs_ctx* ctx, const NormPrep& P, int64_t L, int6
                                 float2* partial, int64_t n_tiles, cudaStream_t st) {
     constexpr int NB = (NCH + 1) / 2;   // 8 x 8 blocks per side of the transposed matrix
     const size_t smem = ((size_t)NCH * 16 + (size_t)(8 * NB) * NRM_TPB) * sizeof(uint64_t);
-    LRS_CUDA(cudaFuncSetAttribute(k_norm<NCH, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    if (!lrs_capturing(st))
+        LRS_CUDA(cudaFuncSetAttribute(k_norm<NCH, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t lblocks = (L + NRM_TPB - 1) / NRM_TPB;
     dim3 grid((unsigned)n_tiles, (unsigned)lblocks);
     k_norm<NCH, NB><<<grid, NRM_TPB, smem, st>>>(ctx->view(), P, L, tt, partial, n_tiles,

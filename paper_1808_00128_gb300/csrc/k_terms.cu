@@ -390,8 +390,9 @@ void specialise_gates(const lrs_ctx* ctx, const lrs_gate* in, int64_t n, lrs_gat
 template <int HB, int TPT>
 static lrs_status launch_apply_hb(lrs_ctx* ctx, const lrs_gate* gates_host, int64_t n_gates, int64_t blocks,
                                   cudaStream_t st) {
-    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford<HB, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SmemRows<HB, TPT>::bytes(64)));
+    if (!lrs_capturing(st))
+        LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford<HB, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SmemRows<HB, TPT>::bytes(64)));
     static thread_local GateList G;
     for (int64_t i0 = 0; i0 < n_gates; i0 += APPLY_PARAM_GATES) {
         const int len = (int)std::min<int64_t>(APPLY_PARAM_GATES, n_gates - i0);
@@ -437,8 +438,9 @@ lrs_status launch_sample_terms(lrs_ctx* ctx, int64_t count, uint64_t seed, uint6
 // keeps zero high bits) and the lane split of the first context.
 template <int HB, int TPT>
 static lrs_status launch_apply_batch_hb(const ApplyBatch& B, int64_t tiles, int nmax, cudaStream_t st) {
-    LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford_batch<HB, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SmemRows<HB, TPT>::bytes(64)));
+    if (!lrs_capturing(st))
+        LRS_CUDA(cudaFuncSetAttribute(k_apply_clifford_batch<HB, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SmemRows<HB, TPT>::bytes(64)));
     k_apply_clifford_batch<HB, TPT><<<(unsigned)tiles, APPLY_TERMS * TPT, SmemRows<HB, TPT>::bytes(nmax), st>>>(B);
     LRS_LAUNCH_CHECK("batched apply_clifford kernel");
     return LRS_OK;

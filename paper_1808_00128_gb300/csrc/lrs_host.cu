@@ -52,6 +52,11 @@ lrs_status lrs_scratch(lrs_ctx* ctx, size_t bytes, void** out) {
 
 static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
+bool lrs_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive;
+}
+
 // ---------------------------------------------------------------------------------
 // Lowering (Sec. 2.3.2): T and RZ(theta) -> 2-term slot (Eq. (Rtheta)); CCZ ->
 // projector form I - 2 P1 P1 P1, or the 8-term form of Eq. (CCZ_decomposition)
@@ -477,11 +482,24 @@ extern "C" lrs_status lrs_init_terms(lrs_ctx* c, const lrs_slot* slots, int64_t 
     c->n_slots = n_slots;
     c->slots_host.assign(slots, slots + n_slots);
     c->kgates_host.assign(k_gates, k_gates + n_k_gates);
-    rc = launch_init_terms(c, mode, seed, l1 / (double)chi_total, st);
+    c->init_scale = l1 / (double)chi_total;
+    rc = launch_init_terms(c, mode, seed, c->init_scale, st);
     if (rc != LRS_OK) return rc;
     c->have_terms = true;
     c->mode = mode;
     c->fresh = true;
+    return LRS_OK;
+}
+
+extern "C" lrs_status lrs_reinit_terms(lrs_ctx* c, uint64_t seed, void* stream) {
+    if (!c) return lrs_fail(LRS_ERR_ARG, "ctx is NULL");
+    if (c->cap == 0 || c->init_scale == 0.0) return lrs_fail(LRS_ERR_STATE, "lrs_init_terms has not been called");
+    LRS_CUDA(cudaSetDevice(c->device));
+    lrs_status rc = launch_init_terms(c, c->mode, seed, c->init_scale, as_stream(stream));
+    if (rc != LRS_OK) return rc;
+    c->have_terms = true;
+    c->fresh = true;
+    c->n_chains = 0;
     return LRS_OK;
 }
 
@@ -578,16 +596,24 @@ extern "C" lrs_status lrs_apply_clifford_batch(lrs_ctx* const* ctxs, const lrs_g
     cudaStream_t st = as_stream(stream);
     for (int32_t i = 0; i < count; ++i) {
         lrs_ctx* c = ctxs[i];
-        size_t have = (size_t)c->gates_cap * sizeof(lrs_gate);
-        lrs_status rc = lrs_ensure((void**)&c->gates_dev, &have, (size_t)std::max<int64_t>(1, n_gates[i]) * sizeof(lrs_gate));
-        if (rc != LRS_OK) return rc;
-        c->gates_cap = (int64_t)(have / sizeof(lrs_gate));
-        if (n_gates[i] > 0) {
-            std::vector<lrs_gate> sg((size_t)n_gates[i]);
-            specialise_gates(c, gates[i], n_gates[i], sg.data());
-            LRS_CUDA(cudaMemcpyAsync(c->gates_dev, sg.data(), (size_t)n_gates[i] * sizeof(lrs_gate),
-                                     cudaMemcpyHostToDevice, st));
-            LRS_CUDA(cudaStreamSynchronize(st));   // the staging vector is freed on return
+        std::vector<lrs_gate> sg((size_t)n_gates[i]);
+        specialise_gates(c, gates[i], n_gates[i], sg.data());
+        // upload only a list that is not resident already (so that a repeated batch,
+        // e.g. one being captured into a CUDA graph, makes no copy and no host wait)
+        const bool resident = sg.size() == c->gates_resident.size() &&
+                              (sg.empty() || memcmp(sg.data(), c->gates_resident.data(), sg.size() * sizeof(lrs_gate)) == 0);
+        if (!resident) {
+            size_t have = (size_t)c->gates_cap * sizeof(lrs_gate);
+            lrs_status rc = lrs_ensure((void**)&c->gates_dev, &have, std::max<size_t>(1, sg.size()) * sizeof(lrs_gate));
+            if (rc != LRS_OK) return rc;
+            c->gates_cap = (int64_t)(have / sizeof(lrs_gate));
+            c->gates_resident.clear();
+            if (!sg.empty()) {
+                LRS_CUDA(cudaMemcpyAsync(c->gates_dev, sg.data(), sg.size() * sizeof(lrs_gate), cudaMemcpyHostToDevice,
+                                         st));
+                LRS_CUDA(cudaStreamSynchronize(st));   // the staging vector is freed on return
+            }
+            c->gates_resident.swap(sg);
         }
         c->batch_n_gates = n_gates[i];
         c->n_chains = 0;
@@ -707,6 +733,7 @@ extern "C" lrs_status lrs_copy_terms(lrs_ctx* dst, const lrs_ctx* src, void* str
     dst->n_chains = 0;
     dst->have_terms = true;
     dst->mode = src->mode;
+    dst->init_scale = src->init_scale;
     dst->fresh = src->fresh;
     return LRS_OK;
 }

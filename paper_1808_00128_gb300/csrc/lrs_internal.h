@@ -68,6 +68,7 @@ struct lrs_ctx {
     bool have_terms = false;
     int32_t mode = -1;              // lrs_init_terms mode of the current terms
     bool fresh = false;             // terms as lrs_init_terms left them (|0^n>, no gate applied)
+    double init_scale = 0.0;        // ||c||_1 / chi_total of the last lrs_init_terms (term weights)
 
     uint64_t *F = nullptr, *G = nullptr, *M = nullptr;
     uint64_t *glo = nullptr, *ghi = nullptr, *v = nullptr, *s = nullptr;
@@ -86,6 +87,7 @@ struct lrs_ctx {
 
     lrs_gate* gates_dev = nullptr;
     int64_t gates_cap = 0;
+    std::vector<lrs_gate> gates_resident;   // the specialised gate list now in gates_dev
     int64_t batch_n_gates = 0;      // gate count uploaded for a batched launch
 
     // scratch for partial sums
@@ -160,6 +162,9 @@ lrs_status lrs_cuda_check(cudaError_t e, const char* what);
 // Grow a device buffer to at least `bytes` (contents not kept).
 lrs_status lrs_ensure(void** ptr, size_t* have, size_t bytes);
 lrs_status lrs_scratch(lrs_ctx* ctx, size_t bytes, void** out);
+// True while `st` is being captured into a CUDA graph: launches then skip the one-time
+// function-attribute calls (made by an earlier uncaptured call) and nested graphs.
+bool lrs_capturing(cudaStream_t st);
 
 // ---- launchers implemented in the kernel translation units --------------------
 lrs_status launch_init_terms(lrs_ctx* ctx, int32_t mode, uint64_t seed, double scale,

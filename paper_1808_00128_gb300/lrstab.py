@@ -33,7 +33,7 @@ SLOT_DT = np.dtype([("n_choices", "<i4"), ("k_off", "<i4", (8,)), ("k_len", "<i4
                     ("c_re", "<f8", (8,)), ("c_im", "<f8", (8,))], align=True)
 COP_DT = np.dtype([("kind", "<i4"), ("q", "<i4", (3,)), ("theta", "<f8")], align=True)
 
-EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", "lrs_init_terms",
+EXPORTED = ["lrs_lower_circuit", "lrs_create", "lrs_destroy", "lrs_last_error", "lrs_init_terms", "lrs_reinit_terms",
             "lrs_apply_clifford", "lrs_amplitude", "lrs_norm_estimate", "lrs_sample_terms",
             "lrs_chains_init", "lrs_metropolis_step", "lrs_export_terms", "lrs_info",
             "lrs_alu_probe", "lrs_amplitude_noalloc", "lrs_mlp_create", "lrs_mlp_destroy",
@@ -97,6 +97,7 @@ def lib():
         "lrs_apply_clifford_batch": [vp, vp, vp, i32, vp],
         "lrs_set_tuning": [vp, i32, i64],
         "lrs_copy_terms": [vp, vp, vp],
+        "lrs_reinit_terms": [vp, u64, vp],
         "lrs_apply_circuit_shared": [vp, vp, i64, vp],
         "lrs_lower_gadget": [i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, vp, vp, i64, vp],
         "lrs_norm_median_of_means": [vp, i64, i32, u64, vp, vp],
@@ -300,6 +301,11 @@ class Simulator:
         self.alpha0 = alpha0
         self.chi_total = chi_total
         self.n_slots = len(lowered.slots)
+
+    def reinit_terms(self, seed: int, stream=None):
+        """The last init_terms again from the tables on the device (new sparsification
+        seed); graph-capturable."""
+        _check(lib().lrs_reinit_terms(self._h, seed & (2 ** 64 - 1), _stream(stream)))
 
     def apply_clifford(self, gates: np.ndarray, stream=None):
         _check(lib().lrs_apply_clifford(self._h, _ptr(gates), len(gates), _stream(stream)))
@@ -558,7 +564,7 @@ def amplitude_batch(sims, xs, outs=None, stream=None):
 
 
 def apply_clifford_batch(sims, gate_lists, stream=None):
-    """One persistent launch pushing each Simulator's terms through its gate list."""
+    """One launch pushing each Simulator's terms through its gate list."""
     k = len(sims)
     handles = (C.c_void_p * k)(*[s._h.value for s in sims])
     garrs = [np.ascontiguousarray(g) for g in gate_lists]
