@@ -189,10 +189,10 @@ def launches_per_step(T, lookahead=1):
 # dram__bytes_write.sum), per unit of work, with the hash of the kernel source the
 # capture ran; `traffic` is reported only while that source is unchanged.
 TRAFFIC = {
-    # k_norm<13, 7> on the profiling case (n = 50 QAOA, chi = 2^16, L = 64): 34,176,000 B
-    # read + 169,984 B written per launch for 2^16 x 64 (A, term) units
-    "norm_estimate": {"bytes_per_unit": (34176000 + 169984) / (65536 * 64),
-                      "source": "paper_1808_00128_gb300/csrc/k_norm.cu", "sha16": "28b312297fb70afe",
+    # k_norm<13, 7> on the profiling case (n = 50 QAOA, chi = 2^16, L = 64): 34,172,672 B
+    # read + 185,088 B written per launch for 2^16 x 64 (A, term) units
+    "norm_estimate": {"bytes_per_unit": (34172672 + 185088) / (65536 * 64),
+                      "source": "paper_1808_00128_gb300/csrc/k_norm.cu", "sha16": "8f42b33d2b5067dc",
                       "profile": "profiles/k_norm_n50_chi65536_L64.md"},
 }
 

@@ -81,18 +81,24 @@ __device__ __forceinline__ void fold_rows(uint64_t* sK, uint64_t h, uint64_t q, 
     }
 }
 
-// Linear terms and signs of eliminating the pair (a, b) (neighbour sets m1 of a without
-// b, m2 of b without a): summing x_a, x_b out leaves the product of the two linear
-// forms, whose constant part goes to the sign and the rest to the linear vectors.
-__device__ __forceinline__ void pivot_terms(int a, int b, uint64_t m1, uint64_t m2, uint64_t& Lre, uint64_t& Lim,
-                                            uint32_t& sre, uint32_t& sim) {
-    const uint64_t c1r = getb(Lre, a), c2r = getb(Lre, b);
-    const uint64_t c1i = getb(Lim, a), c2i = getb(Lim, b);
-    sre ^= (uint32_t)(c1r & c2r);
-    sim ^= (uint32_t)(c1i & c2i);
+// Linear terms and signs of eliminating the pair (a, b) (given as the one-bit masks ba,
+// bb; neighbour sets m1 of a without b, m2 of b without a): summing x_a, x_b out leaves
+// the product of the two linear forms, whose constant part goes to the sign and the
+// rest to the linear vectors.
+__device__ __forceinline__ void pivot_terms(uint64_t ba, uint64_t bb, uint64_t m1, uint64_t m2, uint64_t& Lre,
+                                            uint64_t& Lim, uint32_t& sre, uint32_t& sim) {
+    const bool c1r = (Lre & ba) != 0, c2r = (Lre & bb) != 0;
+    const bool c1i = (Lim & ba) != 0, c2i = (Lim & bb) != 0;
+    sre ^= (uint32_t)(c1r && c2r);
+    sim ^= (uint32_t)(c1i && c2i);
     const uint64_t mm = m1 & m2;
-    Lre ^= (m2 & (0ull - c1r)) ^ (m1 & (0ull - c2r)) ^ mm;
-    Lim ^= (m2 & (0ull - c1i)) ^ (m1 & (0ull - c2i)) ^ mm;
+    uint64_t dr = mm, di = mm;
+    if (c1r) dr ^= m2;
+    if (c2r) dr ^= m1;
+    if (c1i) di ^= m2;
+    if (c2i) di ^= m1;
+    Lre ^= dr;
+    Lim ^= di;
 }
 
 // Sum over variables of (-1)^(quadratic form), lifted from Z4 (Eq. (Q), (real)).
@@ -108,15 +114,17 @@ __device__ __forceinline__ void eliminate(uint64_t* sK, uint64_t v, uint64_t odd
     if (odd) {
         // pair the extra variable X (linear coefficient 0 for Re, 1 for Im) with bq
         const int bq = ffs64(odd);
-        const uint64_t m1 = odd & ~bit64(bq);
-        const uint64_t m2 = sK[bq * NRM_TPB] & act & ~bit64(bq);
+        const uint64_t bb = odd & (0ull - odd);   // bit bq
+        const uint64_t m1 = odd & ~bb;
+        const uint64_t m2 = sK[bq * NRM_TPB] & act & ~bb;
         e += 1;
-        sim ^= (uint32_t)getb(Lim, bq);
+        const bool cr = (Lre & bb) != 0, ci = (Lim & bb) != 0;
+        sim ^= (uint32_t)ci;
         const uint64_t mm = m1 & m2;
-        Lre ^= (getb(Lre, bq) ? m1 : 0ull) ^ mm;
-        Lim ^= m2 ^ (getb(Lim, bq) ? m1 : 0ull) ^ mm;
+        Lre ^= (cr ? m1 : 0ull) ^ mm;
+        Lim ^= m2 ^ (ci ? m1 : 0ull) ^ mm;
         rank_update(sK, m1 | m2, m1, m2, 0ull, 0ull);
-        act &= ~bit64(bq);
+        act &= ~bb;
     } else {
         e += 1;      // sum over x_X of (-1)^0 = 2 (Re), of (-1)^x_X = 0 (Im)
         zim = true;
@@ -135,23 +143,31 @@ __device__ __forceinline__ void eliminate(uint64_t* sK, uint64_t v, uint64_t odd
             if (np != k) continue;
             while (cand) {
                 const int a = ffs64(cand);
+                const uint64_t ba = cand & (0ull - cand);   // bit a
                 uint64_t ra = sK[a * NRM_TPB];
+                // row a as pairs 0..k-1 left it: row j gains P2 if j is in P1, P1 if in P2
 #pragma unroll
-                for (int i = 0; i < k; ++i) ra ^= (P2[i] & (0ull - getb(P1[i], a))) ^ (P1[i] & (0ull - getb(P2[i], a)));
-                ra &= act & ~bit64(a);
+                for (int i = 0; i < k; ++i) {
+                    if (P1[i] & ba) ra ^= P2[i];
+                    if (P2[i] & ba) ra ^= P1[i];
+                }
+                ra &= act & ~ba;
                 if (!ra) {       // isolated: stays isolated
-                    cand &= ~bit64(a);
+                    cand &= ~ba;
                     continue;
                 }
                 const int bq = ffs64(ra);
+                const uint64_t bb = ra & (0ull - ra);       // bit bq
                 uint64_t rb = sK[bq * NRM_TPB];
 #pragma unroll
-                for (int i = 0; i < k; ++i)
-                    rb ^= (P2[i] & (0ull - getb(P1[i], bq))) ^ (P1[i] & (0ull - getb(P2[i], bq)));
-                const uint64_t ab = bit64(a) | bit64(bq);
-                P1[k] = ra & ~bit64(bq);
+                for (int i = 0; i < k; ++i) {
+                    if (P1[i] & bb) rb ^= P2[i];
+                    if (P2[i] & bb) rb ^= P1[i];
+                }
+                const uint64_t ab = ba | bb;
+                P1[k] = ra & ~bb;
                 P2[k] = rb & act & ~ab;
-                pivot_terms(a, bq, P1[k], P2[k], Lre, Lim, sre, sim);
+                pivot_terms(ba, bb, P1[k], P2[k], Lre, Lim, sre, sim);
                 e += 1;
                 act &= ~ab;
                 cand &= ~ab;
@@ -453,19 +469,22 @@ __global__ void __launch_bounds__(NRM_TPB, norm_min_blocks(NCH)) k_norm(TermsVie
                 if (i < mf) {
                     const int p = tPiv[i];
                     const uint64_t h = tH[i];
+                    const uint64_t bp = bit64(p);
                     const uint64_t Dp = NRM_AROW(p) ^ tJ[p];
                     uint64_t r = Dp;
 #pragma unroll
-                    for (int j = 0; j < i; ++j) r ^= Hv[j] & (0ull - getb(Q[j], p));
-                    const uint64_t q = r & actf & ~bit64(p);
-                    const uint64_t op = getb(dlo, p);
-                    const uint64_t lp = getb(lb0, p) ^ (uint64_t)par64(Dp & z0);
-                    dLb ^= h & ((0ull - lp) ^ (oddf & (0ull - op)) ^ q);
-                    oddf ^= h & (0ull - op);
+                    for (int j = 0; j < i; ++j)
+                        if (Q[j] & bp) r ^= Hv[j];
+                    const uint64_t q = r & actf & ~bp;
+                    const bool op = (dlo & bp) != 0;
+                    const bool lp = ((lb0 & bp) != 0) != (par64(Dp & z0) != 0u);
+                    const uint64_t ho = op ? h : 0ull;
+                    dLb ^= (lp ? h : 0ull) ^ (oddf & ho) ^ (h & q);
+                    oddf ^= ho;
                     Q[i] = q;
-                    HQ[i] = q ^ (h & (0ull - op));
+                    HQ[i] = q ^ ho;
                     Hv[i] = h;
-                    actf &= ~bit64(p);
+                    actf &= ~bp;
                 }
             }
             const uint64_t oddm = oddf & actf;
