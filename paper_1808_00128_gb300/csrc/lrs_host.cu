@@ -54,7 +54,11 @@ static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
 bool lrs_capturing(cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();   // the query's own error is not the next launch's
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusActive;
 }
 
 // ---------------------------------------------------------------------------------
